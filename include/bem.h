@@ -1,0 +1,221 @@
+/*
+ * bem.h -- C interface of libbem, a GB300 (sm_103a) boundary-element library for
+ * the compressed matrix-vector product of the PMCHWT surface-integral operator of
+ * a penetrable (lossy dielectric) body, and the solve and dosimetry built on it.
+ *
+ * Problem statement (arXiv:2310.15644).  A body with boundary Gamma in free space
+ * (Sec. II) is illuminated by an incident field; its equivalent surface currents
+ * j (electric) and m (magnetic) satisfy the PMCHWT system of Eq. 7 (rows 2-3),
+ * discretised by Galerkin testing with piecewise-linear bases (Sec. III, Eq. 8 and
+ * the matrices P11..P22 after it).  The library works in three dimensions with
+ * RWG bases on a closed triangle mesh and the kernel e^{-jkR}/(4 pi R) under the
+ * e^{+j w t} convention (the paper's H0^(2) kernel and 1 + j w tau Debye terms of
+ * Eq. 5 fix that convention).  The interior medium has a complex relative
+ * permittivity (Eq. 5 gives the skin model) and the outputs are the currents and
+ * the absorbed power, the dosimetric quantity the paper is after (Sec. I).
+ *
+ * Unknowns and scaling.  For a mesh with ne interior edges the unknown vector has
+ * 2*ne complex entries x = [eta0*J ; M] (J, M the RWG coefficients of j and m, in
+ * the edge order returned by bem_edges), and the operator is
+ *
+ *     Z = [[ T0 + eta_r T1 ,  K0 + K1       ],
+ *          [ -(K0 + K1)    ,  T0 + T1/eta_r ]],      eta_r = eta1/eta0,
+ *
+ *     Tk[m,n] = jk <f_m, G_k f_n> - (j/k) <div f_m, G_k div f_n>,
+ *     Kk[m,n] = p.v. <f_m, grad G_k x f_n>,
+ *
+ * i.e. the paper's P11 = sum of single layers at k0 and k1, P12 = sum of double
+ * layers, P21 = minus that sum, P22 = sum of the dual single layers, with the
+ * impedances scaled out.  The right-hand side is b = [e ; eta0*h] with
+ * e_m = <f_m, E_inc>, h_m = <f_m, H_inc> (the tested fields after Eq. 8).
+ *
+ * Compression.  Edges are ordered by a cluster tree over their midpoints; blocks of
+ * the operator whose clusters are well separated are stored as low-rank factors
+ * U V^H computed by adaptive cross approximation (the skeleton U V^T of Eq. 10),
+ * the other blocks densely.
+ *
+ * Conventions for every entry point:
+ *   - Returns a bem_status and never aborts, throws or exits.  On failure the
+ *     message is available from bem_last_error(ctx).
+ *   - "host" pointers are read (or written) before the call returns; the library
+ *     keeps its own copies.  "device" pointers are caller-owned CUDA device memory,
+ *     accessed asynchronously on the caller's stream (a cudaStream_t passed as
+ *     void*; NULL means the legacy default stream).
+ *   - Complex data are interleaved (re, im) pairs: complex64 = 2 x float,
+ *     complex128 = 2 x double.  Several right-hand sides are stored column-major:
+ *     element (i, r) of a 2*ne x nrhs array is at index i + r * 2*ne.
+ *   - Calls out of order (e.g. bem_matvec before bem_assemble) return BEM_ESTATE.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef BEM_H
+#define BEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bem_ctx bem_ctx;
+
+typedef struct {
+    double re, im;
+} bem_c128;
+
+typedef enum {
+    BEM_OK = 0,
+    BEM_EINVAL = 1,    /* invalid argument or mesh */
+    BEM_ENOMEM = 2,    /* device or host allocation failed */
+    BEM_ECUDA = 3,     /* a CUDA call failed (message holds cudaGetErrorString) */
+    BEM_ENOCONV = 4,   /* iterative solver did not reach its tolerance; x holds the last iterate */
+    BEM_ETIMEOUT = 5,  /* a bounded device wait gave up */
+    BEM_ESTATE = 6     /* call made in the wrong order */
+} bem_status;
+
+/* Precision of the stored operator (bit mask for bem_options.precision). */
+#define BEM_PREC_C64 1   /* near entries and factors in complex64, FP32 arithmetic */
+#define BEM_PREC_C128 2  /* near entries and factors in complex128, FP64 arithmetic */
+
+/* Element type of a vector argument. */
+#define BEM_C64 0
+#define BEM_C128 1
+
+typedef struct {
+    int precision;       /* bit mask of BEM_PREC_*: which operators bem_assemble builds (default C64) */
+    int leaf_size;       /* maximum edges per leaf cluster, 2..64 (default 64) */
+    double eta;          /* admissibility: min(diam) <= eta * dist; eta <= 0 stores every block densely (default 2) */
+    double aca_tol;      /* relative Frobenius tolerance of each compressed block (default 1e-4) */
+    int aca_max_rank;    /* rank cap per compressed block (default 96); blocks that need more make bem_assemble fail */
+    int gmres_restart;   /* GMRES restart length (default 50) */
+    int maxit;           /* maximum inner GMRES iterations in total (default 1000) */
+    double tol;          /* inner GMRES relative residual tolerance (default 1e-6) */
+    double refine_tol;   /* outer FP64 iterative-refinement target; 0 disables refinement (default 0) */
+    int refine_maxit;    /* maximum outer refinement steps (default 10) */
+} bem_options;
+
+/* Summary of an assembled operator (bem_stats). */
+typedef struct {
+    int64_t ne;                 /* RWG edges (unknowns = 2 ne) */
+    int64_t nt;                 /* triangles */
+    int64_t n_clusters;         /* nodes of the cluster tree */
+    int64_t n_leaves;           /* leaf clusters */
+    int64_t n_near;             /* dense (near) blocks */
+    int64_t n_far;              /* compressed (far) blocks */
+    int64_t near_entries;       /* sum of m*n over near blocks (per operator A, B or C) */
+    int64_t factor_entries[3];  /* sum of r*(m+n) over far blocks, for A, B, C */
+    int64_t max_rank;           /* largest ACA rank */
+    int64_t singular_pairs;     /* triangle pairs integrated with singularity extraction */
+    int64_t matvec_bytes_c64;   /* algorithmic HBM bytes of one complex64 product (entries + vectors) */
+    int64_t matvec_bytes_c128;  /* same for complex128 */
+    double assemble_ms;         /* wall time of the last bem_assemble */
+} bem_stats;
+
+/* Fill *opt with the defaults listed above. */
+void bem_default_options(bem_options* opt);
+
+/* Create a context.  opt may be NULL (defaults).  *out receives the context. */
+bem_status bem_create(const bem_options* opt, bem_ctx** out);
+
+/* Release the context and every device buffer it owns.  NULL is accepted. */
+void bem_destroy(bem_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none).  Valid until the next call. */
+const char* bem_last_error(const bem_ctx* ctx);
+
+/* Set the boundary mesh (Sec. III: the mesh of Gamma carrying the bases).
+ * verts: host, nv x 3 double (row-major); tris: host, nt x 3 int32 vertex indices,
+ * counter-clockwise seen from outside (outward normals).  The mesh must be
+ * closed, two-manifold and consistently oriented with no degenerate triangle
+ * (twice the area <= 1e-12 x longest edge squared); otherwise BEM_EINVAL.
+ * RWG edges are numbered in lexicographic order of (min vertex, max vertex); T+ is
+ * the adjacent triangle with the smaller index.  Invalidates any assembled operator. */
+bem_status bem_set_mesh(bem_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris, int64_t nt);
+
+/* Set the media (Sec. III, after Eq. 7): exterior wavenumber k0 > 0 (rad per mesh
+ * unit), interior relative permittivity and permeability for e^{+j w t}
+ * (Im eps_r <= 0 and Im mu_r <= 0 for a lossy medium, else BEM_EINVAL).
+ * k1 = k0 sqrt(eps_r mu_r) and eta_r = sqrt(mu_r/eps_r) use principal square roots.
+ * Invalidates any assembled operator. */
+bem_status bem_set_media(bem_ctx* ctx, double k0, bem_c128 eps_r, bem_c128 mu_r);
+
+/* Double-Debye permittivity of Eq. 5 at freq_hz >= 0:
+ * params = {eps_inf, eps_s, eps_2, tau1 [s], tau2 [s]}; NULL selects the skin
+ * values given after Eq. 5 (3, 60, 3.6, 10 ps, 0.2 ps).  Host only, no context. */
+bem_status bem_debye_eps(double freq_hz, const double* params, bem_c128* eps_out);
+
+/* Build the operator on the GPU: cluster and block trees, singular-pair table,
+ * dense near blocks, ACA factors of far blocks, for every precision requested in
+ * the options.  Blocks until done (it reads block counts and ranks back to size
+ * its buffers) and runs its kernels on `stream`.  Requires bem_set_mesh and
+ * bem_set_media.  BEM_EINVAL if a far block needs more than aca_max_rank. */
+bem_status bem_assemble(bem_ctx* ctx, void* stream);
+
+/* Number of RWG edges ne and of unknowns 2*ne; -1 before bem_set_mesh. */
+int64_t bem_num_edges(const bem_ctx* ctx);
+int64_t bem_num_unknowns(const bem_ctx* ctx);
+
+/* RWG table, host output ne x 4 int32: (v0, v1, T+, T-), v0 < v1. */
+bem_status bem_edges(const bem_ctx* ctx, int32_t* out);
+
+/* Operator summary (after bem_assemble). */
+bem_status bem_stats_get(const bem_ctx* ctx, bem_stats* out);
+
+/* Cluster order and block partition (after bem_assemble), host outputs:
+ * perm: ne int64, perm[k] = edge at position k of the tree order;
+ * near: n_near x 4 int32 and far: n_far x 4 int32 rows (row_lo, m, col_lo, n) in
+ * tree positions, sorted by (row_lo, col_lo).  Any pointer may be NULL. */
+bem_status bem_partition(const bem_ctx* ctx, int64_t* perm, int32_t* near, int32_t* far);
+
+/* Evaluate operator entries directly by quadrature (no compression), device I/O:
+ * rows, cols: device int32[count] edge indices (0..ne-1); out: device, count x 3
+ * complex of type `dtype`: (A, B, C) = (T0 + eta_r T1, K0 + K1, T0 + T1/eta_r) at
+ * (rows[i], cols[i]).  The same quadrature routine fills the dense blocks and
+ * feeds the cross approximation.  Requires bem_assemble (for the singular-pair
+ * table) with the matching precision. */
+bem_status bem_eval_entries(bem_ctx* ctx, const int32_t* rows, const int32_t* cols, int64_t count,
+                            void* out, int dtype, void* stream);
+
+/* y = Z x for nrhs vectors.  x, y: device, 2ne x nrhs complex of type `dtype`
+ * (BEM_C64 or BEM_C128, needing the operator of that precision); x and y must not
+ * overlap.  Asynchronous on `stream`; no allocation after the first call with a
+ * given nrhs.  The product reads each dense entry and each factor once per call. */
+bem_status bem_matvec(bem_ctx* ctx, const void* x, void* y, int nrhs, int dtype, void* stream);
+
+/* Normalised plane-wave right-hand sides (tested fields after Eq. 8):
+ * E_inc = e0 exp(-j k0 khat.r), H_inc = khat x E_inc / eta0, b = [e ; eta0 h].
+ * khat: host nrhs x 3 double unit directions; e0: host nrhs x 3 complex
+ * polarisations; b: device 2ne x nrhs complex of type `dtype`. */
+bem_status bem_rhs_planewave(bem_ctx* ctx, const double* khat, const bem_c128* e0, int nrhs,
+                             void* b, int dtype, void* stream);
+
+/* Solve Z x = b for nrhs right-hand sides, b and x device complex128 2ne x nrhs.
+ * Inner solver: restarted GMRES on the complex64 operator when it exists (else the
+ * complex128 one) with FP64 inner products; if refine_tol > 0 an outer loop
+ * recomputes r = b - Z x with the complex128 operator (which must be assembled) and
+ * corrects x until |r|/|b| <= refine_tol.  x is used as the initial guess.
+ * iters (host, may be NULL): total inner iterations; relres (host, may be NULL):
+ * final relative residual per right-hand side (nrhs doubles), measured with the
+ * most accurate operator available.  Synchronises `stream`.  BEM_ENOCONV if any
+ * right-hand side misses its tolerance. */
+bem_status bem_solve(bem_ctx* ctx, const void* b, void* x, int nrhs, void* stream, int* iters, double* relres);
+
+/* Powers of a solution x (device complex128 2ne x nrhs) for its right-hand side b,
+ * in units of 1/(2 eta0) (efficiency Q = value / (pi a^2 |E0|^2)):
+ *   p_abs = Re(xJ^H X xM),  X[m,n] = int f_m . (n x f_n)   (absorbed, -Re oint E x H* . n)
+ *   p_ext = Re(xJ^H bJ + bM^H xM)                           (extinguished)
+ *   p_sca = oint |E_far|^2 dOmega on a 64 x 128 Gauss-Legendre x uniform grid,
+ *           E_far = (j k0/4pi) (rhat x L - N_t) of the normalised currents.
+ * Host outputs of nrhs doubles each (any may be NULL).  Synchronises `stream`. */
+bem_status bem_power(bem_ctx* ctx, const void* x, const void* b, int nrhs, double* p_abs, double* p_ext,
+                     double* p_sca, void* stream);
+
+/* Absorbed power density per triangle for the first right-hand side of x
+ * (device complex128): per_tri (device, nt doubles) = Re(sum_ij conj(xJ_i) X_t[i,j] xM_j) / area_t,
+ * same units as bem_power. */
+bem_status bem_power_density(bem_ctx* ctx, const void* x, double* per_tri, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEM_H */

@@ -1,0 +1,227 @@
+"""Thin ctypes binding of libbem (include/bem.h): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name; device
+buffers are passed as raw pointers (``tensor.data_ptr()``) and streams as
+``torch.cuda.Stream.cuda_stream``.  There is no fallback: if the shared library
+is missing or fails to load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbem.so")
+
+BEM_OK, BEM_EINVAL, BEM_ENOMEM, BEM_ECUDA, BEM_ENOCONV, BEM_ETIMEOUT, BEM_ESTATE = range(7)
+BEM_PREC_C64, BEM_PREC_C128 = 1, 2
+BEM_C64, BEM_C128 = 0, 1
+STATUS_NAMES = {0: "BEM_OK", 1: "BEM_EINVAL", 2: "BEM_ENOMEM", 3: "BEM_ECUDA", 4: "BEM_ENOCONV",
+                5: "BEM_ETIMEOUT", 6: "BEM_ESTATE"}
+
+# Every entry point declared in include/bem.h (checked by the test-suite).
+EXPORTS = [
+    "bem_default_options", "bem_create", "bem_destroy", "bem_last_error", "bem_set_mesh", "bem_set_media",
+    "bem_debye_eps", "bem_assemble", "bem_num_edges", "bem_num_unknowns", "bem_edges", "bem_stats_get",
+    "bem_partition", "bem_eval_entries", "bem_matvec", "bem_rhs_planewave", "bem_solve", "bem_power",
+    "bem_power_density",
+]
+
+
+class bem_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int), ("leaf_size", ctypes.c_int), ("eta", ctypes.c_double),
+        ("aca_tol", ctypes.c_double), ("aca_max_rank", ctypes.c_int), ("gmres_restart", ctypes.c_int),
+        ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("refine_tol", ctypes.c_double),
+        ("refine_maxit", ctypes.c_int),
+    ]
+
+
+class bem_stats(ctypes.Structure):
+    _fields_ = [
+        ("ne", ctypes.c_int64), ("nt", ctypes.c_int64), ("n_clusters", ctypes.c_int64),
+        ("n_leaves", ctypes.c_int64), ("n_near", ctypes.c_int64), ("n_far", ctypes.c_int64),
+        ("near_entries", ctypes.c_int64), ("factor_entries", ctypes.c_int64 * 3), ("max_rank", ctypes.c_int64),
+        ("singular_pairs", ctypes.c_int64), ("matvec_bytes_c64", ctypes.c_int64),
+        ("matvec_bytes_c128", ctypes.c_int64), ("assemble_ms", ctypes.c_double),
+    ]
+
+
+class bem_c128(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class BemError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libbem.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32p, i64p, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+    ctx = ctypes.c_void_p
+    sig = {
+        "bem_default_options": (None, [ctypes.POINTER(bem_options)]),
+        "bem_create": (ctypes.c_int, [ctypes.POINTER(bem_options), ctypes.POINTER(ctx)]),
+        "bem_destroy": (None, [ctx]),
+        "bem_last_error": (ctypes.c_char_p, [ctx]),
+        "bem_set_mesh": (ctypes.c_int, [ctx, dp, ctypes.c_int64, i32p, ctypes.c_int64]),
+        "bem_set_media": (ctypes.c_int, [ctx, ctypes.c_double, bem_c128, bem_c128]),
+        "bem_debye_eps": (ctypes.c_int, [ctypes.c_double, dp, ctypes.POINTER(bem_c128)]),
+        "bem_assemble": (ctypes.c_int, [ctx, vp]),
+        "bem_num_edges": (ctypes.c_int64, [ctx]),
+        "bem_num_unknowns": (ctypes.c_int64, [ctx]),
+        "bem_edges": (ctypes.c_int, [ctx, i32p]),
+        "bem_stats_get": (ctypes.c_int, [ctx, ctypes.POINTER(bem_stats)]),
+        "bem_partition": (ctypes.c_int, [ctx, i64p, i32p, i32p]),
+        "bem_eval_entries": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int64, vp, ctypes.c_int, vp]),
+        "bem_matvec": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
+        "bem_rhs_planewave": (ctypes.c_int, [ctx, dp, ctypes.POINTER(bem_c128), ctypes.c_int, vp, ctypes.c_int, vp]),
+        "bem_solve": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int), dp]),
+        "bem_power": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, dp, dp, dp, vp]),
+        "bem_power_density": (ctypes.c_int, [ctx, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _np_ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _check(ctx, st):
+    if st != BEM_OK:
+        msg = lib.bem_last_error(ctx) if ctx else b""
+        raise BemError(st, (msg or b"").decode())
+
+
+# ---- one-to-one wrappers (same names as the C entry points) ---------------------------------
+
+def bem_default_options() -> bem_options:
+    o = bem_options()
+    lib.bem_default_options(ctypes.byref(o))
+    return o
+
+
+def bem_create(opt: bem_options | None = None):
+    h = ctypes.c_void_p()
+    st = lib.bem_create(ctypes.byref(opt) if opt is not None else None, ctypes.byref(h))
+    _check(None, st)
+    return h
+
+
+def bem_destroy(ctx) -> None:
+    lib.bem_destroy(ctx)
+
+
+def bem_last_error(ctx) -> str:
+    return (lib.bem_last_error(ctx) or b"").decode()
+
+
+def bem_set_mesh(ctx, verts, tris) -> None:
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    _check(ctx, lib.bem_set_mesh(ctx, _np_ptr(v, ctypes.c_double), len(v), _np_ptr(t, ctypes.c_int32), len(t)))
+
+
+def bem_set_media(ctx, k0: float, eps_r: complex, mu_r: complex = 1.0) -> None:
+    e, m = complex(eps_r), complex(mu_r)
+    _check(ctx, lib.bem_set_media(ctx, float(k0), bem_c128(e.real, e.imag), bem_c128(m.real, m.imag)))
+
+
+def bem_debye_eps(freq_hz: float, params=None) -> complex:
+    out = bem_c128()
+    p = None if params is None else _np_ptr(np.ascontiguousarray(params, dtype=np.float64), ctypes.c_double)
+    _check(None, lib.bem_debye_eps(float(freq_hz), p, ctypes.byref(out)))
+    return complex(out.re, out.im)
+
+
+def bem_assemble(ctx, stream: int = 0) -> None:
+    _check(ctx, lib.bem_assemble(ctx, ctypes.c_void_p(stream)))
+
+
+def bem_num_edges(ctx) -> int:
+    return int(lib.bem_num_edges(ctx))
+
+
+def bem_num_unknowns(ctx) -> int:
+    return int(lib.bem_num_unknowns(ctx))
+
+
+def bem_edges(ctx) -> np.ndarray:
+    ne = bem_num_edges(ctx)
+    out = np.zeros((ne, 4), dtype=np.int32)
+    _check(ctx, lib.bem_edges(ctx, _np_ptr(out, ctypes.c_int32)))
+    return out
+
+
+def bem_stats_get(ctx) -> dict:
+    s = bem_stats()
+    _check(ctx, lib.bem_stats_get(ctx, ctypes.byref(s)))
+    d = {name: getattr(s, name) for name, _ in bem_stats._fields_}
+    d["factor_entries"] = list(s.factor_entries)
+    return d
+
+
+def bem_partition(ctx):
+    s = bem_stats_get(ctx)
+    perm = np.zeros(s["ne"], dtype=np.int64)
+    near = np.zeros((s["n_near"], 4), dtype=np.int32)
+    far = np.zeros((s["n_far"], 4), dtype=np.int32)
+    _check(ctx, lib.bem_partition(ctx, _np_ptr(perm, ctypes.c_int64), _np_ptr(near, ctypes.c_int32),
+                                  _np_ptr(far, ctypes.c_int32)))
+    return perm, near, far
+
+
+def bem_eval_entries(ctx, rows_ptr: int, cols_ptr: int, count: int, out_ptr: int, dtype: int, stream: int = 0) -> None:
+    _check(ctx, lib.bem_eval_entries(ctx, ctypes.c_void_p(rows_ptr), ctypes.c_void_p(cols_ptr), int(count),
+                                     ctypes.c_void_p(out_ptr), int(dtype), ctypes.c_void_p(stream)))
+
+
+def bem_matvec(ctx, x_ptr: int, y_ptr: int, nrhs: int, dtype: int, stream: int = 0) -> None:
+    _check(ctx, lib.bem_matvec(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), int(nrhs), int(dtype),
+                               ctypes.c_void_p(stream)))
+
+
+def bem_rhs_planewave(ctx, khat, e0, b_ptr: int, dtype: int, stream: int = 0) -> None:
+    kh = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
+    e = np.ascontiguousarray(np.atleast_2d(e0), dtype=np.complex128)
+    _check(ctx, lib.bem_rhs_planewave(ctx, _np_ptr(kh, ctypes.c_double), e.ctypes.data_as(ctypes.POINTER(bem_c128)),
+                                      len(kh), ctypes.c_void_p(b_ptr), int(dtype), ctypes.c_void_p(stream)))
+
+
+def bem_solve(ctx, b_ptr: int, x_ptr: int, nrhs: int, stream: int = 0, raise_on_noconv: bool = True):
+    """Returns (iterations, relative residual per right-hand side, status)."""
+    it = ctypes.c_int(0)
+    rel = np.zeros(nrhs, dtype=np.float64)
+    st = lib.bem_solve(ctx, ctypes.c_void_p(b_ptr), ctypes.c_void_p(x_ptr), int(nrhs), ctypes.c_void_p(stream),
+                       ctypes.byref(it), _np_ptr(rel, ctypes.c_double))
+    if st != BEM_OK and not (st == BEM_ENOCONV and not raise_on_noconv):
+        _check(ctx, st)
+    return it.value, rel, st
+
+
+def bem_power(ctx, x_ptr: int, b_ptr: int, nrhs: int, stream: int = 0):
+    pa = np.zeros(nrhs)
+    pe = np.zeros(nrhs)
+    ps = np.zeros(nrhs)
+    _check(ctx, lib.bem_power(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(b_ptr), int(nrhs),
+                              _np_ptr(pa, ctypes.c_double), _np_ptr(pe, ctypes.c_double),
+                              _np_ptr(ps, ctypes.c_double), ctypes.c_void_p(stream)))
+    return pa, pe, ps
+
+
+def bem_power_density(ctx, x_ptr: int, per_tri_ptr: int, stream: int = 0) -> None:
+    _check(ctx, lib.bem_power_density(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(per_tri_ptr),
+                                      ctypes.c_void_p(stream)))

@@ -1,0 +1,1230 @@
+// libbem C interface: context, mesh -> RWG table, operator assembly, product,
+// solve and powers.  Host code orchestrates; every step on the data runs in the
+// kernels of the other translation units.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "common.cuh"
+
+namespace bem {
+
+cudaError_t dalloc(DevBuf& b, size_t bytes) {
+    dfree(b);
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return e;
+    }
+    b.bytes = bytes;
+    return cudaSuccess;
+}
+
+void dfree(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+}  // namespace bem
+
+using namespace bem;
+
+namespace {
+
+struct Operator {
+    bool built = false;
+    DevBuf near;          // 3 * near_stride complex
+    DevBuf arena;         // low-rank factors
+    DevBuf far_rec;       // FarRec[nfar]
+    DevBuf far_order;     // int[nfar]
+    DevBuf xp, t;         // product workspace
+    int64_t t_len = 0;
+    int64_t factor_entries[3] = {0, 0, 0};
+    int max_rank = 0;
+    std::vector<FarRec> recs;
+};
+
+struct GmresWork {
+    int dtype = -1;
+    int64_t n = 0;
+    int restart = 0;
+    DevBuf V, w, z, r, xin, rin, hpart, hdev, npart;
+};
+
+}  // namespace
+
+struct bem_ctx {
+    bem_options opt;
+    std::string err;
+    // mesh and RWG table (host)
+    int64_t nv = 0, nt = 0, ne = 0;
+    std::vector<double> verts;
+    std::vector<int> tris;
+    std::vector<int> edge_v, edge_tri, edge_loc, tri_edge;
+    std::vector<double> tri_coef, area, nrm, cen, diam, tv, mid;
+    bool has_mesh = false, has_media = false;
+    double k0 = 0;
+    c128 eps{1, 0}, mu{1, 0}, k1{0, 0}, eta_r{1, 0};
+    // device geometry
+    DevBuf d_tv, d_area, d_nrm, d_cen, d_diam, d_tvid, d_tri_edge, d_tri_coef, d_edge_tri, d_edge_loc, d_mid;
+    DevBuf d_sing_ptr, d_sing_b, d_sing_val;
+    int64_t n_sing = 0;
+    // cluster tree and partition
+    std::vector<int> node_lo, node_hi, node_child0;
+    std::vector<int64_t> perm;
+    std::vector<int> leaf_lo, leaf_m;
+    std::vector<BlockDesc> near_blocks, far_blocks;  // sorted by (r0, c0)
+    DevBuf d_perm;
+    // product plan (precision independent part)
+    DevBuf d_leaf_r0, d_leaf_m, d_near_ptr, d_near_c0, d_near_n, d_near_off, d_farp_ptr, d_farp_blk, d_farp_row;
+    int64_t near_stride = 0;
+    Operator op[2];
+    bool assembled = false;
+    double assemble_ms = 0;
+    // reductions and small transfers
+    DevBuf d_part, d_red, d_tmp_in, d_one, d_gl;
+    GmresWork gw;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static bem_status fail(bem_ctx* c, bem_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+static bem_status cuda_fail(bem_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? BEM_ENOMEM : BEM_ECUDA, m);
+}
+
+#define CK(expr)                                            \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return cuda_fail(c, _e, #expr); \
+    } while (0)
+
+template <typename T>
+static cudaError_t upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
+    cudaError_t e = dalloc(b, v.size() * sizeof(T));
+    if (e != cudaSuccess || v.empty()) return e;
+    e = cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+static cudaError_t ensure(DevBuf& b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return cudaSuccess;
+    return dalloc(b, bytes);
+}
+
+static int esize_of(int dtype) { return dtype == BEM_C64 ? 8 : 16; }
+
+static GeomDev geom_view(const bem_ctx* c) {
+    GeomDev g;
+    g.nt = (int)c->nt;
+    g.ne = (int)c->ne;
+    g.tv = (const double*)c->d_tv.p;
+    g.area = (const double*)c->d_area.p;
+    g.nrm = (const double*)c->d_nrm.p;
+    g.cen = (const double*)c->d_cen.p;
+    g.diam = (const double*)c->d_diam.p;
+    g.tvid = (const int*)c->d_tvid.p;
+    g.tri_edge = (const int*)c->d_tri_edge.p;
+    g.tri_coef = (const double*)c->d_tri_coef.p;
+    g.edge_tri = (const int*)c->d_edge_tri.p;
+    g.edge_loc = (const int*)c->d_edge_loc.p;
+    g.sing_ptr = (const int*)c->d_sing_ptr.p;
+    g.sing_b = (const int*)c->d_sing_b.p;
+    g.sing_val = (const c128*)c->d_sing_val.p;
+    g.k0 = c->k0;
+    g.k1 = c->k1;
+    g.eta_r = c->eta_r;
+    return g;
+}
+
+static c128 csqrt_principal(c128 z) {
+    double r = std::sqrt(z.re * z.re + z.im * z.im);
+    double a = std::sqrt(std::max(0.0, 0.5 * (r + z.re)));
+    double b = std::sqrt(std::max(0.0, 0.5 * (r - z.re)));
+    if (z.im < 0) b = -b;
+    return mk<double>(a, b);
+}
+
+static void release_operator(Operator& o) {
+    dfree(o.near);
+    dfree(o.arena);
+    dfree(o.far_rec);
+    dfree(o.far_order);
+    dfree(o.xp);
+    dfree(o.t);
+    o.built = false;
+    o.t_len = 0;
+    o.recs.clear();
+    o.max_rank = 0;
+    for (int i = 0; i < 3; ++i) o.factor_entries[i] = 0;
+}
+
+static void invalidate(bem_ctx* c) {
+    c->assembled = false;
+    for (int i = 0; i < 2; ++i) release_operator(c->op[i]);
+}
+
+// ---------------------------------------------------------------------------
+// options, context
+// ---------------------------------------------------------------------------
+extern "C" void bem_default_options(bem_options* o) {
+    if (!o) return;
+    o->precision = BEM_PREC_C64;
+    o->leaf_size = 64;
+    o->eta = 2.0;
+    o->aca_tol = 1e-4;
+    o->aca_max_rank = 96;
+    o->gmres_restart = 50;
+    o->maxit = 1000;
+    o->tol = 1e-6;
+    o->refine_tol = 0.0;
+    o->refine_maxit = 10;
+}
+
+extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
+    if (!out) return BEM_EINVAL;
+    *out = nullptr;
+    bem_options o;
+    bem_default_options(&o);
+    if (opt) o = *opt;
+    if (o.leaf_size < 2 || o.leaf_size > BEM_MAX_LEAF || (o.precision & 3) == 0 || o.aca_tol <= 0 ||
+        o.aca_max_rank < 1 || o.aca_max_rank > 128 || o.gmres_restart < 1 || o.gmres_restart > 200 || o.maxit < 1 ||
+        o.tol <= 0 || o.refine_tol < 0 || o.refine_maxit < 1)
+        return BEM_EINVAL;
+    bem_ctx* c = new (std::nothrow) bem_ctx();
+    if (!c) return BEM_ENOMEM;
+    c->opt = o;
+    *out = c;
+    return BEM_OK;
+}
+
+extern "C" void bem_destroy(bem_ctx* c) {
+    if (!c) return;
+    invalidate(c);
+    DevBuf* bufs[] = {&c->d_tv, &c->d_area, &c->d_nrm, &c->d_cen, &c->d_diam, &c->d_tvid, &c->d_tri_edge,
+                      &c->d_tri_coef, &c->d_edge_tri, &c->d_edge_loc, &c->d_mid, &c->d_sing_ptr, &c->d_sing_b,
+                      &c->d_sing_val, &c->d_perm, &c->d_leaf_r0, &c->d_leaf_m, &c->d_near_ptr, &c->d_near_c0,
+                      &c->d_near_n, &c->d_near_off, &c->d_farp_ptr, &c->d_farp_blk, &c->d_farp_row, &c->d_part,
+                      &c->d_red, &c->d_tmp_in, &c->d_one, &c->d_gl, &c->gw.V, &c->gw.w, &c->gw.z, &c->gw.r,
+                      &c->gw.xin, &c->gw.rin, &c->gw.hpart, &c->gw.hdev, &c->gw.npart};
+    for (DevBuf* b : bufs) dfree(*b);
+    delete c;
+}
+
+extern "C" const char* bem_last_error(const bem_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" int64_t bem_num_edges(const bem_ctx* c) { return (c && c->has_mesh) ? c->ne : -1; }
+extern "C" int64_t bem_num_unknowns(const bem_ctx* c) { return (c && c->has_mesh) ? 2 * c->ne : -1; }
+
+// ---------------------------------------------------------------------------
+// mesh -> RWG table (same conventions as the problem statement in bem.h)
+// ---------------------------------------------------------------------------
+extern "C" bem_status bem_set_mesh(bem_ctx* c, const double* verts, int64_t nv, const int32_t* tris, int64_t nt) {
+    if (!c) return BEM_EINVAL;
+    if (!verts || !tris || nv <= 0 || nt <= 0) return fail(c, BEM_EINVAL, "empty mesh");
+    if (nt > (1 << 29) || nv > (1 << 30)) return fail(c, BEM_EINVAL, "mesh too large");
+    invalidate(c);
+    c->has_mesh = false;
+    for (int64_t t = 0; t < nt; ++t)
+        for (int i = 0; i < 3; ++i) {
+            int v = tris[3 * t + i];
+            if (v < 0 || v >= nv) return fail(c, BEM_EINVAL, "triangle index out of range");
+        }
+    std::vector<double> tv(9 * nt), area(nt), nrm(3 * nt), cen(3 * nt), diam(nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        int a = tris[3 * t], b = tris[3 * t + 1], d = tris[3 * t + 2];
+        if (a == b || b == d || a == d) return fail(c, BEM_EINVAL, "degenerate triangle (repeated vertex)");
+        const double* p[3] = {verts + 3 * a, verts + 3 * b, verts + 3 * d};
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) tv[9 * t + 3 * i + k] = p[i][k];
+        double e1[3], e2[3];
+        for (int k = 0; k < 3; ++k) {
+            e1[k] = p[1][k] - p[0][k];
+            e2[k] = p[2][k] - p[0][k];
+        }
+        double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double dbl = std::sqrt((cr[0] * cr[0] + cr[1] * cr[1]) + cr[2] * cr[2]);
+        double lmax2 = 0.0, lmax = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            const double* u = p[(i + 1) % 3];
+            const double* v = p[(i + 2) % 3];
+            double dx = u[0] - v[0], dy = u[1] - v[1], dz = u[2] - v[2];
+            double s2 = (dx * dx + dy * dy) + dz * dz;
+            lmax2 = std::max(lmax2, s2);
+            lmax = std::max(lmax, std::sqrt(s2));
+        }
+        if (!(dbl > 1e-12 * lmax2)) return fail(c, BEM_EINVAL, "zero-area triangle");
+        area[t] = 0.5 * dbl;
+        for (int k = 0; k < 3; ++k) {
+            nrm[3 * t + k] = cr[k] / dbl;
+            cen[3 * t + k] = ((p[0][k] + p[1][k]) + p[2][k]) / 3.0;
+        }
+        diam[t] = lmax;
+    }
+    // half edges: (min, max, tri, local vertex opposite, direction)
+    struct HE {
+        int lo, hi, t, i, fwd;
+    };
+    std::vector<HE> he(3 * nt);
+    for (int64_t t = 0; t < nt; ++t)
+        for (int i = 0; i < 3; ++i) {
+            int a = tris[3 * t + (i + 1) % 3], b = tris[3 * t + (i + 2) % 3];
+            he[3 * t + i] = {std::min(a, b), std::max(a, b), (int)t, i, a < b ? 1 : 0};
+        }
+    std::sort(he.begin(), he.end(), [](const HE& x, const HE& y) {
+        if (x.lo != y.lo) return x.lo < y.lo;
+        if (x.hi != y.hi) return x.hi < y.hi;
+        return x.t < y.t;
+    });
+    std::vector<int> edge_v, edge_tri, edge_loc;
+    std::vector<int> tri_edge(3 * nt, -1);
+    std::vector<double> tri_coef(3 * nt, 0.0);
+    size_t k = 0;
+    while (k < he.size()) {
+        size_t j = k;
+        while (j < he.size() && he[j].lo == he[k].lo && he[j].hi == he[k].hi) ++j;
+        if (j - k != 2) return fail(c, BEM_EINVAL, "edge not shared by exactly two triangles (mesh not closed two-manifold)");
+        HE a = he[k], b = he[k + 1];
+        if (a.fwd == b.fwd) return fail(c, BEM_EINVAL, "inconsistent triangle orientation");
+        if (a.t == b.t) return fail(c, BEM_EINVAL, "edge used twice by one triangle");
+        if (b.t < a.t) std::swap(a, b);
+        int e = (int)edge_v.size() / 2;
+        edge_v.push_back(a.lo);
+        edge_v.push_back(a.hi);
+        edge_tri.push_back(a.t);
+        edge_tri.push_back(b.t);
+        edge_loc.push_back(a.i);
+        edge_loc.push_back(b.i);
+        const double* pa = verts + 3 * a.lo;
+        const double* pb = verts + 3 * a.hi;
+        double dx = pb[0] - pa[0], dy = pb[1] - pa[1], dz = pb[2] - pa[2];
+        double len = std::sqrt((dx * dx + dy * dy) + dz * dz);
+        tri_edge[3 * a.t + a.i] = e;
+        tri_coef[3 * a.t + a.i] = len;
+        tri_edge[3 * b.t + b.i] = e;
+        tri_coef[3 * b.t + b.i] = -len;
+        k = j;
+    }
+    int64_t ne = (int64_t)edge_v.size() / 2;
+    std::vector<double> mid(3 * ne);
+    for (int64_t e = 0; e < ne; ++e)
+        for (int d = 0; d < 3; ++d) mid[3 * e + d] = (verts[3 * edge_v[2 * e] + d] + verts[3 * edge_v[2 * e + 1] + d]) * 0.5;
+    c->nv = nv;
+    c->nt = nt;
+    c->ne = ne;
+    c->verts.assign(verts, verts + 3 * nv);
+    c->tris.assign(tris, tris + 3 * nt);
+    c->edge_v.swap(edge_v);
+    c->edge_tri.swap(edge_tri);
+    c->edge_loc.swap(edge_loc);
+    c->tri_edge.swap(tri_edge);
+    c->tri_coef.swap(tri_coef);
+    c->area.swap(area);
+    c->nrm.swap(nrm);
+    c->cen.swap(cen);
+    c->diam.swap(diam);
+    c->tv.swap(tv);
+    c->mid.swap(mid);
+    c->has_mesh = true;
+    c->err.clear();
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_set_media(bem_ctx* c, double k0, bem_c128 eps_r, bem_c128 mu_r) {
+    if (!c) return BEM_EINVAL;
+    if (!(k0 > 0) || !std::isfinite(k0)) return fail(c, BEM_EINVAL, "k0 must be positive");
+    if (eps_r.im > 0 || mu_r.im > 0) return fail(c, BEM_EINVAL, "Im eps_r and Im mu_r must be <= 0 (e^{+jwt})");
+    if (eps_r.re == 0 && eps_r.im == 0) return fail(c, BEM_EINVAL, "eps_r must be nonzero");
+    if (mu_r.re == 0 && mu_r.im == 0) return fail(c, BEM_EINVAL, "mu_r must be nonzero");
+    invalidate(c);
+    c->k0 = k0;
+    c->eps = mk<double>(eps_r.re, eps_r.im);
+    c->mu = mk<double>(mu_r.re, mu_r.im);
+    c->k1 = k0 * csqrt_principal(c->eps * c->mu);
+    c->eta_r = csqrt_principal(cdiv(c->mu, c->eps));
+    c->has_media = true;
+    c->err.clear();
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_debye_eps(double f, const double* params, bem_c128* out) {
+    if (!out || !(f >= 0) || !std::isfinite(f)) return BEM_EINVAL;
+    double einf = 3.0, es = 60.0, e2 = 3.6, t1 = 10e-12, t2 = 0.2e-12;
+    if (params) {
+        einf = params[0];
+        es = params[1];
+        e2 = params[2];
+        t1 = params[3];
+        t2 = params[4];
+    }
+    double w = 2.0 * BEM_PI * f;
+    c128 a = cdiv(mk<double>(es - e2, 0.0), mk<double>(1.0, w * t1));
+    c128 b = cdiv(mk<double>(e2 - einf, 0.0), mk<double>(1.0, w * t2));
+    out->re = einf + a.re + b.re;
+    out->im = a.im + b.im;
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_edges(const bem_ctx* c, int32_t* out) {
+    if (!c || !out) return BEM_EINVAL;
+    if (!c->has_mesh) return BEM_ESTATE;
+    for (int64_t e = 0; e < c->ne; ++e) {
+        out[4 * e] = c->edge_v[2 * e];
+        out[4 * e + 1] = c->edge_v[2 * e + 1];
+        out[4 * e + 2] = c->edge_tri[2 * e];
+        out[4 * e + 3] = c->edge_tri[2 * e + 1];
+    }
+    return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// assembly
+// ---------------------------------------------------------------------------
+static bem_status upload_geometry(bem_ctx* c, cudaStream_t st) {
+    std::vector<int> tvid(c->tris.begin(), c->tris.end());
+    CK(upload(c->d_tv, c->tv, st));
+    CK(upload(c->d_area, c->area, st));
+    CK(upload(c->d_nrm, c->nrm, st));
+    CK(upload(c->d_cen, c->cen, st));
+    CK(upload(c->d_diam, c->diam, st));
+    CK(upload(c->d_tvid, tvid, st));
+    CK(upload(c->d_tri_edge, c->tri_edge, st));
+    CK(upload(c->d_tri_coef, c->tri_coef, st));
+    CK(upload(c->d_edge_tri, c->edge_tri, st));
+    CK(upload(c->d_edge_loc, c->edge_loc, st));
+    CK(upload(c->d_mid, c->mid, st));
+    return BEM_OK;
+}
+
+static bem_status build_tree(bem_ctx* c, cudaStream_t st) {
+    const int N = (int)c->ne, leaf = c->opt.leaf_size;
+    // node ranges depend on sizes only: breadth-first layout
+    std::vector<int> lo, hi, child0, level;
+    lo.push_back(0);
+    hi.push_back(N);
+    child0.push_back(-1);
+    level.push_back(0);
+    for (size_t i = 0; i < lo.size(); ++i) {
+        int sz = hi[i] - lo[i];
+        if (sz > leaf) {
+            child0[i] = (int)lo.size();
+            int midp = lo[i] + sz / 2;
+            lo.push_back(lo[i]);
+            hi.push_back(midp);
+            child0.push_back(-1);
+            level.push_back(level[i] + 1);
+            lo.push_back(midp);
+            hi.push_back(hi[i]);
+            child0.push_back(-1);
+            level.push_back(level[i] + 1);
+        }
+    }
+    const int nn = (int)lo.size();
+    DevBuf d_lo, d_hi, d_child0, d_bbmin, d_bbmax, d_pos, d_split, d_perm2;
+    struct Guard {
+        DevBuf* b[8];
+        ~Guard() {
+            for (DevBuf* x : b) dfree(*x);
+        }
+    } guard{{&d_lo, &d_hi, &d_child0, &d_bbmin, &d_bbmax, &d_pos, &d_split, &d_perm2}};
+    CK(upload(d_lo, lo, st));
+    CK(upload(d_hi, hi, st));
+    CK(upload(d_child0, child0, st));
+    CK(dalloc(d_bbmin, sizeof(double) * 3 * nn));
+    CK(dalloc(d_bbmax, sizeof(double) * 3 * nn));
+    std::vector<int64_t> perm(N);
+    std::iota(perm.begin(), perm.end(), 0);
+    CK(upload(c->d_perm, perm, st));
+    CK(dalloc(d_perm2, sizeof(int64_t) * N));
+    CK(dalloc(d_pos, sizeof(int) * N));
+    CK(dalloc(d_split, sizeof(int) * nn));
+    const double* pts = (const double*)c->d_mid.p;
+    int maxlev = *std::max_element(level.begin(), level.end());
+    for (int L = 0; L <= maxlev; ++L) {
+        int ls = (int)(std::find(level.begin(), level.end(), L) - level.begin());
+        int le = ls;
+        while (le < nn && level[le] == L) ++le;
+        bool any = false;
+        std::vector<int> pos(N, -1), split(le - ls, 0);
+        for (int i = ls; i < le; ++i) {
+            split[i - ls] = child0[i] >= 0;
+            any |= child0[i] >= 0;
+            for (int k = lo[i]; k < hi[i]; ++k) pos[k] = i - ls;
+        }
+        if (!any) break;
+        CK(cudaMemcpyAsync(d_pos.p, pos.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_split.p, split.data(), sizeof(int) * split.size(), cudaMemcpyHostToDevice, st));
+        CK(tree_bbox_level(pts, (const int64_t*)c->d_perm.p, (const int*)d_lo.p + ls, (const int*)d_hi.p + ls,
+                           le - ls, (double*)d_bbmin.p + 3 * ls, (double*)d_bbmax.p + 3 * ls, st));
+        CK(tree_split_level(pts, (const int64_t*)c->d_perm.p, (int64_t*)d_perm2.p, (const int*)d_lo.p + ls,
+                            (const int*)d_hi.p + ls, (const double*)d_bbmin.p + 3 * ls,
+                            (const double*)d_bbmax.p + 3 * ls, (const int*)d_split.p, le - ls, (const int*)d_pos.p, N,
+                            st));
+        std::swap(c->d_perm, d_perm2);
+        CK(cudaStreamSynchronize(st));
+    }
+    CK(tree_bbox_level(pts, (const int64_t*)c->d_perm.p, (const int*)d_lo.p, (const int*)d_hi.p, nn,
+                       (double*)d_bbmin.p, (double*)d_bbmax.p, st));
+    CK(cudaMemcpyAsync(perm.data(), c->d_perm.p, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    c->perm.swap(perm);
+    c->node_lo = lo;
+    c->node_hi = hi;
+    c->node_child0 = child0;
+    c->leaf_lo.clear();
+    c->leaf_m.clear();
+    for (int i = 0; i < nn; ++i)
+        if (child0[i] < 0) {
+            c->leaf_lo.push_back(lo[i]);
+            c->leaf_m.push_back(hi[i] - lo[i]);
+        }
+    {
+        std::vector<size_t> idx(c->leaf_lo.size());
+        std::iota(idx.begin(), idx.end(), 0);
+        std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return c->leaf_lo[a] < c->leaf_lo[b]; });
+        std::vector<int> l2, m2;
+        for (size_t i : idx) {
+            l2.push_back(c->leaf_lo[i]);
+            m2.push_back(c->leaf_m[i]);
+        }
+        c->leaf_lo.swap(l2);
+        c->leaf_m.swap(m2);
+    }
+    // block tree, level by level on the device
+    DevBuf d_cand, d_next, d_kind, d_counts, d_offs, d_tot, d_nearl, d_farl;
+    struct Guard2 {
+        DevBuf* b[8];
+        ~Guard2() {
+            for (DevBuf* x : b) dfree(*x);
+        }
+    } guard2{{&d_cand, &d_next, &d_kind, &d_counts, &d_offs, &d_tot, &d_nearl, &d_farl}};
+    std::vector<int> cand0 = {0, 0};
+    CK(upload(d_cand, cand0, st));
+    CK(dalloc(d_tot, sizeof(int) * 3));
+    int ncand = 1;
+    std::vector<BlockDesc> nearv, farv;
+    const double eta = c->opt.eta;
+    while (ncand > 0) {
+        CK(ensure(d_kind, sizeof(int) * ncand));
+        CK(ensure(d_counts, sizeof(int) * 3 * ncand));
+        CK(ensure(d_offs, sizeof(int) * 3 * ncand));
+        CK(tree_block_level((const int*)d_cand.p, ncand, (const int*)d_lo.p, (const int*)d_hi.p,
+                            (const int*)d_child0.p, (const double*)d_bbmin.p, (const double*)d_bbmax.p, eta,
+                            (int*)d_kind.p, (int*)d_counts.p, st));
+        for (int q = 0; q < 3; ++q)
+            CK(scan_exclusive((const int*)d_counts.p + q * ncand, (int*)d_offs.p + q * ncand, ncand,
+                              (int*)d_tot.p + q, st));
+        int tot[3];
+        CK(cudaMemcpyAsync(tot, d_tot.p, sizeof(tot), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        CK(dalloc(d_next, sizeof(int) * 2 * std::max(1, tot[2])));
+        CK(ensure(d_nearl, sizeof(int) * 4 * std::max(1, tot[1])));
+        CK(ensure(d_farl, sizeof(int) * 4 * std::max(1, tot[0])));
+        CK(tree_block_emit((const int*)d_cand.p, ncand, (const int*)d_kind.p, (const int*)d_child0.p,
+                           (const int*)d_offs.p, (int*)d_next.p, (int*)d_nearl.p, (int*)d_farl.p, (const int*)d_lo.p,
+                           (const int*)d_hi.p, st));
+        size_t n0 = nearv.size(), f0 = farv.size();
+        nearv.resize(n0 + tot[1]);
+        farv.resize(f0 + tot[0]);
+        if (tot[1]) CK(cudaMemcpyAsync(nearv.data() + n0, d_nearl.p, sizeof(BlockDesc) * tot[1], cudaMemcpyDeviceToHost, st));
+        if (tot[0]) CK(cudaMemcpyAsync(farv.data() + f0, d_farl.p, sizeof(BlockDesc) * tot[0], cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::swap(d_cand, d_next);
+        ncand = tot[2];
+    }
+    auto canon = [](std::vector<BlockDesc>& v) {
+        std::sort(v.begin(), v.end(), [](const BlockDesc& a, const BlockDesc& b) {
+            return a.r0 != b.r0 ? a.r0 < b.r0 : a.c0 < b.c0;
+        });
+    };
+    canon(nearv);
+    canon(farv);
+    c->near_blocks.swap(nearv);
+    c->far_blocks.swap(farv);
+    return BEM_OK;
+}
+
+static bem_status build_singular(bem_ctx* c, cudaStream_t st) {
+    const int nt = (int)c->nt;
+    DevBuf d_counts, d_pair_a;
+    struct Guard {
+        DevBuf* b[2];
+        ~Guard() {
+            for (DevBuf* x : b) dfree(*x);
+        }
+    } guard{{&d_counts, &d_pair_a}};
+    CK(dalloc(d_counts, sizeof(int) * nt));
+    CK(dalloc(c->d_sing_ptr, sizeof(int) * (nt + 1)));
+    GeomDev g = geom_view(c);
+    CK(singular_count(g, (int*)d_counts.p, st));
+    CK(scan_exclusive((const int*)d_counts.p, (int*)c->d_sing_ptr.p, nt, (int*)c->d_sing_ptr.p + nt, st));
+    std::vector<int> ptr(nt + 1);
+    CK(cudaMemcpyAsync(ptr.data(), c->d_sing_ptr.p, sizeof(int) * (nt + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int64_t total = ptr[nt];
+    c->n_sing = total;
+    CK(dalloc(c->d_sing_b, sizeof(int) * std::max<int64_t>(1, total)));
+    g = geom_view(c);
+    CK(singular_fill(g, (const int*)c->d_sing_ptr.p, (int*)c->d_sing_b.p, st));
+    std::vector<int> pa(total);
+    for (int a = 0; a < nt; ++a)
+        for (int k = ptr[a]; k < ptr[a + 1]; ++k) pa[k] = a;
+    CK(upload(d_pair_a, pa, st));
+    CK(dalloc(c->d_sing_val, sizeof(c128) * 36 * std::max<int64_t>(1, total)));
+    g = geom_view(c);
+    CK(singular_values(g, (int)total, (const int*)d_pair_a.p, (c128*)c->d_sing_val.p, st));
+    CK(cudaStreamSynchronize(st));
+    return BEM_OK;
+}
+
+static bem_status build_plan(bem_ctx* c, cudaStream_t st) {
+    const int nleaf = (int)c->leaf_lo.size();
+    std::vector<int> leaf_of(c->ne + 1, -1);
+    for (int l = 0; l < nleaf; ++l) leaf_of[c->leaf_lo[l]] = l;
+    // near items: one per near block, grouped by row leaf (list is sorted by r0, c0)
+    std::vector<int> nptr(nleaf + 1, 0), nc0, nn;
+    std::vector<int64_t> noff;
+    int64_t off = 0;
+    for (const BlockDesc& b : c->near_blocks) {
+        int l = leaf_of[b.r0];
+        if (l < 0 || c->leaf_m[l] != b.m) return fail(c, BEM_ECUDA, "near block rows are not a leaf");
+        nptr[l + 1]++;
+        nc0.push_back(b.c0);
+        nn.push_back(b.n);
+        noff.push_back(off);
+        off += (int64_t)b.m * 2 * ((b.n + 1) / 2);
+    }
+    for (int l = 0; l < nleaf; ++l) nptr[l + 1] += nptr[l];
+    c->near_stride = off;
+    // far pieces: every leaf inside a far block's row range
+    std::vector<std::vector<std::pair<int, int>>> pieces(nleaf);
+    for (size_t b = 0; b < c->far_blocks.size(); ++b) {
+        const BlockDesc& F = c->far_blocks[b];
+        int l = leaf_of[F.r0];
+        if (l < 0) return fail(c, BEM_ECUDA, "far block does not start at a leaf");
+        for (; l < nleaf && c->leaf_lo[l] < F.r0 + F.m; ++l) pieces[l].push_back({(int)b, c->leaf_lo[l] - F.r0});
+    }
+    std::vector<int> fptr(nleaf + 1, 0), fblk, frow;
+    for (int l = 0; l < nleaf; ++l) {
+        fptr[l + 1] = fptr[l] + (int)pieces[l].size();
+        for (auto& p : pieces[l]) {
+            fblk.push_back(p.first);
+            frow.push_back(p.second);
+        }
+    }
+    CK(upload(c->d_leaf_r0, c->leaf_lo, st));
+    CK(upload(c->d_leaf_m, c->leaf_m, st));
+    CK(upload(c->d_near_ptr, nptr, st));
+    CK(upload(c->d_near_c0, nc0, st));
+    CK(upload(c->d_near_n, nn, st));
+    CK(upload(c->d_near_off, noff, st));
+    CK(upload(c->d_farp_ptr, fptr, st));
+    CK(upload(c->d_farp_blk, fblk, st));
+    CK(upload(c->d_farp_row, frow, st));
+    return BEM_OK;
+}
+
+template <typename R>
+static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
+    const size_t es = sizeof(cx<R>);
+    GeomDev g = geom_view(c);
+    const int64_t* perm = (const int64_t*)c->d_perm.p;
+    // dense blocks
+    {
+        std::vector<int64_t> offs;
+        int64_t off = 0;
+        for (const BlockDesc& b : c->near_blocks) {
+            offs.push_back(off);
+            off += (int64_t)b.m * 2 * ((b.n + 1) / 2);
+        }
+        DevBuf d_blocks, d_offs;
+        CK(upload(d_blocks, c->near_blocks, st));
+        CK(upload(d_offs, offs, st));
+        CK(dalloc(o.near, es * 3 * std::max<int64_t>(1, off)));
+        cudaError_t e = near_assemble<R>(g, perm, (const BlockDesc*)d_blocks.p, (const int64_t*)d_offs.p,
+                                         (int)c->near_blocks.size(), (cx<R>*)o.near.p, off, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        dfree(d_blocks);
+        dfree(d_offs);
+        if (e != cudaSuccess) return cuda_fail(c, e, "near assembly");
+    }
+    // far blocks: ACA in batches bounded by a scratch budget
+    const int nfar = (int)c->far_blocks.size();
+    std::vector<int> ranks(3 * nfar, 0);
+    struct Batch {
+        DevBuf arena;
+        int64_t len;
+    };
+    std::vector<Batch> batches;
+    std::vector<int64_t> task_off_u(3 * nfar), task_off_v(3 * nfar);  // offsets inside their batch arena
+    std::vector<int> task_batch(3 * nfar);
+    const int64_t budget = (int64_t)(sizeof(R) == 4 ? 1 : 2) * (1ll << 30) / (int64_t)es;  // complex elements
+    int tb = 0;
+    const int rcap = c->opt.aca_max_rank;
+    while (tb < 3 * nfar) {
+        std::vector<AcaTask> tasks;
+        int64_t scr = 0;
+        int max_m = 1;
+        int te = tb;
+        while (te < 3 * nfar) {
+            const BlockDesc& F = c->far_blocks[te / 3];
+            int rmax = std::min(rcap, std::min(F.m, F.n));
+            int64_t need = (int64_t)(F.m + F.n) * rmax + F.n;
+            if (!tasks.empty() && scr + need > budget) break;
+            tasks.push_back({F.r0, F.m, F.c0, F.n, te % 3, rmax, scr});
+            scr += need;
+            max_m = std::max(max_m, F.m);
+            ++te;
+        }
+        DevBuf d_tasks, d_scr, d_ranks, d_flags, d_ou, d_ov;
+        struct G3 {
+            DevBuf* b[6];
+            ~G3() {
+                for (DevBuf* x : b) dfree(*x);
+            }
+        } g3{{&d_tasks, &d_scr, &d_ranks, &d_flags, &d_ou, &d_ov}};
+        const int nt = (int)tasks.size();
+        CK(upload(d_tasks, tasks, st));
+        CK(dalloc(d_scr, es * scr));
+        CK(dalloc(d_ranks, sizeof(int) * nt));
+        CK(dalloc(d_flags, sizeof(int) * nt));
+        CK(aca_run<R>(g, perm, (const AcaTask*)d_tasks.p, nt, (cx<R>*)d_scr.p, c->opt.aca_tol, (int*)d_ranks.p,
+                      (int*)d_flags.p, st, max_m));
+        std::vector<int> rk(nt), fl(nt);
+        CK(cudaMemcpyAsync(rk.data(), d_ranks.p, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(fl.data(), d_flags.p, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<int64_t> ou(nt), ov(nt);
+        int64_t len = 0;
+        for (int i = 0; i < nt; ++i) {
+            if (fl[i]) {
+                char buf[200];
+                snprintf(buf, sizeof buf, "ACA did not reach tol %.3g within rank %d on a %d x %d block", c->opt.aca_tol,
+                         tasks[i].rmax, tasks[i].m, tasks[i].n);
+                return fail(c, BEM_EINVAL, buf);
+            }
+            int rp = rk[i] + (rk[i] & 1);
+            ou[i] = len;
+            len += (int64_t)tasks[i].m * rp;
+            ov[i] = len;
+            len += (int64_t)tasks[i].n * rp;
+            ranks[tb + i] = rk[i];
+            task_off_u[tb + i] = ou[i];
+            task_off_v[tb + i] = ov[i];
+            task_batch[tb + i] = (int)batches.size();
+        }
+        Batch B;
+        B.len = len;
+        CK(dalloc(B.arena, es * std::max<int64_t>(1, len)));
+        CK(upload(d_ou, ou, st));
+        CK(upload(d_ov, ov, st));
+        CK(aca_compact<R>((const AcaTask*)d_tasks.p, nt, (const cx<R>*)d_scr.p, (const int*)d_ranks.p,
+                          (const int64_t*)d_ou.p, (const int64_t*)d_ov.p, (cx<R>*)B.arena.p, st));
+        CK(cudaStreamSynchronize(st));
+        batches.push_back(B);
+        tb = te;
+    }
+    // one arena
+    std::vector<int64_t> base(batches.size() + 1, 0);
+    for (size_t i = 0; i < batches.size(); ++i) base[i + 1] = base[i] + batches[i].len;
+    cudaError_t ea = dalloc(o.arena, es * std::max<int64_t>(1, base.back()));
+    for (size_t i = 0; i < batches.size() && ea == cudaSuccess; ++i)
+        if (batches[i].len)
+            ea = cudaMemcpyAsync((char*)o.arena.p + es * base[i], batches[i].arena.p, es * batches[i].len,
+                                 cudaMemcpyDeviceToDevice, st);
+    if (ea == cudaSuccess) ea = cudaStreamSynchronize(st);
+    for (auto& b : batches) dfree(b.arena);
+    if (ea != cudaSuccess) return cuda_fail(c, ea, "factor arena");
+    // far records
+    o.recs.resize(nfar);
+    int64_t toff = 0;
+    o.max_rank = 0;
+    for (int i = 0; i < 3; ++i) o.factor_entries[i] = 0;
+    for (int b = 0; b < nfar; ++b) {
+        const BlockDesc& F = c->far_blocks[b];
+        FarRec& r = o.recs[b];
+        r.r0 = F.r0;
+        r.m = F.m;
+        r.c0 = F.c0;
+        r.n = F.n;
+        int kp[3];
+        for (int q = 0; q < 3; ++q) {
+            int t = 3 * b + q;
+            r.rk[q] = ranks[t];
+            kp[q] = (ranks[t] + 1) / 2;
+            r.off_u[q] = base[task_batch[t]] + task_off_u[t];
+            r.off_v[q] = base[task_batch[t]] + task_off_v[t];
+            o.factor_entries[q] += (int64_t)ranks[t] * (F.m + F.n);
+            o.max_rank = std::max(o.max_rank, ranks[t]);
+        }
+        r.off_t = toff;
+        toff += 2 * (kp[0] + 2 * kp[1] + kp[2]);
+    }
+    o.t_len = toff;
+    std::vector<int> order(nfar);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const FarRec &A = o.recs[a], &B = o.recs[b];
+        int64_t wa = (int64_t)A.n * (A.rk[0] + A.rk[1] + A.rk[2]), wb = (int64_t)B.n * (B.rk[0] + B.rk[1] + B.rk[2]);
+        return wa > wb;
+    });
+    CK(upload(o.far_rec, o.recs, st));
+    CK(upload(o.far_order, order, st));
+    CK(dalloc(o.xp, es * 2 * c->ne));
+    CK(dalloc(o.t, es * std::max<int64_t>(1, o.t_len)));
+    o.built = true;
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_assemble(bem_ctx* c, void* stream) {
+    if (!c) return BEM_EINVAL;
+    if (!c->has_mesh || !c->has_media) return fail(c, BEM_ESTATE, "bem_assemble needs bem_set_mesh and bem_set_media");
+    cudaStream_t st = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    invalidate(c);
+    bem_status s;
+    if ((s = upload_geometry(c, st)) != BEM_OK) return s;
+    if ((s = build_tree(c, st)) != BEM_OK) return s;
+    if ((s = build_singular(c, st)) != BEM_OK) return s;
+    if ((s = build_plan(c, st)) != BEM_OK) return s;
+    if (c->opt.precision & BEM_PREC_C64)
+        if ((s = build_operator<float>(c, c->op[0], st)) != BEM_OK) return s;
+    if (c->opt.precision & BEM_PREC_C128)
+        if ((s = build_operator<double>(c, c->op[1], st)) != BEM_OK) return s;
+    CK(cudaStreamSynchronize(st));
+    c->assemble_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    c->assembled = true;
+    c->err.clear();
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_stats_get(const bem_ctx* cc, bem_stats* out) {
+    bem_ctx* c = const_cast<bem_ctx*>(cc);
+    if (!c || !out) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "not assembled");
+    memset(out, 0, sizeof(*out));
+    out->ne = c->ne;
+    out->nt = c->nt;
+    out->n_clusters = (int64_t)c->node_lo.size();
+    out->n_leaves = (int64_t)c->leaf_lo.size();
+    out->n_near = (int64_t)c->near_blocks.size();
+    out->n_far = (int64_t)c->far_blocks.size();
+    for (const BlockDesc& b : c->near_blocks) out->near_entries += (int64_t)b.m * b.n;
+    const Operator& o = c->op[0].built ? c->op[0] : c->op[1];
+    for (int q = 0; q < 3; ++q) out->factor_entries[q] = o.factor_entries[q];
+    out->max_rank = o.max_rank;
+    out->singular_pairs = c->n_sing;
+    // algorithmic bytes: every stored entry once, x read twice (gather + use), y written once
+    for (int p = 0; p < 2; ++p) {
+        const Operator& q = c->op[p];
+        if (!q.built) continue;
+        int64_t es = p == 0 ? 8 : 16;
+        int64_t ent = 3 * out->near_entries + q.factor_entries[0] + q.factor_entries[1] + q.factor_entries[2];
+        int64_t bytes = es * (ent + 3 * 2 * c->ne);
+        if (p == 0)
+            out->matvec_bytes_c64 = bytes;
+        else
+            out->matvec_bytes_c128 = bytes;
+    }
+    out->assemble_ms = c->assemble_ms;
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_partition(const bem_ctx* cc, int64_t* perm, int32_t* nearo, int32_t* faro) {
+    bem_ctx* c = const_cast<bem_ctx*>(cc);
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "not assembled");
+    if (perm) memcpy(perm, c->perm.data(), sizeof(int64_t) * c->ne);
+    if (nearo) memcpy(nearo, c->near_blocks.data(), sizeof(BlockDesc) * c->near_blocks.size());
+    if (faro) memcpy(faro, c->far_blocks.data(), sizeof(BlockDesc) * c->far_blocks.size());
+    return BEM_OK;
+}
+
+static bool dtype_ok(const bem_ctx* c, int dtype) {
+    if (dtype == BEM_C64) return c->op[0].built;
+    if (dtype == BEM_C128) return c->op[1].built;
+    return false;
+}
+
+extern "C" bem_status bem_eval_entries(bem_ctx* c, const int32_t* rows, const int32_t* cols, int64_t count, void* out,
+                                       int dtype, void* stream) {
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "bem_eval_entries needs bem_assemble");
+    if (count < 0 || (count > 0 && (!rows || !cols || !out))) return fail(c, BEM_EINVAL, "bad arguments");
+    if (dtype != BEM_C64 && dtype != BEM_C128) return fail(c, BEM_EINVAL, "dtype");
+    GeomDev g = geom_view(c);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == BEM_C64)
+        CK(eval_entries<float>(g, rows, cols, count, (c64*)out, st));
+    else
+        CK(eval_entries<double>(g, rows, cols, count, (c128*)out, st));
+    return BEM_OK;
+}
+
+static MatvecPlan make_plan(const bem_ctx* c, const Operator& o) {
+    MatvecPlan p;
+    p.ne = (int)c->ne;
+    p.nleaf = (int)c->leaf_lo.size();
+    p.nfar = (int)c->far_blocks.size();
+    p.perm = (const int64_t*)c->d_perm.p;
+    p.leaf_r0 = (const int*)c->d_leaf_r0.p;
+    p.leaf_m = (const int*)c->d_leaf_m.p;
+    p.near_ptr = (const int*)c->d_near_ptr.p;
+    p.near_c0 = (const int*)c->d_near_c0.p;
+    p.near_n = (const int*)c->d_near_n.p;
+    p.near_off = (const int64_t*)c->d_near_off.p;
+    p.near_op_stride = c->near_stride;
+    p.farp_ptr = (const int*)c->d_farp_ptr.p;
+    p.farp_blk = (const int*)c->d_farp_blk.p;
+    p.farp_row = (const int*)c->d_farp_row.p;
+    p.far = (const FarRec*)o.far_rec.p;
+    p.far_order = (const int*)o.far_order.p;
+    return p;
+}
+
+static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int nrhs, cudaStream_t st) {
+    if (dtype == BEM_C64) {
+        Operator& o = c->op[0];
+        return matvec_run<float>(make_plan(c, o), o.near.p, o.arena.p, (const c64*)x, (c64*)y, (c64*)o.xp.p,
+                                 (c64*)o.t.p, nrhs, o.t_len, st);
+    }
+    Operator& o = c->op[1];
+    return matvec_run<double>(make_plan(c, o), o.near.p, o.arena.p, (const c128*)x, (c128*)y, (c128*)o.xp.p,
+                              (c128*)o.t.p, nrhs, o.t_len, st);
+}
+
+extern "C" bem_status bem_matvec(bem_ctx* c, const void* x, void* y, int nrhs, int dtype, void* stream) {
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "bem_matvec needs bem_assemble");
+    if (!dtype_ok(c, dtype)) return fail(c, BEM_EINVAL, "no operator of that precision was assembled");
+    if (nrhs < 1 || !x || !y) return fail(c, BEM_EINVAL, "bad arguments");
+    int64_t bytes = (int64_t)esize_of(dtype) * 2 * c->ne * nrhs;
+    const char* xa = (const char*)x;
+    const char* ya = (const char*)y;
+    if (xa < ya + bytes && ya < xa + bytes) return fail(c, BEM_EINVAL, "x and y overlap");
+    CK(matvec_any(c, dtype, x, y, nrhs, (cudaStream_t)stream));
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_rhs_planewave(bem_ctx* c, const double* khat, const bem_c128* e0, int nrhs, void* b,
+                                        int dtype, void* stream) {
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "bem_rhs_planewave needs bem_assemble");
+    if (nrhs < 1 || !khat || !e0 || !b || (dtype != BEM_C64 && dtype != BEM_C128))
+        return fail(c, BEM_EINVAL, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> buf(3 * nrhs + 6 * nrhs);
+    memcpy(buf.data(), khat, sizeof(double) * 3 * nrhs);
+    memcpy(buf.data() + 3 * nrhs, e0, sizeof(double) * 6 * nrhs);
+    CK(ensure(c->d_tmp_in, sizeof(double) * buf.size()));
+    CK(cudaMemcpyAsync(c->d_tmp_in.p, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, st));
+    GeomDev g = geom_view(c);
+    const double* kd = (const double*)c->d_tmp_in.p;
+    const c128* ed = (const c128*)(kd + 3 * nrhs);
+    if (dtype == BEM_C64)
+        CK(rhs_planewave<float>(g, kd, ed, nrhs, (c64*)b, st));
+    else
+        CK(rhs_planewave<double>(g, kd, ed, nrhs, (c128*)b, st));
+    CK(cudaStreamSynchronize(st));
+    return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solve: restarted GMRES (FP64 inner products) + optional FP64 refinement
+// ---------------------------------------------------------------------------
+static const int NPART = 304;  // 2 x 152 SMs of reduction partials
+
+static bem_status norm_dev(bem_ctx* c, int dtype, const void* v, int64_t n, double* out, cudaStream_t st) {
+    CK(ensure(c->d_part, sizeof(double) * NPART * 2));
+    CK(kv_norm2(v, dtype, n, (double*)c->d_part.p, NPART, st));
+    double h[NPART];
+    CK(cudaMemcpyAsync(h, c->d_part.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double s = 0;
+    for (int i = 0; i < NPART; ++i) s += h[i];
+    *out = std::sqrt(s);
+    return BEM_OK;
+}
+
+static bem_status gmres_work(bem_ctx* c, int dtype, int restart) {
+    GmresWork& w = c->gw;
+    int64_t n = 2 * c->ne;
+    if (w.dtype == dtype && w.n == n && w.restart == restart && w.V.p) return BEM_OK;
+    size_t es = esize_of(dtype);
+    CK(dalloc(w.V, es * n * (restart + 1)));
+    CK(dalloc(w.w, es * n));
+    CK(dalloc(w.z, es * n));
+    CK(dalloc(w.r, es * n));
+    CK(dalloc(w.xin, es * n));
+    CK(dalloc(w.rin, es * n));
+    CK(dalloc(w.hpart, sizeof(c128) * NPART * (restart + 1)));
+    CK(dalloc(w.hdev, sizeof(c128) * (restart + 1)));
+    w.dtype = dtype;
+    w.n = n;
+    w.restart = restart;
+    return BEM_OK;
+}
+
+// solve Z x = rhs (dtype vectors in gw.rin / gw.xin), x starts at zero; absolute tolerance
+static bem_status gmres(bem_ctx* c, int dtype, double tol_abs, int maxit, int* iters, double* final_res,
+                        cudaStream_t st) {
+    GmresWork& w = c->gw;
+    const int64_t n = w.n;
+    const int m = w.restart;
+    const size_t es = esize_of(dtype);
+    char* V = (char*)w.V.p;
+    CK(cudaMemsetAsync(w.xin.p, 0, es * n, st));
+    CK(cudaMemcpyAsync(w.r.p, w.rin.p, es * n, cudaMemcpyDeviceToDevice, st));
+    std::vector<c128> H((m + 1) * m), g(m + 1), cs(m), sn(m), hv(m + 1);
+    double beta;
+    bem_status s;
+    int it = 0;
+    while (true) {
+        if ((s = norm_dev(c, dtype, w.r.p, n, &beta, st)) != BEM_OK) return s;
+        if (beta <= tol_abs || it >= maxit) break;
+        CK(kv_scale_copy(w.r.p, dtype, 1.0 / beta, n, V, st));
+        std::fill(H.begin(), H.end(), mk<double>(0, 0));
+        std::fill(g.begin(), g.end(), mk<double>(0, 0));
+        g[0] = mk<double>(beta, 0);
+        int jl = -1;
+        for (int j = 0; j < m; ++j) {
+            CK(matvec_any(c, dtype, V + es * n * j, w.w.p, 1, st));
+            for (int pass = 0; pass < 2; ++pass) {
+                CK(kv_multidot(V, dtype, n, j + 1, w.w.p, n, (c128*)w.hpart.p, NPART, st));
+                CK(kv_reduce_partials((const c128*)w.hpart.p, NPART, j + 1, (c128*)w.hdev.p, st));
+                CK(kv_update(w.w.p, V, dtype, n, j + 1, (const c128*)w.hdev.p, -1.0, n, st));
+                CK(cudaMemcpyAsync(hv.data(), w.hdev.p, sizeof(c128) * (j + 1), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                for (int i = 0; i <= j; ++i) H[i * m + j] = H[i * m + j] + hv[i];
+            }
+            double hn;
+            if ((s = norm_dev(c, dtype, w.w.p, n, &hn, st)) != BEM_OK) return s;
+            H[(j + 1) * m + j] = mk<double>(hn, 0);
+            if (hn > 0) CK(kv_scale_copy(w.w.p, dtype, 1.0 / hn, n, V + es * n * (j + 1), st));
+            // previous rotations
+            for (int i = 0; i < j; ++i) {
+                c128 a = H[i * m + j], b = H[(i + 1) * m + j];
+                H[i * m + j] = cs[i] * a + sn[i] * b;
+                H[(i + 1) * m + j] = cconj(sn[i]) * mk<double>(-a.re, -a.im) + cs[i] * b;
+            }
+            c128 a = H[j * m + j], b = H[(j + 1) * m + j];
+            double na = std::sqrt(cabs2(a)), nb = std::sqrt(cabs2(b));
+            double t = std::sqrt(na * na + nb * nb);
+            if (na == 0) {
+                cs[j] = mk<double>(0, 0);
+                sn[j] = mk<double>(1, 0);
+            } else {
+                cs[j] = mk<double>(na / t, 0);
+                sn[j] = (1.0 / t) * (cdiv(a, mk<double>(na, 0)) * cconj(b));
+            }
+            H[j * m + j] = cs[j] * a + sn[j] * b;
+            H[(j + 1) * m + j] = mk<double>(0, 0);
+            g[j + 1] = cconj(sn[j]) * mk<double>(-g[j].re, -g[j].im);
+            g[j] = cs[j] * g[j];
+            ++it;
+            jl = j;
+            double res = std::sqrt(cabs2(g[j + 1]));
+            if (res <= tol_abs || it >= maxit || hn == 0) break;
+        }
+        // y = H^-1 g, x += V y
+        int k = jl + 1;
+        std::vector<c128> y(k);
+        for (int i = k - 1; i >= 0; --i) {
+            c128 acc = g[i];
+            for (int l = i + 1; l < k; ++l) acc = acc - H[i * m + l] * y[l];
+            y[i] = cdiv(acc, H[i * m + i]);
+        }
+        CK(cudaMemcpyAsync(w.hdev.p, y.data(), sizeof(c128) * k, cudaMemcpyHostToDevice, st));
+        CK(kv_update(w.xin.p, V, dtype, n, k, (const c128*)w.hdev.p, 1.0, n, st));
+        // true residual
+        CK(matvec_any(c, dtype, w.xin.p, w.z.p, 1, st));
+        CK(kv_sub(w.rin.p, w.z.p, w.r.p, dtype, n, st));
+    }
+    *iters += it;
+    *final_res = beta;
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_solve(bem_ctx* c, const void* b, void* x, int nrhs, void* stream, int* iters,
+                                double* relres) {
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "bem_solve needs bem_assemble");
+    if (nrhs < 1 || !b || !x) return fail(c, BEM_EINVAL, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int din = c->op[0].built ? BEM_C64 : BEM_C128;
+    const bool out128 = c->op[1].built;
+    if (c->opt.refine_tol > 0 && !out128)
+        return fail(c, BEM_EINVAL, "refinement needs the complex128 operator (precision bit BEM_PREC_C128)");
+    bem_status s;
+    if ((s = gmres_work(c, din, c->opt.gmres_restart)) != BEM_OK) return s;
+    const int64_t n = 2 * c->ne;
+    DevBuf zr, rr;
+    struct G {
+        DevBuf* b[2];
+        ~G() {
+            for (DevBuf* x : b) dfree(*x);
+        }
+    } guard{{&zr, &rr}};
+    CK(dalloc(zr, sizeof(c128) * n));
+    CK(dalloc(rr, sizeof(c128) * n));
+    CK(ensure(c->d_one, sizeof(c128)));
+    c128 one = mk<double>(1, 0);
+    CK(cudaMemcpyAsync(c->d_one.p, &one, sizeof(c128), cudaMemcpyHostToDevice, st));
+    int total_it = 0;
+    bool all_ok = true;
+    for (int r = 0; r < nrhs; ++r) {
+        const c128* br = (const c128*)b + r * n;
+        c128* xr = (c128*)x + r * n;
+        double bn;
+        if ((s = norm_dev(c, BEM_C128, br, n, &bn, st)) != BEM_OK) return s;
+        if (bn == 0) {
+            CK(cudaMemsetAsync(xr, 0, sizeof(c128) * n, st));
+            if (relres) relres[r] = 0;
+            continue;
+        }
+        const bool refine = c->opt.refine_tol > 0;
+        const int steps = refine ? c->opt.refine_maxit : 1;
+        double rel = 0;
+        bool inner_ok = true;
+        for (int step = 0;; ++step) {
+            // r = b - Z x with the most accurate operator
+            if (out128) {
+                CK(matvec_any(c, BEM_C128, xr, zr.p, 1, st));
+            } else {
+                CK(kv_cast<float>(xr, BEM_C128, (c64*)c->gw.z.p, n, st));
+                CK(matvec_any(c, BEM_C64, c->gw.z.p, c->gw.w.p, 1, st));
+                CK(kv_cast<double>(c->gw.w.p, BEM_C64, (c128*)zr.p, n, st));
+            }
+            CK(kv_sub(br, zr.p, rr.p, BEM_C128, n, st));
+            double rn;
+            if ((s = norm_dev(c, BEM_C128, rr.p, n, &rn, st)) != BEM_OK) return s;
+            rel = rn / bn;
+            if (refine ? rel <= c->opt.refine_tol : step >= 1) break;
+            if (step >= steps) break;
+            // inner solve Z d = r
+            if (din == BEM_C64)
+                CK(kv_cast<float>(rr.p, BEM_C128, (c64*)c->gw.rin.p, n, st));
+            else
+                CK(cudaMemcpyAsync(c->gw.rin.p, rr.p, sizeof(c128) * n, cudaMemcpyDeviceToDevice, st));
+            double fres;
+            int before = total_it;
+            if ((s = gmres(c, din, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st)) != BEM_OK)
+                return s;
+            inner_ok = fres <= c->opt.tol * rn * 1.0000001;
+            CK(kv_axpy_c128(xr, c->gw.xin.p, din, (const c128*)c->d_one.p, 1.0, n, 1, n, st));
+            if (total_it >= c->opt.maxit || total_it == before) {
+                // out of iterations (or no progress possible): measure and stop
+                if (out128) {
+                    CK(matvec_any(c, BEM_C128, xr, zr.p, 1, st));
+                } else {
+                    CK(kv_cast<float>(xr, BEM_C128, (c64*)c->gw.z.p, n, st));
+                    CK(matvec_any(c, BEM_C64, c->gw.z.p, c->gw.w.p, 1, st));
+                    CK(kv_cast<double>(c->gw.w.p, BEM_C64, (c128*)zr.p, n, st));
+                }
+                CK(kv_sub(br, zr.p, rr.p, BEM_C128, n, st));
+                if ((s = norm_dev(c, BEM_C128, rr.p, n, &rn, st)) != BEM_OK) return s;
+                rel = rn / bn;
+                break;
+            }
+        }
+        if (relres) relres[r] = rel;
+        bool ok = refine ? rel <= c->opt.refine_tol : inner_ok;
+        all_ok = all_ok && ok;
+    }
+    CK(cudaStreamSynchronize(st));
+    if (iters) *iters = total_it;
+    if (!all_ok) return fail(c, BEM_ENOCONV, "solver did not reach its tolerance");
+    return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// powers
+// ---------------------------------------------------------------------------
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(BEM_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1, p1 = z;
+            for (int j = 2; j <= n; ++j) {
+                double p2 = ((2.0 * j - 1) * z * p1 - (j - 1.0) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1 - z * z) * dp * dp);
+    }
+}
+
+extern "C" bem_status bem_power(bem_ctx* c, const void* x, const void* b, int nrhs, double* p_abs, double* p_ext,
+                                double* p_sca, void* stream) {
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "bem_power needs bem_assemble");
+    if (nrhs < 1 || !x || (p_ext && !b)) return fail(c, BEM_EINVAL, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    GeomDev g = geom_view(c);
+    const int nta = 64, nph = 128;
+    int npa = (int)((c->nt + 255) / 256);
+    size_t need = sizeof(double) * (size_t)nrhs * std::max(npa, std::max(NPART, nta * nph));
+    CK(ensure(c->d_part, need));
+    CK(ensure(c->d_red, sizeof(double) * nrhs));
+    std::vector<double> host(nrhs);
+    if (p_abs) {
+        CK(power_abs(g, (const c128*)x, nrhs, nullptr, (double*)c->d_part.p, npa, st));
+        CK(kv_reduce_real((const double*)c->d_part.p, npa, nrhs, (double*)c->d_red.p, st));
+        CK(cudaMemcpyAsync(p_abs, c->d_red.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    }
+    if (p_ext) {
+        CK(dot_real_parts((const c128*)x, (const c128*)b, c->ne, nrhs, (double*)c->d_part.p, NPART, st));
+        CK(kv_reduce_real((const double*)c->d_part.p, NPART, nrhs, (double*)c->d_red.p, st));
+        CK(cudaMemcpyAsync(host.data(), c->d_red.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        memcpy(p_ext, host.data(), sizeof(double) * nrhs);
+    }
+    if (p_sca) {
+        if (!c->d_gl.p) {
+            std::vector<double> gx, gw;
+            gauss_legendre(nta, gx, gw);
+            gx.insert(gx.end(), gw.begin(), gw.end());
+            CK(upload(c->d_gl, gx, st));
+        }
+        CK(power_sca(g, (const c128*)x, nrhs, (double*)c->d_part.p, nta, nph, (const double*)c->d_gl.p,
+                     (const double*)c->d_gl.p + nta, st));
+        CK(kv_reduce_real((const double*)c->d_part.p, nta * nph, nrhs, (double*)c->d_red.p, st));
+        CK(cudaMemcpyAsync(host.data(), c->d_red.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        memcpy(p_sca, host.data(), sizeof(double) * nrhs);
+    }
+    CK(cudaStreamSynchronize(st));
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_power_density(bem_ctx* c, const void* x, double* per_tri, void* stream) {
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "bem_power_density needs bem_assemble");
+    if (!x || !per_tri) return fail(c, BEM_EINVAL, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    GeomDev g = geom_view(c);
+    int npa = (int)((c->nt + 255) / 256);
+    CK(ensure(c->d_part, sizeof(double) * std::max(npa, NPART)));
+    CK(power_abs(g, (const c128*)x, 1, per_tri, (double*)c->d_part.p, npa, st));
+    return BEM_OK;
+}

@@ -1,0 +1,207 @@
+// Internal definitions shared by the libbem translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/bem.h"
+
+#define BEM_PI 3.14159265358979323846
+#define BEM_MAX_LEAF 64
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on interleaved (re, im) pairs
+// ---------------------------------------------------------------------------
+template <typename R>
+struct cx {
+    R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> mk(R a, R b) {
+    cx<R> z;
+    z.re = a;
+    z.im = b;
+    return z;
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return mk<R>(a.re + b.re, a.im + b.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return mk<R>(a.re - b.re, a.im - b.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+    return mk<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return mk<R>(s * a.re, s * a.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cconj(cx<R> a) { return mk<R>(a.re, -a.im); }
+template <typename R>
+__host__ __device__ __forceinline__ R cabs2(cx<R> a) { return a.re * a.re + a.im * a.im; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cdiv(cx<R> a, cx<R> b) {
+    R d = b.re * b.re + b.im * b.im;
+    return mk<R>((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
+}
+// a += b * c
+template <typename R>
+__host__ __device__ __forceinline__ void cfma(cx<R>& a, cx<R> b, cx<R> c) {
+    a.re += b.re * c.re - b.im * c.im;
+    a.im += b.re * c.im + b.im * c.re;
+}
+// a += conj(b) * c
+template <typename R>
+__host__ __device__ __forceinline__ void cfma_conj(cx<R>& a, cx<R> b, cx<R> c) {
+    a.re += b.re * c.re + b.im * c.im;
+    a.im += b.re * c.im - b.im * c.re;
+}
+
+typedef cx<float> c64;
+typedef cx<double> c128;
+
+// ---------------------------------------------------------------------------
+// device view of the mesh, media and singular-pair table
+// ---------------------------------------------------------------------------
+struct GeomDev {
+    int nt, ne;
+    const double* tv;        // nt x 9: vertices v0, v1, v2 of each triangle
+    const double* area;      // nt
+    const double* nrm;       // nt x 3 unit outward normal
+    const double* cen;       // nt x 3 centroid ((v0 + v1) + v2) / 3
+    const double* diam;      // nt longest edge
+    const int* tvid;         // nt x 3 vertex indices
+    const int* tri_edge;     // nt x 3 edge opposite local vertex i
+    const double* tri_coef;  // nt x 3 s_i * l_i (sign +1 on T+, -1 on T-, times edge length)
+    const int* edge_tri;     // ne x 2 (T+, T-)
+    const int* edge_loc;     // ne x 2 local index of the free vertex in T+, T-
+    // singular pairs: CSR by test triangle, partners sorted ascending
+    const int* sing_ptr;     // nt + 1
+    const int* sing_b;       // partner triangle
+    const c128* sing_val;    // per pair 36 complex: T^0[3][3], K0[3][3], T^1[3][3], K1[3][3]
+    // media
+    double k0;
+    c128 k1;
+    c128 eta_r;
+};
+
+// Block descriptors (tree positions)
+struct BlockDesc {
+    int r0, m, c0, n;
+};
+
+// Far block record used by the product kernels
+struct FarRec {
+    int r0, m, c0, n;
+    int rk[3];          // ranks of A, B, C (padded to even in storage)
+    int64_t off_u[3];   // offset (in complex elements) of U of A, B, C
+    int64_t off_v[3];   // offset of V-bar (the conjugate of V) of A, B, C
+    int64_t off_t;      // offset of this block's t values: [tA | tB(J) | tB(M) | tC], each padded rank
+};
+
+// Kernel-side launch helpers implemented in the .cu files
+namespace bem {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+cudaError_t dalloc(DevBuf& b, size_t bytes);
+void dfree(DevBuf& b);
+
+// tree.cu
+cudaError_t tree_bbox_level(const double* pts, const int64_t* perm, const int* lo, const int* hi, int ncl,
+                            double* bbmin, double* bbmax, cudaStream_t st);
+cudaError_t tree_split_level(const double* pts, const int64_t* perm_in, int64_t* perm_out, const int* lo,
+                             const int* hi, const double* bbmin, const double* bbmax, const int* split_cl,
+                             int nsplit, const int* pos_cl, int npos_total, cudaStream_t st);
+cudaError_t tree_block_level(const int* cand, int ncand, const int* nlo, const int* nhi, const int* child0,
+                             const double* bbmin, const double* bbmax, double eta, int* kind, int* counts,
+                             cudaStream_t st);
+cudaError_t tree_block_emit(const int* cand, int ncand, const int* kind, const int* child0, const int* offs,
+                            int* next_cand, int* near_out, int* far_out, const int* nlo, const int* nhi,
+                            cudaStream_t st);
+cudaError_t scan_exclusive(const int* in, int* out, int n, int* total_dev, cudaStream_t st);
+
+// singular.cu
+cudaError_t singular_count(GeomDev g, int* counts, cudaStream_t st);
+cudaError_t singular_fill(GeomDev g, const int* ptr, int* partners, cudaStream_t st);
+cudaError_t singular_values(GeomDev g, int npairs, const int* pair_a, c128* vals, cudaStream_t st);
+
+// assemble.cu
+template <typename R>
+cudaError_t near_assemble(GeomDev g, const int64_t* perm, const BlockDesc* blocks, const int64_t* entry_off,
+                          int nblocks, cx<R>* entries, int64_t op_stride, cudaStream_t st);
+template <typename R>
+cudaError_t eval_entries(GeomDev g, const int* rows, const int* cols, int64_t count, cx<R>* out,
+                         cudaStream_t st);
+struct AcaTask {
+    int r0, m, c0, n;
+    int op;             // 0 = A, 1 = B, 2 = C
+    int rmax;
+    int64_t scratch;    // offset of this task's scratch (complex elements)
+};
+template <typename R>
+cudaError_t aca_run(GeomDev g, const int64_t* perm, const AcaTask* tasks, int ntasks, cx<R>* scratch, double tol,
+                    int* ranks, int* flags, cudaStream_t st, int max_m);
+template <typename R>
+cudaError_t aca_compact(const AcaTask* tasks, int ntasks, const cx<R>* scratch, const int* ranks,
+                        const int64_t* off_u, const int64_t* off_v, cx<R>* arena, cudaStream_t st);
+
+// matvec.cu
+struct MatvecPlan {
+    int ne, nleaf, nfar;
+    const int64_t* perm;         // tree position -> edge
+    const int* leaf_r0;          // nleaf
+    const int* leaf_m;           // nleaf
+    const int* near_ptr;         // nleaf + 1: near items of each leaf
+    const int* near_c0;          // per near item: column start
+    const int* near_n;           // per near item: columns
+    const int64_t* near_off;     // per near item: offset (complex elements) of its A entries
+    int64_t near_op_stride;      // distance between the A, B, C arrays
+    const int* farp_ptr;         // nleaf + 1: far pieces of each leaf
+    const int* farp_blk;         // far block index
+    const int* farp_row;         // row offset of the leaf inside the far block
+    const FarRec* far;           // nfar
+    const int* far_order;        // nfar: processing order for the V^H x kernel (largest first)
+};
+template <typename R>
+cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x,
+                       cx<R>* y, cx<R>* xp, cx<R>* t, int nrhs, int64_t t_len, cudaStream_t st);
+
+// rhs_power.cu
+template <typename R>
+cudaError_t rhs_planewave(GeomDev g, const double* khat, const c128* e0, int nrhs, cx<R>* b, cudaStream_t st);
+cudaError_t power_abs(GeomDev g, const c128* x, int nrhs, double* per_tri, double* partial, int npart,
+                      cudaStream_t st);
+cudaError_t power_sca(GeomDev g, const c128* x, int nrhs, double* partial, int ntheta, int nphi,
+                      const double* ct, const double* wt, cudaStream_t st);
+cudaError_t dot_real_parts(const c128* a, const c128* b, int64_t n, int nrhs, double* partial, int npart,
+                           cudaStream_t st);
+
+// krylov.cu
+template <typename R>
+cudaError_t kv_cast(const void* src, int src_dtype, cx<R>* dst, int64_t n, cudaStream_t st);
+cudaError_t kv_multidot(const void* V, int dtype, int64_t ld, int k, const void* w, int64_t n, c128* out_partial,
+                        int npart, cudaStream_t st);
+cudaError_t kv_reduce_partials(const c128* partial, int npart, int count, c128* out, cudaStream_t st);
+cudaError_t kv_reduce_real(const double* partial, int npart, int count, double* out, cudaStream_t st);
+cudaError_t kv_update(void* w, const void* V, int dtype, int64_t ld, int k, const c128* h, double sign, int64_t n,
+                      cudaStream_t st);
+cudaError_t kv_norm2(const void* w, int dtype, int64_t n, double* out_partial, int npart, cudaStream_t st);
+cudaError_t kv_scale_copy(const void* w, int dtype, double s, int64_t n, void* v, cudaStream_t st);
+cudaError_t kv_axpy_c128(c128* y, const void* x, int dtype, const c128* coef, double sign, int64_t n, int k,
+                         int64_t ld, cudaStream_t st);
+cudaError_t kv_sub(const void* b, const void* zx, void* r, int dtype, int64_t n, cudaStream_t st);
+
+}  // namespace bem
+
+#define BEM_CUDA_TRY(expr)                      \
+    do {                                        \
+        cudaError_t _e = (expr);                \
+        if (_e != cudaSuccess) return _e;       \
+    } while (0)

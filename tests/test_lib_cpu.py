@@ -1,0 +1,101 @@
+"""CPU checks of the C library: it loads, exports every declared entry point, and
+its host-side logic (argument checks, mesh -> RWG table, Debye helper) agrees
+with the oracle.  No compute call reaches the GPU here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import debye, rwg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2310_15644_gb300.build import build
+
+    build()
+    import paper_2310_15644_gb300.bem as mod
+
+    return mod
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bem.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bem_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(B):
+    declared = _declared()
+    assert declared, "no declarations parsed"
+    assert sorted(B.EXPORTS) == declared
+    lib = ctypes.CDLL(B.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (bem_[a-z0-9_]+)$", out, flags=re.M))
+    assert set(declared) <= exported
+
+
+def test_rwg_table_matches_oracle(B):
+    for v, t in (W.icosphere(2), W.box_mesh(1.0, 0.7, 0.3, 5, 4, 2)):
+        h = B.bem_create()
+        try:
+            B.bem_set_mesh(h, v, t)
+            e = B.bem_edges(h)
+            g = rwg.build(v, t)
+            assert np.array_equal(e[:, :2], g.edges)
+            assert np.array_equal(e[:, 2], g.tplus)
+            assert np.array_equal(e[:, 3], g.tminus)
+            assert B.bem_num_unknowns(h) == 2 * g.ne
+        finally:
+            B.bem_destroy(h)
+
+
+def test_invalid_inputs_rejected_before_any_launch(B):
+    v, t = W.icosphere(1)
+    h = B.bem_create()
+    try:
+        with pytest.raises(B.BemError) as ei:
+            B.bem_set_mesh(h, v, t[1:])
+        assert ei.value.status == B.BEM_EINVAL
+        bad = t.copy()
+        bad[0] = bad[0][[0, 2, 1]]
+        with pytest.raises(B.BemError):
+            B.bem_set_mesh(h, v, bad)
+        vz = v.copy()
+        vz[t[0, 2]] = 0.5 * (vz[t[0, 0]] + vz[t[0, 1]])
+        with pytest.raises(B.BemError):
+            B.bem_set_mesh(h, vz, t)
+        B.bem_set_mesh(h, v, t)
+        with pytest.raises(B.BemError) as ei:
+            B.bem_set_media(h, 2.0, 3.2 + 1.9j)       # gain medium under e^{+jwt}
+        assert ei.value.status == B.BEM_EINVAL
+        with pytest.raises(B.BemError):
+            B.bem_set_media(h, -1.0, 3.0)
+        # product before assembly
+        with pytest.raises(B.BemError) as ei:
+            B.bem_matvec(h, 0, 0, 1, B.BEM_C64)
+        assert ei.value.status == B.BEM_ESTATE
+        with pytest.raises(B.BemError) as ei:
+            B.bem_assemble(h)                            # media not set yet
+        assert ei.value.status == B.BEM_ESTATE
+    finally:
+        B.bem_destroy(h)
+    opt = B.bem_default_options()
+    opt.leaf_size = 65
+    with pytest.raises(B.BemError):
+        B.bem_create(opt)
+
+
+def test_debye_helper_matches_oracle(B):
+    for f in (0.0, 1e9, 1e11, 1e12, 3e12):
+        assert abs(B.bem_debye_eps(f) - debye.eps_r(f)) < 1e-12 * abs(debye.eps_r(f))
+    p = [4.0, 50.0, 5.0, 8e-12, 0.1e-12]
+    assert abs(B.bem_debye_eps(1e12, p) - debye.eps_r(1e12, *p)) < 1e-12 * 10
