@@ -1,0 +1,419 @@
+#!/usr/bin/env python3
+"""Benchmark of the compressed PMCHWT product on one GB300 (replicas for N > 1).
+
+Workload: lossy dielectric sphere, icosahedral mesh with 20480 triangles
+(30720 RWG edges, 61440 unknowns), k0 a = 10, eps_r = 3.2 - 1.9j, cluster leaf
+64, admissibility eta = 2, ACA tolerance 1e-4; complex64 operator.  A step is
+one product y = Z x with x already resident in HBM; the operator (about 3 GB)
+is far larger than L2, so every step streams it from HBM (no flush needed).
+
+Reported beside the headline value:
+  roofline      dominant kernel's algorithmic bytes / its mean CUDA-event time,
+                against the measured HBM copy bandwidth;
+  e2e           the same product through the C interface with host buffers
+                (pinned H2D of x and D2H of y inside the timed region);
+  fp64_baseline the same product with the complex128 operator (plain FP64 GPU
+                form), and both products' error against the float64 oracle on
+                sampled rows of the dense product;
+  cpu_baseline  the oracle's on-the-fly dense rows, timed on the host cores.
+`--impl reference` times the oracle alone (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "compressed BEM matvecs/s and HBM GB/s at 61k/200k unknowns; mixed vs FP64 at 1e-4 err"
+UNIT = "matvecs/s"
+K0, EPS, LEAF, ETA, ACA_TOL = 10.0, 3.2 - 1.9j, 64, 2.0, 1e-4
+LEVEL = 5          # icosphere refinement: 20 * 4**LEVEL triangles (5 -> 20480)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_name(level):
+    nt = 20 * 4 ** level
+    return f"sphere-ico{level}-{nt}tri-{3 * nt}unk-k0a10-eps3.2-1.9j-leaf64-eta2-aca1e-4"
+
+
+def config_dict(extra=None):
+    nt = 20 * 4 ** LEVEL
+    d = {"workload": workload_name(LEVEL), "unknowns": 3 * nt, "triangles": nt, "rwg_edges": 3 * nt // 2, "k0a": K0,
+         "eps_r": [EPS.real, EPS.imag], "leaf_size": LEAF, "eta": ETA, "aca_tol": ACA_TOL, "nrhs": 1,
+         "l2": "operator data ~3 GB per product >> 129 MB L2; no flush needed", "parallelism": "replicas"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (host cores)
+# ---------------------------------------------------------------------------
+def oracle_rows(g, x, rows, threads):
+    from oracle import operators as O
+
+    chunks = [rows[i::threads] for i in range(threads) if len(rows[i::threads])]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=len(chunks)) as ex:
+        parts = list(ex.map(lambda r: (r, O.pmchwt_rows_apply(g, K0, EPS, x, r)), chunks))
+    dt = time.perf_counter() - t0
+    out = {}
+    for r, v in parts:
+        for i, val in zip(r, v):
+            out[int(i)] = val
+    return np.array([out[int(i)] for i in rows]), dt
+
+
+def sample_rows(ne, count, seed=11):
+    return np.random.default_rng(seed).choice(2 * ne, count, replace=False)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_uuid):
+        self.samples = []
+        self.proc = None
+        self.uuid = gpu_uuid
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu=uuid,{self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[0]:
+                continue
+            self.samples.append((time.perf_counter(), parts[1:]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        if not self.samples:
+            return None
+        inside = [s for s in self.samples if t0 <= s[0] <= t1]
+        where = "inside timed region"
+        if not inside:
+            inside = sorted(self.samples, key=lambda s: min(abs(s[0] - t0), abs(s[0] - t1)))[:3]
+            where = "nearest samples (timed region shorter than the sampling period)"
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(s[1][0]) for s in inside if num(s[1][0]) is not None]
+        mx = [num(s[1][1]) for s in inside if num(s[1][1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in inside for i in range(4) if s[1][4 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(inside), "where": where}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_traffic(name):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    src = os.path.join(ROOT, "paper_2310_15644_gb300", "csrc", "matvec.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == name and parts[2] == digest:
+            return float(parts[1])
+    return None
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+def run_native(args, rank, world, dist):
+    import torch
+
+    import paper_2310_15644_gb300.bem as B
+    import workloads as W
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    v, t = W.icosphere(LEVEL)
+
+    def context(prec):
+        opt = B.bem_default_options()
+        opt.precision = prec
+        opt.leaf_size = LEAF
+        opt.eta = ETA
+        opt.aca_tol = ACA_TOL
+        h = B.bem_create(opt)
+        B.bem_set_mesh(h, v, t)
+        B.bem_set_media(h, K0, EPS)
+        t0 = time.perf_counter()
+        B.bem_assemble(h, sp)
+        torch.cuda.synchronize(dev)
+        return h, (time.perf_counter() - t0) * 1e3
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def time_steps(h, xd, yd, dtype, K, W_, profile):
+        for _ in range(W_):
+            B.bem_matvec(h, xd.data_ptr(), yd.data_ptr(), 1, dtype, sp)
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if profile:
+            B.bem_profile_begin(h)
+        w0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(K):
+            B.bem_matvec(h, xd.data_ptr(), yd.data_ptr(), 1, dtype, sp)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        w1 = time.perf_counter()
+        barrier()
+        torch.cuda.synchronize(dev)
+        prof = B.bem_profile_end(h) if profile else None
+        return e0.elapsed_time(e1), (w0, w1), prof
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid).replace("GPU-", "")[:8]
+    except Exception:
+        pass
+    h64, asm64_ms = context(B.BEM_PREC_C64)
+    stats = B.bem_stats_get(h64)
+    n = B.bem_num_unknowns(h64)
+    x = W.complex_normal(n, seed=0).astype(np.complex64)
+    xd = torch.from_numpy(x).to(dev)
+    yd = torch.empty_like(xd)
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    ms, (w0, w1), (kms, kcnt) = time_steps(h64, xd, yd, B.BEM_C64, args.steps, args.warmup, True)
+    clocks.stop()
+    clk = clocks.summary(w0, w1)
+    y64 = yd.cpu().numpy().astype(np.complex128)
+
+    # whole job: max over ranks
+    t_ms = ms
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / args.steps
+    value = world * args.steps / (t_ms / 1e3)
+
+    # roofline of the dominant kernel
+    peak, peak_kind = measured_peak()
+    kb = stats["kernel_bytes_c64"]
+    names = B.KERNEL_NAMES
+    mean_ms = [kms[i] / max(1, kcnt[i]) for i in range(3)]
+    dom = int(np.argmax(mean_ms))
+    achieved = kb[dom] / (mean_ms[dom] * 1e-3) / 1e9
+    traffic = kernel_traffic(names[dom])
+    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": f"{peak_kind} HBM copy bandwidth",
+                "algorithmic_bytes_per_launch": int(kb[dom]), "mean_launch_ms": round(mean_ms[dom], 5),
+                "kernels": {names[i]: {"mean_ms": round(mean_ms[i], 5), "launches": int(kcnt[i]),
+                                       "algorithmic_bytes": int(kb[i]),
+                                       "GBps": round(kb[i] / (mean_ms[i] * 1e-3) / 1e9, 1) if mean_ms[i] > 0 else None,
+                                       "share": round(kms[i] / max(1e-9, sum(kms)), 4)} for i in range(3)}}
+    step_gbs = stats["matvec_bytes_c64"] / (ms_per_step * 1e-3) / 1e9
+
+    # end to end through the C interface with host buffers
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xe = torch.empty_like(xd)
+    ye = torch.empty_like(xd)
+    for _ in range(args.warmup):
+        xe.copy_(xh, non_blocking=True)
+        B.bem_matvec(h64, xe.data_ptr(), ye.data_ptr(), 1, B.BEM_C64, sp)
+        yh.copy_(ye, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        xe.copy_(xh, non_blocking=True)
+        B.bem_matvec(h64, xe.data_ptr(), ye.data_ptr(), 1, B.BEM_C64, sp)
+        yh.copy_(ye, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e = {"value": round(world * args.steps / (e2e_ms / 1e3), 2), "unit": UNIT,
+           "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
+           "d2h_bytes_per_step": int(yh.numel() * yh.element_size())}
+    B.bem_destroy(h64)
+
+    out = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "complex64 (fp32)", "data": "synthetic",
+           "config": config_dict(), "hbm_gbps_algorithmic": round(step_gbs, 1),
+           "hbm_frac_of_peak": round(step_gbs / peak, 4), "roofline": roofline, "e2e": e2e,
+           "gpu_launches": int(sum(kcnt)), "clocks": clk,
+           "assembly": {"ms": round(asm64_ms, 1), "near_entries_per_op": stats["near_entries"],
+                        "factor_entries": stats["factor_entries"], "max_rank": stats["max_rank"],
+                        "far_blocks": stats["n_far"], "far_blocks_dense": stats["n_far_dense"],
+                        "near_blocks": stats["n_near"], "bytes_per_product": stats["matvec_bytes_c64"]}}
+
+    if rank == 0 and world == 1:
+        g = None
+        rows = None
+        if not args.no_fp64 or not args.no_cpu_baseline:
+            from oracle import rwg
+
+            g = rwg.build(v, t)
+            rows = sample_rows(g.ne, args.cpu_rows)
+        if not args.no_fp64:
+            h128, asm128_ms = context(B.BEM_PREC_C128)
+            s128 = B.bem_stats_get(h128)
+            xd2 = torch.from_numpy(x.astype(np.complex128)).to(dev)
+            yd2 = torch.empty_like(xd2)
+            k128 = max(3, args.steps // 8)
+            ms2, _, _ = time_steps(h128, xd2, yd2, B.BEM_C128, k128, max(3, args.warmup // 4), False)
+            y128 = yd2.cpu().numpy()
+            out["fp64_baseline"] = {"value": round(k128 / (ms2 / 1e3), 2), "unit": UNIT,
+                                    "ms_per_step": round(ms2 / k128, 4), "steps": k128, "dtype": "complex128 (fp64)",
+                                    "assembly_ms": round(asm128_ms, 1),
+                                    "hbm_gbps_algorithmic": round(s128["matvec_bytes_c128"] / (ms2 / k128 * 1e-3) / 1e9, 1),
+                                    "complex64_speedup": round((ms2 / k128) / ms_per_step, 2)}
+            B.bem_destroy(h128)
+        if not args.no_cpu_baseline:
+            threads = min(os.cpu_count() or 1, len(rows))
+            ref, dt = oracle_rows(g, x.astype(np.complex128), rows, threads)
+            scale = float(np.sqrt(np.mean(np.abs(y64) ** 2)))
+            out["rel_err_vs_oracle"] = float(np.abs(y64[rows] - ref).max() / scale)
+            if "fp64_baseline" in out:
+                out["fp64_baseline"]["rel_err_vs_oracle"] = float(np.abs(y128[rows] - ref).max() / scale)
+            out["cpu_baseline"] = {"value": round(len(rows) / dt / (2 * g.ne), 6), "unit": UNIT, "cores": threads,
+                                   "kind": "oracle",
+                                   "sample": f"{len(rows)} of {2 * g.ne} rows of the dense float64 PMCHWT product, "
+                                             f"evaluated on the fly (numpy, {threads} threads), {dt:.1f} s",
+                                   "error_metric": "max |y_gpu - y_oracle| over sampled rows / rms(y_gpu)"}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle alone on host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    import workloads as W
+    from oracle import rwg
+
+    v, t = W.icosphere(LEVEL)
+    g = rwg.build(v, t)
+    x = W.complex_normal(2 * g.ne, seed=0).astype(np.complex64).astype(np.complex128)
+    threads = min(os.cpu_count() or 1, args.ref_rows)
+    rng = np.random.default_rng(5)
+    for _ in range(args.warmup):
+        oracle_rows(g, x, rng.choice(2 * g.ne, args.ref_rows, replace=False), threads)
+    tot = 0.0
+    for _ in range(args.steps):
+        _, dt = oracle_rows(g, x, rng.choice(2 * g.ne, args.ref_rows, replace=False), threads)
+        tot += dt
+    value = args.steps * args.ref_rows / tot / (2 * g.ne)
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "complex128 (fp64)",
+            "data": "synthetic",
+            "config": config_dict({"reference": "float64 CPU oracle (dense PMCHWT rows on the fly)"}),
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"each step: {args.ref_rows} random rows of the {2 * g.ne}-row dense product"},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--cpu-rows", type=int, default=32, help="oracle rows timed for cpu_baseline")
+    ap.add_argument("--ref-rows", type=int, default=8, help="oracle rows per step of the reference arm")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the complex128 GPU comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--level", type=int, default=5,
+                    help="icosphere level (5 = the 61440-unknown workload; smaller levels for profiling captures)")
+    args = ap.parse_args()
+    global LEVEL
+    LEVEL = args.level
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args)), flush=True)
+        return 0
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    out = run_native(args, rank, world, dist)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

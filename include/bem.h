@@ -85,7 +85,8 @@ typedef struct {
     int leaf_size;       /* maximum edges per leaf cluster, 2..64 (default 64) */
     double eta;          /* admissibility: min(diam) <= eta * dist; eta <= 0 stores every block densely (default 2) */
     double aca_tol;      /* relative Frobenius tolerance of each compressed block (default 1e-4) */
-    int aca_max_rank;    /* rank cap per compressed block (default 96); blocks that need more make bem_assemble fail */
+    int aca_max_rank;    /* rank cap per compressed block, 1..128 (default 96); a block that needs more, or more
+                            than the break-even m n / (m + n), is stored densely instead */
     int gmres_restart;   /* GMRES restart length (default 50) */
     int maxit;           /* maximum inner GMRES iterations in total (default 1000) */
     double tol;          /* inner GMRES relative residual tolerance (default 1e-6) */
@@ -100,15 +101,26 @@ typedef struct {
     int64_t n_clusters;         /* nodes of the cluster tree */
     int64_t n_leaves;           /* leaf clusters */
     int64_t n_near;             /* dense (near) blocks */
-    int64_t n_far;              /* compressed (far) blocks */
-    int64_t near_entries;       /* sum of m*n over near blocks (per operator A, B or C) */
+    int64_t n_far;              /* admissible (far) blocks of the partition */
+    int64_t n_far_dense;        /* far blocks stored densely: their ACA rank would pass m n / (m + n) */
+    int64_t near_entries;       /* sum of m*n over densely stored blocks (per operator A, B or C) */
     int64_t factor_entries[3];  /* sum of r*(m+n) over far blocks, for A, B, C */
     int64_t max_rank;           /* largest ACA rank */
     int64_t singular_pairs;     /* triangle pairs integrated with singularity extraction */
-    int64_t matvec_bytes_c64;   /* algorithmic HBM bytes of one complex64 product (entries + vectors) */
+    int64_t matvec_bytes_c64;   /* algorithmic HBM bytes of one complex64 product: every stored entry once,
+                                   x read once, y written once */
     int64_t matvec_bytes_c128;  /* same for complex128 */
+    int64_t kernel_bytes_c64[3];  /* algorithmic bytes of the product's kernels (gather, vhx, rows), complex64:
+                                     gather: x read + permuted copy written; vhx: V factors + x;
+                                     rows: dense entries + U factors + x + y */
+    int64_t kernel_bytes_c128[3]; /* same for complex128 */
     double assemble_ms;         /* wall time of the last bem_assemble */
 } bem_stats;
+
+/* Kernels of one product, in launch order (index into the profiling arrays). */
+#define BEM_KERNEL_GATHER 0  /* x -> tree order */
+#define BEM_KERNEL_VHX 1     /* t = V^H x for every far block */
+#define BEM_KERNEL_ROWS 2    /* per leaf: dense items + U t, writes y */
 
 /* Fill *opt with the defaults listed above. */
 void bem_default_options(bem_options* opt);
@@ -147,7 +159,7 @@ bem_status bem_debye_eps(double freq_hz, const double* params, bem_c128* eps_out
  * dense near blocks, ACA factors of far blocks, for every precision requested in
  * the options.  Blocks until done (it reads block counts and ranks back to size
  * its buffers) and runs its kernels on `stream`.  Requires bem_set_mesh and
- * bem_set_media.  BEM_EINVAL if a far block needs more than aca_max_rank. */
+ * bem_set_media. */
 bem_status bem_assemble(bem_ctx* ctx, void* stream);
 
 /* Number of RWG edges ne and of unknowns 2*ne; -1 before bem_set_mesh. */
@@ -180,6 +192,15 @@ bem_status bem_eval_entries(bem_ctx* ctx, const int32_t* rows, const int32_t* co
  * overlap.  Asynchronous on `stream`; no allocation after the first call with a
  * given nrhs.  The product reads each dense entry and each factor once per call. */
 bem_status bem_matvec(bem_ctx* ctx, const void* x, void* y, int nrhs, int dtype, void* stream);
+
+/* Kernel timing of bem_matvec.  After bem_profile_begin, every bem_matvec on ctx
+ * records a CUDA event pair around each of its kernels on the caller's stream
+ * (a few microseconds of overhead per product); bem_profile_end synchronises those
+ * events and returns, per kernel (BEM_KERNEL_*), the summed device time in
+ * milliseconds (ms_sum, host, 3 doubles) and the number of launches (launches,
+ * host, 3 int64), then stops recording.  Either output may be NULL. */
+bem_status bem_profile_begin(bem_ctx* ctx);
+bem_status bem_profile_end(bem_ctx* ctx, double* ms_sum, int64_t* launches);
 
 /* Normalised plane-wave right-hand sides (tested fields after Eq. 8):
  * E_inc = e0 exp(-j k0 khat.r), H_inc = khat x E_inc / eta0, b = [e ; eta0 h].

@@ -26,8 +26,9 @@ EXPORTS = [
     "bem_default_options", "bem_create", "bem_destroy", "bem_last_error", "bem_set_mesh", "bem_set_media",
     "bem_debye_eps", "bem_assemble", "bem_num_edges", "bem_num_unknowns", "bem_edges", "bem_stats_get",
     "bem_partition", "bem_eval_entries", "bem_matvec", "bem_rhs_planewave", "bem_solve", "bem_power",
-    "bem_power_density",
+    "bem_power_density", "bem_profile_begin", "bem_profile_end",
 ]
+KERNEL_NAMES = ["k_gather", "k_vhx", "k_rows"]   # BEM_KERNEL_GATHER, _VHX, _ROWS
 
 
 class bem_options(ctypes.Structure):
@@ -43,9 +44,10 @@ class bem_stats(ctypes.Structure):
     _fields_ = [
         ("ne", ctypes.c_int64), ("nt", ctypes.c_int64), ("n_clusters", ctypes.c_int64),
         ("n_leaves", ctypes.c_int64), ("n_near", ctypes.c_int64), ("n_far", ctypes.c_int64),
-        ("near_entries", ctypes.c_int64), ("factor_entries", ctypes.c_int64 * 3), ("max_rank", ctypes.c_int64),
+        ("n_far_dense", ctypes.c_int64), ("near_entries", ctypes.c_int64), ("factor_entries", ctypes.c_int64 * 3), ("max_rank", ctypes.c_int64),
         ("singular_pairs", ctypes.c_int64), ("matvec_bytes_c64", ctypes.c_int64),
-        ("matvec_bytes_c128", ctypes.c_int64), ("assemble_ms", ctypes.c_double),
+        ("matvec_bytes_c128", ctypes.c_int64), ("kernel_bytes_c64", ctypes.c_int64 * 3),
+        ("kernel_bytes_c128", ctypes.c_int64 * 3), ("assemble_ms", ctypes.c_double),
     ]
 
 
@@ -85,6 +87,8 @@ def _load():
         "bem_solve": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int), dp]),
         "bem_power": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, dp, dp, dp, vp]),
         "bem_power_density": (ctypes.c_int, [ctx, vp, vp, vp]),
+        "bem_profile_begin": (ctypes.c_int, [ctx]),
+        "bem_profile_end": (ctypes.c_int, [ctx, dp, i64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -170,7 +174,8 @@ def bem_stats_get(ctx) -> dict:
     s = bem_stats()
     _check(ctx, lib.bem_stats_get(ctx, ctypes.byref(s)))
     d = {name: getattr(s, name) for name, _ in bem_stats._fields_}
-    d["factor_entries"] = list(s.factor_entries)
+    for k in ("factor_entries", "kernel_bytes_c64", "kernel_bytes_c128"):
+        d[k] = list(getattr(s, k))
     return d
 
 
@@ -225,3 +230,15 @@ def bem_power(ctx, x_ptr: int, b_ptr: int, nrhs: int, stream: int = 0):
 def bem_power_density(ctx, x_ptr: int, per_tri_ptr: int, stream: int = 0) -> None:
     _check(ctx, lib.bem_power_density(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(per_tri_ptr),
                                       ctypes.c_void_p(stream)))
+
+
+def bem_profile_begin(ctx) -> None:
+    _check(ctx, lib.bem_profile_begin(ctx))
+
+
+def bem_profile_end(ctx):
+    """Returns (ms_sum[3], launches[3]) per kernel of the product."""
+    ms = np.zeros(3)
+    cnt = np.zeros(3, dtype=np.int64)
+    _check(ctx, lib.bem_profile_end(ctx, _np_ptr(ms, ctypes.c_double), _np_ptr(cnt, ctypes.c_int64)))
+    return ms, cnt

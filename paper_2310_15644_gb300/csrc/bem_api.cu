@@ -37,6 +37,12 @@ namespace {
 
 struct Operator {
     bool built = false;
+    // product plan of this precision: dense items (leaf row x column range) and far pieces
+    std::vector<BlockDesc> items;      // dense items sorted by (r0, c0); rows are one leaf
+    std::vector<int> far_keep;         // partition far blocks stored as factors
+    int64_t n_far_dense = 0;           // partition far blocks stored densely (rank above break-even)
+    int64_t near_stride = 0;
+    DevBuf d_near_ptr, d_near_c0, d_near_n, d_near_off, d_farp_ptr, d_farp_blk, d_farp_row;
     DevBuf near;          // 3 * near_stride complex
     DevBuf arena;         // low-rank factors
     DevBuf far_rec;       // FarRec[nfar]
@@ -80,14 +86,17 @@ struct bem_ctx {
     std::vector<BlockDesc> near_blocks, far_blocks;  // sorted by (r0, c0)
     DevBuf d_perm;
     // product plan (precision independent part)
-    DevBuf d_leaf_r0, d_leaf_m, d_near_ptr, d_near_c0, d_near_n, d_near_off, d_farp_ptr, d_farp_blk, d_farp_row;
-    int64_t near_stride = 0;
+    DevBuf d_leaf_r0, d_leaf_m;
     Operator op[2];
     bool assembled = false;
     double assemble_ms = 0;
     // reductions and small transfers
     DevBuf d_part, d_red, d_tmp_in, d_one, d_gl;
     GmresWork gw;
+    // kernel timing of bem_matvec
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;   // created once, reused
+    size_t ev_used = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -157,6 +166,13 @@ static c128 csqrt_principal(c128 z) {
 }
 
 static void release_operator(Operator& o) {
+    DevBuf* plan[] = {&o.d_near_ptr, &o.d_near_c0, &o.d_near_n, &o.d_near_off, &o.d_farp_ptr, &o.d_farp_blk,
+                      &o.d_farp_row};
+    for (DevBuf* b : plan) dfree(*b);
+    o.items.clear();
+    o.far_keep.clear();
+    o.n_far_dense = 0;
+    o.near_stride = 0;
     dfree(o.near);
     dfree(o.arena);
     dfree(o.far_rec);
@@ -212,10 +228,10 @@ extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
 extern "C" void bem_destroy(bem_ctx* c) {
     if (!c) return;
     invalidate(c);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     DevBuf* bufs[] = {&c->d_tv, &c->d_area, &c->d_nrm, &c->d_cen, &c->d_diam, &c->d_tvid, &c->d_tri_edge,
                       &c->d_tri_coef, &c->d_edge_tri, &c->d_edge_loc, &c->d_mid, &c->d_sing_ptr, &c->d_sing_b,
-                      &c->d_sing_val, &c->d_perm, &c->d_leaf_r0, &c->d_leaf_m, &c->d_near_ptr, &c->d_near_c0,
-                      &c->d_near_n, &c->d_near_off, &c->d_farp_ptr, &c->d_farp_blk, &c->d_farp_row, &c->d_part,
+                      &c->d_sing_val, &c->d_perm, &c->d_leaf_r0, &c->d_leaf_m, &c->d_part,
                       &c->d_red, &c->d_tmp_in, &c->d_one, &c->d_gl, &c->gw.V, &c->gw.w, &c->gw.z, &c->gw.r,
                       &c->gw.xin, &c->gw.rin, &c->gw.hpart, &c->gw.hdev, &c->gw.npart};
     for (DevBuf* b : bufs) dfree(*b);
@@ -588,17 +604,23 @@ static bem_status build_singular(bem_ctx* c, cudaStream_t st) {
     return BEM_OK;
 }
 
-static bem_status build_plan(bem_ctx* c, cudaStream_t st) {
+static bem_status build_leaves(bem_ctx* c, cudaStream_t st) {
+    CK(upload(c->d_leaf_r0, c->leaf_lo, st));
+    CK(upload(c->d_leaf_m, c->leaf_m, st));
+    return BEM_OK;
+}
+
+// Dense items and far pieces of one operator, grouped by row leaf.
+static bem_status build_operator_plan(bem_ctx* c, Operator& o, cudaStream_t st) {
     const int nleaf = (int)c->leaf_lo.size();
     std::vector<int> leaf_of(c->ne + 1, -1);
     for (int l = 0; l < nleaf; ++l) leaf_of[c->leaf_lo[l]] = l;
-    // near items: one per near block, grouped by row leaf (list is sorted by r0, c0)
     std::vector<int> nptr(nleaf + 1, 0), nc0, nn;
     std::vector<int64_t> noff;
     int64_t off = 0;
-    for (const BlockDesc& b : c->near_blocks) {
+    for (const BlockDesc& b : o.items) {
         int l = leaf_of[b.r0];
-        if (l < 0 || c->leaf_m[l] != b.m) return fail(c, BEM_ECUDA, "near block rows are not a leaf");
+        if (l < 0 || c->leaf_m[l] != b.m) return fail(c, BEM_ECUDA, "dense item rows are not a leaf");
         nptr[l + 1]++;
         nc0.push_back(b.c0);
         nn.push_back(b.n);
@@ -606,14 +628,13 @@ static bem_status build_plan(bem_ctx* c, cudaStream_t st) {
         off += (int64_t)b.m * 2 * ((b.n + 1) / 2);
     }
     for (int l = 0; l < nleaf; ++l) nptr[l + 1] += nptr[l];
-    c->near_stride = off;
-    // far pieces: every leaf inside a far block's row range
+    o.near_stride = off;
     std::vector<std::vector<std::pair<int, int>>> pieces(nleaf);
-    for (size_t b = 0; b < c->far_blocks.size(); ++b) {
-        const BlockDesc& F = c->far_blocks[b];
+    for (size_t k = 0; k < o.far_keep.size(); ++k) {
+        const BlockDesc& F = c->far_blocks[o.far_keep[k]];
         int l = leaf_of[F.r0];
         if (l < 0) return fail(c, BEM_ECUDA, "far block does not start at a leaf");
-        for (; l < nleaf && c->leaf_lo[l] < F.r0 + F.m; ++l) pieces[l].push_back({(int)b, c->leaf_lo[l] - F.r0});
+        for (; l < nleaf && c->leaf_lo[l] < F.r0 + F.m; ++l) pieces[l].push_back({(int)k, c->leaf_lo[l] - F.r0});
     }
     std::vector<int> fptr(nleaf + 1, 0), fblk, frow;
     for (int l = 0; l < nleaf; ++l) {
@@ -623,15 +644,13 @@ static bem_status build_plan(bem_ctx* c, cudaStream_t st) {
             frow.push_back(p.second);
         }
     }
-    CK(upload(c->d_leaf_r0, c->leaf_lo, st));
-    CK(upload(c->d_leaf_m, c->leaf_m, st));
-    CK(upload(c->d_near_ptr, nptr, st));
-    CK(upload(c->d_near_c0, nc0, st));
-    CK(upload(c->d_near_n, nn, st));
-    CK(upload(c->d_near_off, noff, st));
-    CK(upload(c->d_farp_ptr, fptr, st));
-    CK(upload(c->d_farp_blk, fblk, st));
-    CK(upload(c->d_farp_row, frow, st));
+    CK(upload(o.d_near_ptr, nptr, st));
+    CK(upload(o.d_near_c0, nc0, st));
+    CK(upload(o.d_near_n, nn, st));
+    CK(upload(o.d_near_off, noff, st));
+    CK(upload(o.d_farp_ptr, fptr, st));
+    CK(upload(o.d_farp_blk, fblk, st));
+    CK(upload(o.d_farp_row, frow, st));
     return BEM_OK;
 }
 
@@ -640,38 +659,27 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
     const size_t es = sizeof(cx<R>);
     GeomDev g = geom_view(c);
     const int64_t* perm = (const int64_t*)c->d_perm.p;
-    // dense blocks
-    {
-        std::vector<int64_t> offs;
-        int64_t off = 0;
-        for (const BlockDesc& b : c->near_blocks) {
-            offs.push_back(off);
-            off += (int64_t)b.m * 2 * ((b.n + 1) / 2);
-        }
-        DevBuf d_blocks, d_offs;
-        CK(upload(d_blocks, c->near_blocks, st));
-        CK(upload(d_offs, offs, st));
-        CK(dalloc(o.near, es * 3 * std::max<int64_t>(1, off)));
-        cudaError_t e = near_assemble<R>(g, perm, (const BlockDesc*)d_blocks.p, (const int64_t*)d_offs.p,
-                                         (int)c->near_blocks.size(), (cx<R>*)o.near.p, off, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        dfree(d_blocks);
-        dfree(d_offs);
-        if (e != cudaSuccess) return cuda_fail(c, e, "near assembly");
-    }
-    // far blocks: ACA in batches bounded by a scratch budget
+    // 1. ACA of every far block, in batches bounded by a scratch budget.  A block's rank
+    //    is capped at the break-even m n / (m + n) (and the user cap); a block that does
+    //    not reach the tolerance within it is stored densely instead.
     const int nfar = (int)c->far_blocks.size();
-    std::vector<int> ranks(3 * nfar, 0);
+    std::vector<int> ranks(3 * nfar, 0), flags(3 * nfar, 0);
     struct Batch {
         DevBuf arena;
         int64_t len;
     };
     std::vector<Batch> batches;
-    std::vector<int64_t> task_off_u(3 * nfar), task_off_v(3 * nfar);  // offsets inside their batch arena
+    struct BatchGuard {
+        std::vector<Batch>* v;
+        ~BatchGuard() {
+            for (auto& b : *v) dfree(b.arena);
+        }
+    } bguard{&batches};
+    std::vector<int64_t> task_off_u(3 * nfar), task_off_v(3 * nfar);
     std::vector<int> task_batch(3 * nfar);
     const int64_t budget = (int64_t)(sizeof(R) == 4 ? 1 : 2) * (1ll << 30) / (int64_t)es;  // complex elements
-    int tb = 0;
     const int rcap = c->opt.aca_max_rank;
+    int tb = 0;
     while (tb < 3 * nfar) {
         std::vector<AcaTask> tasks;
         int64_t scr = 0;
@@ -679,7 +687,8 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
         int te = tb;
         while (te < 3 * nfar) {
             const BlockDesc& F = c->far_blocks[te / 3];
-            int rmax = std::min(rcap, std::min(F.m, F.n));
+            int even = (int)std::max<int64_t>(1, (int64_t)F.m * F.n / (F.m + F.n));
+            int rmax = std::min(rcap, std::min(even, std::min(F.m, F.n)));
             int64_t need = (int64_t)(F.m + F.n) * rmax + F.n;
             if (!tasks.empty() && scr + need > budget) break;
             tasks.push_back({F.r0, F.m, F.c0, F.n, te % 3, rmax, scr});
@@ -708,52 +717,93 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
         std::vector<int64_t> ou(nt), ov(nt);
         int64_t len = 0;
         for (int i = 0; i < nt; ++i) {
-            if (fl[i]) {
-                char buf[200];
-                snprintf(buf, sizeof buf, "ACA did not reach tol %.3g within rank %d on a %d x %d block", c->opt.aca_tol,
-                         tasks[i].rmax, tasks[i].m, tasks[i].n);
-                return fail(c, BEM_EINVAL, buf);
-            }
-            int rp = rk[i] + (rk[i] & 1);
+            int r = fl[i] ? 0 : rk[i];  // a failed task keeps no factors
+            int rp = r + (r & 1);
             ou[i] = len;
             len += (int64_t)tasks[i].m * rp;
             ov[i] = len;
             len += (int64_t)tasks[i].n * rp;
-            ranks[tb + i] = rk[i];
+            ranks[tb + i] = r;
+            flags[tb + i] = fl[i];
             task_off_u[tb + i] = ou[i];
             task_off_v[tb + i] = ov[i];
             task_batch[tb + i] = (int)batches.size();
+            rk[i] = r;
         }
+        CK(cudaMemcpyAsync(d_ranks.p, rk.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st));
         Batch B;
         B.len = len;
+        B.arena = DevBuf();
         CK(dalloc(B.arena, es * std::max<int64_t>(1, len)));
+        batches.push_back(B);
         CK(upload(d_ou, ou, st));
         CK(upload(d_ov, ov, st));
         CK(aca_compact<R>((const AcaTask*)d_tasks.p, nt, (const cx<R>*)d_scr.p, (const int*)d_ranks.p,
-                          (const int64_t*)d_ou.p, (const int64_t*)d_ov.p, (cx<R>*)B.arena.p, st));
+                          (const int64_t*)d_ou.p, (const int64_t*)d_ov.p, (cx<R>*)batches.back().arena.p, st));
         CK(cudaStreamSynchronize(st));
-        batches.push_back(B);
         tb = te;
     }
-    // one arena
+    // 2. dense items: leaf x leaf near blocks plus the leaf row slices of dense far blocks
+    o.items = c->near_blocks;
+    o.far_keep.clear();
+    o.n_far_dense = 0;
+    const int nleaf = (int)c->leaf_lo.size();
+    for (int b = 0; b < nfar; ++b) {
+        const BlockDesc& F = c->far_blocks[b];
+        if (flags[3 * b] || flags[3 * b + 1] || flags[3 * b + 2]) {
+            ++o.n_far_dense;
+            int l = (int)(std::lower_bound(c->leaf_lo.begin(), c->leaf_lo.end(), F.r0) - c->leaf_lo.begin());
+            for (; l < nleaf && c->leaf_lo[l] < F.r0 + F.m; ++l) o.items.push_back({c->leaf_lo[l], c->leaf_m[l], F.c0, F.n});
+        } else {
+            o.far_keep.push_back(b);
+        }
+    }
+    std::sort(o.items.begin(), o.items.end(), [](const BlockDesc& a, const BlockDesc& b) {
+        return a.r0 != b.r0 ? a.r0 < b.r0 : a.c0 < b.c0;
+    });
+    bem_status s;
+    if ((s = build_operator_plan(c, o, st)) != BEM_OK) return s;
+    // 3. dense entries
+    {
+        std::vector<int64_t> offs;
+        int64_t off = 0;
+        for (const BlockDesc& b : o.items) {
+            offs.push_back(off);
+            off += (int64_t)b.m * 2 * ((b.n + 1) / 2);
+        }
+        DevBuf d_blocks, d_offs;
+        struct G4 {
+            DevBuf* b[2];
+            ~G4() {
+                for (DevBuf* x : b) dfree(*x);
+            }
+        } g4{{&d_blocks, &d_offs}};
+        CK(upload(d_blocks, o.items, st));
+        CK(upload(d_offs, offs, st));
+        CK(dalloc(o.near, es * 3 * std::max<int64_t>(1, off)));
+        CK(near_assemble<R>(g, perm, (const BlockDesc*)d_blocks.p, (const int64_t*)d_offs.p, (int)o.items.size(),
+                            (cx<R>*)o.near.p, off, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    // 4. one factor arena
     std::vector<int64_t> base(batches.size() + 1, 0);
     for (size_t i = 0; i < batches.size(); ++i) base[i + 1] = base[i] + batches[i].len;
-    cudaError_t ea = dalloc(o.arena, es * std::max<int64_t>(1, base.back()));
-    for (size_t i = 0; i < batches.size() && ea == cudaSuccess; ++i)
+    CK(dalloc(o.arena, es * std::max<int64_t>(1, base.back())));
+    for (size_t i = 0; i < batches.size(); ++i)
         if (batches[i].len)
-            ea = cudaMemcpyAsync((char*)o.arena.p + es * base[i], batches[i].arena.p, es * batches[i].len,
-                                 cudaMemcpyDeviceToDevice, st);
-    if (ea == cudaSuccess) ea = cudaStreamSynchronize(st);
-    for (auto& b : batches) dfree(b.arena);
-    if (ea != cudaSuccess) return cuda_fail(c, ea, "factor arena");
-    // far records
-    o.recs.resize(nfar);
+            CK(cudaMemcpyAsync((char*)o.arena.p + es * base[i], batches[i].arena.p, es * batches[i].len,
+                               cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    // 5. records of the blocks kept as factors
+    const int nkeep = (int)o.far_keep.size();
+    o.recs.resize(nkeep);
     int64_t toff = 0;
     o.max_rank = 0;
     for (int i = 0; i < 3; ++i) o.factor_entries[i] = 0;
-    for (int b = 0; b < nfar; ++b) {
+    for (int k = 0; k < nkeep; ++k) {
+        int b = o.far_keep[k];
         const BlockDesc& F = c->far_blocks[b];
-        FarRec& r = o.recs[b];
+        FarRec& r = o.recs[k];
         r.r0 = F.r0;
         r.m = F.m;
         r.c0 = F.c0;
@@ -772,7 +822,7 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
         toff += 2 * (kp[0] + 2 * kp[1] + kp[2]);
     }
     o.t_len = toff;
-    std::vector<int> order(nfar);
+    std::vector<int> order(nkeep);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         const FarRec &A = o.recs[a], &B = o.recs[b];
@@ -797,7 +847,7 @@ extern "C" bem_status bem_assemble(bem_ctx* c, void* stream) {
     if ((s = upload_geometry(c, st)) != BEM_OK) return s;
     if ((s = build_tree(c, st)) != BEM_OK) return s;
     if ((s = build_singular(c, st)) != BEM_OK) return s;
-    if ((s = build_plan(c, st)) != BEM_OK) return s;
+    if ((s = build_leaves(c, st)) != BEM_OK) return s;
     if (c->opt.precision & BEM_PREC_C64)
         if ((s = build_operator<float>(c, c->op[0], st)) != BEM_OK) return s;
     if (c->opt.precision & BEM_PREC_C128)
@@ -820,18 +870,30 @@ extern "C" bem_status bem_stats_get(const bem_ctx* cc, bem_stats* out) {
     out->n_leaves = (int64_t)c->leaf_lo.size();
     out->n_near = (int64_t)c->near_blocks.size();
     out->n_far = (int64_t)c->far_blocks.size();
-    for (const BlockDesc& b : c->near_blocks) out->near_entries += (int64_t)b.m * b.n;
     const Operator& o = c->op[0].built ? c->op[0] : c->op[1];
+    for (const BlockDesc& b : o.items) out->near_entries += (int64_t)b.m * b.n;
+    out->n_far_dense = o.n_far_dense;
     for (int q = 0; q < 3; ++q) out->factor_entries[q] = o.factor_entries[q];
     out->max_rank = o.max_rank;
     out->singular_pairs = c->n_sing;
-    // algorithmic bytes: every stored entry once, x read twice (gather + use), y written once
+    // algorithmic bytes: every stored entry once, x read once, y written once
+    const int64_t nv = 2 * c->ne;
     for (int p = 0; p < 2; ++p) {
         const Operator& q = c->op[p];
         if (!q.built) continue;
         int64_t es = p == 0 ? 8 : 16;
-        int64_t ent = 3 * out->near_entries + q.factor_entries[0] + q.factor_entries[1] + q.factor_entries[2];
-        int64_t bytes = es * (ent + 3 * 2 * c->ne);
+        int64_t dense = 0, fu = 0, fv = 0;
+        for (const BlockDesc& b : q.items) dense += (int64_t)b.m * b.n;
+        for (const FarRec& r : q.recs)
+            for (int k = 0; k < 3; ++k) {
+                fu += (int64_t)r.rk[k] * r.m;
+                fv += (int64_t)r.rk[k] * r.n;
+            }
+        int64_t* kb = p == 0 ? out->kernel_bytes_c64 : out->kernel_bytes_c128;
+        kb[BEM_KERNEL_GATHER] = es * 2 * nv;
+        kb[BEM_KERNEL_VHX] = es * (fv + nv);
+        kb[BEM_KERNEL_ROWS] = es * (3 * dense + fu + 2 * nv);
+        int64_t bytes = es * (3 * dense + fu + fv + 2 * nv);
         if (p == 0)
             out->matvec_bytes_c64 = bytes;
         else
@@ -876,32 +938,72 @@ static MatvecPlan make_plan(const bem_ctx* c, const Operator& o) {
     MatvecPlan p;
     p.ne = (int)c->ne;
     p.nleaf = (int)c->leaf_lo.size();
-    p.nfar = (int)c->far_blocks.size();
+    p.nfar = (int)o.far_keep.size();
     p.perm = (const int64_t*)c->d_perm.p;
     p.leaf_r0 = (const int*)c->d_leaf_r0.p;
     p.leaf_m = (const int*)c->d_leaf_m.p;
-    p.near_ptr = (const int*)c->d_near_ptr.p;
-    p.near_c0 = (const int*)c->d_near_c0.p;
-    p.near_n = (const int*)c->d_near_n.p;
-    p.near_off = (const int64_t*)c->d_near_off.p;
-    p.near_op_stride = c->near_stride;
-    p.farp_ptr = (const int*)c->d_farp_ptr.p;
-    p.farp_blk = (const int*)c->d_farp_blk.p;
-    p.farp_row = (const int*)c->d_farp_row.p;
+    p.near_ptr = (const int*)o.d_near_ptr.p;
+    p.near_c0 = (const int*)o.d_near_c0.p;
+    p.near_n = (const int*)o.d_near_n.p;
+    p.near_off = (const int64_t*)o.d_near_off.p;
+    p.near_op_stride = o.near_stride;
+    p.farp_ptr = (const int*)o.d_farp_ptr.p;
+    p.farp_blk = (const int*)o.d_farp_blk.p;
+    p.farp_row = (const int*)o.d_farp_row.p;
     p.far = (const FarRec*)o.far_rec.p;
     p.far_order = (const int*)o.far_order.p;
     return p;
 }
 
-static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int nrhs, cudaStream_t st) {
+static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int nrhs, cudaStream_t st,
+                              bool record = false) {
+    const cudaEvent_t* ev = nullptr;
+    if (record && c->prof) {
+        size_t need = c->ev_used + 6 * (size_t)nrhs;
+        while (c->ev_pool.size() < need) {
+            cudaEvent_t e;
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return err;
+            c->ev_pool.push_back(e);
+        }
+        ev = c->ev_pool.data() + c->ev_used;
+        c->ev_used = need;
+    }
     if (dtype == BEM_C64) {
         Operator& o = c->op[0];
         return matvec_run<float>(make_plan(c, o), o.near.p, o.arena.p, (const c64*)x, (c64*)y, (c64*)o.xp.p,
-                                 (c64*)o.t.p, nrhs, o.t_len, st);
+                                 (c64*)o.t.p, nrhs, o.t_len, st, ev);
     }
     Operator& o = c->op[1];
     return matvec_run<double>(make_plan(c, o), o.near.p, o.arena.p, (const c128*)x, (c128*)y, (c128*)o.xp.p,
-                              (c128*)o.t.p, nrhs, o.t_len, st);
+                              (c128*)o.t.p, nrhs, o.t_len, st, ev);
+}
+
+extern "C" bem_status bem_profile_begin(bem_ctx* c) {
+    if (!c) return BEM_EINVAL;
+    c->prof = true;
+    c->ev_used = 0;
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_profile_end(bem_ctx* c, double* ms_sum, int64_t* launches) {
+    if (!c) return BEM_EINVAL;
+    if (!c->prof) return fail(c, BEM_ESTATE, "bem_profile_end without bem_profile_begin");
+    double ms[3] = {0, 0, 0};
+    int64_t cnt[3] = {0, 0, 0};
+    for (size_t i = 0; i + 6 <= c->ev_used; i += 6)
+        for (int k = 0; k < 3; ++k) {
+            CK(cudaEventSynchronize(c->ev_pool[i + 2 * k + 1]));
+            float t = 0;
+            CK(cudaEventElapsedTime(&t, c->ev_pool[i + 2 * k], c->ev_pool[i + 2 * k + 1]));
+            ms[k] += t;
+            cnt[k] += 1;
+        }
+    c->prof = false;
+    c->ev_used = 0;
+    if (ms_sum) memcpy(ms_sum, ms, sizeof(ms));
+    if (launches) memcpy(launches, cnt, sizeof(cnt));
+    return BEM_OK;
 }
 
 extern "C" bem_status bem_matvec(bem_ctx* c, const void* x, void* y, int nrhs, int dtype, void* stream) {
@@ -913,7 +1015,7 @@ extern "C" bem_status bem_matvec(bem_ctx* c, const void* x, void* y, int nrhs, i
     const char* xa = (const char*)x;
     const char* ya = (const char*)y;
     if (xa < ya + bytes && ya < xa + bytes) return fail(c, BEM_EINVAL, "x and y overlap");
-    CK(matvec_any(c, dtype, x, y, nrhs, (cudaStream_t)stream));
+    CK(matvec_any(c, dtype, x, y, nrhs, (cudaStream_t)stream, true));
     return BEM_OK;
 }
 

@@ -169,9 +169,11 @@ struct MatvecPlan {
     const FarRec* far;           // nfar
     const int* far_order;        // nfar: processing order for the V^H x kernel (largest first)
 };
+// ev: NULL, or 6 events per right-hand side recorded around the three kernels
 template <typename R>
 cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x,
-                       cx<R>* y, cx<R>* xp, cx<R>* t, int nrhs, int64_t t_len, cudaStream_t st);
+                       cx<R>* y, cx<R>* xp, cx<R>* t, int nrhs, int64_t t_len, cudaStream_t st,
+                       const cudaEvent_t* ev);
 
 // rhs_power.cu
 template <typename R>

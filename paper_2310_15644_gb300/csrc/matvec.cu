@@ -242,27 +242,34 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const cx<R>*
 
 template <typename R>
 cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x, cx<R>* y,
-                       cx<R>* xp, cx<R>* t, int nrhs, int64_t t_len, cudaStream_t st) {
+                       cx<R>* xp, cx<R>* t, int nrhs, int64_t t_len, cudaStream_t st, const cudaEvent_t* ev) {
     const int64_t nn = 2 * (int64_t)p.ne;
     for (int r = 0; r < nrhs; ++r) {
         const cx<R>* xr = x + r * nn;
         cx<R>* yr = y + r * nn;
+        const cudaEvent_t* e = ev ? ev + 6 * r : nullptr;
+        if (e) BEM_CUDA_TRY(cudaEventRecord(e[0], st));
         k_gather<R><<<(p.ne + 255) / 256, 256, 0, st>>>(xr, p.perm, xp, p.ne);
         BEM_CUDA_TRY(cudaGetLastError());
+        if (e) BEM_CUDA_TRY(cudaEventRecord(e[1], st));
+        if (e) BEM_CUDA_TRY(cudaEventRecord(e[2], st));
         if (p.nfar > 0) {
             k_vhx<R><<<p.nfar, VHX_THREADS, 0, st>>>(p.far, p.far_order, (const cx<R>*)arena, xp, t, p.ne);
             BEM_CUDA_TRY(cudaGetLastError());
         }
+        if (e) BEM_CUDA_TRY(cudaEventRecord(e[3], st));
+        if (e) BEM_CUDA_TRY(cudaEventRecord(e[4], st));
         k_rows<R><<<p.nleaf, ROW_THREADS, 0, st>>>(p, (const cx<R>*)near_entries, (const cx<R>*)arena, xp, t, yr);
         BEM_CUDA_TRY(cudaGetLastError());
+        if (e) BEM_CUDA_TRY(cudaEventRecord(e[5], st));
     }
     (void)t_len;
     return cudaSuccess;
 }
 
 template cudaError_t matvec_run<float>(const MatvecPlan&, const void*, const void*, const c64*, c64*, c64*, c64*, int,
-                                       int64_t, cudaStream_t);
+                                       int64_t, cudaStream_t, const cudaEvent_t*);
 template cudaError_t matvec_run<double>(const MatvecPlan&, const void*, const void*, const c128*, c128*, c128*,
-                                        c128*, int, int64_t, cudaStream_t);
+                                        c128*, int, int64_t, cudaStream_t, const cudaEvent_t*);
 
 }  // namespace bem

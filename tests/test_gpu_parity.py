@@ -181,7 +181,13 @@ def test_compressed_product_equals_oracle(B, sphere3, dtype, aca_tol, tol):
     h = make(B, v, t, k0=10.0, prec=1 if dtype == 0 else 2, leaf=32, eta=2.0, aca_tol=aca_tol)
     try:
         st = B.bem_stats_get(h)
-        assert st["n_far"] > 0 and st["near_entries"] < g.ne * g.ne
+        assert st["n_far"] > 0
+        if aca_tol >= 1e-4:
+            # blocks below the break-even rank are kept as factors
+            assert sum(st["factor_entries"]) > 0 and st["near_entries"] < g.ne * g.ne
+        else:
+            # tight tolerances push blocks past the break-even rank: they are stored densely
+            assert st["n_far_dense"] > 0
         x = W.complex_normal(2 * g.ne, seed=4)
         if dtype == 0:
             x = x.astype(np.complex64).astype(np.complex128)
