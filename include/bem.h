@@ -235,6 +235,25 @@ bem_status bem_power(bem_ctx* ctx, const void* x, const void* b, int nrhs, doubl
  * same units as bem_power. */
 bem_status bem_power_density(bem_ctx* ctx, const void* x, double* per_tri, void* stream);
 
+/* Absorbed power written to device memory, with no device allocation.
+ * No counterpart in the paper: this entry point exists for callers that cannot
+ * let a library allocate device memory during the call -- a framework that owns
+ * all device memory through its own pool allocator and budget, or a
+ * latency-critical loop that must not take the implicit synchronisation of
+ * cudaMalloc/cudaFree.  It computes the p_abs of bem_power (same units) for nrhs
+ * right-hand sides: x device complex128 2ne x nrhs, p_abs device nrhs doubles,
+ * asynchronously on `stream`; nothing is copied to the host.  Its partial sums
+ * live in a fixed 512 KiB array inside the library on each device (65536 doubles,
+ * held until the process exits): nrhs * ceil(nt / 256) must not exceed 65536,
+ * else BEM_EINVAL with the sizes in bem_last_error.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) once; make that
+ * first call before any stream capture.  All calls share the array and every
+ * call rewrites the partial sums it reads, so nothing carries over between
+ * calls; calls whose work can overlap on the GPU (different streams without
+ * ordering between them) race on the array, so order them.  Requires
+ * bem_assemble. */
+bem_status bem_absorbed_power_static(bem_ctx* ctx, const void* x, int nrhs, double* p_abs, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ EXPORTS = [
     "bem_default_options", "bem_create", "bem_destroy", "bem_last_error", "bem_set_mesh", "bem_set_media",
     "bem_debye_eps", "bem_assemble", "bem_num_edges", "bem_num_unknowns", "bem_edges", "bem_stats_get",
     "bem_partition", "bem_eval_entries", "bem_matvec", "bem_rhs_planewave", "bem_solve", "bem_power",
-    "bem_power_density", "bem_profile_begin", "bem_profile_end",
+    "bem_power_density", "bem_profile_begin", "bem_profile_end", "bem_absorbed_power_static",
 ]
 KERNEL_NAMES = ["k_gather", "k_vhx", "k_rows"]   # BEM_KERNEL_GATHER, _VHX, _ROWS
 
@@ -89,6 +89,7 @@ def _load():
         "bem_power_density": (ctypes.c_int, [ctx, vp, vp, vp]),
         "bem_profile_begin": (ctypes.c_int, [ctx]),
         "bem_profile_end": (ctypes.c_int, [ctx, dp, i64p]),
+        "bem_absorbed_power_static": (ctypes.c_int, [ctx, vp, ctypes.c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -242,3 +243,9 @@ def bem_profile_end(ctx):
     cnt = np.zeros(3, dtype=np.int64)
     _check(ctx, lib.bem_profile_end(ctx, _np_ptr(ms, ctypes.c_double), _np_ptr(cnt, ctypes.c_int64)))
     return ms, cnt
+
+
+def bem_absorbed_power_static(ctx, x_ptr: int, nrhs: int, p_abs_ptr: int, stream: int = 0) -> None:
+    """Absorbed power into device memory (p_abs_ptr: nrhs doubles) without any device allocation."""
+    _check(ctx, lib.bem_absorbed_power_static(ctx, ctypes.c_void_p(x_ptr), int(nrhs), ctypes.c_void_p(p_abs_ptr),
+                                              ctypes.c_void_p(stream)))

@@ -1330,3 +1330,10 @@ extern "C" bem_status bem_power_density(bem_ctx* c, const void* x, double* per_t
     CK(power_abs(g, (const c128*)x, 1, per_tri, (double*)c->d_part.p, npa, st));
     return BEM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// accessors for the fixed-scratch entry point (static_scratch.cu)
+// ---------------------------------------------------------------------------
+GeomDev bem_geom_view_for_static(const bem_ctx* c) { return geom_view(c); }
+bool bem_ctx_has_geometry(const bem_ctx* c) { return c->assembled; }
+void bem_ctx_set_error(bem_ctx* c, const char* msg) { c->err = msg; }
