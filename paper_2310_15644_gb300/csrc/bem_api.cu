@@ -42,7 +42,8 @@ struct Operator {
     std::vector<int> far_keep;         // partition far blocks stored as factors
     int64_t n_far_dense = 0;           // partition far blocks stored densely (rank above break-even)
     int64_t near_stride = 0;
-    DevBuf d_near_ptr, d_near_c0, d_near_n, d_near_off, d_farp_ptr, d_farp_blk, d_farp_row;
+    int parts = 1;                     // CTAs per leaf in the rows kernel
+    DevBuf d_work_ptr, d_work_item, d_near_c0, d_near_n, d_near_off, d_farp_blk, d_farp_row, d_ypart, d_arrive;
     DevBuf near;          // 3 * near_stride complex
     DevBuf arena;         // low-rank factors
     DevBuf far_rec;       // FarRec[nfar]
@@ -166,8 +167,8 @@ static c128 csqrt_principal(c128 z) {
 }
 
 static void release_operator(Operator& o) {
-    DevBuf* plan[] = {&o.d_near_ptr, &o.d_near_c0, &o.d_near_n, &o.d_near_off, &o.d_farp_ptr, &o.d_farp_blk,
-                      &o.d_farp_row};
+    DevBuf* plan[] = {&o.d_work_ptr, &o.d_work_item, &o.d_near_c0, &o.d_near_n, &o.d_near_off,
+                      &o.d_farp_blk, &o.d_farp_row, &o.d_ypart, &o.d_arrive};
     for (DevBuf* b : plan) dfree(*b);
     o.items.clear();
     o.far_keep.clear();
@@ -610,47 +611,82 @@ static bem_status build_leaves(bem_ctx* c, cudaStream_t st) {
     return BEM_OK;
 }
 
-// Dense items and far pieces of one operator, grouped by row leaf.
-static bem_status build_operator_plan(bem_ctx* c, Operator& o, cudaStream_t st) {
+// Work schedule of the rows kernel for one operator.  Every leaf's dense items
+// and far pieces are split over parts x 4 work slots (one 64-thread group each),
+// largest item first to the least loaded slot (ties: lowest slot), so that the
+// groups of a leaf stream about the same number of bytes.
+static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaStream_t st) {
     const int nleaf = (int)c->leaf_lo.size();
+    const int G = 4;  // groups per CTA in the rows kernel
     std::vector<int> leaf_of(c->ne + 1, -1);
     for (int l = 0; l < nleaf; ++l) leaf_of[c->leaf_lo[l]] = l;
-    std::vector<int> nptr(nleaf + 1, 0), nc0, nn;
+    // dense items
+    std::vector<int> nc0, nn;
     std::vector<int64_t> noff;
+    std::vector<std::vector<std::pair<int64_t, int>>> items(nleaf);  // (cost, encoded item)
     int64_t off = 0;
-    for (const BlockDesc& b : o.items) {
+    for (size_t k = 0; k < o.items.size(); ++k) {
+        const BlockDesc& b = o.items[k];
         int l = leaf_of[b.r0];
         if (l < 0 || c->leaf_m[l] != b.m) return fail(c, BEM_ECUDA, "dense item rows are not a leaf");
-        nptr[l + 1]++;
         nc0.push_back(b.c0);
         nn.push_back(b.n);
         noff.push_back(off);
-        off += (int64_t)b.m * 2 * ((b.n + 1) / 2);
+        int64_t cost = (int64_t)b.m * 2 * ((b.n + 1) / 2);
+        off += cost;
+        items[l].push_back({3 * cost, (int)k});
     }
-    for (int l = 0; l < nleaf; ++l) nptr[l + 1] += nptr[l];
     o.near_stride = off;
-    std::vector<std::vector<std::pair<int, int>>> pieces(nleaf);
+    // far pieces: every leaf inside a far block's row range
+    std::vector<int> fblk, frow;
     for (size_t k = 0; k < o.far_keep.size(); ++k) {
         const BlockDesc& F = c->far_blocks[o.far_keep[k]];
+        const FarRec& R = o.recs[k];
+        int64_t kp2 = 2 * (int64_t)((R.rk[0] + 1) / 2 + (R.rk[1] + 1) / 2 + (R.rk[2] + 1) / 2);
         int l = leaf_of[F.r0];
         if (l < 0) return fail(c, BEM_ECUDA, "far block does not start at a leaf");
-        for (; l < nleaf && c->leaf_lo[l] < F.r0 + F.m; ++l) pieces[l].push_back({(int)k, c->leaf_lo[l] - F.r0});
-    }
-    std::vector<int> fptr(nleaf + 1, 0), fblk, frow;
-    for (int l = 0; l < nleaf; ++l) {
-        fptr[l + 1] = fptr[l] + (int)pieces[l].size();
-        for (auto& p : pieces[l]) {
-            fblk.push_back(p.first);
-            frow.push_back(p.second);
+        for (; l < nleaf && c->leaf_lo[l] < F.r0 + F.m; ++l) {
+            int id = (int)fblk.size();
+            fblk.push_back((int)k);
+            frow.push_back(c->leaf_lo[l] - F.r0);
+            items[l].push_back({(int64_t)c->leaf_m[l] * kp2, -1 - id});
         }
     }
-    CK(upload(o.d_near_ptr, nptr, st));
+    // parts per leaf: aim at about 8 resident CTAs per SM on 152 SMs
+    const int target = 8 * 152;
+    o.parts = std::max(1, std::min(8, (target + nleaf - 1) / std::max(1, nleaf)));
+    const int S = o.parts * G;
+    std::vector<int> wptr(1, 0), witem;
+    for (int l = 0; l < nleaf; ++l) {
+        auto& v = items[l];
+        std::stable_sort(v.begin(), v.end(), [](const std::pair<int64_t, int>& x, const std::pair<int64_t, int>& y) {
+            return x.first > y.first;
+        });
+        std::vector<int64_t> load(S, 0);
+        std::vector<std::vector<int>> slot(S);
+        for (auto& it : v) {
+            int best = 0;
+            for (int q = 1; q < S; ++q)
+                if (load[q] < load[best]) best = q;
+            load[best] += it.first;
+            slot[best].push_back(it.second);
+        }
+        for (int q = 0; q < S; ++q) {
+            for (int e : slot[q]) witem.push_back(e);
+            wptr.push_back((int)witem.size());
+        }
+    }
+    CK(upload(o.d_work_ptr, wptr, st));
+    CK(upload(o.d_work_item, witem, st));
     CK(upload(o.d_near_c0, nc0, st));
     CK(upload(o.d_near_n, nn, st));
     CK(upload(o.d_near_off, noff, st));
-    CK(upload(o.d_farp_ptr, fptr, st));
     CK(upload(o.d_farp_blk, fblk, st));
     CK(upload(o.d_farp_row, frow, st));
+    CK(dalloc(o.d_ypart, es * 2 * c->ne * (o.parts > 1 ? o.parts : 1)));
+    CK(dalloc(o.d_arrive, sizeof(unsigned int) * std::max(1, nleaf)));
+    CK(cudaMemsetAsync(o.d_arrive.p, 0, sizeof(unsigned int) * std::max(1, nleaf), st));
+    CK(cudaStreamSynchronize(st));
     return BEM_OK;
 }
 
@@ -761,8 +797,6 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
     std::sort(o.items.begin(), o.items.end(), [](const BlockDesc& a, const BlockDesc& b) {
         return a.r0 != b.r0 ? a.r0 < b.r0 : a.c0 < b.c0;
     });
-    bem_status s;
-    if ((s = build_operator_plan(c, o, st)) != BEM_OK) return s;
     // 3. dense entries
     {
         std::vector<int64_t> offs;
@@ -831,6 +865,8 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
     });
     CK(upload(o.far_rec, o.recs, st));
     CK(upload(o.far_order, order, st));
+    bem_status s;
+    if ((s = build_operator_plan(c, o, es, st)) != BEM_OK) return s;
     CK(dalloc(o.xp, es * 2 * c->ne));
     CK(dalloc(o.t, es * std::max<int64_t>(1, o.t_len)));
     o.built = true;
@@ -942,12 +978,15 @@ static MatvecPlan make_plan(const bem_ctx* c, const Operator& o) {
     p.perm = (const int64_t*)c->d_perm.p;
     p.leaf_r0 = (const int*)c->d_leaf_r0.p;
     p.leaf_m = (const int*)c->d_leaf_m.p;
-    p.near_ptr = (const int*)o.d_near_ptr.p;
+    p.parts = o.parts;
+    p.work_ptr = (const int*)o.d_work_ptr.p;
+    p.work_item = (const int*)o.d_work_item.p;
+    p.ypart = o.d_ypart.p;
+    p.arrive = (unsigned int*)o.d_arrive.p;
     p.near_c0 = (const int*)o.d_near_c0.p;
     p.near_n = (const int*)o.d_near_n.p;
     p.near_off = (const int64_t*)o.d_near_off.p;
     p.near_op_stride = o.near_stride;
-    p.farp_ptr = (const int*)o.d_farp_ptr.p;
     p.farp_blk = (const int*)o.d_farp_blk.p;
     p.farp_row = (const int*)o.d_farp_row.p;
     p.far = (const FarRec*)o.far_rec.p;

@@ -155,19 +155,22 @@ cudaError_t aca_compact(const AcaTask* tasks, int ntasks, const cx<R>* scratch, 
 // matvec.cu
 struct MatvecPlan {
     int ne, nleaf, nfar;
+    int parts;                   // CTAs per leaf in the rows kernel
     const int64_t* perm;         // tree position -> edge
     const int* leaf_r0;          // nleaf
     const int* leaf_m;           // nleaf
-    const int* near_ptr;         // nleaf + 1: near items of each leaf
-    const int* near_c0;          // per near item: column start
-    const int* near_n;           // per near item: columns
-    const int64_t* near_off;     // per near item: offset (complex elements) of its A entries
+    const int* work_ptr;         // nleaf * parts * 4 + 1: work slot -> range of work_item
+    const int* work_item;        // >= 0: dense item; < 0: far piece -1 - item
+    const int* near_c0;          // per dense item: column start
+    const int* near_n;           // per dense item: columns
+    const int64_t* near_off;     // per dense item: offset (complex elements) of its A entries
     int64_t near_op_stride;      // distance between the A, B, C arrays
-    const int* farp_ptr;         // nleaf + 1: far pieces of each leaf
-    const int* farp_blk;         // far block index
-    const int* farp_row;         // row offset of the leaf inside the far block
+    const int* farp_blk;         // per far piece: far block index
+    const int* farp_row;         // per far piece: row offset of the leaf inside the far block
     const FarRec* far;           // nfar
     const int* far_order;        // nfar: processing order for the V^H x kernel (largest first)
+    void* ypart;                 // parts x 2ne partial rows (parts > 1)
+    unsigned int* arrive;        // nleaf arrival counters, zero between products
 };
 // ev: NULL, or 6 events per right-hand side recorded around the three kernels
 template <typename R>

@@ -44,6 +44,16 @@ struct Pair<double> {
     }
 };
 
+// load bypassing L1 (data written by other CTAs of the same launch)
+__device__ __forceinline__ c64 ld_cg(const c64* q) {
+    float2 v = __ldcg(reinterpret_cast<const float2*>(q));
+    return mk<float>(v.x, v.y);
+}
+__device__ __forceinline__ c128 ld_cg(const c128* q) {
+    double2 v = __ldcg(reinterpret_cast<const double2*>(q));
+    return mk<double>(v.x, v.y);
+}
+
 template <typename R>
 __global__ void k_gather(const cx<R>* __restrict__ x, const int64_t* __restrict__ perm, cx<R>* __restrict__ xp,
                          int ne) {
@@ -56,6 +66,7 @@ __global__ void k_gather(const cx<R>* __restrict__ x, const int64_t* __restrict_
 
 #define VHX_THREADS 256
 #define VHX_TILE 1024
+#define VHX_UNROLL 4
 
 // t for one far block: items (op, kp) spread over warps, rows tiled through shared memory
 template <typename R>
@@ -64,20 +75,22 @@ __global__ void __launch_bounds__(VHX_THREADS) k_vhx(const FarRec* __restrict__ 
                                                      cx<R>* __restrict__ t, int ne) {
     __shared__ cx<R> sxJ[VHX_TILE], sxM[VHX_TILE];
     __shared__ cx<R> tacc[4 * 2 * 64];  // up to 4 segments x 128 columns (rank cap)
-    const FarRec F = far[order[blockIdx.x]];
-    const int kpA = (F.rk[0] + 1) >> 1, kpB = (F.rk[1] + 1) >> 1, kpC = (F.rk[2] + 1) >> 1;
+    const FarRec* Fp = far + order[blockIdx.x];
+    const int Fn = Fp->n, Fc0 = Fp->c0;
+    const int64_t Foff_t = Fp->off_t;
+    const int kpA = (Fp->rk[0] + 1) >> 1, kpB = (Fp->rk[1] + 1) >> 1, kpC = (Fp->rk[2] + 1) >> 1;
     const int nitems = kpA + kpB + kpC;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = VHX_THREADS / 32;
     // t segment offsets inside tacc (in complex elements)
     const int sA = 0, sBJ = 2 * kpA, sBM = 2 * (kpA + kpB), sC = 2 * (kpA + 2 * kpB);
     const int ttot = 2 * (kpA + 2 * kpB + kpC);
     for (int e = threadIdx.x; e < ttot; e += VHX_THREADS) tacc[e] = mk<R>(0, 0);
-    for (int j0 = 0; j0 < F.n; j0 += VHX_TILE) {
-        const int tn = min(VHX_TILE, F.n - j0);
+    for (int j0 = 0; j0 < Fn; j0 += VHX_TILE) {
+        const int tn = min(VHX_TILE, Fn - j0);
         __syncthreads();
         for (int j = threadIdx.x; j < tn; j += VHX_THREADS) {
-            sxJ[j] = xp[F.c0 + j0 + j];
-            sxM[j] = xp[ne + F.c0 + j0 + j];
+            sxJ[j] = xp[Fc0 + j0 + j];
+            sxM[j] = xp[ne + Fc0 + j0 + j];
         }
         __syncthreads();
         for (int it = wid; it < nitems; it += nw) {
@@ -92,25 +105,37 @@ __global__ void __launch_bounds__(VHX_THREADS) k_vhx(const FarRec* __restrict__ 
                 op = 2;
                 kp = it - kpA - kpB;
             }
-            const cx<R>* V = arena + F.off_v[op];
+            // column pair kp of W, rows j0.. (pair index kp*n + row; two complex values per pair)
+            const cx<R>* V = arena + Fp->off_v[op] + 2 * ((int64_t)kp * Fn + j0);
+            const cx<R>* xs = (op == 2) ? sxM : sxJ;   // x of the column range: J for A and B, M for C
             cx<R> a0 = mk<R>(0, 0), a1 = a0, b0 = a0, b1 = a0;
-            for (int j = lane; j < tn; j += 32) {
+            int j = lane;
+            for (; j + 32 * (VHX_UNROLL - 1) < tn; j += 32 * VHX_UNROLL) {
+                cx<R> w0[VHX_UNROLL], w1[VHX_UNROLL];
+#pragma unroll
+                for (int u = 0; u < VHX_UNROLL; ++u) Pair<R>::ld(V, j + 32 * u, w0[u], w1[u]);
+#pragma unroll
+                for (int u = 0; u < VHX_UNROLL; ++u) {
+                    const cx<R> xv = xs[j + 32 * u];
+                    cfma(a0, w0[u], xv);
+                    cfma(a1, w1[u], xv);
+                    if (op == 1) {
+                        const cx<R> xm = sxM[j + 32 * u];
+                        cfma(b0, w0[u], xm);
+                        cfma(b1, w1[u], xm);
+                    }
+                }
+            }
+            for (; j < tn; j += 32) {
                 cx<R> w0, w1;
-                Pair<R>::ld(V, (int64_t)kp * F.n + j0 + j, w0, w1);
-                if (op == 0) {
-                    cx<R> xj = sxJ[j];
-                    cfma(a0, w0, xj);
-                    cfma(a1, w1, xj);
-                } else if (op == 1) {
-                    cx<R> xj = sxJ[j], xm = sxM[j];
-                    cfma(a0, w0, xj);
-                    cfma(a1, w1, xj);
+                Pair<R>::ld(V, j, w0, w1);
+                const cx<R> xv = xs[j];
+                cfma(a0, w0, xv);
+                cfma(a1, w1, xv);
+                if (op == 1) {
+                    const cx<R> xm = sxM[j];
                     cfma(b0, w0, xm);
                     cfma(b1, w1, xm);
-                } else {
-                    cx<R> xm = sxM[j];
-                    cfma(a0, w0, xm);
-                    cfma(a1, w1, xm);
                 }
             }
             for (int o = 16; o > 0; o >>= 1) {
@@ -135,109 +160,235 @@ __global__ void __launch_bounds__(VHX_THREADS) k_vhx(const FarRec* __restrict__ 
         }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < ttot; e += VHX_THREADS) t[F.off_t + e] = tacc[e];
+    for (int e = threadIdx.x; e < ttot; e += VHX_THREADS) t[Foff_t + e] = tacc[e];
 }
 
 #define ROW_GROUPS 4
 #define ROW_THREADS (64 * ROW_GROUPS)
+#define ROW_UNROLL 4
 
+// One dense item (leaf rows x n columns): y_J += A xJ + B xM, y_M += C xM - B xJ.
 template <typename R>
-__global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const cx<R>* __restrict__ near,
-                                                      const cx<R>* __restrict__ arena,
-                                                      const cx<R>* __restrict__ xp, const cx<R>* __restrict__ t,
-                                                      cx<R>* __restrict__ y) {
-    __shared__ cx<R> sJ[ROW_GROUPS][64], sM[ROW_GROUPS][64];
-    const int leaf = blockIdx.x;
-    const int r0 = p.leaf_r0[leaf], m = p.leaf_m[leaf];
-    const int gi = threadIdx.x >> 6, i = threadIdx.x & 63;
-    const bool act = i < m;
-    const int ne = p.ne;
-    cx<R> aJ = mk<R>(0, 0), aM = aJ;
-    // dense items
-    const int n0 = p.near_ptr[leaf], n1 = p.near_ptr[leaf + 1];
-    for (int it = n0 + gi; it < n1; it += ROW_GROUPS) {
-        const int c0 = p.near_c0[it], n = p.near_n[it];
-        const int64_t off = p.near_off[it];
-        const cx<R>* A = near + off;
-        const cx<R>* B = A + p.near_op_stride;
-        const cx<R>* C = B + p.near_op_stride;
-        const int npair = (n + 1) >> 1;
-        if (act) {
-            for (int cp = 0; cp < npair; ++cp) {
-                cx<R> a0, a1, b0, b1, c0v, c1v;
-                const int64_t idx = (int64_t)cp * m + i;
-                Pair<R>::ld(A, idx, a0, a1);
-                Pair<R>::ld(B, idx, b0, b1);
-                Pair<R>::ld(C, idx, c0v, c1v);
-                const int j = c0 + 2 * cp;
-                cx<R> xJ0 = xp[j], xM0 = xp[ne + j];
-                cx<R> xJ1 = mk<R>(0, 0), xM1 = xJ1;
-                if (2 * cp + 1 < n) {
-                    xJ1 = xp[j + 1];
-                    xM1 = xp[ne + j + 1];
-                }
-                cfma(aJ, a0, xJ0);
-                cfma(aJ, a1, xJ1);
-                cfma(aJ, b0, xM0);
-                cfma(aJ, b1, xM1);
-                cfma(aM, c0v, xM0);
-                cfma(aM, c1v, xM1);
-                cx<R> bx = b0 * xJ0;
-                cfma(bx, b1, xJ1);
-                aM = aM - bx;
-            }
+__device__ __forceinline__ void dense_item(const cx<R>* __restrict__ A, int64_t stride, int m, int i, int n,
+                                           const cx<R>* __restrict__ xJ, const cx<R>* __restrict__ xM, cx<R>& aJ,
+                                           cx<R>& aM) {
+    const cx<R>* B = A + stride;
+    const cx<R>* C = B + stride;
+    const int nfull = n >> 1;  // column pairs with both columns inside the item
+    int cp = 0;
+    for (; cp + ROW_UNROLL <= nfull; cp += ROW_UNROLL) {
+        cx<R> a0[ROW_UNROLL], a1[ROW_UNROLL], b0[ROW_UNROLL], b1[ROW_UNROLL], c0[ROW_UNROLL], c1[ROW_UNROLL];
+#pragma unroll
+        for (int u = 0; u < ROW_UNROLL; ++u) {
+            const int64_t idx = (int64_t)(cp + u) * m + i;
+            Pair<R>::ld(A, idx, a0[u], a1[u]);
+            Pair<R>::ld(B, idx, b0[u], b1[u]);
+            Pair<R>::ld(C, idx, c0[u], c1[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < ROW_UNROLL; ++u) {
+            const int j = 2 * (cp + u);
+            const cx<R> xj0 = xJ[j], xj1 = xJ[j + 1], xm0 = xM[j], xm1 = xM[j + 1];
+            cfma(aJ, a0[u], xj0);
+            cfma(aJ, a1[u], xj1);
+            cfma(aJ, b0[u], xm0);
+            cfma(aJ, b1[u], xm1);
+            cfma(aM, c0[u], xm0);
+            cfma(aM, c1[u], xm1);
+            cx<R> bx = b0[u] * xj0;
+            cfma(bx, b1[u], xj1);
+            aM = aM - bx;
         }
     }
-    // far pieces
-    const int f0 = p.farp_ptr[leaf], f1 = p.farp_ptr[leaf + 1];
-    for (int it = f0 + gi; it < f1; it += ROW_GROUPS) {
-        const FarRec F = p.far[p.farp_blk[it]];
-        const int ro = p.farp_row[it];
-        if (!act) continue;
-        const int kpA = (F.rk[0] + 1) >> 1, kpB = (F.rk[1] + 1) >> 1, kpC = (F.rk[2] + 1) >> 1;
-        const cx<R>* tb = t + F.off_t;
-        const cx<R>* tA = tb;
-        const cx<R>* tBJ = tb + 2 * kpA;
-        const cx<R>* tBM = tBJ + 2 * kpB;
-        const cx<R>* tC = tBM + 2 * kpB;
-        const cx<R>* UA = arena + F.off_u[0];
-        const cx<R>* UB = arena + F.off_u[1];
-        const cx<R>* UC = arena + F.off_u[2];
-        for (int kp = 0; kp < kpA; ++kp) {
+    for (; cp < nfull; ++cp) {
+        cx<R> a0, a1, b0, b1, c0, c1;
+        const int64_t idx = (int64_t)cp * m + i;
+        Pair<R>::ld(A, idx, a0, a1);
+        Pair<R>::ld(B, idx, b0, b1);
+        Pair<R>::ld(C, idx, c0, c1);
+        const int j = 2 * cp;
+        const cx<R> xj0 = xJ[j], xj1 = xJ[j + 1], xm0 = xM[j], xm1 = xM[j + 1];
+        cfma(aJ, a0, xj0);
+        cfma(aJ, a1, xj1);
+        cfma(aJ, b0, xm0);
+        cfma(aJ, b1, xm1);
+        cfma(aM, c0, xm0);
+        cfma(aM, c1, xm1);
+        cx<R> bx = b0 * xj0;
+        cfma(bx, b1, xj1);
+        aM = aM - bx;
+    }
+    if (n & 1) {  // last column; its pair partner is a stored zero column
+        cx<R> a0, a1, b0, b1, c0, c1;
+        const int64_t idx = (int64_t)nfull * m + i;
+        Pair<R>::ld(A, idx, a0, a1);
+        Pair<R>::ld(B, idx, b0, b1);
+        Pair<R>::ld(C, idx, c0, c1);
+        const cx<R> xj0 = xJ[n - 1], xm0 = xM[n - 1];
+        cfma(aJ, a0, xj0);
+        cfma(aJ, b0, xm0);
+        cfma(aM, c0, xm0);
+        aM = aM - b0 * xj0;
+    }
+}
+
+// y_J += U_A tA + U_B tBM, y_M += U_C tC - U_B tBJ for rows ro + i of one far block
+template <typename R>
+__device__ __forceinline__ void far_piece(const FarRec& F, int ro, int i, const cx<R>* __restrict__ arena,
+                                          const cx<R>* __restrict__ t, cx<R>& aJ, cx<R>& aM) {
+    const int kpA = (F.rk[0] + 1) >> 1, kpB = (F.rk[1] + 1) >> 1, kpC = (F.rk[2] + 1) >> 1;
+    const cx<R>* tA = t + F.off_t;
+    const cx<R>* tBJ = tA + 2 * kpA;
+    const cx<R>* tBM = tBJ + 2 * kpB;
+    const cx<R>* tC = tBM + 2 * kpB;
+    const int64_t row = ro + i;
+    {
+        const cx<R>* U = arena + F.off_u[0];
+        int kp = 0;
+        for (; kp + ROW_UNROLL <= kpA; kp += ROW_UNROLL) {
+            cx<R> u0[ROW_UNROLL], u1[ROW_UNROLL];
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; ++u) Pair<R>::ld(U, (int64_t)(kp + u) * F.m + row, u0[u], u1[u]);
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; ++u) {
+                cfma(aJ, u0[u], tA[2 * (kp + u)]);
+                cfma(aJ, u1[u], tA[2 * (kp + u) + 1]);
+            }
+        }
+        for (; kp < kpA; ++kp) {
             cx<R> u0, u1;
-            Pair<R>::ld(UA, (int64_t)kp * F.m + ro + i, u0, u1);
+            Pair<R>::ld(U, (int64_t)kp * F.m + row, u0, u1);
             cfma(aJ, u0, tA[2 * kp]);
             cfma(aJ, u1, tA[2 * kp + 1]);
         }
-        for (int kp = 0; kp < kpB; ++kp) {
+    }
+    {
+        const cx<R>* U = arena + F.off_u[1];
+        int kp = 0;
+        for (; kp + ROW_UNROLL <= kpB; kp += ROW_UNROLL) {
+            cx<R> u0[ROW_UNROLL], u1[ROW_UNROLL];
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; ++u) Pair<R>::ld(U, (int64_t)(kp + u) * F.m + row, u0[u], u1[u]);
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; ++u) {
+                cfma(aJ, u0[u], tBM[2 * (kp + u)]);
+                cfma(aJ, u1[u], tBM[2 * (kp + u) + 1]);
+                cx<R> bx = u0[u] * tBJ[2 * (kp + u)];
+                cfma(bx, u1[u], tBJ[2 * (kp + u) + 1]);
+                aM = aM - bx;
+            }
+        }
+        for (; kp < kpB; ++kp) {
             cx<R> u0, u1;
-            Pair<R>::ld(UB, (int64_t)kp * F.m + ro + i, u0, u1);
+            Pair<R>::ld(U, (int64_t)kp * F.m + row, u0, u1);
             cfma(aJ, u0, tBM[2 * kp]);
             cfma(aJ, u1, tBM[2 * kp + 1]);
             cx<R> bx = u0 * tBJ[2 * kp];
             cfma(bx, u1, tBJ[2 * kp + 1]);
             aM = aM - bx;
         }
-        for (int kp = 0; kp < kpC; ++kp) {
+    }
+    {
+        const cx<R>* U = arena + F.off_u[2];
+        int kp = 0;
+        for (; kp + ROW_UNROLL <= kpC; kp += ROW_UNROLL) {
+            cx<R> u0[ROW_UNROLL], u1[ROW_UNROLL];
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; ++u) Pair<R>::ld(U, (int64_t)(kp + u) * F.m + row, u0[u], u1[u]);
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; ++u) {
+                cfma(aM, u0[u], tC[2 * (kp + u)]);
+                cfma(aM, u1[u], tC[2 * (kp + u) + 1]);
+            }
+        }
+        for (; kp < kpC; ++kp) {
             cx<R> u0, u1;
-            Pair<R>::ld(UC, (int64_t)kp * F.m + ro + i, u0, u1);
+            Pair<R>::ld(U, (int64_t)kp * F.m + row, u0, u1);
             cfma(aM, u0, tC[2 * kp]);
             cfma(aM, u1, tC[2 * kp + 1]);
+        }
+    }
+}
+
+// Grid: nleaf x parts CTAs.  CTA (leaf, part) runs work slots part*4 .. part*4+3 of
+// its leaf, one per 64-thread group (a balanced split of the leaf's dense items and
+// far pieces made at assembly).  With one part the CTA writes y; with several, each
+// writes its partial rows, and the last CTA of the leaf to finish (arrival counter,
+// after a memory fence) adds the parts in index order and writes y -- the sum does
+// not depend on which CTA finishes last.
+template <typename R>
+__global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const cx<R>* __restrict__ near,
+                                                      const cx<R>* __restrict__ arena,
+                                                      const cx<R>* __restrict__ xp, const cx<R>* __restrict__ t,
+                                                      cx<R>* __restrict__ y, cx<R>* __restrict__ ypart,
+                                                      unsigned int* __restrict__ arrive) {
+    __shared__ cx<R> sJ[ROW_GROUPS][64], sM[ROW_GROUPS][64];
+    __shared__ bool s_last;
+    const int P = p.parts;
+    const int leaf = blockIdx.x / P, part = blockIdx.x % P;
+    const int r0 = p.leaf_r0[leaf], m = p.leaf_m[leaf];
+    const int gi = threadIdx.x >> 6, i = threadIdx.x & 63;
+    const bool act = i < m;
+    const int ne = p.ne;
+    cx<R> aJ = mk<R>(0, 0), aM = aJ;
+    const int slot = (leaf * P + part) * ROW_GROUPS + gi;
+    const int w0 = p.work_ptr[slot], w1 = p.work_ptr[slot + 1];
+    if (act) {
+        for (int w = w0; w < w1; ++w) {
+            const int item = p.work_item[w];
+            if (item >= 0) {
+                const int c0 = p.near_c0[item];
+                dense_item<R>(near + p.near_off[item], p.near_op_stride, m, i, p.near_n[item], xp + c0,
+                              xp + ne + c0, aJ, aM);
+            } else {
+                const int fp = -1 - item;
+                const FarRec F = p.far[p.farp_blk[fp]];
+                far_piece<R>(F, p.farp_row[fp], i, arena, t, aJ, aM);
+            }
         }
     }
     sJ[gi][i] = aJ;
     sM[gi][i] = aM;
     __syncthreads();
-    if (gi == 0 && act) {
-        cx<R> J = sJ[0][i], M = sM[0][i];
+    cx<R> J = mk<R>(0, 0), M = J;
+    if (gi == 0) {
+        J = sJ[0][i];
+        M = sM[0][i];
         for (int g2 = 1; g2 < ROW_GROUPS; ++g2) {
             J = J + sJ[g2][i];
             M = M + sM[g2][i];
         }
-        const int64_t e = p.perm[r0 + i];
-        y[e] = J;
-        y[ne + e] = M;
     }
+    if (P == 1) {
+        if (gi == 0 && act) {
+            const int64_t e = p.perm[r0 + i];
+            y[e] = J;
+            y[ne + e] = M;
+        }
+        return;
+    }
+    const int64_t nn = 2 * (int64_t)ne;
+    if (gi == 0 && act) {
+        ypart[part * nn + r0 + i] = J;
+        ypart[part * nn + ne + r0 + i] = M;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(arrive + leaf, 1u) == (unsigned)(P - 1));
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (gi == 0 && act) {
+        cx<R> sj = mk<R>(0, 0), sm = sj;
+        for (int q = 0; q < P; ++q) {
+            sj = sj + ld_cg(ypart + q * nn + r0 + i);
+            sm = sm + ld_cg(ypart + q * nn + ne + r0 + i);
+        }
+        const int64_t e = p.perm[r0 + i];
+        y[e] = sj;
+        y[ne + e] = sm;
+    }
+    if (threadIdx.x == 0) arrive[leaf] = 0u;  // ready for the next product
 }
 
 template <typename R>
@@ -259,7 +410,8 @@ cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void
         }
         if (e) BEM_CUDA_TRY(cudaEventRecord(e[3], st));
         if (e) BEM_CUDA_TRY(cudaEventRecord(e[4], st));
-        k_rows<R><<<p.nleaf, ROW_THREADS, 0, st>>>(p, (const cx<R>*)near_entries, (const cx<R>*)arena, xp, t, yr);
+        k_rows<R><<<p.nleaf * p.parts, ROW_THREADS, 0, st>>>(p, (const cx<R>*)near_entries, (const cx<R>*)arena, xp,
+                                                              t, yr, (cx<R>*)p.ypart, p.arrive);
         BEM_CUDA_TRY(cudaGetLastError());
         if (e) BEM_CUDA_TRY(cudaEventRecord(e[5], st));
     }
