@@ -485,28 +485,37 @@ cudaError_t aca_run(GeomDev g, const int64_t* perm, const AcaTask* tasks, int nt
     return cudaGetLastError();
 }
 
-// Copy the rank-r factors to the product layout: column pairs of U (m rows) and
-// of W = conj(V) (n rows), element (row, 2kp + h) at 2 (kp rows + row) + h; an odd
-// rank is padded with a zero column.
+// Copy the rank-r factors to the product layout (an odd rank is padded with a
+// zero column):
+//   U  slice-major: the block's rows are cut at leaf boundaries; the slice of
+//      leaf rows [ro, ro + ms) holds all column pairs kp, row i of the slice,
+//      at pair index ro * kpc + kp * ms + i (kpc = padded rank / 2), so that the
+//      rows kernel streams one contiguous run per (leaf, block, operator);
+//   W = conj(V) column-pair-major: pair index kp * n + j, one contiguous run per
+//      column pair for the V^H x kernel.
+// pos_leaf_lo / pos_leaf_m give, for every tree position, its leaf's start and size.
 template <typename R>
 __global__ void k_compact(const AcaTask* __restrict__ tasks, const cx<R>* __restrict__ scratch,
                           const int* __restrict__ ranks, const int64_t* __restrict__ off_u,
-                          const int64_t* __restrict__ off_v, cx<R>* __restrict__ arena) {
+                          const int64_t* __restrict__ off_v, cx<R>* __restrict__ arena,
+                          const int* __restrict__ pos_leaf_lo, const int* __restrict__ pos_leaf_m) {
     AcaTask T = tasks[blockIdx.x];
     int r = ranks[blockIdx.x];
     int rp = r + (r & 1);
+    int kpc = rp >> 1;
     const cx<R>* U = scratch + T.scratch;
     const cx<R>* W = U + (int64_t)T.m * T.rmax;
     cx<R>* Uo = arena + off_u[blockIdx.x];
     cx<R>* Vo = arena + off_v[blockIdx.x];
     int64_t nu = (int64_t)T.m * rp, nv = (int64_t)T.n * rp;
     for (int64_t e = threadIdx.x; e < nu; e += blockDim.x) {
-        int h = (int)(e & 1);
-        int64_t rest = e >> 1;
-        int i = (int)(rest % T.m);
-        int kp = (int)(rest / T.m);
-        int l = 2 * kp + h;
-        Uo[e] = (l < r) ? U[(int64_t)l * T.m + i] : mk<R>(0, 0);
+        // source element (row i, column l) -> destination in the slice-major layout
+        int i = (int)(e % T.m);
+        int l = (int)(e / T.m);
+        int kp = l >> 1, h = l & 1;
+        int ro = pos_leaf_lo[T.r0 + i] - T.r0, ms = pos_leaf_m[T.r0 + i];
+        int64_t pair = (int64_t)ro * kpc + (int64_t)kp * ms + (i - ro);
+        Uo[2 * pair + h] = (l < r) ? U[(int64_t)l * T.m + i] : mk<R>(0, 0);
     }
     for (int64_t e = threadIdx.x; e < nv; e += blockDim.x) {
         int h = (int)(e & 1);
@@ -520,9 +529,10 @@ __global__ void k_compact(const AcaTask* __restrict__ tasks, const cx<R>* __rest
 
 template <typename R>
 cudaError_t aca_compact(const AcaTask* tasks, int ntasks, const cx<R>* scratch, const int* ranks,
-                        const int64_t* off_u, const int64_t* off_v, cx<R>* arena, cudaStream_t st) {
+                        const int64_t* off_u, const int64_t* off_v, cx<R>* arena, const int* pos_leaf_lo,
+                        const int* pos_leaf_m, cudaStream_t st) {
     if (ntasks <= 0) return cudaSuccess;
-    k_compact<R><<<ntasks, 256, 0, st>>>(tasks, scratch, ranks, off_u, off_v, arena);
+    k_compact<R><<<ntasks, 256, 0, st>>>(tasks, scratch, ranks, off_u, off_v, arena, pos_leaf_lo, pos_leaf_m);
     return cudaGetLastError();
 }
 
@@ -537,8 +547,8 @@ template cudaError_t aca_run<float>(GeomDev, const int64_t*, const AcaTask*, int
 template cudaError_t aca_run<double>(GeomDev, const int64_t*, const AcaTask*, int, c128*, double, int*, int*,
                                      cudaStream_t, int);
 template cudaError_t aca_compact<float>(const AcaTask*, int, const c64*, const int*, const int64_t*,
-                                        const int64_t*, c64*, cudaStream_t);
+                                        const int64_t*, c64*, const int*, const int*, cudaStream_t);
 template cudaError_t aca_compact<double>(const AcaTask*, int, const c128*, const int*, const int64_t*,
-                                         const int64_t*, c128*, cudaStream_t);
+                                         const int64_t*, c128*, const int*, const int*, cudaStream_t);
 
 }  // namespace bem

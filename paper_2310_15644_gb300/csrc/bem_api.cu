@@ -47,9 +47,10 @@ struct Operator {
     DevBuf near;          // 3 * near_stride complex
     DevBuf arena;         // low-rank factors
     DevBuf far_rec;       // FarRec[nfar]
-    DevBuf far_order;     // int[nfar]
+    DevBuf far_order;     // int2[nvhx]: V^H x units
     DevBuf xp, t;         // product workspace
     int64_t t_len = 0;
+    int nvhx = 0;                      // units of the V^H x kernel
     int64_t factor_entries[3] = {0, 0, 0};
     int max_rank = 0;
     std::vector<FarRec> recs;
@@ -87,7 +88,7 @@ struct bem_ctx {
     std::vector<BlockDesc> near_blocks, far_blocks;  // sorted by (r0, c0)
     DevBuf d_perm;
     // product plan (precision independent part)
-    DevBuf d_leaf_r0, d_leaf_m;
+    DevBuf d_leaf_r0, d_leaf_m, d_pos_leaf_lo, d_pos_leaf_m;
     Operator op[2];
     bool assembled = false;
     double assemble_ms = 0;
@@ -232,7 +233,8 @@ extern "C" void bem_destroy(bem_ctx* c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     DevBuf* bufs[] = {&c->d_tv, &c->d_area, &c->d_nrm, &c->d_cen, &c->d_diam, &c->d_tvid, &c->d_tri_edge,
                       &c->d_tri_coef, &c->d_edge_tri, &c->d_edge_loc, &c->d_mid, &c->d_sing_ptr, &c->d_sing_b,
-                      &c->d_sing_val, &c->d_perm, &c->d_leaf_r0, &c->d_leaf_m, &c->d_part,
+                      &c->d_sing_val, &c->d_perm, &c->d_leaf_r0, &c->d_leaf_m, &c->d_pos_leaf_lo,
+                      &c->d_pos_leaf_m, &c->d_part,
                       &c->d_red, &c->d_tmp_in, &c->d_one, &c->d_gl, &c->gw.V, &c->gw.w, &c->gw.z, &c->gw.r,
                       &c->gw.xin, &c->gw.rin, &c->gw.hpart, &c->gw.hdev, &c->gw.npart};
     for (DevBuf* b : bufs) dfree(*b);
@@ -608,16 +610,24 @@ static bem_status build_singular(bem_ctx* c, cudaStream_t st) {
 static bem_status build_leaves(bem_ctx* c, cudaStream_t st) {
     CK(upload(c->d_leaf_r0, c->leaf_lo, st));
     CK(upload(c->d_leaf_m, c->leaf_m, st));
+    std::vector<int> plo(c->ne), pm(c->ne);
+    for (size_t l = 0; l < c->leaf_lo.size(); ++l)
+        for (int k = c->leaf_lo[l]; k < c->leaf_lo[l] + c->leaf_m[l]; ++k) {
+            plo[k] = c->leaf_lo[l];
+            pm[k] = c->leaf_m[l];
+        }
+    CK(upload(c->d_pos_leaf_lo, plo, st));
+    CK(upload(c->d_pos_leaf_m, pm, st));
     return BEM_OK;
 }
 
 // Work schedule of the rows kernel for one operator.  Every leaf's dense items
-// and far pieces are split over parts x 4 work slots (one 64-thread group each),
+// and far pieces are split over parts x BEM_ROW_GROUPS work slots (one 64-thread group each),
 // largest item first to the least loaded slot (ties: lowest slot), so that the
 // groups of a leaf stream about the same number of bytes.
 static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaStream_t st) {
     const int nleaf = (int)c->leaf_lo.size();
-    const int G = 4;  // groups per CTA in the rows kernel
+    const int G = BEM_ROW_GROUPS;  // groups per CTA in the rows kernel
     std::vector<int> leaf_of(c->ne + 1, -1);
     for (int l = 0; l < nleaf; ++l) leaf_of[c->leaf_lo[l]] = l;
     // dense items
@@ -652,9 +662,9 @@ static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaSt
             items[l].push_back({(int64_t)c->leaf_m[l] * kp2, -1 - id});
         }
     }
-    // parts per leaf: aim at about 8 resident CTAs per SM on 152 SMs
-    const int target = 8 * 152;
-    o.parts = std::max(1, std::min(8, (target + nleaf - 1) / std::max(1, nleaf)));
+    // parts per leaf: aim at BEM_ROW_TARGET_CTAS CTAs in total (a few per SM resident at once)
+    const int target = BEM_ROW_TARGET_CTAS;
+    o.parts = std::max(1, std::min(32, (target + nleaf - 1) / std::max(1, nleaf)));
     const int S = o.parts * G;
     std::vector<int> wptr(1, 0), witem;
     for (int l = 0; l < nleaf; ++l) {
@@ -775,7 +785,8 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
         CK(upload(d_ou, ou, st));
         CK(upload(d_ov, ov, st));
         CK(aca_compact<R>((const AcaTask*)d_tasks.p, nt, (const cx<R>*)d_scr.p, (const int*)d_ranks.p,
-                          (const int64_t*)d_ou.p, (const int64_t*)d_ov.p, (cx<R>*)batches.back().arena.p, st));
+                          (const int64_t*)d_ou.p, (const int64_t*)d_ov.p, (cx<R>*)batches.back().arena.p,
+                          (const int*)c->d_pos_leaf_lo.p, (const int*)c->d_pos_leaf_m.p, st));
         CK(cudaStreamSynchronize(st));
         tb = te;
     }
@@ -856,6 +867,7 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
         toff += 2 * (kp[0] + 2 * kp[1] + kp[2]);
     }
     o.t_len = toff;
+    // V^H x units: (block, 8 items) for every kept block, largest blocks first
     std::vector<int> order(nkeep);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -863,8 +875,15 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
         int64_t wa = (int64_t)A.n * (A.rk[0] + A.rk[1] + A.rk[2]), wb = (int64_t)B.n * (B.rk[0] + B.rk[1] + B.rk[2]);
         return wa > wb;
     });
+    std::vector<int2> units;
+    for (int k : order) {
+        const FarRec& r = o.recs[k];
+        int items = (r.rk[0] + 1) / 2 + (r.rk[1] + 1) / 2 + (r.rk[2] + 1) / 2;
+        for (int u = 0; u < (items + 7) / 8; ++u) units.push_back(make_int2(k, u));
+    }
+    o.nvhx = (int)units.size();
     CK(upload(o.far_rec, o.recs, st));
-    CK(upload(o.far_order, order, st));
+    CK(upload(o.far_order, units, st));
     bem_status s;
     if ((s = build_operator_plan(c, o, es, st)) != BEM_OK) return s;
     CK(dalloc(o.xp, es * 2 * c->ne));
@@ -990,7 +1009,8 @@ static MatvecPlan make_plan(const bem_ctx* c, const Operator& o) {
     p.farp_blk = (const int*)o.d_farp_blk.p;
     p.farp_row = (const int*)o.d_farp_row.p;
     p.far = (const FarRec*)o.far_rec.p;
-    p.far_order = (const int*)o.far_order.p;
+    p.vhx_units = (const int2*)o.far_order.p;
+    p.nvhx = o.nvhx;
     return p;
 }
 

@@ -12,6 +12,8 @@
 
 #define BEM_PI 3.14159265358979323846
 #define BEM_MAX_LEAF 64
+#define BEM_ROW_GROUPS 1     // 64-thread groups per CTA of the rows kernel (one work slot each)
+#define BEM_ROW_TARGET_CTAS (48 * 152)  // rows-kernel CTAs aimed at per product (about 3 waves)
 
 // ---------------------------------------------------------------------------
 // complex arithmetic on interleaved (re, im) pairs
@@ -148,9 +150,11 @@ struct AcaTask {
 template <typename R>
 cudaError_t aca_run(GeomDev g, const int64_t* perm, const AcaTask* tasks, int ntasks, cx<R>* scratch, double tol,
                     int* ranks, int* flags, cudaStream_t st, int max_m);
+// U is written slice-major (leaf slices of the block rows), W column-pair-major
 template <typename R>
 cudaError_t aca_compact(const AcaTask* tasks, int ntasks, const cx<R>* scratch, const int* ranks,
-                        const int64_t* off_u, const int64_t* off_v, cx<R>* arena, cudaStream_t st);
+                        const int64_t* off_u, const int64_t* off_v, cx<R>* arena, const int* pos_leaf_lo,
+                        const int* pos_leaf_m, cudaStream_t st);
 
 // matvec.cu
 struct MatvecPlan {
@@ -168,7 +172,8 @@ struct MatvecPlan {
     const int* farp_blk;         // per far piece: far block index
     const int* farp_row;         // per far piece: row offset of the leaf inside the far block
     const FarRec* far;           // nfar
-    const int* far_order;        // nfar: processing order for the V^H x kernel (largest first)
+    const int2* vhx_units;       // nvhx units of the V^H x kernel: (far block, group of 8 items), largest first
+    int nvhx;
     void* ypart;                 // parts x 2ne partial rows (parts > 1)
     unsigned int* arrive;        // nleaf arrival counters, zero between products
 };

@@ -10,8 +10,8 @@
 //                the same column-pair layout; t = W^T x = V^H x.
 // Kernels per product (one stream, in order):
 //   1. gather  xp = x[perm]           (tree order; complex vector, L2-resident)
-//   2. vhx     t_b = V_b^H xp_sigma   one CTA per far block, largest first; the
-//                                      block's xp slice staged in shared memory
+//   2. vhx     t_b = V_b^H xp_sigma   64-thread CTAs of 8 column-pair items (8 lanes
+//                                      each), largest blocks first
 //   3. rows    per leaf cluster tau:  y_tau = sum_near Z_{tau,sigma} xp_sigma
 //                                             + sum_far U_b[tau rows] t_b
 //              with the 2x2 PMCHWT structure [[A, B], [-B, C]] (B read once,
@@ -22,14 +22,15 @@
 
 namespace bem {
 
-// 16-byte pair loads/stores of two consecutive complex values
+// 16-byte loads of two consecutive complex values of the stored operator.  The
+// operator is read once per product, so the loads are marked streaming
+// (evict-first): they must not push the reused vectors (x, t) out of L1 and L2.
 template <typename R>
 struct Pair;
 template <>
 struct Pair<float> {
-    typedef float4 V;
     static __device__ __forceinline__ void ld(const void* base, int64_t idx, c64& a, c64& b) {
-        float4 v = __ldg(reinterpret_cast<const float4*>(base) + idx);
+        float4 v = __ldcs(reinterpret_cast<const float4*>(base) + idx);
         a = mk<float>(v.x, v.y);
         b = mk<float>(v.z, v.w);
     }
@@ -38,7 +39,7 @@ template <>
 struct Pair<double> {
     static __device__ __forceinline__ void ld(const void* base, int64_t idx, c128& a, c128& b) {
         const double2* p = reinterpret_cast<const double2*>(base) + 2 * idx;
-        double2 u = __ldg(p), v = __ldg(p + 1);
+        double2 u = __ldcs(p), v = __ldcs(p + 1);
         a = mk<double>(u.x, u.y);
         b = mk<double>(v.x, v.y);
     }
@@ -64,107 +65,103 @@ __global__ void k_gather(const cx<R>* __restrict__ x, const int64_t* __restrict_
     xp[ne + i] = x[ne + e];
 }
 
-#define VHX_THREADS 256
-#define VHX_TILE 1024
+#define VHX_THREADS 64   // 8 items of 8 lanes
 #define VHX_UNROLL 4
 
-// t for one far block: items (op, kp) spread over warps, rows tiled through shared memory
+// t = W^T x for a slice of one far block's items.  An item is one column pair kp
+// of one operator's W (A and C use x_J and x_M respectively; B uses both and gives
+// the two t segments of B).  Unit u covers items [8 lo, 8 lo + 8) of block b; an
+// item is handled by 8 lanes (rows jj, jj+8, ...) and its t values are written by
+// the group's first lane -- no shared memory, no barrier, no cross-CTA sum.
 template <typename R>
-__global__ void __launch_bounds__(VHX_THREADS) k_vhx(const FarRec* __restrict__ far, const int* __restrict__ order,
-                                                     const cx<R>* __restrict__ arena, const cx<R>* __restrict__ xp,
-                                                     cx<R>* __restrict__ t, int ne) {
-    __shared__ cx<R> sxJ[VHX_TILE], sxM[VHX_TILE];
-    __shared__ cx<R> tacc[4 * 2 * 64];  // up to 4 segments x 128 columns (rank cap)
-    const FarRec* Fp = far + order[blockIdx.x];
-    const int Fn = Fp->n, Fc0 = Fp->c0;
-    const int64_t Foff_t = Fp->off_t;
+__device__ __forceinline__ void vhx_unit(const FarRec* __restrict__ far, int2 un, const cx<R>* __restrict__ arena,
+                                         const cx<R>* __restrict__ xp, cx<R>* __restrict__ t, int ne) {
+    const FarRec* Fp = far + un.x;
+    const int n = Fp->n;
     const int kpA = (Fp->rk[0] + 1) >> 1, kpB = (Fp->rk[1] + 1) >> 1, kpC = (Fp->rk[2] + 1) >> 1;
-    const int nitems = kpA + kpB + kpC;
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = VHX_THREADS / 32;
-    // t segment offsets inside tacc (in complex elements)
-    const int sA = 0, sBJ = 2 * kpA, sBM = 2 * (kpA + kpB), sC = 2 * (kpA + 2 * kpB);
-    const int ttot = 2 * (kpA + 2 * kpB + kpC);
-    for (int e = threadIdx.x; e < ttot; e += VHX_THREADS) tacc[e] = mk<R>(0, 0);
-    for (int j0 = 0; j0 < Fn; j0 += VHX_TILE) {
-        const int tn = min(VHX_TILE, Fn - j0);
-        __syncthreads();
-        for (int j = threadIdx.x; j < tn; j += VHX_THREADS) {
-            sxJ[j] = xp[Fc0 + j0 + j];
-            sxM[j] = xp[ne + Fc0 + j0 + j];
-        }
-        __syncthreads();
-        for (int it = wid; it < nitems; it += nw) {
-            int op, kp;
-            if (it < kpA) {
-                op = 0;
-                kp = it;
-            } else if (it < kpA + kpB) {
-                op = 1;
-                kp = it - kpA;
-            } else {
-                op = 2;
-                kp = it - kpA - kpB;
-            }
-            // column pair kp of W, rows j0.. (pair index kp*n + row; two complex values per pair)
-            const cx<R>* V = arena + Fp->off_v[op] + 2 * ((int64_t)kp * Fn + j0);
-            const cx<R>* xs = (op == 2) ? sxM : sxJ;   // x of the column range: J for A and B, M for C
-            cx<R> a0 = mk<R>(0, 0), a1 = a0, b0 = a0, b1 = a0;
-            int j = lane;
-            for (; j + 32 * (VHX_UNROLL - 1) < tn; j += 32 * VHX_UNROLL) {
-                cx<R> w0[VHX_UNROLL], w1[VHX_UNROLL];
+    const int it = un.y * 8 + (threadIdx.x >> 3);
+    const int jj = threadIdx.x & 7;
+    if (it >= kpA + kpB + kpC) return;  // whole 8-lane group leaves this unit together
+    int op, kp;
+    if (it < kpA) {
+        op = 0;
+        kp = it;
+    } else if (it < kpA + kpB) {
+        op = 1;
+        kp = it - kpA;
+    } else {
+        op = 2;
+        kp = it - kpA - kpB;
+    }
+    // column pair kp of W, all rows: pair index kp*n + row (two complex values per pair)
+    const cx<R>* V = arena + Fp->off_v[op] + 2 * (int64_t)kp * n;
+    const cx<R>* xs = xp + ((op == 2) ? ne : 0) + Fp->c0;  // J for A and B, M for C
+    const cx<R>* xm = xp + ne + Fp->c0;
+    cx<R> a0 = mk<R>(0, 0), a1 = a0, b0 = a0, b1 = a0;
+    int j = jj;
+    for (; j + 8 * (VHX_UNROLL - 1) < n; j += 8 * VHX_UNROLL) {
+        cx<R> w0[VHX_UNROLL], w1[VHX_UNROLL];
 #pragma unroll
-                for (int u = 0; u < VHX_UNROLL; ++u) Pair<R>::ld(V, j + 32 * u, w0[u], w1[u]);
+        for (int q = 0; q < VHX_UNROLL; ++q) Pair<R>::ld(V, j + 8 * q, w0[q], w1[q]);
 #pragma unroll
-                for (int u = 0; u < VHX_UNROLL; ++u) {
-                    const cx<R> xv = xs[j + 32 * u];
-                    cfma(a0, w0[u], xv);
-                    cfma(a1, w1[u], xv);
-                    if (op == 1) {
-                        const cx<R> xm = sxM[j + 32 * u];
-                        cfma(b0, w0[u], xm);
-                        cfma(b1, w1[u], xm);
-                    }
-                }
-            }
-            for (; j < tn; j += 32) {
-                cx<R> w0, w1;
-                Pair<R>::ld(V, j, w0, w1);
-                const cx<R> xv = xs[j];
-                cfma(a0, w0, xv);
-                cfma(a1, w1, xv);
-                if (op == 1) {
-                    const cx<R> xm = sxM[j];
-                    cfma(b0, w0, xm);
-                    cfma(b1, w1, xm);
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                a0.re += __shfl_xor_sync(0xffffffffu, a0.re, o);
-                a0.im += __shfl_xor_sync(0xffffffffu, a0.im, o);
-                a1.re += __shfl_xor_sync(0xffffffffu, a1.re, o);
-                a1.im += __shfl_xor_sync(0xffffffffu, a1.im, o);
-                b0.re += __shfl_xor_sync(0xffffffffu, b0.re, o);
-                b0.im += __shfl_xor_sync(0xffffffffu, b0.im, o);
-                b1.re += __shfl_xor_sync(0xffffffffu, b1.re, o);
-                b1.im += __shfl_xor_sync(0xffffffffu, b1.im, o);
-            }
-            if (lane == 0) {
-                int s = (op == 0) ? sA : ((op == 1) ? sBJ : sC);
-                tacc[s + 2 * kp] = tacc[s + 2 * kp] + a0;
-                tacc[s + 2 * kp + 1] = tacc[s + 2 * kp + 1] + a1;
-                if (op == 1) {
-                    tacc[sBM + 2 * kp] = tacc[sBM + 2 * kp] + b0;
-                    tacc[sBM + 2 * kp + 1] = tacc[sBM + 2 * kp + 1] + b1;
-                }
+        for (int q = 0; q < VHX_UNROLL; ++q) {
+            const cx<R> xv = xs[j + 8 * q];
+            cfma(a0, w0[q], xv);
+            cfma(a1, w1[q], xv);
+            if (op == 1) {
+                const cx<R> xv2 = xm[j + 8 * q];
+                cfma(b0, w0[q], xv2);
+                cfma(b1, w1[q], xv2);
             }
         }
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < ttot; e += VHX_THREADS) t[Foff_t + e] = tacc[e];
+    for (; j < n; j += 8) {
+        cx<R> w0, w1;
+        Pair<R>::ld(V, j, w0, w1);
+        const cx<R> xv = xs[j];
+        cfma(a0, w0, xv);
+        cfma(a1, w1, xv);
+        if (op == 1) {
+            const cx<R> xv2 = xm[j];
+            cfma(b0, w0, xv2);
+            cfma(b1, w1, xv2);
+        }
+    }
+    // sum over the 8 lanes of the group (xor offsets stay inside the group)
+    const unsigned mask = 0xffu << (threadIdx.x & 24);
+    for (int o = 4; o > 0; o >>= 1) {
+        a0.re += __shfl_xor_sync(mask, a0.re, o);
+        a0.im += __shfl_xor_sync(mask, a0.im, o);
+        a1.re += __shfl_xor_sync(mask, a1.re, o);
+        a1.im += __shfl_xor_sync(mask, a1.im, o);
+        b0.re += __shfl_xor_sync(mask, b0.re, o);
+        b0.im += __shfl_xor_sync(mask, b0.im, o);
+        b1.re += __shfl_xor_sync(mask, b1.re, o);
+        b1.im += __shfl_xor_sync(mask, b1.im, o);
+    }
+    if (jj == 0) {
+        // t segments of the block: [tA | tB(J) | tB(M) | tC], 2 values per column pair
+        cx<R>* tb = t + Fp->off_t;
+        const int seg = (op == 0) ? 0 : ((op == 1) ? 2 * kpA : 2 * (kpA + 2 * kpB));
+        tb[seg + 2 * kp] = a0;
+        tb[seg + 2 * kp + 1] = a1;
+        if (op == 1) {
+            tb[2 * (kpA + kpB) + 2 * kp] = b0;
+            tb[2 * (kpA + kpB) + 2 * kp + 1] = b1;
+        }
+    }
 }
 
-#define ROW_GROUPS 4
-#define ROW_THREADS (64 * ROW_GROUPS)
+// one CTA per unit; the hardware scheduler balances the (largest-first) units
+template <typename R>
+__global__ void __launch_bounds__(VHX_THREADS) k_vhx(const FarRec* __restrict__ far, const int2* __restrict__ units,
+                                                     int nunits, const cx<R>* __restrict__ arena,
+                                                     const cx<R>* __restrict__ xp, cx<R>* __restrict__ t, int ne) {
+    if ((int)blockIdx.x < nunits) vhx_unit<R>(far, units[blockIdx.x], arena, xp, t, ne);
+}
+
+#define ROW_THREADS (64 * BEM_ROW_GROUPS)
+#define ROW_GROUPS BEM_ROW_GROUPS
 #define ROW_UNROLL 4
 
 // One dense item (leaf rows x n columns): y_J += A xJ + B xM, y_M += C xM - B xJ.
@@ -232,82 +229,68 @@ __device__ __forceinline__ void dense_item(const cx<R>* __restrict__ A, int64_t 
     }
 }
 
-// y_J += U_A tA + U_B tBM, y_M += U_C tC - U_B tBJ for rows ro + i of one far block
+// y_J += U_A tA + U_B tBM, y_M += U_C tC - U_B tBJ for rows ro + i of one far block.
+// U is slice-major: the leaf's slice (ms rows starting at ro) of operator q is one
+// contiguous run, pair (kp, i) at ro * kpc + kp * ms + i.
 template <typename R>
-__device__ __forceinline__ void far_piece(const FarRec& F, int ro, int i, const cx<R>* __restrict__ arena,
+__device__ __forceinline__ void far_slice(const cx<R>* __restrict__ U, int kpc, int ms, int i,
+                                          const cx<R>* __restrict__ tv, const cx<R>* __restrict__ tv2, int mode,
+                                          cx<R>& aJ, cx<R>& aM) {
+    // mode 0: aJ += U tv; mode 1: aJ += U tv (tBM), aM -= U tv2 (tBJ); mode 2: aM += U tv
+    int kp = 0;
+    for (; kp + ROW_UNROLL <= kpc; kp += ROW_UNROLL) {
+        cx<R> u0[ROW_UNROLL], u1[ROW_UNROLL];
+#pragma unroll
+        for (int u = 0; u < ROW_UNROLL; ++u) Pair<R>::ld(U, (int64_t)(kp + u) * ms + i, u0[u], u1[u]);
+#pragma unroll
+        for (int u = 0; u < ROW_UNROLL; ++u) {
+            const int k2 = 2 * (kp + u);
+            if (mode == 0) {
+                cfma(aJ, u0[u], tv[k2]);
+                cfma(aJ, u1[u], tv[k2 + 1]);
+            } else if (mode == 1) {
+                cfma(aJ, u0[u], tv[k2]);
+                cfma(aJ, u1[u], tv[k2 + 1]);
+                cx<R> bx = u0[u] * tv2[k2];
+                cfma(bx, u1[u], tv2[k2 + 1]);
+                aM = aM - bx;
+            } else {
+                cfma(aM, u0[u], tv[k2]);
+                cfma(aM, u1[u], tv[k2 + 1]);
+            }
+        }
+    }
+    for (; kp < kpc; ++kp) {
+        cx<R> u0, u1;
+        Pair<R>::ld(U, (int64_t)kp * ms + i, u0, u1);
+        const int k2 = 2 * kp;
+        if (mode == 0) {
+            cfma(aJ, u0, tv[k2]);
+            cfma(aJ, u1, tv[k2 + 1]);
+        } else if (mode == 1) {
+            cfma(aJ, u0, tv[k2]);
+            cfma(aJ, u1, tv[k2 + 1]);
+            cx<R> bx = u0 * tv2[k2];
+            cfma(bx, u1, tv2[k2 + 1]);
+            aM = aM - bx;
+        } else {
+            cfma(aM, u0, tv[k2]);
+            cfma(aM, u1, tv[k2 + 1]);
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void far_piece(const FarRec& F, int ro, int ms, int i, const cx<R>* __restrict__ arena,
                                           const cx<R>* __restrict__ t, cx<R>& aJ, cx<R>& aM) {
     const int kpA = (F.rk[0] + 1) >> 1, kpB = (F.rk[1] + 1) >> 1, kpC = (F.rk[2] + 1) >> 1;
     const cx<R>* tA = t + F.off_t;
     const cx<R>* tBJ = tA + 2 * kpA;
     const cx<R>* tBM = tBJ + 2 * kpB;
     const cx<R>* tC = tBM + 2 * kpB;
-    const int64_t row = ro + i;
-    {
-        const cx<R>* U = arena + F.off_u[0];
-        int kp = 0;
-        for (; kp + ROW_UNROLL <= kpA; kp += ROW_UNROLL) {
-            cx<R> u0[ROW_UNROLL], u1[ROW_UNROLL];
-#pragma unroll
-            for (int u = 0; u < ROW_UNROLL; ++u) Pair<R>::ld(U, (int64_t)(kp + u) * F.m + row, u0[u], u1[u]);
-#pragma unroll
-            for (int u = 0; u < ROW_UNROLL; ++u) {
-                cfma(aJ, u0[u], tA[2 * (kp + u)]);
-                cfma(aJ, u1[u], tA[2 * (kp + u) + 1]);
-            }
-        }
-        for (; kp < kpA; ++kp) {
-            cx<R> u0, u1;
-            Pair<R>::ld(U, (int64_t)kp * F.m + row, u0, u1);
-            cfma(aJ, u0, tA[2 * kp]);
-            cfma(aJ, u1, tA[2 * kp + 1]);
-        }
-    }
-    {
-        const cx<R>* U = arena + F.off_u[1];
-        int kp = 0;
-        for (; kp + ROW_UNROLL <= kpB; kp += ROW_UNROLL) {
-            cx<R> u0[ROW_UNROLL], u1[ROW_UNROLL];
-#pragma unroll
-            for (int u = 0; u < ROW_UNROLL; ++u) Pair<R>::ld(U, (int64_t)(kp + u) * F.m + row, u0[u], u1[u]);
-#pragma unroll
-            for (int u = 0; u < ROW_UNROLL; ++u) {
-                cfma(aJ, u0[u], tBM[2 * (kp + u)]);
-                cfma(aJ, u1[u], tBM[2 * (kp + u) + 1]);
-                cx<R> bx = u0[u] * tBJ[2 * (kp + u)];
-                cfma(bx, u1[u], tBJ[2 * (kp + u) + 1]);
-                aM = aM - bx;
-            }
-        }
-        for (; kp < kpB; ++kp) {
-            cx<R> u0, u1;
-            Pair<R>::ld(U, (int64_t)kp * F.m + row, u0, u1);
-            cfma(aJ, u0, tBM[2 * kp]);
-            cfma(aJ, u1, tBM[2 * kp + 1]);
-            cx<R> bx = u0 * tBJ[2 * kp];
-            cfma(bx, u1, tBJ[2 * kp + 1]);
-            aM = aM - bx;
-        }
-    }
-    {
-        const cx<R>* U = arena + F.off_u[2];
-        int kp = 0;
-        for (; kp + ROW_UNROLL <= kpC; kp += ROW_UNROLL) {
-            cx<R> u0[ROW_UNROLL], u1[ROW_UNROLL];
-#pragma unroll
-            for (int u = 0; u < ROW_UNROLL; ++u) Pair<R>::ld(U, (int64_t)(kp + u) * F.m + row, u0[u], u1[u]);
-#pragma unroll
-            for (int u = 0; u < ROW_UNROLL; ++u) {
-                cfma(aM, u0[u], tC[2 * (kp + u)]);
-                cfma(aM, u1[u], tC[2 * (kp + u) + 1]);
-            }
-        }
-        for (; kp < kpC; ++kp) {
-            cx<R> u0, u1;
-            Pair<R>::ld(U, (int64_t)kp * F.m + row, u0, u1);
-            cfma(aM, u0, tC[2 * kp]);
-            cfma(aM, u1, tC[2 * kp + 1]);
-        }
-    }
+    far_slice<R>(arena + F.off_u[0] + 2 * (int64_t)ro * kpA, kpA, ms, i, tA, nullptr, 0, aJ, aM);
+    far_slice<R>(arena + F.off_u[1] + 2 * (int64_t)ro * kpB, kpB, ms, i, tBM, tBJ, 1, aJ, aM);
+    far_slice<R>(arena + F.off_u[2] + 2 * (int64_t)ro * kpC, kpC, ms, i, tC, nullptr, 2, aJ, aM);
 }
 
 // Grid: nleaf x parts CTAs.  CTA (leaf, part) runs work slots part*4 .. part*4+3 of
@@ -343,7 +326,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const cx<R>*
             } else {
                 const int fp = -1 - item;
                 const FarRec F = p.far[p.farp_blk[fp]];
-                far_piece<R>(F, p.farp_row[fp], i, arena, t, aJ, aM);
+                far_piece<R>(F, p.farp_row[fp], m, i, arena, t, aJ, aM);
             }
         }
     }
@@ -404,8 +387,8 @@ cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void
         BEM_CUDA_TRY(cudaGetLastError());
         if (e) BEM_CUDA_TRY(cudaEventRecord(e[1], st));
         if (e) BEM_CUDA_TRY(cudaEventRecord(e[2], st));
-        if (p.nfar > 0) {
-            k_vhx<R><<<p.nfar, VHX_THREADS, 0, st>>>(p.far, p.far_order, (const cx<R>*)arena, xp, t, p.ne);
+        if (p.nvhx > 0) {
+            k_vhx<R><<<p.nvhx, VHX_THREADS, 0, st>>>(p.far, p.vhx_units, p.nvhx, (const cx<R>*)arena, xp, t, p.ne);
             BEM_CUDA_TRY(cudaGetLastError());
         }
         if (e) BEM_CUDA_TRY(cudaEventRecord(e[3], st));
