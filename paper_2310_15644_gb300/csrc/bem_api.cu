@@ -693,7 +693,7 @@ static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaSt
     CK(upload(o.d_near_off, noff, st));
     CK(upload(o.d_farp_blk, fblk, st));
     CK(upload(o.d_farp_row, frow, st));
-    CK(dalloc(o.d_ypart, es * 2 * c->ne * (o.parts > 1 ? o.parts : 1)));
+    CK(dalloc(o.d_ypart, es * 2 * c->ne * (o.parts > 1 ? o.parts : 1) * BEM_MAX_NR));
     CK(dalloc(o.d_arrive, sizeof(unsigned int) * std::max(1, nleaf)));
     CK(cudaMemsetAsync(o.d_arrive.p, 0, sizeof(unsigned int) * std::max(1, nleaf), st));
     CK(cudaStreamSynchronize(st));
@@ -886,8 +886,8 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
     CK(upload(o.far_order, units, st));
     bem_status s;
     if ((s = build_operator_plan(c, o, es, st)) != BEM_OK) return s;
-    CK(dalloc(o.xp, es * 2 * c->ne));
-    CK(dalloc(o.t, es * std::max<int64_t>(1, o.t_len)));
+    CK(dalloc(o.xp, es * 2 * c->ne * BEM_MAX_NR));
+    CK(dalloc(o.t, es * std::max<int64_t>(1, o.t_len) * BEM_MAX_NR));
     o.built = true;
     return BEM_OK;
 }

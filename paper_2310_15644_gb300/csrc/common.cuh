@@ -12,6 +12,7 @@
 
 #define BEM_PI 3.14159265358979323846
 #define BEM_MAX_LEAF 64
+#define BEM_MAX_NR 8   // right-hand sides applied per pass over the operator
 #define BEM_ROW_GROUPS 1     // 64-thread groups per CTA of the rows kernel (one work slot each)
 #define BEM_ROW_TARGET_CTAS (48 * 152)  // rows-kernel CTAs aimed at per product (about 3 waves)
 
