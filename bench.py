@@ -182,12 +182,14 @@ def run_native(args, rank, world, dist):
     sp = stream.cuda_stream
     v, t = W.icosphere(LEVEL)
 
-    def context(prec):
+    def context(prec, **kw):
         opt = B.bem_default_options()
         opt.precision = prec
         opt.leaf_size = LEAF
         opt.eta = ETA
         opt.aca_tol = ACA_TOL
+        for key, val in kw.items():
+            setattr(opt, key, val)
         h = B.bem_create(opt)
         B.bem_set_mesh(h, v, t)
         B.bem_set_media(h, K0, EPS)
@@ -341,7 +343,27 @@ def run_native(args, rank, world, dist):
 
             g = rwg.build(v, t)
             rows = sample_rows(g.ne, args.cpu_rows)
+        def solve(h, label):
+            bd = torch.empty(n, dtype=torch.complex128, device=dev)
+            B.bem_rhs_planewave(h, [0.0, 0.0, 1.0], [1.0, 0.0, 0.0], bd.data_ptr(), B.BEM_C128, sp)
+            xs = torch.zeros_like(bd)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            it, rel, status = B.bem_solve(h, bd.data_ptr(), xs.data_ptr(), 1, sp, raise_on_noconv=False)
+            torch.cuda.synchronize(dev)
+            dt = time.perf_counter() - t0
+            pa, pe, ps = B.bem_power(h, xs.data_ptr(), bd.data_ptr(), 1, sp)
+            return {"form": label, "seconds": round(dt, 3), "solves_per_s": round(1.0 / dt, 3), "iterations": it,
+                    "relative_residual": float(rel[0]), "converged": status == 0,
+                    "Q_abs": pa[0] / np.pi, "Q_ext": pe[0] / np.pi, "Q_sca": ps[0] / np.pi}
+
+        solves = []
         if not args.no_fp64:
+            # complex64 GMRES to 1e-6
+            opt_s = dict(maxit=3000, gmres_restart=80)
+            hs, _ = context(B.BEM_PREC_C64, **opt_s)
+            solves.append(solve(hs, "complex64 GMRES, tol 1e-6"))
+            B.bem_destroy(hs)
             h128, asm128_ms = context(B.BEM_PREC_C128)
             s128 = B.bem_stats_get(h128)
             xd2 = torch.from_numpy(x.astype(np.complex128)).to(dev)
@@ -355,6 +377,13 @@ def run_native(args, rank, world, dist):
                                     "hbm_gbps_algorithmic": round(s128["matvec_bytes_c128"] / (ms2 / k128 * 1e-3) / 1e9, 1),
                                     "complex64_speedup": round((ms2 / k128) / ms_per_step, 2)}
             B.bem_destroy(h128)
+            hs, _ = context(B.BEM_PREC_C128, **opt_s)
+            solves.append(solve(hs, "complex128 GMRES, tol 1e-6 (plain FP64 GPU form)"))
+            B.bem_destroy(hs)
+            hs, _ = context(B.BEM_PREC_C64 | B.BEM_PREC_C128, tol=1e-4, refine_tol=1e-8, **opt_s)
+            solves.append(solve(hs, "complex64 GMRES (tol 1e-4) inside FP64 refinement to 1e-8"))
+            B.bem_destroy(hs)
+            out["solve"] = solves
         if not args.no_cpu_baseline:
             threads = min(os.cpu_count() or 1, len(rows))
             ref, dt = oracle_rows(g, x.astype(np.complex128), rows, threads)
@@ -405,7 +434,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--cpu-rows", type=int, default=32, help="oracle rows timed for cpu_baseline")
+    ap.add_argument("--cpu-rows", type=int, default=256, help="oracle rows timed for cpu_baseline")
     ap.add_argument("--ref-rows", type=int, default=8, help="oracle rows per step of the reference arm")
     ap.add_argument("--no-fp64", action="store_true", help="skip the complex128 GPU comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")

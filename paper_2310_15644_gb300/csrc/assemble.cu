@@ -477,8 +477,12 @@ template <typename R>
 cudaError_t aca_run(GeomDev g, const int64_t* perm, const AcaTask* tasks, int ntasks, cx<R>* scratch, double tol,
                     int* ranks, int* flags, cudaStream_t st, int max_m) {
     if (ntasks <= 0) return cudaSuccess;
+    // dynamic shared memory: one byte per block row; opt in when it and the kernel's
+    // static shared memory together pass the default 48 KiB
     size_t smem = (size_t)max_m;
-    if (smem > 48 * 1024) {
+    cudaFuncAttributes fa;
+    BEM_CUDA_TRY(cudaFuncGetAttributes(&fa, k_aca<R>));
+    if (smem + fa.sharedSizeBytes > 48 * 1024) {
         BEM_CUDA_TRY(cudaFuncSetAttribute(k_aca<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     k_aca<R><<<ntasks, ACA_THREADS, smem, st>>>(g, perm, tasks, scratch, tol, ranks, flags);

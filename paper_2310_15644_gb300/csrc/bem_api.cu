@@ -754,8 +754,16 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
         CK(dalloc(d_scr, es * scr));
         CK(dalloc(d_ranks, sizeof(int) * nt));
         CK(dalloc(d_flags, sizeof(int) * nt));
-        CK(aca_run<R>(g, perm, (const AcaTask*)d_tasks.p, nt, (cx<R>*)d_scr.p, c->opt.aca_tol, (int*)d_ranks.p,
-                      (int*)d_flags.p, st, max_m));
+        {
+            cudaError_t e = aca_run<R>(g, perm, (const AcaTask*)d_tasks.p, nt, (cx<R>*)d_scr.p, c->opt.aca_tol,
+                                       (int*)d_ranks.p, (int*)d_flags.p, st, max_m);
+            if (e != cudaSuccess) {
+                char buf[256];
+                snprintf(buf, sizeof buf, "ACA batch (%d tasks, largest block %d rows, %lld scratch elements): %s", nt,
+                         max_m, (long long)scr, cudaGetErrorString(e));
+                return fail(c, e == cudaErrorMemoryAllocation ? BEM_ENOMEM : BEM_ECUDA, buf);
+            }
+        }
         std::vector<int> rk(nt), fl(nt);
         CK(cudaMemcpyAsync(rk.data(), d_ranks.p, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(fl.data(), d_flags.p, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
