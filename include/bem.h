@@ -86,7 +86,8 @@ typedef struct {
     double eta;          /* admissibility: min(diam) <= eta * dist; eta <= 0 stores every block densely (default 2) */
     double aca_tol;      /* relative Frobenius tolerance of each compressed block (default 1e-4) */
     int aca_max_rank;    /* rank cap per compressed block, 1..128 (default 96); a block that needs more, or more
-                            than the break-even m n / (m + n), is stored densely instead */
+                            than the break-even m n / (m + n), is split into its children's block pairs
+                            (stored densely once both clusters are leaves) */
     int gmres_restart;   /* GMRES restart length (default 50) */
     int maxit;           /* maximum inner GMRES iterations in total (default 1000) */
     double tol;          /* inner GMRES relative residual tolerance (default 1e-6) */
@@ -102,7 +103,9 @@ typedef struct {
     int64_t n_leaves;           /* leaf clusters */
     int64_t n_near;             /* dense (near) blocks */
     int64_t n_far;              /* admissible (far) blocks of the partition */
-    int64_t n_far_dense;        /* far blocks stored densely: their ACA rank would pass m n / (m + n) */
+    int64_t n_far_dense;        /* leaf x leaf far blocks stored densely (ACA rank above the cap) */
+    int64_t n_far_split;        /* far blocks split into their children's pairs (ACA rank above the cap) */
+    int64_t n_far_factored;     /* blocks stored as low-rank factors after splitting */
     int64_t near_entries;       /* sum of m*n over densely stored blocks (per operator A, B or C) */
     int64_t factor_entries[3];  /* sum of r*(m+n) over far blocks, for A, B, C */
     int64_t max_rank;           /* largest ACA rank */

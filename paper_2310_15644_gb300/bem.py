@@ -44,7 +44,8 @@ class bem_stats(ctypes.Structure):
     _fields_ = [
         ("ne", ctypes.c_int64), ("nt", ctypes.c_int64), ("n_clusters", ctypes.c_int64),
         ("n_leaves", ctypes.c_int64), ("n_near", ctypes.c_int64), ("n_far", ctypes.c_int64),
-        ("n_far_dense", ctypes.c_int64), ("near_entries", ctypes.c_int64), ("factor_entries", ctypes.c_int64 * 3), ("max_rank", ctypes.c_int64),
+        ("n_far_dense", ctypes.c_int64), ("n_far_split", ctypes.c_int64), ("n_far_factored", ctypes.c_int64),
+        ("near_entries", ctypes.c_int64), ("factor_entries", ctypes.c_int64 * 3), ("max_rank", ctypes.c_int64),
         ("singular_pairs", ctypes.c_int64), ("matvec_bytes_c64", ctypes.c_int64),
         ("matvec_bytes_c128", ctypes.c_int64), ("kernel_bytes_c64", ctypes.c_int64 * 3),
         ("kernel_bytes_c128", ctypes.c_int64 * 3), ("assemble_ms", ctypes.c_double),

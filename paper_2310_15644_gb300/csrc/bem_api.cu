@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <numeric>
 
 #include "common.cuh"
@@ -39,7 +40,8 @@ struct Operator {
     bool built = false;
     // product plan of this precision: dense items (leaf row x column range) and far pieces
     std::vector<BlockDesc> items;      // dense items sorted by (r0, c0); rows are one leaf
-    std::vector<int> far_keep;         // partition far blocks stored as factors
+    std::vector<BlockDesc> far_desc;   // blocks stored as factors (partition far blocks, or their splits)
+    int64_t n_far_split = 0;           // far blocks split because their rank passed the cap
     int64_t n_far_dense = 0;           // partition far blocks stored densely (rank above break-even)
     int64_t near_stride = 0;
     int parts = 1;                     // CTAs per leaf in the rows kernel
@@ -172,8 +174,9 @@ static void release_operator(Operator& o) {
                       &o.d_farp_blk, &o.d_farp_row, &o.d_ypart, &o.d_arrive};
     for (DevBuf* b : plan) dfree(*b);
     o.items.clear();
-    o.far_keep.clear();
+    o.far_desc.clear();
     o.n_far_dense = 0;
+    o.n_far_split = 0;
     o.near_stride = 0;
     dfree(o.near);
     dfree(o.arena);
@@ -649,8 +652,8 @@ static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaSt
     o.near_stride = off;
     // far pieces: every leaf inside a far block's row range
     std::vector<int> fblk, frow;
-    for (size_t k = 0; k < o.far_keep.size(); ++k) {
-        const BlockDesc& F = c->far_blocks[o.far_keep[k]];
+    for (size_t k = 0; k < o.far_desc.size(); ++k) {
+        const BlockDesc& F = o.far_desc[k];
         const FarRec& R = o.recs[k];
         int64_t kp2 = 2 * (int64_t)((R.rk[0] + 1) / 2 + (R.rk[1] + 1) / 2 + (R.rk[2] + 1) / 2);
         int l = leaf_of[F.r0];
@@ -705,11 +708,12 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
     const size_t es = sizeof(cx<R>);
     GeomDev g = geom_view(c);
     const int64_t* perm = (const int64_t*)c->d_perm.p;
-    // 1. ACA of every far block, in batches bounded by a scratch budget.  A block's rank
-    //    is capped at the break-even m n / (m + n) (and the user cap); a block that does
-    //    not reach the tolerance within it is stored densely instead.
-    const int nfar = (int)c->far_blocks.size();
-    std::vector<int> ranks(3 * nfar, 0), flags(3 * nfar, 0);
+    // 1. ACA of the far blocks, in rounds; each round in batches bounded by a scratch
+    //    budget.  A block's rank is capped at the break-even m n / (m + n) and at the
+    //    user cap.  A block that does not reach the tolerance within the cap is split
+    //    into the pairs of its clusters' children (still admissible: they are no
+    //    larger and no closer) for the next round; a leaf x leaf block that fails is
+    //    stored densely.
     struct Batch {
         DevBuf arena;
         int64_t len;
@@ -721,98 +725,142 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
             for (auto& b : *v) dfree(b.arena);
         }
     } bguard{&batches};
-    std::vector<int64_t> task_off_u(3 * nfar), task_off_v(3 * nfar);
-    std::vector<int> task_batch(3 * nfar);
+    struct Kept {
+        BlockDesc F;
+        int rk[3], batch[3];
+        int64_t ou[3], ov[3];
+    };
+    std::vector<Kept> kept;
+    std::vector<BlockDesc> dense_far;
+    std::map<std::pair<int, int>, int> node_of;
+    for (size_t i = 0; i < c->node_lo.size(); ++i) node_of[{c->node_lo[i], c->node_hi[i]}] = (int)i;
+    auto children = [&](int lo, int sz, std::vector<std::pair<int, int>>& out) {
+        out.clear();
+        auto it = node_of.find({lo, lo + sz});
+        int ch = (it == node_of.end()) ? -1 : c->node_child0[it->second];
+        if (ch < 0) {
+            out.push_back({lo, sz});
+            return false;
+        }
+        for (int k = 0; k < 2; ++k) out.push_back({c->node_lo[ch + k], c->node_hi[ch + k] - c->node_lo[ch + k]});
+        return true;
+    };
     const int64_t budget = (int64_t)(sizeof(R) == 4 ? 1 : 2) * (1ll << 30) / (int64_t)es;  // complex elements
     const int rcap = c->opt.aca_max_rank;
-    int tb = 0;
-    while (tb < 3 * nfar) {
-        std::vector<AcaTask> tasks;
-        int64_t scr = 0;
-        int max_m = 1;
-        int te = tb;
-        while (te < 3 * nfar) {
-            const BlockDesc& F = c->far_blocks[te / 3];
-            int even = (int)std::max<int64_t>(1, (int64_t)F.m * F.n / (F.m + F.n));
-            int rmax = std::min(rcap, std::min(even, std::min(F.m, F.n)));
-            int64_t need = (int64_t)(F.m + F.n) * rmax + F.n;
-            if (!tasks.empty() && scr + need > budget) break;
-            tasks.push_back({F.r0, F.m, F.c0, F.n, te % 3, rmax, scr});
-            scr += need;
-            max_m = std::max(max_m, F.m);
-            ++te;
-        }
-        DevBuf d_tasks, d_scr, d_ranks, d_flags, d_ou, d_ov;
-        struct G3 {
-            DevBuf* b[6];
-            ~G3() {
-                for (DevBuf* x : b) dfree(*x);
+    std::vector<BlockDesc> work = c->far_blocks;
+    o.n_far_split = 0;
+    while (!work.empty()) {
+        const int nw = (int)work.size();
+        std::vector<int> ranks(3 * nw, 0), flags(3 * nw, 0), task_batch(3 * nw, 0);
+        std::vector<int64_t> task_off_u(3 * nw), task_off_v(3 * nw);
+        int tb = 0;
+        while (tb < 3 * nw) {
+            std::vector<AcaTask> tasks;
+            int64_t scr = 0;
+            int max_m = 1;
+            int te = tb;
+            while (te < 3 * nw) {
+                const BlockDesc& F = work[te / 3];
+                int even = (int)std::max<int64_t>(1, (int64_t)F.m * F.n / (F.m + F.n));
+                int rmax = std::min(rcap, std::min(even, std::min(F.m, F.n)));
+                int64_t need = (int64_t)(F.m + F.n) * rmax + F.n;
+                if (!tasks.empty() && scr + need > budget) break;
+                tasks.push_back({F.r0, F.m, F.c0, F.n, te % 3, rmax, scr});
+                scr += need;
+                max_m = std::max(max_m, F.m);
+                ++te;
             }
-        } g3{{&d_tasks, &d_scr, &d_ranks, &d_flags, &d_ou, &d_ov}};
-        const int nt = (int)tasks.size();
-        CK(upload(d_tasks, tasks, st));
-        CK(dalloc(d_scr, es * scr));
-        CK(dalloc(d_ranks, sizeof(int) * nt));
-        CK(dalloc(d_flags, sizeof(int) * nt));
-        {
-            cudaError_t e = aca_run<R>(g, perm, (const AcaTask*)d_tasks.p, nt, (cx<R>*)d_scr.p, c->opt.aca_tol,
-                                       (int*)d_ranks.p, (int*)d_flags.p, st, max_m);
-            if (e != cudaSuccess) {
-                char buf[256];
-                snprintf(buf, sizeof buf, "ACA batch (%d tasks, largest block %d rows, %lld scratch elements): %s", nt,
-                         max_m, (long long)scr, cudaGetErrorString(e));
-                return fail(c, e == cudaErrorMemoryAllocation ? BEM_ENOMEM : BEM_ECUDA, buf);
+            DevBuf d_tasks, d_scr, d_ranks, d_flags, d_ou, d_ov;
+            struct G3 {
+                DevBuf* b[6];
+                ~G3() {
+                    for (DevBuf* x : b) dfree(*x);
+                }
+            } g3{{&d_tasks, &d_scr, &d_ranks, &d_flags, &d_ou, &d_ov}};
+            const int nt = (int)tasks.size();
+            CK(upload(d_tasks, tasks, st));
+            CK(dalloc(d_scr, es * scr));
+            CK(dalloc(d_ranks, sizeof(int) * nt));
+            CK(dalloc(d_flags, sizeof(int) * nt));
+            {
+                cudaError_t e = aca_run<R>(g, perm, (const AcaTask*)d_tasks.p, nt, (cx<R>*)d_scr.p, c->opt.aca_tol,
+                                           (int*)d_ranks.p, (int*)d_flags.p, st, max_m);
+                if (e != cudaSuccess) {
+                    char buf[256];
+                    snprintf(buf, sizeof buf, "ACA batch (%d tasks, largest block %d rows, %lld scratch elements): %s",
+                             nt, max_m, (long long)scr, cudaGetErrorString(e));
+                    return fail(c, e == cudaErrorMemoryAllocation ? BEM_ENOMEM : BEM_ECUDA, buf);
+                }
             }
+            std::vector<int> rk(nt), fl(nt);
+            CK(cudaMemcpyAsync(rk.data(), d_ranks.p, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(fl.data(), d_flags.p, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            // a block keeps its factors only if all three operators converged
+            for (int i = 0; i < nt; ++i) flags[tb + i] = fl[i];
+            std::vector<int64_t> ou(nt), ov(nt);
+            int64_t len = 0;
+            for (int i = 0; i < nt; ++i) {
+                int r = fl[i] ? 0 : rk[i];
+                int rp = r + (r & 1);
+                ou[i] = len;
+                len += (int64_t)tasks[i].m * rp;
+                ov[i] = len;
+                len += (int64_t)tasks[i].n * rp;
+                ranks[tb + i] = r;
+                task_off_u[tb + i] = ou[i];
+                task_off_v[tb + i] = ov[i];
+                task_batch[tb + i] = (int)batches.size();
+                rk[i] = r;
+            }
+            CK(cudaMemcpyAsync(d_ranks.p, rk.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st));
+            Batch Bt;
+            Bt.len = len;
+            Bt.arena = DevBuf();
+            CK(dalloc(Bt.arena, es * std::max<int64_t>(1, len)));
+            batches.push_back(Bt);
+            CK(upload(d_ou, ou, st));
+            CK(upload(d_ov, ov, st));
+            CK(aca_compact<R>((const AcaTask*)d_tasks.p, nt, (const cx<R>*)d_scr.p, (const int*)d_ranks.p,
+                              (const int64_t*)d_ou.p, (const int64_t*)d_ov.p, (cx<R>*)batches.back().arena.p,
+                              (const int*)c->d_pos_leaf_lo.p, (const int*)c->d_pos_leaf_m.p, st));
+            CK(cudaStreamSynchronize(st));
+            tb = te;
         }
-        std::vector<int> rk(nt), fl(nt);
-        CK(cudaMemcpyAsync(rk.data(), d_ranks.p, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(fl.data(), d_flags.p, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        std::vector<int64_t> ou(nt), ov(nt);
-        int64_t len = 0;
-        for (int i = 0; i < nt; ++i) {
-            int r = fl[i] ? 0 : rk[i];  // a failed task keeps no factors
-            int rp = r + (r & 1);
-            ou[i] = len;
-            len += (int64_t)tasks[i].m * rp;
-            ov[i] = len;
-            len += (int64_t)tasks[i].n * rp;
-            ranks[tb + i] = r;
-            flags[tb + i] = fl[i];
-            task_off_u[tb + i] = ou[i];
-            task_off_v[tb + i] = ov[i];
-            task_batch[tb + i] = (int)batches.size();
-            rk[i] = r;
+        std::vector<BlockDesc> next;
+        std::vector<std::pair<int, int>> ct, cs;
+        for (int b = 0; b < nw; ++b) {
+            const BlockDesc& F = work[b];
+            if (!(flags[3 * b] || flags[3 * b + 1] || flags[3 * b + 2])) {
+                Kept k;
+                k.F = F;
+                for (int q = 0; q < 3; ++q) {
+                    k.rk[q] = ranks[3 * b + q];
+                    k.batch[q] = task_batch[3 * b + q];
+                    k.ou[q] = task_off_u[3 * b + q];
+                    k.ov[q] = task_off_v[3 * b + q];
+                }
+                kept.push_back(k);
+                continue;
+            }
+            // a failed block keeps nothing (its factors occupy no arena space)
+            bool st_ = children(F.r0, F.m, ct);
+            bool ss_ = children(F.c0, F.n, cs);
+            if (!st_ && !ss_) {
+                dense_far.push_back(F);
+                continue;
+            }
+            ++o.n_far_split;
+            for (auto& a2 : ct)
+                for (auto& b2 : cs) next.push_back({a2.first, a2.second, b2.first, b2.second});
         }
-        CK(cudaMemcpyAsync(d_ranks.p, rk.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st));
-        Batch B;
-        B.len = len;
-        B.arena = DevBuf();
-        CK(dalloc(B.arena, es * std::max<int64_t>(1, len)));
-        batches.push_back(B);
-        CK(upload(d_ou, ou, st));
-        CK(upload(d_ov, ov, st));
-        CK(aca_compact<R>((const AcaTask*)d_tasks.p, nt, (const cx<R>*)d_scr.p, (const int*)d_ranks.p,
-                          (const int64_t*)d_ou.p, (const int64_t*)d_ov.p, (cx<R>*)batches.back().arena.p,
-                          (const int*)c->d_pos_leaf_lo.p, (const int*)c->d_pos_leaf_m.p, st));
-        CK(cudaStreamSynchronize(st));
-        tb = te;
+        work.swap(next);
     }
-    // 2. dense items: leaf x leaf near blocks plus the leaf row slices of dense far blocks
+    // 2. dense items: leaf x leaf near blocks plus leaf x leaf far blocks above the rank cap
     o.items = c->near_blocks;
-    o.far_keep.clear();
-    o.n_far_dense = 0;
-    const int nleaf = (int)c->leaf_lo.size();
-    for (int b = 0; b < nfar; ++b) {
-        const BlockDesc& F = c->far_blocks[b];
-        if (flags[3 * b] || flags[3 * b + 1] || flags[3 * b + 2]) {
-            ++o.n_far_dense;
-            int l = (int)(std::lower_bound(c->leaf_lo.begin(), c->leaf_lo.end(), F.r0) - c->leaf_lo.begin());
-            for (; l < nleaf && c->leaf_lo[l] < F.r0 + F.m; ++l) o.items.push_back({c->leaf_lo[l], c->leaf_m[l], F.c0, F.n});
-        } else {
-            o.far_keep.push_back(b);
-        }
-    }
+    o.far_desc.clear();
+    o.n_far_dense = (int64_t)dense_far.size();
+    for (const BlockDesc& F : dense_far) o.items.push_back(F);
     std::sort(o.items.begin(), o.items.end(), [](const BlockDesc& a, const BlockDesc& b) {
         return a.r0 != b.r0 ? a.r0 < b.r0 : a.c0 < b.c0;
     });
@@ -848,14 +896,16 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
                                cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
     // 5. records of the blocks kept as factors
-    const int nkeep = (int)o.far_keep.size();
+    const int nkeep = (int)kept.size();
     o.recs.resize(nkeep);
+    o.far_desc.resize(nkeep);
     int64_t toff = 0;
     o.max_rank = 0;
     for (int i = 0; i < 3; ++i) o.factor_entries[i] = 0;
     for (int k = 0; k < nkeep; ++k) {
-        int b = o.far_keep[k];
-        const BlockDesc& F = c->far_blocks[b];
+        const Kept& K = kept[k];
+        const BlockDesc& F = K.F;
+        o.far_desc[k] = F;
         FarRec& r = o.recs[k];
         r.r0 = F.r0;
         r.m = F.m;
@@ -863,13 +913,12 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
         r.n = F.n;
         int kp[3];
         for (int q = 0; q < 3; ++q) {
-            int t = 3 * b + q;
-            r.rk[q] = ranks[t];
-            kp[q] = (ranks[t] + 1) / 2;
-            r.off_u[q] = base[task_batch[t]] + task_off_u[t];
-            r.off_v[q] = base[task_batch[t]] + task_off_v[t];
-            o.factor_entries[q] += (int64_t)ranks[t] * (F.m + F.n);
-            o.max_rank = std::max(o.max_rank, ranks[t]);
+            r.rk[q] = K.rk[q];
+            kp[q] = (K.rk[q] + 1) / 2;
+            r.off_u[q] = base[K.batch[q]] + K.ou[q];
+            r.off_v[q] = base[K.batch[q]] + K.ov[q];
+            o.factor_entries[q] += (int64_t)K.rk[q] * (F.m + F.n);
+            o.max_rank = std::max(o.max_rank, K.rk[q]);
         }
         r.off_t = toff;
         toff += 2 * (kp[0] + 2 * kp[1] + kp[2]);
@@ -936,6 +985,8 @@ extern "C" bem_status bem_stats_get(const bem_ctx* cc, bem_stats* out) {
     const Operator& o = c->op[0].built ? c->op[0] : c->op[1];
     for (const BlockDesc& b : o.items) out->near_entries += (int64_t)b.m * b.n;
     out->n_far_dense = o.n_far_dense;
+    out->n_far_split = o.n_far_split;
+    out->n_far_factored = (int64_t)o.far_desc.size();
     for (int q = 0; q < 3; ++q) out->factor_entries[q] = o.factor_entries[q];
     out->max_rank = o.max_rank;
     out->singular_pairs = c->n_sing;
@@ -1001,7 +1052,7 @@ static MatvecPlan make_plan(const bem_ctx* c, const Operator& o) {
     MatvecPlan p;
     p.ne = (int)c->ne;
     p.nleaf = (int)c->leaf_lo.size();
-    p.nfar = (int)o.far_keep.size();
+    p.nfar = (int)o.far_desc.size();
     p.perm = (const int64_t*)c->d_perm.p;
     p.leaf_r0 = (const int*)c->d_leaf_r0.p;
     p.leaf_m = (const int*)c->d_leaf_m.p;
