@@ -95,6 +95,14 @@ typedef struct {
     int refine_maxit;    /* maximum outer refinement steps (default 10) */
 } bem_options;
 
+/* Parts of bem_assemble timed in bem_stats.assemble_phase_ms (host wall time, milliseconds). */
+#define BEM_PHASE_TREE 0     /* geometry upload, cluster tree, block partition, leaf tables */
+#define BEM_PHASE_SINGULAR 1 /* list and analytic integrals of the singular triangle pairs */
+#define BEM_PHASE_ACA 2      /* adaptive cross approximation of the far blocks (all splitting rounds) */
+#define BEM_PHASE_NEAR 3     /* quadrature of the densely stored blocks */
+#define BEM_PHASE_PLAN 4     /* factor arena, product plan and work slots */
+#define BEM_PHASES 5
+
 /* Summary of an assembled operator (bem_stats). */
 typedef struct {
     int64_t ne;                 /* RWG edges (unknowns = 2 ne) */
@@ -118,6 +126,7 @@ typedef struct {
                                      rows: dense entries + U factors + x + y */
     int64_t kernel_bytes_c128[3]; /* same for complex128 */
     double assemble_ms;         /* wall time of the last bem_assemble */
+    double assemble_phase_ms[BEM_PHASES]; /* its parts: see BEM_PHASE_* (ACA, near and plan summed over precisions) */
 } bem_stats;
 
 /* Kernels of one product, in launch order (index into the profiling arrays). */

@@ -40,6 +40,10 @@ class bem_options(ctypes.Structure):
     ]
 
 
+# parts of bem_assemble, in the order of BEM_PHASE_* in bem.h
+PHASE_NAMES = ("tree", "singular", "aca", "near", "plan")
+
+
 class bem_stats(ctypes.Structure):
     _fields_ = [
         ("ne", ctypes.c_int64), ("nt", ctypes.c_int64), ("n_clusters", ctypes.c_int64),
@@ -49,6 +53,7 @@ class bem_stats(ctypes.Structure):
         ("singular_pairs", ctypes.c_int64), ("matvec_bytes_c64", ctypes.c_int64),
         ("matvec_bytes_c128", ctypes.c_int64), ("kernel_bytes_c64", ctypes.c_int64 * 3),
         ("kernel_bytes_c128", ctypes.c_int64 * 3), ("assemble_ms", ctypes.c_double),
+        ("assemble_phase_ms", ctypes.c_double * 5),
     ]
 
 
@@ -178,6 +183,7 @@ def bem_stats_get(ctx) -> dict:
     d = {name: getattr(s, name) for name, _ in bem_stats._fields_}
     for k in ("factor_entries", "kernel_bytes_c64", "kernel_bytes_c128"):
         d[k] = list(getattr(s, k))
+    d["assemble_phase_ms"] = dict(zip(PHASE_NAMES, s.assemble_phase_ms))
     return d
 
 

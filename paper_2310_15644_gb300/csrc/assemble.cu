@@ -59,56 +59,122 @@ __device__ __forceinline__ float r_exp<float>(float x) { return expf(x); }
 template <>
 __device__ __forceinline__ double r_exp<double>(double x) { return exp(x); }
 
+// Geometry of a triangle pair (a test, b source) in the arithmetic R, with
+// coordinates relative to a's centroid: vertices va, vb; areas; edge coefficients
+// of the local bases (ca, cb); the squared centroid distance d2 and the larger
+// longest edge dm (for the singular-pair test).
+template <typename R>
+struct PairGeom {
+    R va[3][3], vb[3][3];
+    R Aa, Ab, inv_AA;
+    R ca[3], cb[3];
+    R d2, dm;
+};
+
+template <typename R>
+__device__ __forceinline__ void pair_geom(const GeomDev& g, int a, int b, PairGeom<R>& P);
+
+template <>
+__device__ __forceinline__ void pair_geom<float>(const GeomDev& g, int a, int b, PairGeom<float>& P) {
+    const TriF* ta = g.trif + a;
+    const TriF* tb = g.trif + b;
+    const float4 ha = ta->c_hi, la = ta->c_lo, hb = tb->c_hi, lb = tb->c_lo;
+    // centroid difference from the high and low parts
+    const float dx = (hb.x - ha.x) + (lb.x - la.x);
+    const float dy = (hb.y - ha.y) + (lb.y - la.y);
+    const float dz = (hb.z - ha.z) + (lb.z - la.z);
+    for (int v = 0; v < 3; ++v) {
+        const float4 pa = ta->v[v], pb = tb->v[v];
+        P.va[v][0] = pa.x;
+        P.va[v][1] = pa.y;
+        P.va[v][2] = pa.z;
+        P.vb[v][0] = pb.x + dx;
+        P.vb[v][1] = pb.y + dy;
+        P.vb[v][2] = pb.z + dz;
+    }
+    const float4 ka = ta->coef, kb = tb->coef;
+    P.Aa = ha.w;
+    P.Ab = hb.w;
+    P.inv_AA = ka.w * kb.w;
+    P.ca[0] = ka.x;
+    P.ca[1] = ka.y;
+    P.ca[2] = ka.z;
+    P.cb[0] = kb.x;
+    P.cb[1] = kb.y;
+    P.cb[2] = kb.z;
+    P.d2 = dx * dx + dy * dy + dz * dz;
+    P.dm = fmaxf(la.w, lb.w);
+}
+
+template <>
+__device__ __forceinline__ void pair_geom<double>(const GeomDev& g, int a, int b, PairGeom<double>& P) {
+    const double* oa = g.cen + 3 * a;
+    for (int v = 0; v < 3; ++v)
+        for (int d = 0; d < 3; ++d) {
+            P.va[v][d] = g.tv[9 * a + 3 * v + d] - oa[d];
+            P.vb[v][d] = g.tv[9 * b + 3 * v + d] - oa[d];
+        }
+    P.Aa = g.area[a];
+    P.Ab = g.area[b];
+    P.inv_AA = 1.0 / (P.Aa * P.Ab);
+    for (int i = 0; i < 3; ++i) {
+        P.ca[i] = g.tri_coef[3 * a + i];
+        P.cb[i] = g.tri_coef[3 * b + i];
+    }
+    double dx = g.cen[3 * b] - oa[0], dy = g.cen[3 * b + 1] - oa[1], dz = g.cen[3 * b + 2] - oa[2];
+    P.d2 = dx * dx + dy * dy + dz * dz;
+    P.dm = fmax(g.diam[a], g.diam[b]);
+}
+
 // Local integrals of one regular triangle pair for the basis functions with free
-// vertices li (test) and lj (source), at k0 and k1.
+// vertices li (test) and lj (source), at k0 and k1, over the test points
+// p_lo <= p < p_hi of the 7-point rule (all 7 source points):
 //   WANT_T: ff = sum W G (r-v_i).(r'-v_j), i0 = sum W G
 //   WANT_K: kk = sum W g (r-v_i).((r-r') x (r'-v_j))
 template <typename R, bool WANT_T, bool WANT_K>
-__device__ void regular_pair(const GeomDev& g, int a, int li, int b, int lj, cx<R> ff[2], cx<R> i0[2],
-                             cx<R> kk[2]) {
-    const double* oa = g.cen + 3 * a;
-    R va[3][3], vb[3][3];
-    for (int v = 0; v < 3; ++v)
-        for (int d = 0; d < 3; ++d) {
-            va[v][d] = (R)(g.tv[9 * a + 3 * v + d] - oa[d]);
-            vb[v][d] = (R)(g.tv[9 * b + 3 * v + d] - oa[d]);
-        }
-    const R Aa = (R)g.area[a], Ab = (R)g.area[b];
-    R pa[7][3], ua[7][3], wa[7];
+__device__ __forceinline__ void regular_pair(const PairGeom<R>& P, const MediaConst<R>& M, int li, int lj, int p_lo,
+                                             int p_hi, cx<R> ff[2], cx<R> i0[2], cx<R> kk[2]) {
     R pb[7][3], wbv[7][3], wb[7];
+#pragma unroll
     for (int q = 0; q < 7; ++q) {
-        double l0, l1, l2, w;
-        rule7_d(q, l0, l1, l2, w);
+        R l0, l1, l2, w;
+        rule7<R>(q, l0, l1, l2, w);
         for (int d = 0; d < 3; ++d) {
-            pa[q][d] = (R)l0 * va[0][d] + (R)l1 * va[1][d] + (R)l2 * va[2][d];
-            ua[q][d] = pa[q][d] - va[li][d];
-            pb[q][d] = (R)l0 * vb[0][d] + (R)l1 * vb[1][d] + (R)l2 * vb[2][d];
-            wbv[q][d] = pb[q][d] - vb[lj][d];
+            pb[q][d] = l0 * P.vb[0][d] + l1 * P.vb[1][d] + l2 * P.vb[2][d];
+            wbv[q][d] = pb[q][d] - P.vb[lj][d];
         }
-        wa[q] = (R)w * Aa;
-        wb[q] = (R)w * Ab;
+        wb[q] = w * P.Ab;
     }
-    const R k0 = (R)g.k0;
-    const R k1r = (R)g.k1.re, k1i = (R)g.k1.im;
+    const R k0 = M.k0, k1r = M.k1r, k1i = M.k1i;
     const R inv4pi = (R)(1.0 / (4.0 * BEM_PI));
     for (int s = 0; s < 2; ++s) ff[s] = i0[s] = kk[s] = mk<R>(0, 0);
 #pragma unroll 1
-    for (int p = 0; p < 7; ++p) {
+    for (int p = p_lo; p < p_hi; ++p) {
+        R pa[3], ua[3], wa;
+        {
+            R l0, l1, l2, w;
+            rule7<R>(p, l0, l1, l2, w);
+            for (int d = 0; d < 3; ++d) {
+                pa[d] = l0 * P.va[0][d] + l1 * P.va[1][d] + l2 * P.va[2][d];
+                ua[d] = pa[d] - P.va[li][d];
+            }
+            wa = w * P.Aa;
+        }
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
-            R d0 = pa[p][0] - pb[q][0], d1 = pa[p][1] - pb[q][1], d2 = pa[p][2] - pb[q][2];
+            R d0 = pa[0] - pb[q][0], d1 = pa[1] - pb[q][1], d2 = pa[2] - pb[q][2];
             R R2 = d0 * d0 + d1 * d1 + d2 * d2;
             R Rr = r_sqrt<R>(R2);
             R invR = (R)1 / Rr;
-            R W = wa[p] * wb[q] * inv4pi * invR;
+            R W = wa * wb[q] * inv4pi * invR;
             R fpq = 0, kpq = 0;
-            if (WANT_T) fpq = ua[p][0] * wbv[q][0] + ua[p][1] * wbv[q][1] + ua[p][2] * wbv[q][2];
+            if (WANT_T) fpq = ua[0] * wbv[q][0] + ua[1] * wbv[q][1] + ua[2] * wbv[q][2];
             if (WANT_K) {
                 // (r - v_i) . ((r - r') x (r' - v_j))
                 R c0 = d1 * wbv[q][2] - d2 * wbv[q][1];
                 R c1 = d2 * wbv[q][0] - d0 * wbv[q][2];
                 R c2 = d0 * wbv[q][1] - d1 * wbv[q][0];
-                kpq = ua[p][0] * c0 + ua[p][1] * c1 + ua[p][2] * c2;
+                kpq = ua[0] * c0 + ua[1] * c1 + ua[2] * c2;
             }
             // k0 (real)
             {
@@ -148,56 +214,95 @@ __device__ void regular_pair(const GeomDev& g, int a, int li, int b, int lj, cx<
     }
 }
 
-// Entries of A, B, C at RWG edges (m, n); OPS bit 0 = A, 1 = B, 2 = C.
+// T^_0, T^_1, K_0, K_1 contributions of the triangle pair (a with local basis li,
+// b with lj) over test points [p_lo, p_hi): the singular-pair table's FP64 local
+// matrix when the pair is listed (counted once, by the call with p_lo == 0), else
+// the product rule.  Only pairs whose centroids are closer than twice the larger
+// longest edge (with a margin for rounding) can be listed, so the table search is
+// skipped for the others.
+template <typename R, bool WT, bool WK>
+__device__ __forceinline__ void pair_terms(const GeomDev& g, int a, int li, int b, int lj, int p_lo, int p_hi,
+                                           cx<R>& T0, cx<R>& T1, cx<R>& K0, cx<R>& K1) {
+    PairGeom<R> P;
+    pair_geom<R>(g, a, b, P);
+    const R lim = (R)2 * P.dm;
+    const int slot = (P.d2 > lim * lim * (R)1.001) ? -1 : find_singular(g, a, b);
+    if (slot >= 0) {
+        if (p_lo != 0) return;
+        const c128* v = g.sing_val + (int64_t)slot * 36;
+        int ij = 3 * li + lj;
+        if (WT) {
+            T0 = T0 + mk<R>((R)v[ij].re, (R)v[ij].im);
+            T1 = T1 + mk<R>((R)v[18 + ij].re, (R)v[18 + ij].im);
+        }
+        if (WK) {
+            K0 = K0 + mk<R>((R)v[9 + ij].re, (R)v[9 + ij].im);
+            K1 = K1 + mk<R>((R)v[27 + ij].re, (R)v[27 + ij].im);
+        }
+        return;
+    }
+    const MediaConst<R>& M = media<R>(g);
+    cx<R> ff[2], i0[2], kk[2];
+    regular_pair<R, WT, WK>(P, M, li, lj, p_lo, p_hi, ff, i0, kk);
+    const R cc = P.ca[li] * P.cb[lj];
+    const R c1 = P.inv_AA * cc, c4 = (R)0.25 * c1;
+    if (WT) {
+        T0 = T0 + c4 * (M.jk0 * ff[0]) - c1 * (M.jok0 * i0[0]);
+        T1 = T1 + c4 * (M.jk1 * ff[1]) - c1 * (M.jok1 * i0[1]);
+    }
+    if (WK) {
+        K0 = K0 + c4 * kk[0];
+        K1 = K1 + c4 * kk[1];
+    }
+}
+
+// A = T^_0 + eta_r T^_1, B = K_0 + K_1, C = T^_0 + T^_1 / eta_r
+template <typename R>
+__device__ __forceinline__ void combine_ops(const GeomDev& g, int ops, cx<R> T0, cx<R> T1, cx<R> K0, cx<R> K1,
+                                            cx<R> out[3]) {
+    const MediaConst<R>& M = media<R>(g);
+    if (ops & 1) out[0] = T0 + M.er * T1;
+    if (ops & 2) out[1] = K0 + K1;
+    if (ops & 4) out[2] = T0 + M.ie * T1;
+}
+
+// Entries of A, B, C at RWG edges (m, n); OPS bit 0 = A, 1 = B, 2 = C.  One thread.
 template <typename R, int OPS>
 __device__ void eval_entry(const GeomDev& g, int m, int n, cx<R> out[3]) {
     constexpr bool WT = (OPS & 5) != 0;
     constexpr bool WK = (OPS & 2) != 0;
     cx<R> T0 = mk<R>(0, 0), T1 = T0, K0 = T0, K1 = T0;
-    const cx<R> jk0 = mk<R>(0, (R)g.k0);
-    const cx<R> jk1 = mk<R>(-(R)g.k1.im, (R)g.k1.re);
-    const cx<R> jok0 = mk<R>(0, (R)(1.0 / g.k0));
-    const c128 jok1d = cdiv(mk<double>(0.0, 1.0), g.k1);
-    const cx<R> jok1 = mk<R>((R)jok1d.re, (R)jok1d.im);
     for (int sa = 0; sa < 2; ++sa) {
         int a = g.edge_tri[2 * m + sa], li = g.edge_loc[2 * m + sa];
         for (int sb = 0; sb < 2; ++sb) {
             int b = g.edge_tri[2 * n + sb], lj = g.edge_loc[2 * n + sb];
-            int slot = find_singular(g, a, b);
-            if (slot >= 0) {
-                const c128* v = g.sing_val + (int64_t)slot * 36;
-                int ij = 3 * li + lj;
-                if (WT) {
-                    T0 = T0 + mk<R>((R)v[ij].re, (R)v[ij].im);
-                    T1 = T1 + mk<R>((R)v[18 + ij].re, (R)v[18 + ij].im);
-                }
-                if (WK) {
-                    K0 = K0 + mk<R>((R)v[9 + ij].re, (R)v[9 + ij].im);
-                    K1 = K1 + mk<R>((R)v[27 + ij].re, (R)v[27 + ij].im);
-                }
-            } else {
-                cx<R> ff[2], i0[2], kk[2];
-                regular_pair<R, WT, WK>(g, a, li, b, lj, ff, i0, kk);
-                double AA = g.area[a] * g.area[b];
-                R cc = (R)(g.tri_coef[3 * a + li] * g.tri_coef[3 * b + lj]);
-                R c4 = (R)(1.0 / (4.0 * AA)) * cc, c1 = (R)(1.0 / AA) * cc;
-                if (WT) {
-                    T0 = T0 + c4 * (jk0 * ff[0]) - c1 * (jok0 * i0[0]);
-                    T1 = T1 + c4 * (jk1 * ff[1]) - c1 * (jok1 * i0[1]);
-                }
-                if (WK) {
-                    K0 = K0 + c4 * kk[0];
-                    K1 = K1 + c4 * kk[1];
-                }
-            }
+            pair_terms<R, WT, WK>(g, a, li, b, lj, 0, 7, T0, T1, K0, K1);
         }
     }
-    const cx<R> er = mk<R>((R)g.eta_r.re, (R)g.eta_r.im);
-    const c128 ier = cdiv(mk<double>(1.0, 0.0), g.eta_r);
-    const cx<R> ie = mk<R>((R)ier.re, (R)ier.im);
-    if (OPS & 1) out[0] = T0 + er * T1;
-    if (OPS & 2) out[1] = K0 + K1;
-    if (OPS & 4) out[2] = T0 + ie * T1;
+    combine_ops<R>(g, OPS, T0, T1, K0, K1, out);
+}
+
+// Entry (m, n) of operator OP (0 = A, 1 = B, 2 = C) by one warp: lane L < 28 takes
+// the triangle pair (L / 14, (L / 7) mod 2) of the two supports at test point
+// L mod 7; the warp's sum, returned to every lane, is the entry.
+template <typename R, int OP>
+__device__ __forceinline__ cx<R> entry_warp(const GeomDev& g, int m, int n, int lane) {
+    constexpr bool WT = OP != 1, WK = OP == 1;
+    cx<R> T0 = mk<R>(0, 0), T1 = T0, K0 = T0, K1 = T0;
+    if (lane < 28) {
+        const int sa = lane / 14, sb = (lane / 7) & 1, p = lane % 7;
+        const int a = g.edge_tri[2 * m + sa], li = g.edge_loc[2 * m + sa];
+        const int b = g.edge_tri[2 * n + sb], lj = g.edge_loc[2 * n + sb];
+        pair_terms<R, WT, WK>(g, a, li, b, lj, p, p + 1, T0, T1, K0, K1);
+    }
+    cx<R> out[3];
+    combine_ops<R>(g, 1 << OP, T0, T1, K0, K1, out);
+    cx<R> v = out[OP];
+    for (int o = 16; o > 0; o >>= 1) {
+        v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+        v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+    }
+    return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -267,14 +372,8 @@ cudaError_t eval_entries(GeomDev g, const int* rows, const int* cols, int64_t co
 // ACA
 // ---------------------------------------------------------------------------
 #define ACA_THREADS 256
+#define ACA_THREADS_WIDE 1024
 #define ACA_RMAX 128
-
-template <typename R, int OP>
-__device__ __forceinline__ cx<R> entry_op(const GeomDev& g, int m, int n) {
-    cx<R> v[3];
-    eval_entry<R, (1 << OP)>(g, m, n, v);
-    return v[OP];
-}
 
 // block-wide argmax of val with smallest index on ties; returns (val, idx) to all threads
 __device__ __forceinline__ void argmax_merge(double& v, int& i, double v2, int i2) {
@@ -335,14 +434,15 @@ __device__ void aca_task(const GeomDev& g, const int64_t* __restrict__ perm, con
                          double tol, int* rank_out, int* flag_out) {
     extern __shared__ unsigned char used[];
     __shared__ cx<R> srow[ACA_RMAX];
-    __shared__ double sred[ACA_THREADS / 32];
-    __shared__ int sidx[ACA_THREADS / 32];
+    __shared__ double sred[32];
+    __shared__ int sidx[32];
     __shared__ double scross[ACA_RMAX][4];
     const int m = T.m, n = T.n, rmax = T.rmax;
     cx<R>* U = scratch + T.scratch;
     cx<R>* W = U + (int64_t)m * rmax;
     cx<R>* row = W + (int64_t)n * rmax;
     const int tid = threadIdx.x, bs = blockDim.x;
+    const int wid = tid >> 5, lane = tid & 31, nwarp = bs >> 5;
     for (int i = tid; i < m; i += bs) used[i] = 0;
     __syncthreads();
     int i = 0, k = 0;
@@ -352,12 +452,18 @@ __device__ void aca_task(const GeomDev& g, const int64_t* __restrict__ perm, con
         if (tid == 0) used[i] = 1;
         for (int l = tid; l < k; l += bs) srow[l] = U[(int64_t)l * m + i];
         __syncthreads();
-        // residual row i
+        // residual row i: entries by warps, then the rank-k update by threads
         double bv = -1.0;
         int bi = 0x7fffffff;
         const int em = (int)perm[T.r0 + i];
+        for (int j = wid; j < n; j += nwarp) {
+            cx<R> z = entry_warp<R, OP>(g, em, (int)perm[T.c0 + j], lane);
+            if (lane == 0) row[j] = z;
+        }
+        __syncthreads();
         for (int j = tid; j < n; j += bs) {
-            cx<R> z = entry_op<R, OP>(g, em, (int)perm[T.c0 + j]);
+            cx<R> z = row[j];
+#pragma unroll 4
             for (int l = 0; l < k; ++l) z = z - srow[l] * W[(int64_t)l * n + j];
             row[j] = z;
             argmax_merge(bv, bi, (double)cabs2(z), j);
@@ -394,27 +500,35 @@ __device__ void aca_task(const GeomDev& g, const int64_t* __restrict__ perm, con
         // residual column jp
         double nu2 = 0.0;
         const int en = (int)perm[T.c0 + jp];
+        for (int r = wid; r < m; r += nwarp) {
+            cx<R> z = entry_warp<R, OP>(g, (int)perm[T.r0 + r], en, lane);
+            if (lane == 0) U[(int64_t)k * m + r] = z;
+        }
+        __syncthreads();
         for (int r = tid; r < m; r += bs) {
-            cx<R> z = entry_op<R, OP>(g, (int)perm[T.r0 + r], en);
+            cx<R> z = U[(int64_t)k * m + r];
+#pragma unroll 4
             for (int l = 0; l < k; ++l) z = z - srow[l] * U[(int64_t)l * m + r];
             U[(int64_t)k * m + r] = z;
             nu2 += (double)cabs2(z);
         }
         nu2 = block_sum(nu2, sred);  // also orders the U/W writes before the cross products
         // cross terms (u_l^H u)(w_l^H w): one warp per l
-        const int wid = tid >> 5, lane = tid & 31, nwarp = bs >> 5;
         for (int l = wid; l < k; l += nwarp) {
-            double ur = 0, ui = 0, wr = 0, wi = 0;
+            // per-lane sums in the factors' arithmetic, across lanes in FP64 (the sums
+            // only steer the stopping test)
+            R ur_ = 0, ui_ = 0, wr_ = 0, wi_ = 0;
             for (int r = lane; r < m; r += 32) {
                 cx<R> a = U[(int64_t)l * m + r], b = U[(int64_t)k * m + r];
-                ur += (double)a.re * b.re + (double)a.im * b.im;
-                ui += (double)a.re * b.im - (double)a.im * b.re;
+                ur_ += a.re * b.re + a.im * b.im;
+                ui_ += a.re * b.im - a.im * b.re;
             }
             for (int j = lane; j < n; j += 32) {
                 cx<R> a = W[(int64_t)l * n + j], b = W[(int64_t)k * n + j];
-                wr += (double)a.re * b.re + (double)a.im * b.im;
-                wi += (double)a.re * b.im - (double)a.im * b.re;
+                wr_ += a.re * b.re + a.im * b.im;
+                wi_ += a.re * b.im - a.im * b.re;
             }
+            double ur = ur_, ui = ui_, wr = wr_, wi = wi_;
             for (int o = 16; o > 0; o >>= 1) {
                 ur += __shfl_xor_sync(0xffffffffu, ur, o);
                 ui += __shfl_xor_sync(0xffffffffu, ui, o);
@@ -460,33 +574,102 @@ __device__ void aca_task(const GeomDev& g, const int64_t* __restrict__ perm, con
     }
 }
 
+// CTAs per SM the register budget is sized for: the FP32 kernel fits 64 registers
+// per thread (four 256-thread CTAs per SM); the FP64 one keeps its registers.
 template <typename R>
-__global__ void __launch_bounds__(ACA_THREADS) k_aca(GeomDev g, const int64_t* __restrict__ perm,
-                                                     const AcaTask* __restrict__ tasks, cx<R>* scratch,
-                                                     double tol, int* ranks, int* flags) {
+struct AcaOccupancy {
+    static constexpr int ctas = 1;
+};
+template <>
+struct AcaOccupancy<float> {
+    static constexpr int ctas = 4;
+};
+
+// One CTA per task; one kernel per operator keeps each kernel's code small.
+template <typename R, int OP>
+__global__ void __launch_bounds__(ACA_THREADS, AcaOccupancy<R>::ctas)
+    k_aca(GeomDev g, const int64_t* __restrict__ perm, const AcaTask* __restrict__ tasks, cx<R>* scratch, double tol,
+          int* ranks, int* flags) {
     AcaTask T = tasks[blockIdx.x];
-    if (T.op == 0)
-        aca_task<R, 0>(g, perm, T, scratch, tol, ranks + blockIdx.x, flags + blockIdx.x);
-    else if (T.op == 1)
-        aca_task<R, 1>(g, perm, T, scratch, tol, ranks + blockIdx.x, flags + blockIdx.x);
-    else
-        aca_task<R, 2>(g, perm, T, scratch, tol, ranks + blockIdx.x, flags + blockIdx.x);
+    aca_task<R, OP>(g, perm, T, scratch, tol, ranks + blockIdx.x, flags + blockIdx.x);
 }
 
-template <typename R>
-cudaError_t aca_run(GeomDev g, const int64_t* perm, const AcaTask* tasks, int ntasks, cx<R>* scratch, double tol,
-                    int* ranks, int* flags, cudaStream_t st, int max_m) {
-    if (ntasks <= 0) return cudaSuccess;
+// The same with a whole SM (1024 threads) per task, for the few largest blocks:
+// a batch holds few of them, and each one's rows and columns are long enough to
+// keep 32 warps busy.  FP32 only.
+template <int OP>
+__global__ void __launch_bounds__(ACA_THREADS_WIDE, 1)
+    k_aca_wide(GeomDev g, const int64_t* __restrict__ perm, const AcaTask* __restrict__ tasks, c64* scratch,
+               double tol, int* ranks, int* flags) {
+    AcaTask T = tasks[blockIdx.x];
+    aca_task<float, OP>(g, perm, T, scratch, tol, ranks + blockIdx.x, flags + blockIdx.x);
+}
+
+template <typename K>
+static cudaError_t aca_smem_optin(K kernel, size_t smem) {
     // dynamic shared memory: one byte per block row; opt in when it and the kernel's
     // static shared memory together pass the default 48 KiB
-    size_t smem = (size_t)max_m;
     cudaFuncAttributes fa;
-    BEM_CUDA_TRY(cudaFuncGetAttributes(&fa, k_aca<R>));
-    if (smem + fa.sharedSizeBytes > 48 * 1024) {
-        BEM_CUDA_TRY(cudaFuncSetAttribute(k_aca<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess && smem + fa.sharedSizeBytes > 48 * 1024)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+}
+
+template <typename R, int OP>
+static cudaError_t aca_launch(GeomDev g, const int64_t* perm, const AcaTask* tasks, int ntasks, cx<R>* scratch,
+                              double tol, int* ranks, int* flags, cudaStream_t st, size_t smem, bool wide) {
+    if (ntasks <= 0) return cudaSuccess;
+    if constexpr (sizeof(R) == 4) {
+        if (wide) {
+            BEM_CUDA_TRY(aca_smem_optin(k_aca_wide<OP>, smem));
+            k_aca_wide<OP><<<ntasks, ACA_THREADS_WIDE, smem, st>>>(g, perm, tasks, scratch, tol, ranks, flags);
+            return cudaGetLastError();
+        }
     }
-    k_aca<R><<<ntasks, ACA_THREADS, smem, st>>>(g, perm, tasks, scratch, tol, ranks, flags);
+    if (wide) return cudaErrorInvalidValue;
+    BEM_CUDA_TRY(aca_smem_optin(k_aca<R, OP>, smem));
+    k_aca<R, OP><<<ntasks, ACA_THREADS, smem, st>>>(g, perm, tasks, scratch, tol, ranks, flags);
     return cudaGetLastError();
+}
+
+// Tasks are grouped as counts[6]: wide A, B, C (FP32 only), then ordinary A, B, C.
+// The wide kernels run on a second stream beside the ordinary ones.
+template <typename R>
+cudaError_t aca_run(GeomDev g, const int64_t* perm, const AcaTask* tasks, const int counts[6], cx<R>* scratch,
+                    double tol, int* ranks, int* flags, cudaStream_t st, int max_m) {
+    const size_t smem = (size_t)max_m;
+    int off[7] = {0};
+    for (int q = 0; q < 6; ++q) off[q + 1] = off[q] + counts[q];
+    const bool any_wide = off[3] > 0, any_norm = off[6] > off[3];
+    cudaStream_t side = st;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (any_wide && any_norm) {
+        e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_fork, 0);
+    }
+    for (int q = 0; q < 6 && e == cudaSuccess; ++q) {
+        const bool wide = q < 3;
+        const int op = q % 3;
+        cudaStream_t s = wide ? side : st;
+        const AcaTask* tq = tasks + off[q];
+        int *rq = ranks + off[q], *fq = flags + off[q];
+        if (op == 0) e = aca_launch<R, 0>(g, perm, tq, counts[q], scratch, tol, rq, fq, s, smem, wide);
+        if (op == 1) e = aca_launch<R, 1>(g, perm, tq, counts[q], scratch, tol, rq, fq, s, smem, wide);
+        if (op == 2) e = aca_launch<R, 2>(g, perm, tq, counts[q], scratch, tol, rq, fq, s, smem, wide);
+    }
+    if (side != st) {
+        if (e == cudaSuccess) e = cudaEventRecord(ev_join, side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_join, 0);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        cudaStreamDestroy(side);
+    }
+    return e;
 }
 
 // Copy the rank-r factors to the product layout (an odd rank is padded with a
@@ -546,9 +729,9 @@ template cudaError_t near_assemble<double>(GeomDev, const int64_t*, const BlockD
                                            int64_t, cudaStream_t);
 template cudaError_t eval_entries<float>(GeomDev, const int*, const int*, int64_t, c64*, cudaStream_t);
 template cudaError_t eval_entries<double>(GeomDev, const int*, const int*, int64_t, c128*, cudaStream_t);
-template cudaError_t aca_run<float>(GeomDev, const int64_t*, const AcaTask*, int, c64*, double, int*, int*,
+template cudaError_t aca_run<float>(GeomDev, const int64_t*, const AcaTask*, const int*, c64*, double, int*, int*,
                                     cudaStream_t, int);
-template cudaError_t aca_run<double>(GeomDev, const int64_t*, const AcaTask*, int, c128*, double, int*, int*,
+template cudaError_t aca_run<double>(GeomDev, const int64_t*, const AcaTask*, const int*, c128*, double, int*, int*,
                                      cudaStream_t, int);
 template cudaError_t aca_compact<float>(const AcaTask*, int, const c64*, const int*, const int64_t*,
                                         const int64_t*, c64*, const int*, const int*, cudaStream_t);

@@ -91,9 +91,11 @@ struct bem_ctx {
     DevBuf d_perm;
     // product plan (precision independent part)
     DevBuf d_leaf_r0, d_leaf_m, d_pos_leaf_lo, d_pos_leaf_m;
+    DevBuf d_trif;
     Operator op[2];
     bool assembled = false;
     double assemble_ms = 0;
+    double phase_ms[BEM_PHASES] = {0, 0, 0, 0, 0};
     // reductions and small transfers
     DevBuf d_part, d_red, d_tmp_in, d_one, d_gl;
     GmresWork gw;
@@ -155,9 +157,31 @@ static GeomDev geom_view(const bem_ctx* c) {
     g.sing_ptr = (const int*)c->d_sing_ptr.p;
     g.sing_b = (const int*)c->d_sing_b.p;
     g.sing_val = (const c128*)c->d_sing_val.p;
+    g.trif = (const TriF*)c->d_trif.p;
     g.k0 = c->k0;
     g.k1 = c->k1;
     g.eta_r = c->eta_r;
+    MediaConst<double> md;
+    md.k0 = c->k0;
+    md.k1r = c->k1.re;
+    md.k1i = c->k1.im;
+    md.jk0 = mk<double>(0.0, c->k0);
+    md.jk1 = mk<double>(-c->k1.im, c->k1.re);
+    md.jok0 = mk<double>(0.0, 1.0 / c->k0);
+    md.jok1 = cdiv(mk<double>(0.0, 1.0), c->k1);
+    md.er = c->eta_r;
+    md.ie = cdiv(mk<double>(1.0, 0.0), c->eta_r);
+    g.md = md;
+    auto f = [](c128 z) { return mk<float>((float)z.re, (float)z.im); };
+    g.mf.k0 = (float)md.k0;
+    g.mf.k1r = (float)md.k1r;
+    g.mf.k1i = (float)md.k1i;
+    g.mf.jk0 = f(md.jk0);
+    g.mf.jk1 = f(md.jk1);
+    g.mf.jok0 = f(md.jok0);
+    g.mf.jok1 = f(md.jok1);
+    g.mf.er = f(md.er);
+    g.mf.ie = f(md.ie);
     return g;
 }
 
@@ -237,7 +261,7 @@ extern "C" void bem_destroy(bem_ctx* c) {
     DevBuf* bufs[] = {&c->d_tv, &c->d_area, &c->d_nrm, &c->d_cen, &c->d_diam, &c->d_tvid, &c->d_tri_edge,
                       &c->d_tri_coef, &c->d_edge_tri, &c->d_edge_loc, &c->d_mid, &c->d_sing_ptr, &c->d_sing_b,
                       &c->d_sing_val, &c->d_perm, &c->d_leaf_r0, &c->d_leaf_m, &c->d_pos_leaf_lo,
-                      &c->d_pos_leaf_m, &c->d_part,
+                      &c->d_pos_leaf_m, &c->d_part, &c->d_trif,
                       &c->d_red, &c->d_tmp_in, &c->d_one, &c->d_gl, &c->gw.V, &c->gw.w, &c->gw.z, &c->gw.r,
                       &c->gw.xin, &c->gw.rin, &c->gw.hpart, &c->gw.hdev, &c->gw.npart};
     for (DevBuf* b : bufs) dfree(*b);
@@ -426,6 +450,26 @@ static bem_status upload_geometry(bem_ctx* c, cudaStream_t st) {
     CK(upload(c->d_edge_tri, c->edge_tri, st));
     CK(upload(c->d_edge_loc, c->edge_loc, st));
     CK(upload(c->d_mid, c->mid, st));
+    // FP32 triangle records
+    std::vector<TriF> tf(c->nt);
+    for (int64_t a = 0; a < c->nt; ++a) {
+        TriF& r = tf[a];
+        const double* cc = &c->cen[3 * a];
+        float hi[3], lo[3];
+        for (int d = 0; d < 3; ++d) {
+            hi[d] = (float)cc[d];
+            lo[d] = (float)(cc[d] - (double)hi[d]);
+        }
+        r.c_hi = make_float4(hi[0], hi[1], hi[2], (float)c->area[a]);
+        r.c_lo = make_float4(lo[0], lo[1], lo[2], (float)c->diam[a]);
+        for (int v = 0; v < 3; ++v) {
+            const double* p = &c->tv[9 * a + 3 * v];
+            r.v[v] = make_float4((float)(p[0] - cc[0]), (float)(p[1] - cc[1]), (float)(p[2] - cc[2]), 0.f);
+        }
+        r.coef = make_float4((float)c->tri_coef[3 * a], (float)c->tri_coef[3 * a + 1], (float)c->tri_coef[3 * a + 2],
+                             (float)(1.0 / c->area[a]));
+    }
+    CK(upload(c->d_trif, tf, st));
     return BEM_OK;
 }
 
@@ -579,17 +623,62 @@ static bem_status build_tree(bem_ctx* c, cudaStream_t st) {
 
 static bem_status build_singular(bem_ctx* c, cudaStream_t st) {
     const int nt = (int)c->nt;
-    DevBuf d_counts, d_pair_a;
+    DevBuf d_counts, d_pair_a, d_cell_start, d_cell_tri, d_tri_cell;
     struct Guard {
-        DevBuf* b[2];
+        DevBuf* b[5];
         ~Guard() {
             for (DevBuf* x : b) dfree(*x);
         }
-    } guard{{&d_counts, &d_pair_a}};
+    } guard{{&d_counts, &d_pair_a, &d_cell_start, &d_cell_tri, &d_tri_cell}};
+    // centroid grid: cell edge h > 2 x (longest edge), so a pair closer than twice
+    // the larger of its longest edges, or sharing a vertex, sits in adjacent cells
+    SingGrid G;
+    {
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, dmax = 0.0;
+        for (int a = 0; a < nt; ++a) {
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], c->cen[3 * a + d]);
+                hi[d] = std::max(hi[d], c->cen[3 * a + d]);
+            }
+            dmax = std::max(dmax, c->diam[a]);
+        }
+        double h = 2.0 * dmax * (1.0 + 1e-6) + 1e-300;
+        int dims[3];
+        for (;;) {
+            int64_t cells = 1;
+            for (int d = 0; d < 3; ++d) {
+                dims[d] = (int)std::floor((hi[d] - lo[d]) / h) + 1;
+                cells *= dims[d];
+            }
+            if (cells <= 4 * (int64_t)nt + 64) break;
+            h *= 1.5;
+        }
+        const int ncell = dims[0] * dims[1] * dims[2];
+        std::vector<int> tri_cell(nt), start(ncell + 1, 0), order(nt);
+        for (int a = 0; a < nt; ++a) {
+            int ci[3];
+            for (int d = 0; d < 3; ++d)
+                ci[d] = std::min(dims[d] - 1, std::max(0, (int)std::floor((c->cen[3 * a + d] - lo[d]) / h)));
+            tri_cell[a] = (ci[2] * dims[1] + ci[1]) * dims[0] + ci[0];
+            ++start[tri_cell[a] + 1];
+        }
+        for (int k = 0; k < ncell; ++k) start[k + 1] += start[k];
+        std::vector<int> fillp(start.begin(), start.end() - 1);
+        for (int a = 0; a < nt; ++a) order[fillp[tri_cell[a]]++] = a;
+        CK(upload(d_cell_start, start, st));
+        CK(upload(d_cell_tri, order, st));
+        CK(upload(d_tri_cell, tri_cell, st));
+        G.nx = dims[0];
+        G.ny = dims[1];
+        G.nz = dims[2];
+        G.cell_start = (const int*)d_cell_start.p;
+        G.cell_tri = (const int*)d_cell_tri.p;
+        G.tri_cell = (const int*)d_tri_cell.p;
+    }
     CK(dalloc(d_counts, sizeof(int) * nt));
     CK(dalloc(c->d_sing_ptr, sizeof(int) * (nt + 1)));
     GeomDev g = geom_view(c);
-    CK(singular_count(g, (int*)d_counts.p, st));
+    CK(singular_count(g, G, (int*)d_counts.p, st));
     CK(scan_exclusive((const int*)d_counts.p, (int*)c->d_sing_ptr.p, nt, (int*)c->d_sing_ptr.p + nt, st));
     std::vector<int> ptr(nt + 1);
     CK(cudaMemcpyAsync(ptr.data(), c->d_sing_ptr.p, sizeof(int) * (nt + 1), cudaMemcpyDeviceToHost, st));
@@ -598,7 +687,7 @@ static bem_status build_singular(bem_ctx* c, cudaStream_t st) {
     c->n_sing = total;
     CK(dalloc(c->d_sing_b, sizeof(int) * std::max<int64_t>(1, total)));
     g = geom_view(c);
-    CK(singular_fill(g, (const int*)c->d_sing_ptr.p, (int*)c->d_sing_b.p, st));
+    CK(singular_fill(g, G, (const int*)c->d_sing_ptr.p, (int*)c->d_sing_b.p, st));
     std::vector<int> pa(total);
     for (int a = 0; a < nt; ++a)
         for (int k = ptr[a]; k < ptr[a + 1]; ++k) pa[k] = a;
@@ -708,6 +797,12 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
     const size_t es = sizeof(cx<R>);
     GeomDev g = geom_view(c);
     const int64_t* perm = (const int64_t*)c->d_perm.p;
+    auto tp = std::chrono::steady_clock::now();
+    auto lap = [&](int phase) {
+        auto now = std::chrono::steady_clock::now();
+        c->phase_ms[phase] += std::chrono::duration<double, std::milli>(now - tp).count();
+        tp = now;
+    };
     // 1. ACA of the far blocks, in rounds; each round in batches bounded by a scratch
     //    budget.  A block's rank is capped at the break-even m n / (m + n) and at the
     //    user cap.  A block that does not reach the tolerance within the cap is split
@@ -745,30 +840,59 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
         for (int k = 0; k < 2; ++k) out.push_back({c->node_lo[ch + k], c->node_hi[ch + k] - c->node_lo[ch + k]});
         return true;
     };
-    const int64_t budget = (int64_t)(sizeof(R) == 4 ? 1 : 2) * (1ll << 30) / (int64_t)es;  // complex elements
+    // scratch budget per batch: 4 GiB (complex64) or 8 GiB (complex128), at most a
+    // quarter of the free device memory
+    int64_t budget_bytes = (int64_t)(sizeof(R) == 4 ? 4 : 8) << 30;
+    {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget_bytes = std::min<int64_t>(budget_bytes, (int64_t)fr / 4);
+    }
+    const int64_t budget = std::max<int64_t>(1, budget_bytes / (int64_t)es);  // complex elements
     const int rcap = c->opt.aca_max_rank;
     std::vector<BlockDesc> work = c->far_blocks;
     o.n_far_split = 0;
     while (!work.empty()) {
         const int nw = (int)work.size();
-        std::vector<int> ranks(3 * nw, 0), flags(3 * nw, 0), task_batch(3 * nw, 0);
-        std::vector<int64_t> task_off_u(3 * nw), task_off_v(3 * nw);
-        int tb = 0;
-        while (tb < 3 * nw) {
-            std::vector<AcaTask> tasks;
+        const int ntask = 3 * nw;  // task t: block t / 3, operator t % 3
+        std::vector<int> ranks(ntask, 0), flags(ntask, 0), task_batch(ntask, 0), rmax_of(ntask);
+        std::vector<int64_t> task_off_u(ntask), task_off_v(ntask), cost(ntask);
+        for (int t = 0; t < ntask; ++t) {
+            const BlockDesc& F = work[t / 3];
+            int even = (int)std::max<int64_t>(1, (int64_t)F.m * F.n / (F.m + F.n));
+            rmax_of[t] = std::min(rcap, std::min(even, std::min(F.m, F.n)));
+            cost[t] = (int64_t)(F.m + F.n) * rmax_of[t];
+        }
+        // largest tasks first: each batch is a run of this order, so its CTAs are
+        // scheduled longest-first and the batches holding the largest blocks come first
+        std::vector<int> order(ntask);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        size_t ob = 0;
+        while (ob < order.size()) {
+            std::vector<int> ids;
             int64_t scr = 0;
-            int max_m = 1;
-            int te = tb;
-            while (te < 3 * nw) {
-                const BlockDesc& F = work[te / 3];
-                int even = (int)std::max<int64_t>(1, (int64_t)F.m * F.n / (F.m + F.n));
-                int rmax = std::min(rcap, std::min(even, std::min(F.m, F.n)));
-                int64_t need = (int64_t)(F.m + F.n) * rmax + F.n;
-                if (!tasks.empty() && scr + need > budget) break;
-                tasks.push_back({F.r0, F.m, F.c0, F.n, te % 3, rmax, scr});
+            size_t oe = ob;
+            while (oe < order.size()) {
+                const int t = order[oe];
+                int64_t need = cost[t] + work[t / 3].n;
+                if (!ids.empty() && scr + need > budget) break;
+                ids.push_back(t);
                 scr += need;
+                ++oe;
+            }
+            // one kernel per (CTA width, operator): group the batch so, order kept
+            auto group = [&](int t) { return (sizeof(R) == 4 && cost[t] >= BEM_ACA_WIDE_COST ? 0 : 3) + t % 3; };
+            std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) { return group(x) < group(y); });
+            std::vector<AcaTask> tasks;
+            int counts[6] = {0, 0, 0, 0, 0, 0};
+            int max_m = 1;
+            scr = 0;
+            for (int t : ids) {
+                const BlockDesc& F = work[t / 3];
+                tasks.push_back({F.r0, F.m, F.c0, F.n, t % 3, rmax_of[t], scr});
+                scr += cost[t] + F.n;
+                ++counts[group(t)];
                 max_m = std::max(max_m, F.m);
-                ++te;
             }
             DevBuf d_tasks, d_scr, d_ranks, d_flags, d_ou, d_ov;
             struct G3 {
@@ -783,8 +907,8 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
             CK(dalloc(d_ranks, sizeof(int) * nt));
             CK(dalloc(d_flags, sizeof(int) * nt));
             {
-                cudaError_t e = aca_run<R>(g, perm, (const AcaTask*)d_tasks.p, nt, (cx<R>*)d_scr.p, c->opt.aca_tol,
-                                           (int*)d_ranks.p, (int*)d_flags.p, st, max_m);
+                cudaError_t e = aca_run<R>(g, perm, (const AcaTask*)d_tasks.p, counts, (cx<R>*)d_scr.p,
+                                           c->opt.aca_tol, (int*)d_ranks.p, (int*)d_flags.p, st, max_m);
                 if (e != cudaSuccess) {
                     char buf[256];
                     snprintf(buf, sizeof buf, "ACA batch (%d tasks, largest block %d rows, %lld scratch elements): %s",
@@ -796,21 +920,22 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
             CK(cudaMemcpyAsync(rk.data(), d_ranks.p, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
             CK(cudaMemcpyAsync(fl.data(), d_flags.p, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            // a block keeps its factors only if all three operators converged
-            for (int i = 0; i < nt; ++i) flags[tb + i] = fl[i];
+            // factors of a converged task are kept (a failed task stores nothing)
             std::vector<int64_t> ou(nt), ov(nt);
             int64_t len = 0;
             for (int i = 0; i < nt; ++i) {
+                const int t = ids[i];
+                flags[t] = fl[i];
                 int r = fl[i] ? 0 : rk[i];
                 int rp = r + (r & 1);
                 ou[i] = len;
                 len += (int64_t)tasks[i].m * rp;
                 ov[i] = len;
                 len += (int64_t)tasks[i].n * rp;
-                ranks[tb + i] = r;
-                task_off_u[tb + i] = ou[i];
-                task_off_v[tb + i] = ov[i];
-                task_batch[tb + i] = (int)batches.size();
+                ranks[t] = r;
+                task_off_u[t] = ou[i];
+                task_off_v[t] = ov[i];
+                task_batch[t] = (int)batches.size();
                 rk[i] = r;
             }
             CK(cudaMemcpyAsync(d_ranks.p, rk.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st));
@@ -825,7 +950,7 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
                               (const int64_t*)d_ou.p, (const int64_t*)d_ov.p, (cx<R>*)batches.back().arena.p,
                               (const int*)c->d_pos_leaf_lo.p, (const int*)c->d_pos_leaf_m.p, st));
             CK(cudaStreamSynchronize(st));
-            tb = te;
+            ob = oe;
         }
         std::vector<BlockDesc> next;
         std::vector<std::pair<int, int>> ct, cs;
@@ -856,6 +981,7 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
         }
         work.swap(next);
     }
+    lap(BEM_PHASE_ACA);
     // 2. dense items: leaf x leaf near blocks plus leaf x leaf far blocks above the rank cap
     o.items = c->near_blocks;
     o.far_desc.clear();
@@ -886,6 +1012,7 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
                             (cx<R>*)o.near.p, off, st));
         CK(cudaStreamSynchronize(st));
     }
+    lap(BEM_PHASE_NEAR);
     // 4. one factor arena
     std::vector<int64_t> base(batches.size() + 1, 0);
     for (size_t i = 0; i < batches.size(); ++i) base[i + 1] = base[i] + batches[i].len;
@@ -945,6 +1072,7 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
     if ((s = build_operator_plan(c, o, es, st)) != BEM_OK) return s;
     CK(dalloc(o.xp, es * 2 * c->ne * BEM_MAX_NR));
     CK(dalloc(o.t, es * std::max<int64_t>(1, o.t_len) * BEM_MAX_NR));
+    lap(BEM_PHASE_PLAN);
     o.built = true;
     return BEM_OK;
 }
@@ -955,11 +1083,18 @@ extern "C" bem_status bem_assemble(bem_ctx* c, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     invalidate(c);
+    for (double& p : c->phase_ms) p = 0.0;
     bem_status s;
     if ((s = upload_geometry(c, st)) != BEM_OK) return s;
     if ((s = build_tree(c, st)) != BEM_OK) return s;
-    if ((s = build_singular(c, st)) != BEM_OK) return s;
     if ((s = build_leaves(c, st)) != BEM_OK) return s;
+    CK(cudaStreamSynchronize(st));
+    auto t1 = std::chrono::steady_clock::now();
+    c->phase_ms[BEM_PHASE_TREE] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    if ((s = build_singular(c, st)) != BEM_OK) return s;
+    CK(cudaStreamSynchronize(st));
+    c->phase_ms[BEM_PHASE_SINGULAR] =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
     if (c->opt.precision & BEM_PREC_C64)
         if ((s = build_operator<float>(c, c->op[0], st)) != BEM_OK) return s;
     if (c->opt.precision & BEM_PREC_C128)
@@ -1014,6 +1149,7 @@ extern "C" bem_status bem_stats_get(const bem_ctx* cc, bem_stats* out) {
             out->matvec_bytes_c128 = bytes;
     }
     out->assemble_ms = c->assemble_ms;
+    for (int i = 0; i < BEM_PHASES; ++i) out->assemble_phase_ms[i] = c->phase_ms[i];
     return BEM_OK;
 }
 

@@ -12,6 +12,9 @@
 
 #define BEM_PI 3.14159265358979323846
 #define BEM_MAX_LEAF 64
+// ACA tasks whose scratch (m + n) * rank cap reaches this many elements get a whole
+// SM (1024 threads) in the FP32 build
+#define BEM_ACA_WIDE_COST (1 << 19)
 #define BEM_MAX_NR 8   // right-hand sides applied per pass over the operator
 #define BEM_ROW_GROUPS 1     // 64-thread groups per CTA of the rows kernel (one work slot each)
 #define BEM_ROW_TARGET_CTAS (48 * 152)  // rows-kernel CTAs aimed at per product (about 3 waves)
@@ -69,8 +72,29 @@ typedef cx<double> c128;
 // ---------------------------------------------------------------------------
 // device view of the mesh, media and singular-pair table
 // ---------------------------------------------------------------------------
+// Constants of the two media in the arithmetic of one precision (computed on the
+// host in FP64, so the quadrature kernels do no FP64 work in their FP32 build).
+template <typename R>
+struct MediaConst {
+    R k0, k1r, k1i;          // wavenumbers (k1 = k1r + j k1i, k1i <= 0)
+    cx<R> jk0, jk1;          // j k0, j k1
+    cx<R> jok0, jok1;        // j / k0, j / k1
+    cx<R> er, ie;            // eta_r = eta1 / eta0 and 1 / eta_r
+};
+
+// One triangle for the FP32 quadrature: the centroid split into a high and a low
+// float (centroid differences keep ~48 bits), the vertices relative to the
+// centroid, the signed edge coefficients and 1 / area.
+struct TriF {
+    float4 c_hi;  // x, y, z high parts; w = area
+    float4 c_lo;  // x, y, z low parts; w = longest edge
+    float4 v[3];  // vertex - centroid; w = 0
+    float4 coef;  // tri_coef[0..2]; w = 1 / area
+};
+
 struct GeomDev {
     int nt, ne;
+    const TriF* trif;        // nt FP32 triangle records
     const double* tv;        // nt x 9: vertices v0, v1, v2 of each triangle
     const double* area;      // nt
     const double* nrm;       // nt x 3 unit outward normal
@@ -89,7 +113,20 @@ struct GeomDev {
     double k0;
     c128 k1;
     c128 eta_r;
+    MediaConst<float> mf;
+    MediaConst<double> md;
 };
+
+template <typename R>
+__device__ __forceinline__ const MediaConst<R>& media(const GeomDev& g);
+template <>
+__device__ __forceinline__ const MediaConst<float>& media<float>(const GeomDev& g) {
+    return g.mf;
+}
+template <>
+__device__ __forceinline__ const MediaConst<double>& media<double>(const GeomDev& g) {
+    return g.md;
+}
 
 // Block descriptors (tree positions)
 struct BlockDesc {
@@ -131,8 +168,17 @@ cudaError_t tree_block_emit(const int* cand, int ncand, const int* kind, const i
 cudaError_t scan_exclusive(const int* in, int* out, int n, int* total_dev, cudaStream_t st);
 
 // singular.cu
-cudaError_t singular_count(GeomDev g, int* counts, cudaStream_t st);
-cudaError_t singular_fill(GeomDev g, const int* ptr, int* partners, cudaStream_t st);
+// Uniform grid of triangle centroids with cells no smaller than twice the longest
+// edge of the mesh: every singular partner of a triangle lies in its own or an
+// adjacent cell.
+struct SingGrid {
+    int nx, ny, nz;
+    const int* cell_start;  // nx ny nz + 1
+    const int* cell_tri;    // triangles sorted by cell
+    const int* tri_cell;    // nt: cell of each triangle
+};
+cudaError_t singular_count(GeomDev g, SingGrid G, int* counts, cudaStream_t st);
+cudaError_t singular_fill(GeomDev g, SingGrid G, const int* ptr, int* partners, cudaStream_t st);
 cudaError_t singular_values(GeomDev g, int npairs, const int* pair_a, c128* vals, cudaStream_t st);
 
 // assemble.cu
@@ -149,8 +195,8 @@ struct AcaTask {
     int64_t scratch;    // offset of this task's scratch (complex elements)
 };
 template <typename R>
-cudaError_t aca_run(GeomDev g, const int64_t* perm, const AcaTask* tasks, int ntasks, cx<R>* scratch, double tol,
-                    int* ranks, int* flags, cudaStream_t st, int max_m);
+cudaError_t aca_run(GeomDev g, const int64_t* perm, const AcaTask* tasks, const int counts[6], cx<R>* scratch,
+                    double tol, int* ranks, int* flags, cudaStream_t st, int max_m);
 // U is written slice-major (leaf slices of the block rows), W column-pair-major
 template <typename R>
 cudaError_t aca_compact(const AcaTask* tasks, int ntasks, const cx<R>* scratch, const int* ranks,

@@ -22,6 +22,26 @@ __device__ __forceinline__ void rule7_d(int q, double& l0, double& l1, double& l
     }
 }
 
+// the same rule in the arithmetic R (constants folded at compile time)
+template <typename R>
+__device__ __forceinline__ void rule7(int q, R& l0, R& l1, R& l2, R& w) {
+    constexpr double s = 3.872983346207416885;  // sqrt(15)
+    constexpr double a1 = (6.0 - s) / 21.0, b1 = 1.0 - 2.0 * a1;
+    constexpr double a2 = (6.0 + s) / 21.0, b2 = 1.0 - 2.0 * a2;
+    constexpr double w1 = (155.0 - s) / 1200.0, w2 = (155.0 + s) / 1200.0;
+    constexpr R third = (R)(1.0 / 3.0), w0 = (R)(9.0 / 40.0);
+    constexpr R A1 = (R)a1, B1 = (R)b1, A2 = (R)a2, B2 = (R)b2, W1 = (R)w1, W2 = (R)w2;
+    switch (q) {
+        case 0: l0 = l1 = l2 = third; w = w0; break;
+        case 1: l0 = B1; l1 = A1; l2 = A1; w = W1; break;
+        case 2: l0 = A1; l1 = B1; l2 = A1; w = W1; break;
+        case 3: l0 = A1; l1 = A1; l2 = B1; w = W1; break;
+        case 4: l0 = B2; l1 = A2; l2 = A2; w = W2; break;
+        case 5: l0 = A2; l1 = B2; l2 = A2; w = W2; break;
+        default: l0 = A2; l1 = A2; l2 = B2; w = W2; break;
+    }
+}
+
 struct d3 {
     double x, y, z;
 };

@@ -136,28 +136,59 @@ __device__ __forceinline__ bool is_singular(const GeomDev& g, int a, int b) {
     return d < 2.0 * fmax(g.diam[a], g.diam[b]);
 }
 
-__global__ void k_sing_count(GeomDev g, int* counts) {
+// Visit the triangles of the 27 cells around triangle a's cell.
+template <typename F>
+__device__ __forceinline__ void for_each_neighbour(const SingGrid& G, int a, F f) {
+    const int cid = G.tri_cell[a];
+    const int cx0 = cid % G.nx, cy0 = (cid / G.nx) % G.ny, cz0 = cid / (G.nx * G.ny);
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int cz = cz0 + dz;
+        if (cz < 0 || cz >= G.nz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int cy = cy0 + dy;
+            if (cy < 0 || cy >= G.ny) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int cx = cx0 + dx;
+                if (cx < 0 || cx >= G.nx) continue;
+                const int cell = (cz * G.ny + cy) * G.nx + cx;
+                for (int k = G.cell_start[cell]; k < G.cell_start[cell + 1]; ++k) f(G.cell_tri[k]);
+            }
+        }
+    }
+}
+
+__global__ void k_sing_count(GeomDev g, SingGrid G, int* counts) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= g.nt) return;
     int c = 0;
-    for (int b = 0; b < g.nt; ++b) c += is_singular(g, a, b);
+    for_each_neighbour(G, a, [&](int b) { c += is_singular(g, a, b); });
     counts[a] = c;
 }
 
-__global__ void k_sing_fill(GeomDev g, const int* ptr, int* partners) {
+// partners of a, ascending (insertion sort of the short list)
+__global__ void k_sing_fill(GeomDev g, SingGrid G, const int* ptr, int* partners) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= g.nt) return;
-    int o = ptr[a];
-    for (int b = 0; b < g.nt; ++b)
-        if (is_singular(g, a, b)) partners[o++] = b;
+    const int o = ptr[a];
+    int n = 0;
+    for_each_neighbour(G, a, [&](int b) {
+        if (is_singular(g, a, b)) {
+            int k = n++;
+            while (k > 0 && partners[o + k - 1] > b) {
+                partners[o + k] = partners[o + k - 1];
+                --k;
+            }
+            partners[o + k] = b;
+        }
+    });
 }
 
-cudaError_t singular_count(GeomDev g, int* counts, cudaStream_t st) {
-    k_sing_count<<<(g.nt + 127) / 128, 128, 0, st>>>(g, counts);
+cudaError_t singular_count(GeomDev g, SingGrid G, int* counts, cudaStream_t st) {
+    k_sing_count<<<(g.nt + 127) / 128, 128, 0, st>>>(g, G, counts);
     return cudaGetLastError();
 }
-cudaError_t singular_fill(GeomDev g, const int* ptr, int* partners, cudaStream_t st) {
-    k_sing_fill<<<(g.nt + 127) / 128, 128, 0, st>>>(g, ptr, partners);
+cudaError_t singular_fill(GeomDev g, SingGrid G, const int* ptr, int* partners, cudaStream_t st) {
+    k_sing_fill<<<(g.nt + 127) / 128, 128, 0, st>>>(g, G, ptr, partners);
     return cudaGetLastError();
 }
 

@@ -99,3 +99,24 @@ def test_debye_helper_matches_oracle(B):
         assert abs(B.bem_debye_eps(f) - debye.eps_r(f)) < 1e-12 * abs(debye.eps_r(f))
     p = [4.0, 50.0, 5.0, 8e-12, 0.1e-12]
     assert abs(B.bem_debye_eps(1e12, p) - debye.eps_r(1e12, *p)) < 1e-12 * 10
+
+
+def test_struct_layout_matches_header(B, tmp_path):
+    """The ctypes mirrors of bem_options and bem_stats have the C layout of bem.h."""
+    structs = {"bem_options": B.bem_options, "bem_stats": B.bem_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bem.h"', "int main(void) {"]
+    for sname, cls in structs.items():
+        lines.append(f'printf("{sname} size %zu\\n", sizeof({sname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{sname} {fname} %zu\\n", offsetof({sname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, out):
+        sname, what, val = line.split()
+        cls = structs[sname]
+        got = ctypes.sizeof(cls) if what == "size" else getattr(cls, what).offset
+        assert got == int(val), (sname, what, got, val)
