@@ -15,7 +15,12 @@ Reported beside the headline value:
   fp64_baseline the same product with the complex128 operator (plain FP64 GPU
                 form), and both products' error against the float64 oracle on
                 sampled rows of the dense product;
-  cpu_baseline  the oracle's on-the-fly dense rows, timed on the host cores.
+  cpu_baseline  the oracle's on-the-fly dense rows, timed on the host cores;
+  large         the 602,208-unknown lossy slab (10 x 10 x 1 wavelengths): products
+                with complex64 and with BF16 factors, their error on oracle rows,
+                a BF16-inner solve refined in FP64, and the 1/8-scale copy's
+                currents and absorbed power density against the stored oracle
+                solution.
 `--impl reference` times the oracle alone (the reference arm).
 """
 from __future__ import annotations
@@ -43,6 +48,13 @@ LEVEL = 5          # icosphere refinement: 20 * 4**LEVEL triangles (5 -> 20480)
 FALLBACK_HBM_GBS = 6800.0
 
 
+# the large workload: closed lossy slab 10 x 10 x 1 free-space wavelengths (k0 = 2 pi),
+# 204 x 204 x 21 face divisions: 200,736 triangles, 301,104 RWG edges, 602,208 unknowns
+SLAB = (10.0, 10.0, 1.0, 204, 204, 21)
+SLAB_K0 = 2.0 * math.pi
+SLAB_NAME = "slab-10x10x1lambda-204x204x21-200736tri-602208unk-k0=2pi-eps3.2-1.9j-leaf64-eta2-aca1e-4"
+
+
 def workload_name(level):
     nt = 20 * 4 ** level
     return f"sphere-ico{level}-{nt}tri-{3 * nt}unk-k0a10-eps3.2-1.9j-leaf64-eta2-aca1e-4"
@@ -61,13 +73,13 @@ def config_dict(extra=None):
 # ---------------------------------------------------------------------------
 # oracle timing (host cores)
 # ---------------------------------------------------------------------------
-def oracle_rows(g, x, rows, threads):
+def oracle_rows(g, x, rows, threads, k0=K0):
     from oracle import operators as O
 
     chunks = [rows[i::threads] for i in range(threads) if len(rows[i::threads])]
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=len(chunks)) as ex:
-        parts = list(ex.map(lambda r: (r, O.pmchwt_rows_apply(g, K0, EPS, x, r)), chunks))
+        parts = list(ex.map(lambda r: (r, O.pmchwt_rows_apply(g, k0, EPS, x, r)), chunks))
     dt = time.perf_counter() - t0
     out = {}
     for r, v in parts:
@@ -396,6 +408,133 @@ def run_native(args, rank, world, dist):
                                    "sample": f"{len(rows)} of {2 * g.ne} rows of the dense float64 PMCHWT product, "
                                              f"evaluated on the fly (numpy, {threads} threads), {dt:.1f} s",
                                    "error_metric": "max |y_gpu - y_oracle| over sampled rows / rms(y_gpu)"}
+        if not args.no_large:
+            out["large"] = run_large(args, dev, stream, B, W, peak, not args.no_cpu_baseline)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# large workload: the slab
+# ---------------------------------------------------------------------------
+def run_large(args, dev, stream, B, W, peak, with_oracle):
+    """Products of the 602,208-unknown slab with complex64 and with BF16 factors,
+    per-kernel bandwidth, error against oracle rows, and a BF16-inner refined solve
+    with its absorbed power; plus the 1/8-scale copy against the stored oracle
+    solution (absorbed power and its per-triangle density)."""
+    import torch
+
+    sp = stream.cuda_stream
+    v, t = W.box_mesh(*SLAB)
+    opt = B.bem_default_options()
+    opt.precision = B.BEM_PREC_C64 | B.BEM_PREC_BF16F
+    opt.leaf_size, opt.eta, opt.aca_tol = LEAF, ETA, ACA_TOL
+    opt.tol, opt.refine_tol, opt.maxit, opt.gmres_restart = 1e-3, 1e-6, 5000, 80
+    h = B.bem_create(opt)
+    B.bem_set_mesh(h, v, t)
+    B.bem_set_media(h, SLAB_K0, EPS)
+    t0 = time.perf_counter()
+    B.bem_assemble(h, sp)
+    torch.cuda.synchronize(dev)
+    asm_ms = (time.perf_counter() - t0) * 1e3
+    st = B.bem_stats_get(h)
+    n = B.bem_num_unknowns(h)
+    x = W.complex_normal(n, seed=0).astype(np.complex64)
+    xd = torch.from_numpy(x).to(dev)
+    out = {"workload": SLAB_NAME, "unknowns": n, "triangles": len(t),
+           "assembly": {"ms": round(asm_ms, 1), "phases_ms": {k: round(val, 1) for k, val in st["assemble_phase_ms"].items()},
+                        "near_entries_per_op": st["near_entries"], "factor_entries": st["factor_entries"],
+                        "far_blocks": st["n_far"], "far_blocks_split": st["n_far_split"],
+                        "blocks_factored": st["n_far_factored"], "far_blocks_dense": st["n_far_dense"],
+                        "max_rank": st["max_rank"]}}
+    ys = {}
+    K = max(10, args.steps // 40)
+    for dtype, label, total_key, kern_key in ((B.BEM_C64, "complex64", "matvec_bytes_c64", "kernel_bytes_c64"),
+                                              (B.BEM_C64_BF16F, "bf16_factors", "matvec_bytes_bf16f",
+                                               "kernel_bytes_bf16f")):
+        yd = torch.empty_like(xd)
+        for _ in range(3):
+            B.bem_matvec(h, xd.data_ptr(), yd.data_ptr(), 1, dtype, sp)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        B.bem_profile_begin(h)
+        e0.record(stream)
+        for _ in range(K):
+            B.bem_matvec(h, xd.data_ptr(), yd.data_ptr(), 1, dtype, sp)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        kms, kcnt = B.bem_profile_end(h)
+        ms = e0.elapsed_time(e1) / K
+        kb = st[kern_key]
+        gbs = st[total_key] / (ms * 1e-3) / 1e9
+        out[label] = {"matvecs_per_s": round(1e3 / ms, 2), "ms_per_step": round(ms, 4), "steps": K,
+                      "bytes_per_product": int(st[total_key]), "hbm_gbps_algorithmic": round(gbs, 1),
+                      "hbm_frac_of_peak": round(gbs / peak, 4),
+                      "kernels": {B.KERNEL_NAMES[i]: {"mean_ms": round(kms[i] / max(1, kcnt[i]), 4),
+                                                      "GBps": round(kb[i] / (kms[i] / max(1, kcnt[i]) * 1e-3) / 1e9, 1)
+                                                      if kms[i] > 0 else None} for i in range(3)}}
+        ys[label] = yd.cpu().numpy().astype(np.complex128)
+    if with_oracle:
+        from oracle import rwg
+
+        g = rwg.build(v, t)
+        rows = sample_rows(g.ne, 16)
+        ref, dt = oracle_rows(g, x.astype(np.complex128), rows, min(os.cpu_count() or 1, 16), k0=SLAB_K0)
+        for label, y in ys.items():
+            scale = float(np.sqrt(np.mean(np.abs(y) ** 2)))
+            out[label]["rel_err_vs_oracle"] = float(np.abs(y[rows] - ref).max() / scale)
+        out["oracle_rows"] = {"rows": len(rows), "seconds": round(dt, 1)}
+    # solve: BF16-factor GMRES (tol 1e-3 per step) inside FP64 refinement on the complex64 operator
+    bd = torch.empty(n, dtype=torch.complex128, device=dev)
+    B.bem_rhs_planewave(h, [0.0, 0.0, -1.0], [1.0, 0.0, 0.0], bd.data_ptr(), B.BEM_C128, sp)
+    xs = torch.zeros_like(bd)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    it, relres, status = B.bem_solve(h, bd.data_ptr(), xs.data_ptr(), 1, sp, raise_on_noconv=False)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    pa, pe, ps = B.bem_power(h, xs.data_ptr(), bd.data_ptr(), 1, sp)
+    out["solve"] = {"form": "BF16-factor GMRES (tol 1e-3) inside FP64 refinement to 1e-6 (complex64 operator)",
+                    "seconds": round(dt, 3), "iterations": it, "relative_residual": float(relres[0]),
+                    "converged": status == 0, "p_abs": pa[0], "p_ext": pe[0], "p_sca": ps[0]}
+    B.bem_destroy(h)
+    # the 1/8-scale copy against the stored oracle solution
+    gold = os.path.join(ROOT, "tests", "golden", "slab_eighth_oracle.npz")
+    if os.path.exists(gold):
+        d = np.load(gold)
+        dims = [float(a) if i < 3 else int(a) for i, a in enumerate(d["dims"])]
+        v8, t8 = W.box_mesh(*dims)
+        res8 = {"mesh": "1/8-scale slab 1.25x1.25x1 lambda, 26x26x21, %d unknowns" % d["x"].shape[0]}
+        for aca in (1e-4, 1e-5):
+            o8 = B.bem_default_options()
+            o8.precision = B.BEM_PREC_C64 | B.BEM_PREC_BF16F
+            o8.leaf_size, o8.eta, o8.aca_tol = LEAF, ETA, aca
+            o8.tol, o8.refine_tol, o8.maxit = 1e-3, 1e-9, 5000
+            h8 = B.bem_create(o8)
+            B.bem_set_mesh(h8, v8, t8)
+            B.bem_set_media(h8, float(d["k0"]), complex(d["eps_r"]))
+            B.bem_assemble(h8, sp)
+            n8 = B.bem_num_unknowns(h8)
+            b8 = torch.empty(n8, dtype=torch.complex128, device=dev)
+            B.bem_rhs_planewave(h8, d["khat"].tolist(), d["e0"].tolist(), b8.data_ptr(), B.BEM_C128, sp)
+            x8 = torch.zeros_like(b8)
+            t0 = time.perf_counter()
+            it8, rr8, s8 = B.bem_solve(h8, b8.data_ptr(), x8.data_ptr(), 1, sp, raise_on_noconv=False)
+            torch.cuda.synchronize(dev)
+            dt8 = time.perf_counter() - t0
+            pa8, pe8, _ = B.bem_power(h8, x8.data_ptr(), b8.data_ptr(), 1, sp)
+            dens = torch.empty(len(t8), dtype=torch.float64, device=dev)
+            B.bem_power_density(h8, x8.data_ptr(), dens.data_ptr(), sp)
+            torch.cuda.synchronize(dev)
+            xh8 = x8.cpu().numpy()
+            ne8 = n8 // 2
+            relv = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
+            res8[f"aca{aca:g}"] = {"seconds": round(dt8, 3), "iterations": it8, "relative_residual": float(rr8[0]),
+                                   "err_J": relv(xh8[:ne8], d["x"][:ne8]), "err_M": relv(xh8[ne8:], d["x"][ne8:]),
+                                   "err_p_abs": abs(pa8[0] - float(d["p_abs"])) / abs(float(d["p_abs"])),
+                                   "err_density": relv(dens.cpu().numpy(), d["density"])}
+            B.bem_destroy(h8)
+        out["eighth_scale_vs_oracle"] = res8
     return out
 
 
@@ -438,6 +577,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=8, help="oracle rows per step of the reference arm")
     ap.add_argument("--no-fp64", action="store_true", help="skip the complex128 GPU comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--no-large", action="store_true", help="skip the 602,208-unknown slab")
     ap.add_argument("--level", type=int, default=5,
                     help="icosphere level (5 = the 61440-unknown workload; smaller levels for profiling captures)")
     args = ap.parse_args()

@@ -75,10 +75,13 @@ typedef enum {
 /* Precision of the stored operator (bit mask for bem_options.precision). */
 #define BEM_PREC_C64 1   /* near entries and factors in complex64, FP32 arithmetic */
 #define BEM_PREC_C128 2  /* near entries and factors in complex128, FP64 arithmetic */
+#define BEM_PREC_BF16F 4 /* the complex64 operator also keeps a BF16 copy of its far factors (4 bytes per
+                            complex value; products in FP32); implies BEM_PREC_C64 */
 
 /* Element type of a vector argument. */
 #define BEM_C64 0
 #define BEM_C128 1
+#define BEM_C64_BF16F 2  /* complex64 vectors; bem_matvec uses the complex64 near entries and the BF16 factors */
 
 typedef struct {
     int precision;       /* bit mask of BEM_PREC_*: which operators bem_assemble builds (default C64) */
@@ -125,6 +128,8 @@ typedef struct {
                                      gather: x read + permuted copy written; vhx: V factors + x;
                                      rows: dense entries + U factors + x + y */
     int64_t kernel_bytes_c128[3]; /* same for complex128 */
+    int64_t matvec_bytes_bf16f;   /* same as matvec_bytes_c64 with the factors read as BF16 (BEM_C64_BF16F) */
+    int64_t kernel_bytes_bf16f[3]; /* same as kernel_bytes_c64 for BEM_C64_BF16F */
     double assemble_ms;         /* wall time of the last bem_assemble */
     double assemble_phase_ms[BEM_PHASES]; /* its parts: see BEM_PHASE_* (ACA, near and plan summed over precisions) */
 } bem_stats;
@@ -200,7 +205,9 @@ bem_status bem_eval_entries(bem_ctx* ctx, const int32_t* rows, const int32_t* co
                             void* out, int dtype, void* stream);
 
 /* y = Z x for nrhs vectors.  x, y: device, 2ne x nrhs complex of type `dtype`
- * (BEM_C64 or BEM_C128, needing the operator of that precision); x and y must not
+ * (BEM_C64, BEM_C128 or BEM_C64_BF16F, needing the operator of that precision:
+ * BEM_PREC_C64, BEM_PREC_C128 or BEM_PREC_BF16F; BEM_C64_BF16F vectors are
+ * complex64); x and y must not
  * overlap.  Asynchronous on `stream`; no allocation after the first call with a
  * given nrhs.  The product reads each dense entry and each factor once per call. */
 bem_status bem_matvec(bem_ctx* ctx, const void* x, void* y, int nrhs, int dtype, void* stream);
@@ -222,10 +229,12 @@ bem_status bem_rhs_planewave(bem_ctx* ctx, const double* khat, const bem_c128* e
                              void* b, int dtype, void* stream);
 
 /* Solve Z x = b for nrhs right-hand sides, b and x device complex128 2ne x nrhs.
- * Inner solver: restarted GMRES on the complex64 operator when it exists (else the
- * complex128 one) with FP64 inner products; if refine_tol > 0 an outer loop
- * recomputes r = b - Z x with the complex128 operator (which must be assembled) and
- * corrects x until |r|/|b| <= refine_tol.  x is used as the initial guess.
+ * Inner solver: restarted GMRES with FP64 inner products on the least precise
+ * operator assembled (BF16 factors, else complex64, else complex128); if
+ * refine_tol > 0 an outer loop recomputes r = b - Z x with FP64 vectors and sums
+ * through the most precise operator assembled (complex128 entries, else the
+ * complex64 entries and FP32 factors) and corrects x until |r|/|b| <= refine_tol.
+ * x is used as the initial guess.
  * iters (host, may be NULL): total inner iterations; relres (host, may be NULL):
  * final relative residual per right-hand side (nrhs doubles), measured with the
  * most accurate operator available.  Synchronises `stream`.  BEM_ENOCONV if any

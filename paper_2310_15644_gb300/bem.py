@@ -16,8 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbem.so")
 
 BEM_OK, BEM_EINVAL, BEM_ENOMEM, BEM_ECUDA, BEM_ENOCONV, BEM_ETIMEOUT, BEM_ESTATE = range(7)
-BEM_PREC_C64, BEM_PREC_C128 = 1, 2
-BEM_C64, BEM_C128 = 0, 1
+BEM_PREC_C64, BEM_PREC_C128, BEM_PREC_BF16F = 1, 2, 4
+BEM_C64, BEM_C128, BEM_C64_BF16F = 0, 1, 2
 STATUS_NAMES = {0: "BEM_OK", 1: "BEM_EINVAL", 2: "BEM_ENOMEM", 3: "BEM_ECUDA", 4: "BEM_ENOCONV",
                 5: "BEM_ETIMEOUT", 6: "BEM_ESTATE"}
 
@@ -52,7 +52,8 @@ class bem_stats(ctypes.Structure):
         ("near_entries", ctypes.c_int64), ("factor_entries", ctypes.c_int64 * 3), ("max_rank", ctypes.c_int64),
         ("singular_pairs", ctypes.c_int64), ("matvec_bytes_c64", ctypes.c_int64),
         ("matvec_bytes_c128", ctypes.c_int64), ("kernel_bytes_c64", ctypes.c_int64 * 3),
-        ("kernel_bytes_c128", ctypes.c_int64 * 3), ("assemble_ms", ctypes.c_double),
+        ("kernel_bytes_c128", ctypes.c_int64 * 3),
+        ("matvec_bytes_bf16f", ctypes.c_int64), ("kernel_bytes_bf16f", ctypes.c_int64 * 3), ("assemble_ms", ctypes.c_double),
         ("assemble_phase_ms", ctypes.c_double * 5),
     ]
 
@@ -181,7 +182,7 @@ def bem_stats_get(ctx) -> dict:
     s = bem_stats()
     _check(ctx, lib.bem_stats_get(ctx, ctypes.byref(s)))
     d = {name: getattr(s, name) for name, _ in bem_stats._fields_}
-    for k in ("factor_entries", "kernel_bytes_c64", "kernel_bytes_c128"):
+    for k in ("factor_entries", "kernel_bytes_c64", "kernel_bytes_c128", "kernel_bytes_bf16f"):
         d[k] = list(getattr(s, k))
     d["assemble_phase_ms"] = dict(zip(PHASE_NAMES, s.assemble_phase_ms))
     return d

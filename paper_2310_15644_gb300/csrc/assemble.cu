@@ -373,6 +373,7 @@ cudaError_t eval_entries(GeomDev g, const int* rows, const int* cols, int64_t co
 // ---------------------------------------------------------------------------
 #define ACA_THREADS 256
 #define ACA_THREADS_WIDE 1024
+#define ACA_MAX_CHECKS 8  // sampled-row checks per task before the stopping test is accepted
 #define ACA_RMAX 128
 
 // block-wide argmax of val with smallest index on ties; returns (val, idx) to all threads
@@ -437,6 +438,8 @@ __device__ void aca_task(const GeomDev& g, const int64_t* __restrict__ perm, con
     __shared__ double sred[32];
     __shared__ int sidx[32];
     __shared__ double scross[ACA_RMAX][4];
+    __shared__ int vis[ACA_RMAX + ACA_MAX_CHECKS + 1];  // rows visited (pivot, zero or checked), ascending
+    __shared__ int nvis, s_check;
     const int m = T.m, n = T.n, rmax = T.rmax;
     cx<R>* U = scratch + T.scratch;
     cx<R>* W = U + (int64_t)m * rmax;
@@ -444,31 +447,57 @@ __device__ void aca_task(const GeomDev& g, const int64_t* __restrict__ perm, con
     const int tid = threadIdx.x, bs = blockDim.x;
     const int wid = tid >> 5, lane = tid & 31, nwarp = bs >> 5;
     for (int i = tid; i < m; i += bs) used[i] = 0;
+    if (tid == 0) nvis = 0;
     __syncthreads();
-    int i = 0, k = 0;
-    double norm2 = 0.0;
-    bool converged = false;
-    while (k < rmax) {
-        if (tid == 0) used[i] = 1;
-        for (int l = tid; l < k; l += bs) srow[l] = U[(int64_t)l * m + i];
+    // mark row r visited (thread 0; callers synchronise); the ordered list keeps the
+    // first rows visited if it fills up (only the choice of check rows uses it)
+    auto visit = [&](int r) {
+        if (used[r]) return;
+        used[r] = 1;
+        if (nvis >= ACA_RMAX + ACA_MAX_CHECKS + 1) return;
+        int q = nvis++;
+        while (q > 0 && vis[q - 1] > r) {
+            vis[q] = vis[q - 1];
+            --q;
+        }
+        vis[q] = r;
+    };
+    // residual of row r after k terms into row[]; returns its squared norm and the
+    // position and size of its largest entry (all threads)
+    auto residual_row = [&](int r, int kk, double& bv, int& bi) -> double {
+        for (int l = tid; l < kk; l += bs) srow[l] = U[(int64_t)l * m + r];
         __syncthreads();
-        // residual row i: entries by warps, then the rank-k update by threads
-        double bv = -1.0;
-        int bi = 0x7fffffff;
-        const int em = (int)perm[T.r0 + i];
+        const int em = (int)perm[T.r0 + r];
         for (int j = wid; j < n; j += nwarp) {
             cx<R> z = entry_warp<R, OP>(g, em, (int)perm[T.c0 + j], lane);
             if (lane == 0) row[j] = z;
         }
         __syncthreads();
+        bv = -1.0;
+        bi = 0x7fffffff;
+        double e2 = 0.0;
         for (int j = tid; j < n; j += bs) {
             cx<R> z = row[j];
 #pragma unroll 4
-            for (int l = 0; l < k; ++l) z = z - srow[l] * W[(int64_t)l * n + j];
+            for (int l = 0; l < kk; ++l) z = z - srow[l] * W[(int64_t)l * n + j];
             row[j] = z;
-            argmax_merge(bv, bi, (double)cabs2(z), j);
+            const double a2 = (double)cabs2(z);
+            e2 += a2;
+            argmax_merge(bv, bi, a2, j);
         }
         block_argmax(bv, bi, sred, sidx);
+        return block_sum(e2, sred);
+    };
+    int i = 0, k = 0, checks = 0;
+    double norm2 = 0.0;
+    bool converged = false;
+    while (k < rmax) {
+        if (tid == 0) visit(i);
+        __syncthreads();
+        // residual row i: entries by warps, then the rank-k update by threads
+        double bv;
+        int bi;
+        residual_row(i, k, bv, bi);
         if (!(bv > 0.0)) {
             // zero residual row: move to the first unused row
             int fi = 0x7fffffff;
@@ -553,8 +582,47 @@ __device__ void aca_task(const GeomDev& g, const int64_t* __restrict__ perm, con
         __syncthreads();
         ++k;
         if (sqrt(nu2 * nw2) <= tol * sqrt(fmax(norm2, 0.0))) {
-            converged = true;
-            break;
+            // The partial-pivot criterion only sees the rows it has visited: a block
+            // whose entries vanish on a sub-block (the double-layer kernel between
+            // coplanar faces of a box, say) can look converged while a whole group
+            // of rows is still missing.  Before stopping, the residual of the unvisited
+            // row farthest (in tree order) from every visited row is computed; if
+            // its energy exceeds the per-row share tol^2 |S|^2 / m of the tolerance,
+            // that row becomes the next pivot row.
+            int resume = -1;
+            while (resume < 0 && checks < ACA_MAX_CHECKS) {
+                if (tid == 0) {
+                    int best = -1, bd = 0;
+                    if (vis[0] > 0) {
+                        best = 0;
+                        bd = vis[0];
+                    }
+                    for (int q = 0; q + 1 < nvis; ++q) {
+                        const int gap = vis[q + 1] - vis[q];
+                        if (gap >= 2 && gap / 2 > bd) {
+                            best = vis[q] + gap / 2;
+                            bd = gap / 2;
+                        }
+                    }
+                    if (vis[nvis - 1] < m - 1 && m - 1 - vis[nvis - 1] > bd) best = m - 1;
+                    s_check = best;
+                    if (best >= 0) visit(best);
+                }
+                __syncthreads();
+                const int ic = s_check;
+                if (ic < 0) break;
+                ++checks;
+                double cv;
+                int ci;
+                const double e2 = residual_row(ic, k, cv, ci);
+                if (e2 > tol * tol * fmax(norm2, 0.0) / m) resume = ic;
+            }
+            if (resume < 0) {
+                converged = true;
+                break;
+            }
+            i = resume;
+            continue;
         }
         // next row: largest |u| among unused rows
         double cv = -1.0;

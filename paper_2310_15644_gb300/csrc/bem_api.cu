@@ -48,6 +48,8 @@ struct Operator {
     DevBuf d_work_ptr, d_work_item, d_near_c0, d_near_n, d_near_off, d_farp_blk, d_farp_row, d_ypart, d_arrive;
     DevBuf near;          // 3 * near_stride complex
     DevBuf arena;         // low-rank factors
+    DevBuf arena_bf16;    // BF16 copy of the factors (complex64 operator, BEM_PREC_BF16F)
+    int64_t arena_len = 0;
     DevBuf far_rec;       // FarRec[nfar]
     DevBuf far_order;     // int2[nvhx]: V^H x units
     DevBuf xp, t;         // product workspace
@@ -138,7 +140,11 @@ static cudaError_t ensure(DevBuf& b, size_t bytes) {
     return dalloc(b, bytes);
 }
 
-static int esize_of(int dtype) { return dtype == BEM_C64 ? 8 : 16; }
+// internal product dtype: complex128 vectors, complex64 operator, FP64 sums
+#define DT_C64_IN_FP64 100
+static int esize_of(int dtype) { return (dtype == BEM_C128 || dtype == DT_C64_IN_FP64) ? 16 : 8; }
+// element type of the vectors of a product dtype
+static int vec_dtype(int dtype) { return dtype == BEM_C64_BF16F ? BEM_C64 : dtype; }
 
 static GeomDev geom_view(const bem_ctx* c) {
     GeomDev g;
@@ -204,6 +210,8 @@ static void release_operator(Operator& o) {
     o.near_stride = 0;
     dfree(o.near);
     dfree(o.arena);
+    dfree(o.arena_bf16);
+    o.arena_len = 0;
     dfree(o.far_rec);
     dfree(o.far_order);
     dfree(o.xp);
@@ -243,8 +251,8 @@ extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
     bem_options o;
     bem_default_options(&o);
     if (opt) o = *opt;
-    if (o.leaf_size < 2 || o.leaf_size > BEM_MAX_LEAF || (o.precision & 3) == 0 || o.aca_tol <= 0 ||
-        o.aca_max_rank < 1 || o.aca_max_rank > 128 || o.gmres_restart < 1 || o.gmres_restart > 200 || o.maxit < 1 ||
+    if (o.leaf_size < 2 || o.leaf_size > BEM_MAX_LEAF || (o.precision & 7) == 0 || (o.precision & ~7) != 0 ||
+        o.aca_tol <= 0 || o.aca_max_rank < 1 || o.aca_max_rank > 128 || o.gmres_restart < 1 || o.gmres_restart > 200 || o.maxit < 1 ||
         o.tol <= 0 || o.refine_tol < 0 || o.refine_maxit < 1)
         return BEM_EINVAL;
     bem_ctx* c = new (std::nothrow) bem_ctx();
@@ -1022,6 +1030,14 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
             CK(cudaMemcpyAsync((char*)o.arena.p + es * base[i], batches[i].arena.p, es * batches[i].len,
                                cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
+    o.arena_len = base.back();
+    if constexpr (sizeof(R) == 4) {
+        if (c->opt.precision & BEM_PREC_BF16F) {
+            CK(dalloc(o.arena_bf16, sizeof(bf16c) * std::max<int64_t>(1, o.arena_len)));
+            CK(factors_to_bf16((const c64*)o.arena.p, (bf16c*)o.arena_bf16.p, o.arena_len, st));
+            CK(cudaStreamSynchronize(st));
+        }
+    }
     // 5. records of the blocks kept as factors
     const int nkeep = (int)kept.size();
     o.recs.resize(nkeep);
@@ -1095,7 +1111,7 @@ extern "C" bem_status bem_assemble(bem_ctx* c, void* stream) {
     CK(cudaStreamSynchronize(st));
     c->phase_ms[BEM_PHASE_SINGULAR] =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
-    if (c->opt.precision & BEM_PREC_C64)
+    if (c->opt.precision & (BEM_PREC_C64 | BEM_PREC_BF16F))
         if ((s = build_operator<float>(c, c->op[0], st)) != BEM_OK) return s;
     if (c->opt.precision & BEM_PREC_C128)
         if ((s = build_operator<double>(c, c->op[1], st)) != BEM_OK) return s;
@@ -1143,6 +1159,13 @@ extern "C" bem_status bem_stats_get(const bem_ctx* cc, bem_stats* out) {
         kb[BEM_KERNEL_VHX] = es * (fv + nv);
         kb[BEM_KERNEL_ROWS] = es * (3 * dense + fu + 2 * nv);
         int64_t bytes = es * (3 * dense + fu + fv + 2 * nv);
+        if (p == 0 && q.arena_bf16.p) {
+            // factors as BF16 (4 bytes per complex value), everything else complex64
+            out->kernel_bytes_bf16f[BEM_KERNEL_GATHER] = es * 2 * nv;
+            out->kernel_bytes_bf16f[BEM_KERNEL_VHX] = 4 * fv + es * nv;
+            out->kernel_bytes_bf16f[BEM_KERNEL_ROWS] = es * (3 * dense + 2 * nv) + 4 * fu;
+            out->matvec_bytes_bf16f = es * (3 * dense + 2 * nv) + 4 * (fu + fv);
+        }
         if (p == 0)
             out->matvec_bytes_c64 = bytes;
         else
@@ -1166,6 +1189,7 @@ extern "C" bem_status bem_partition(const bem_ctx* cc, int64_t* perm, int32_t* n
 static bool dtype_ok(const bem_ctx* c, int dtype) {
     if (dtype == BEM_C64) return c->op[0].built;
     if (dtype == BEM_C128) return c->op[1].built;
+    if (dtype == BEM_C64_BF16F) return c->op[0].built && c->op[0].arena_bf16.p != nullptr;
     return false;
 }
 
@@ -1223,10 +1247,19 @@ static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int
         ev = c->ev_pool.data() + c->ev_used;
         c->ev_used = need;
     }
-    if (dtype == BEM_C64) {
+    if (dtype == BEM_C64 || dtype == BEM_C64_BF16F) {
         Operator& o = c->op[0];
-        return matvec_run<float>(make_plan(c, o), o.near.p, o.arena.p, (const c64*)x, (c64*)y, (c64*)o.xp.p,
-                                 (c64*)o.t.p, nrhs, o.t_len, st, ev);
+        const bool bf = dtype == BEM_C64_BF16F;
+        return matvec_run<float>(make_plan(c, o), o.near.p, bf ? o.arena_bf16.p : o.arena.p, (const c64*)x, (c64*)y,
+                                 (c64*)o.xp.p, (c64*)o.t.p, nrhs, o.t_len, st, ev,
+                                 bf ? BEM_FORM_BF16F : BEM_FORM_NATIVE);
+    }
+    if (dtype == DT_C64_IN_FP64) {
+        // complex128 vectors through the complex64 operator (its workspaces hold one
+        // complex128 right-hand side)
+        Operator& o = c->op[0];
+        return matvec_run<double>(make_plan(c, o), o.near.p, o.arena.p, (const c128*)x, (c128*)y, (c128*)o.xp.p,
+                                  (c128*)o.t.p, nrhs, o.t_len, st, ev, BEM_FORM_C64_IN_FP64);
     }
     Operator& o = c->op[1];
     return matvec_run<double>(make_plan(c, o), o.near.p, o.arena.p, (const c128*)x, (c128*)y, (c128*)o.xp.p,
@@ -1333,8 +1366,9 @@ static bem_status gmres_work(bem_ctx* c, int dtype, int restart) {
 }
 
 // solve Z x = rhs (dtype vectors in gw.rin / gw.xin), x starts at zero; absolute tolerance
-static bem_status gmres(bem_ctx* c, int dtype, double tol_abs, int maxit, int* iters, double* final_res,
+static bem_status gmres(bem_ctx* c, int pdt, double tol_abs, int maxit, int* iters, double* final_res,
                         cudaStream_t st) {
+    const int dtype = vec_dtype(pdt);  // vectors; pdt selects the product
     GmresWork& w = c->gw;
     const int64_t n = w.n;
     const int m = w.restart;
@@ -1355,7 +1389,7 @@ static bem_status gmres(bem_ctx* c, int dtype, double tol_abs, int maxit, int* i
         g[0] = mk<double>(beta, 0);
         int jl = -1;
         for (int j = 0; j < m; ++j) {
-            CK(matvec_any(c, dtype, V + es * n * j, w.w.p, 1, st));
+            CK(matvec_any(c, pdt, V + es * n * j, w.w.p, 1, st));
             for (int pass = 0; pass < 2; ++pass) {
                 CK(kv_multidot(V, dtype, n, j + 1, w.w.p, n, (c128*)w.hpart.p, NPART, st));
                 CK(kv_reduce_partials((const c128*)w.hpart.p, NPART, j + 1, (c128*)w.hdev.p, st));
@@ -1404,7 +1438,7 @@ static bem_status gmres(bem_ctx* c, int dtype, double tol_abs, int maxit, int* i
         CK(cudaMemcpyAsync(w.hdev.p, y.data(), sizeof(c128) * k, cudaMemcpyHostToDevice, st));
         CK(kv_update(w.xin.p, V, dtype, n, k, (const c128*)w.hdev.p, 1.0, n, st));
         // true residual
-        CK(matvec_any(c, dtype, w.xin.p, w.z.p, 1, st));
+        CK(matvec_any(c, pdt, w.xin.p, w.z.p, 1, st));
         CK(kv_sub(w.rin.p, w.z.p, w.r.p, dtype, n, st));
     }
     *iters += it;
@@ -1418,12 +1452,11 @@ extern "C" bem_status bem_solve(bem_ctx* c, const void* b, void* x, int nrhs, vo
     if (!c->assembled) return fail(c, BEM_ESTATE, "bem_solve needs bem_assemble");
     if (nrhs < 1 || !b || !x) return fail(c, BEM_EINVAL, "bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    const int din = c->op[0].built ? BEM_C64 : BEM_C128;
+    const int din = dtype_ok(c, BEM_C64_BF16F) ? BEM_C64_BF16F : (c->op[0].built ? BEM_C64 : BEM_C128);
+    const int vin = vec_dtype(din);
     const bool out128 = c->op[1].built;
-    if (c->opt.refine_tol > 0 && !out128)
-        return fail(c, BEM_EINVAL, "refinement needs the complex128 operator (precision bit BEM_PREC_C128)");
     bem_status s;
-    if ((s = gmres_work(c, din, c->opt.gmres_restart)) != BEM_OK) return s;
+    if ((s = gmres_work(c, vin, c->opt.gmres_restart)) != BEM_OK) return s;
     const int64_t n = 2 * c->ne;
     DevBuf zr, rr;
     struct G {
@@ -1455,13 +1488,7 @@ extern "C" bem_status bem_solve(bem_ctx* c, const void* b, void* x, int nrhs, vo
         bool inner_ok = true;
         for (int step = 0;; ++step) {
             // r = b - Z x with the most accurate operator
-            if (out128) {
-                CK(matvec_any(c, BEM_C128, xr, zr.p, 1, st));
-            } else {
-                CK(kv_cast<float>(xr, BEM_C128, (c64*)c->gw.z.p, n, st));
-                CK(matvec_any(c, BEM_C64, c->gw.z.p, c->gw.w.p, 1, st));
-                CK(kv_cast<double>(c->gw.w.p, BEM_C64, (c128*)zr.p, n, st));
-            }
+            CK(matvec_any(c, out128 ? BEM_C128 : DT_C64_IN_FP64, xr, zr.p, 1, st));
             CK(kv_sub(br, zr.p, rr.p, BEM_C128, n, st));
             double rn;
             if ((s = norm_dev(c, BEM_C128, rr.p, n, &rn, st)) != BEM_OK) return s;
@@ -1469,7 +1496,7 @@ extern "C" bem_status bem_solve(bem_ctx* c, const void* b, void* x, int nrhs, vo
             if (refine ? rel <= c->opt.refine_tol : step >= 1) break;
             if (step >= steps) break;
             // inner solve Z d = r
-            if (din == BEM_C64)
+            if (vin == BEM_C64)
                 CK(kv_cast<float>(rr.p, BEM_C128, (c64*)c->gw.rin.p, n, st));
             else
                 CK(cudaMemcpyAsync(c->gw.rin.p, rr.p, sizeof(c128) * n, cudaMemcpyDeviceToDevice, st));
@@ -1478,16 +1505,10 @@ extern "C" bem_status bem_solve(bem_ctx* c, const void* b, void* x, int nrhs, vo
             if ((s = gmres(c, din, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st)) != BEM_OK)
                 return s;
             inner_ok = fres <= c->opt.tol * rn * 1.0000001;
-            CK(kv_axpy_c128(xr, c->gw.xin.p, din, (const c128*)c->d_one.p, 1.0, n, 1, n, st));
+            CK(kv_axpy_c128(xr, c->gw.xin.p, vin, (const c128*)c->d_one.p, 1.0, n, 1, n, st));
             if (total_it >= c->opt.maxit || total_it == before) {
                 // out of iterations (or no progress possible): measure and stop
-                if (out128) {
-                    CK(matvec_any(c, BEM_C128, xr, zr.p, 1, st));
-                } else {
-                    CK(kv_cast<float>(xr, BEM_C128, (c64*)c->gw.z.p, n, st));
-                    CK(matvec_any(c, BEM_C64, c->gw.z.p, c->gw.w.p, 1, st));
-                    CK(kv_cast<double>(c->gw.w.p, BEM_C64, (c128*)zr.p, n, st));
-                }
+                CK(matvec_any(c, out128 ? BEM_C128 : DT_C64_IN_FP64, xr, zr.p, 1, st));
                 CK(kv_sub(br, zr.p, rr.p, BEM_C128, n, st));
                 if ((s = norm_dev(c, BEM_C128, rr.p, n, &rn, st)) != BEM_OK) return s;
                 rel = rn / bn;

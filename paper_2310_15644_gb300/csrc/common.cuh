@@ -1,6 +1,7 @@
 // Internal definitions shared by the libbem translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -12,6 +13,10 @@
 
 #define BEM_PI 3.14159265358979323846
 #define BEM_MAX_LEAF 64
+// storage/arithmetic forms of a product (matvec_run)
+#define BEM_FORM_NATIVE 0       // entries and factors stored in the product's arithmetic
+#define BEM_FORM_BF16F 1        // complex64 product, far factors stored as BF16
+#define BEM_FORM_C64_IN_FP64 2  // complex64 entries and factors, FP64 vectors and sums
 // ACA tasks whose scratch (m + n) * rank cap reaches this many elements get a whole
 // SM (1024 threads) in the FP32 build
 #define BEM_ACA_WIDE_COST (1 << 19)
@@ -68,6 +73,22 @@ __host__ __device__ __forceinline__ void cfma_conj(cx<R>& a, cx<R> b, cx<R> c) {
 
 typedef cx<float> c64;
 typedef cx<double> c128;
+
+// A complex value stored as two BF16 numbers (real part in the low 16 bits of the
+// 32-bit word).  A BF16 number is the upper half of an IEEE binary32, so widening
+// is a shift; narrowing rounds to nearest even.
+struct __align__(4) bf16c {
+    __nv_bfloat16 re, im;
+};
+__device__ __forceinline__ float2 bf16c_to_float2(unsigned int w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+__device__ __forceinline__ bf16c float2_to_bf16c(float re, float im) {
+    bf16c r;
+    r.re = __float2bfloat16_rn(re);
+    r.im = __float2bfloat16_rn(im);
+    return r;
+}
 
 // ---------------------------------------------------------------------------
 // device view of the mesh, media and singular-pair table
@@ -228,7 +249,9 @@ struct MatvecPlan {
 template <typename R>
 cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x,
                        cx<R>* y, cx<R>* xp, cx<R>* t, int nrhs, int64_t t_len, cudaStream_t st,
-                       const cudaEvent_t* ev);
+                       const cudaEvent_t* ev, int form = BEM_FORM_NATIVE);
+// BF16 copy of n complex64 factor values
+cudaError_t factors_to_bf16(const c64* in, bf16c* out, int64_t n, cudaStream_t st);
 
 // rhs_power.cu
 template <typename R>

@@ -22,26 +22,41 @@
 
 namespace bem {
 
-// 16-byte loads of two consecutive complex values of the stored operator.  The
-// operator is read once per product, so the loads are marked streaming
-// (evict-first): they must not push the reused vectors (x, t) out of L1 and L2.
-template <typename R>
-struct Pair;
+// Loads of two consecutive complex values of the stored operator, converted to
+// the arithmetic R of the product.  Storage F: complex64 (one 16-byte load),
+// complex128 (two), or BF16 pairs (one 8-byte load; far factors of the complex64
+// product only).  The operator is read once per product, so the loads are marked
+// streaming (evict-first): they must not push the reused vectors (x, t) out of L1
+// and L2.
+template <typename F>
+struct FPair;
 template <>
-struct Pair<float> {
-    static __device__ __forceinline__ void ld(const void* base, int64_t idx, c64& a, c64& b) {
-        float4 v = __ldcs(reinterpret_cast<const float4*>(base) + idx);
-        a = mk<float>(v.x, v.y);
-        b = mk<float>(v.z, v.w);
+struct FPair<c64> {
+    template <typename R>
+    static __device__ __forceinline__ void ld(const c64* base, int64_t idx, cx<R>& a, cx<R>& b) {
+        const float4 v = __ldcs(reinterpret_cast<const float4*>(base) + idx);
+        a = mk<R>((R)v.x, (R)v.y);
+        b = mk<R>((R)v.z, (R)v.w);
     }
 };
 template <>
-struct Pair<double> {
-    static __device__ __forceinline__ void ld(const void* base, int64_t idx, c128& a, c128& b) {
+struct FPair<c128> {
+    template <typename R>
+    static __device__ __forceinline__ void ld(const c128* base, int64_t idx, cx<R>& a, cx<R>& b) {
         const double2* p = reinterpret_cast<const double2*>(base) + 2 * idx;
-        double2 u = __ldcs(p), v = __ldcs(p + 1);
-        a = mk<double>(u.x, u.y);
-        b = mk<double>(v.x, v.y);
+        const double2 u = __ldcs(p), v = __ldcs(p + 1);
+        a = mk<R>((R)u.x, (R)u.y);
+        b = mk<R>((R)v.x, (R)v.y);
+    }
+};
+template <>
+struct FPair<bf16c> {
+    template <typename R>
+    static __device__ __forceinline__ void ld(const bf16c* base, int64_t idx, cx<R>& a, cx<R>& b) {
+        const uint2 u = __ldcs(reinterpret_cast<const uint2*>(base) + idx);
+        const float2 fa = bf16c_to_float2(u.x), fb = bf16c_to_float2(u.y);
+        a = mk<R>((R)fa.x, (R)fa.y);
+        b = mk<R>((R)fb.x, (R)fb.y);
     }
 };
 
@@ -94,10 +109,11 @@ __global__ void k_gather(const cx<R>* __restrict__ x, const int64_t* __restrict_
 // item is handled by 8 lanes (rows jj, jj+8, ...) and its t values are written by
 // the group's first lane -- no shared memory, no barrier, no cross-CTA sum.
 // Every loaded pair of W is applied to NR right-hand sides.
-template <typename R, int NR>
-__device__ __forceinline__ void vhx_unit(const FarRec* __restrict__ far, int2 un, const cx<R>* __restrict__ arena,
+template <typename R, typename F, int NR>
+__device__ __forceinline__ void vhx_unit(const FarRec* __restrict__ far, int2 un, const F* __restrict__ arena,
                                          const cx<R>* __restrict__ xp, cx<R>* __restrict__ t, int ne) {
-    constexpr int UN = NR == 1 ? 4 : (NR == 2 ? 2 : 1);
+    // BF16 factors move half the bytes per load: twice as many loads in flight
+    constexpr int UN = (NR == 1 ? 4 : (NR == 2 ? 2 : 1)) * (sizeof(F) == 4 ? 2 : 1);
     const FarRec* Fp = far + un.x;
     const int n = Fp->n;
     const int kpA = (Fp->rk[0] + 1) >> 1, kpB = (Fp->rk[1] + 1) >> 1, kpC = (Fp->rk[2] + 1) >> 1;
@@ -116,7 +132,7 @@ __device__ __forceinline__ void vhx_unit(const FarRec* __restrict__ far, int2 un
         kp = it - kpA - kpB;
     }
     // column pair kp of W, all rows: pair index kp*n + row (two complex values per pair)
-    const cx<R>* V = arena + Fp->off_v[op] + 2 * (int64_t)kp * n;
+    const F* V = arena + Fp->off_v[op] + 2 * (int64_t)kp * n;
     const cx<R>* xs = xp + ((int64_t)((op == 2) ? ne : 0) + Fp->c0) * NR;  // J for A and B, M for C
     const cx<R>* xm = xp + ((int64_t)ne + Fp->c0) * NR;
     cx<R> a0[NR], a1[NR], b0[NR], b1[NR];
@@ -143,13 +159,13 @@ __device__ __forceinline__ void vhx_unit(const FarRec* __restrict__ far, int2 un
     for (; j + 8 * (UN - 1) < n; j += 8 * UN) {
         cx<R> w0[UN], w1[UN];
 #pragma unroll
-        for (int q = 0; q < UN; ++q) Pair<R>::ld(V, j + 8 * q, w0[q], w1[q]);
+        for (int q = 0; q < UN; ++q) FPair<F>::template ld<R>(V, j + 8 * q, w0[q], w1[q]);
 #pragma unroll
         for (int q = 0; q < UN; ++q) step(w0[q], w1[q], j + 8 * q);
     }
     for (; j < n; j += 8) {
         cx<R> w0, w1;
-        Pair<R>::ld(V, j, w0, w1);
+        FPair<F>::template ld<R>(V, j, w0, w1);
         step(w0, w1, j);
     }
     // sum over the 8 lanes of the group (xor offsets stay inside the group)
@@ -185,11 +201,11 @@ __device__ __forceinline__ void vhx_unit(const FarRec* __restrict__ far, int2 un
 }
 
 // one CTA per unit; the hardware scheduler balances the (largest-first) units
-template <typename R, int NR>
+template <typename R, typename F, int NR>
 __global__ void __launch_bounds__(VHX_THREADS) k_vhx(const FarRec* __restrict__ far, const int2* __restrict__ units,
-                                                     int nunits, const cx<R>* __restrict__ arena,
+                                                     int nunits, const F* __restrict__ arena,
                                                      const cx<R>* __restrict__ xp, cx<R>* __restrict__ t, int ne) {
-    if ((int)blockIdx.x < nunits) vhx_unit<R, NR>(far, units[blockIdx.x], arena, xp, t, ne);
+    if ((int)blockIdx.x < nunits) vhx_unit<R, F, NR>(far, units[blockIdx.x], arena, xp, t, ne);
 }
 
 #define ROW_THREADS (64 * BEM_ROW_GROUPS)
@@ -197,13 +213,13 @@ __global__ void __launch_bounds__(VHX_THREADS) k_vhx(const FarRec* __restrict__ 
 
 // One dense item (leaf rows x n columns): y_J += A xJ + B xM, y_M += C xM - B xJ
 // for NR right-hand sides (xJ, xM: NR values per column).
-template <typename R, int NR>
-__device__ __forceinline__ void dense_item(const cx<R>* __restrict__ A, int64_t stride, int m, int i, int n,
+template <typename R, typename NS, int NR>
+__device__ __forceinline__ void dense_item(const NS* __restrict__ A, int64_t stride, int m, int i, int n,
                                            const cx<R>* __restrict__ xJ, const cx<R>* __restrict__ xM,
                                            cx<R> (&aJ)[NR], cx<R> (&aM)[NR]) {
     constexpr int UN = NR == 1 ? 4 : (NR == 2 ? 2 : 1);
-    const cx<R>* B = A + stride;
-    const cx<R>* C = B + stride;
+    const NS* B = A + stride;
+    const NS* C = B + stride;
     const int nfull = n >> 1;  // column pairs with both columns inside the item
     auto apply = [&](const cx<R>& a0, const cx<R>& a1, const cx<R>& b0, const cx<R>& b1, const cx<R>& c0,
                      const cx<R>& c1, int j) {
@@ -231,9 +247,9 @@ __device__ __forceinline__ void dense_item(const cx<R>* __restrict__ A, int64_t 
 #pragma unroll
         for (int u = 0; u < UN; ++u) {
             const int64_t idx = (int64_t)(cp + u) * m + i;
-            Pair<R>::ld(A, idx, a0[u], a1[u]);
-            Pair<R>::ld(B, idx, b0[u], b1[u]);
-            Pair<R>::ld(C, idx, c0[u], c1[u]);
+            FPair<NS>::template ld<R>(A, idx, a0[u], a1[u]);
+            FPair<NS>::template ld<R>(B, idx, b0[u], b1[u]);
+            FPair<NS>::template ld<R>(C, idx, c0[u], c1[u]);
         }
 #pragma unroll
         for (int u = 0; u < UN; ++u) apply(a0[u], a1[u], b0[u], b1[u], c0[u], c1[u], 2 * (cp + u));
@@ -241,17 +257,17 @@ __device__ __forceinline__ void dense_item(const cx<R>* __restrict__ A, int64_t 
     for (; cp < nfull; ++cp) {
         cx<R> a0, a1, b0, b1, c0, c1;
         const int64_t idx = (int64_t)cp * m + i;
-        Pair<R>::ld(A, idx, a0, a1);
-        Pair<R>::ld(B, idx, b0, b1);
-        Pair<R>::ld(C, idx, c0, c1);
+        FPair<NS>::template ld<R>(A, idx, a0, a1);
+        FPair<NS>::template ld<R>(B, idx, b0, b1);
+        FPair<NS>::template ld<R>(C, idx, c0, c1);
         apply(a0, a1, b0, b1, c0, c1, 2 * cp);
     }
     if (n & 1) {  // last column; its pair partner is a stored zero column
         cx<R> a0, a1, b0, b1, c0, c1;
         const int64_t idx = (int64_t)nfull * m + i;
-        Pair<R>::ld(A, idx, a0, a1);
-        Pair<R>::ld(B, idx, b0, b1);
-        Pair<R>::ld(C, idx, c0, c1);
+        FPair<NS>::template ld<R>(A, idx, a0, a1);
+        FPair<NS>::template ld<R>(B, idx, b0, b1);
+        FPair<NS>::template ld<R>(C, idx, c0, c1);
         cx<R> xj0[NR], xm0[NR];
         ldv<R, NR>(xJ + (int64_t)(n - 1) * NR, xj0);
         ldv<R, NR>(xM + (int64_t)(n - 1) * NR, xm0);
@@ -268,12 +284,13 @@ __device__ __forceinline__ void dense_item(const cx<R>* __restrict__ A, int64_t 
 // y_J += U_A tA + U_B tBM, y_M += U_C tC - U_B tBJ for rows ro + i of one far block.
 // U is slice-major: the leaf's slice (ms rows starting at ro) of operator q is one
 // contiguous run, pair (kp, i) at ro * kpc + kp * ms + i.  t values: NR per column.
-template <typename R, int NR, int MODE>
-__device__ __forceinline__ void far_slice(const cx<R>* __restrict__ U, int kpc, int ms, int i,
+template <typename R, typename F, int NR, int MODE>
+__device__ __forceinline__ void far_slice(const F* __restrict__ U, int kpc, int ms, int i,
                                           const cx<R>* __restrict__ tv, const cx<R>* __restrict__ tv2,
                                           cx<R> (&aJ)[NR], cx<R> (&aM)[NR]) {
     // MODE 0: aJ += U tv; 1: aJ += U tv (tBM), aM -= U tv2 (tBJ); 2: aM += U tv
-    constexpr int UN = NR == 1 ? 4 : (NR == 2 ? 2 : 1);
+    // BF16 factors move half the bytes per load: twice as many loads in flight
+    constexpr int UN = (NR == 1 ? 4 : (NR == 2 ? 2 : 1)) * (sizeof(F) == 4 ? 2 : 1);
     auto apply = [&](const cx<R>& u0, const cx<R>& u1, int kp) {
         const int k2 = 2 * kp;
         cx<R> p0[NR], p1[NR];
@@ -303,28 +320,28 @@ __device__ __forceinline__ void far_slice(const cx<R>* __restrict__ U, int kpc, 
     for (; kp + UN <= kpc; kp += UN) {
         cx<R> u0[UN], u1[UN];
 #pragma unroll
-        for (int u = 0; u < UN; ++u) Pair<R>::ld(U, (int64_t)(kp + u) * ms + i, u0[u], u1[u]);
+        for (int u = 0; u < UN; ++u) FPair<F>::template ld<R>(U, (int64_t)(kp + u) * ms + i, u0[u], u1[u]);
 #pragma unroll
         for (int u = 0; u < UN; ++u) apply(u0[u], u1[u], kp + u);
     }
     for (; kp < kpc; ++kp) {
         cx<R> u0, u1;
-        Pair<R>::ld(U, (int64_t)kp * ms + i, u0, u1);
+        FPair<F>::template ld<R>(U, (int64_t)kp * ms + i, u0, u1);
         apply(u0, u1, kp);
     }
 }
 
-template <typename R, int NR>
-__device__ __forceinline__ void far_piece(const FarRec& F, int ro, int ms, int i, const cx<R>* __restrict__ arena,
+template <typename R, typename FS, int NR>
+__device__ __forceinline__ void far_piece(const FarRec& F, int ro, int ms, int i, const FS* __restrict__ arena,
                                           const cx<R>* __restrict__ t, cx<R> (&aJ)[NR], cx<R> (&aM)[NR]) {
     const int kpA = (F.rk[0] + 1) >> 1, kpB = (F.rk[1] + 1) >> 1, kpC = (F.rk[2] + 1) >> 1;
     const cx<R>* tA = t + F.off_t * NR;
     const cx<R>* tBJ = tA + 2 * kpA * NR;
     const cx<R>* tBM = tBJ + 2 * kpB * NR;
     const cx<R>* tC = tBM + 2 * kpB * NR;
-    far_slice<R, NR, 0>(arena + F.off_u[0] + 2 * (int64_t)ro * kpA, kpA, ms, i, tA, nullptr, aJ, aM);
-    far_slice<R, NR, 1>(arena + F.off_u[1] + 2 * (int64_t)ro * kpB, kpB, ms, i, tBM, tBJ, aJ, aM);
-    far_slice<R, NR, 2>(arena + F.off_u[2] + 2 * (int64_t)ro * kpC, kpC, ms, i, tC, nullptr, aJ, aM);
+    far_slice<R, FS, NR, 0>(arena + F.off_u[0] + 2 * (int64_t)ro * kpA, kpA, ms, i, tA, nullptr, aJ, aM);
+    far_slice<R, FS, NR, 1>(arena + F.off_u[1] + 2 * (int64_t)ro * kpB, kpB, ms, i, tBM, tBJ, aJ, aM);
+    far_slice<R, FS, NR, 2>(arena + F.off_u[2] + 2 * (int64_t)ro * kpC, kpC, ms, i, tC, nullptr, aJ, aM);
 }
 
 // Grid: one 64-thread CTA per work slot (nleaf x parts; a balanced split of the
@@ -333,9 +350,9 @@ __device__ __forceinline__ void far_piece(const FarRec& F, int ro, int ms, int i
 // leaf to finish (arrival counter, after a memory fence) adds the parts in index
 // order and writes y -- the sum does not depend on which CTA finishes last.
 // y is in the caller's layout: right-hand side r at y + r * 2ne.
-template <typename R, int NR>
-__global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const cx<R>* __restrict__ near,
-                                                      const cx<R>* __restrict__ arena,
+template <typename R, typename NS, typename FS, int NR>
+__global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const NS* __restrict__ near,
+                                                      const FS* __restrict__ arena,
                                                       const cx<R>* __restrict__ xp, const cx<R>* __restrict__ t,
                                                       cx<R>* __restrict__ y, cx<R>* __restrict__ ypart,
                                                       unsigned int* __restrict__ arrive) {
@@ -357,12 +374,12 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const cx<R>*
             const int item = p.work_item[w];
             if (item >= 0) {
                 const int c0 = p.near_c0[item];
-                dense_item<R, NR>(near + p.near_off[item], p.near_op_stride, m, i, p.near_n[item],
+                dense_item<R, NS, NR>(near + p.near_off[item], p.near_op_stride, m, i, p.near_n[item],
                                   xp + (int64_t)c0 * NR, xp + ((int64_t)ne + c0) * NR, aJ, aM);
             } else {
                 const int fp = -1 - item;
                 const FarRec F = p.far[p.farp_blk[fp]];
-                far_piece<R, NR>(F, p.farp_row[fp], m, i, arena, t, aJ, aM);
+                far_piece<R, FS, NR>(F, p.farp_row[fp], m, i, arena, t, aJ, aM);
             }
         }
     }
@@ -406,7 +423,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const cx<R>*
     if (threadIdx.x == 0) arrive[leaf] = 0u;  // ready for the next product
 }
 
-template <typename R, int NR>
+template <typename R, typename NS, typename FS, int NR>
 static cudaError_t product_chunk(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x,
                                  cx<R>* y, cx<R>* xp, cx<R>* t, cudaStream_t st, const cudaEvent_t* e) {
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[0], st));
@@ -415,13 +432,13 @@ static cudaError_t product_chunk(const MatvecPlan& p, const void* near_entries, 
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[1], st));
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[2], st));
     if (p.nvhx > 0) {
-        k_vhx<R, NR><<<p.nvhx, VHX_THREADS, 0, st>>>(p.far, p.vhx_units, p.nvhx, (const cx<R>*)arena, xp, t, p.ne);
+        k_vhx<R, FS, NR><<<p.nvhx, VHX_THREADS, 0, st>>>(p.far, p.vhx_units, p.nvhx, (const FS*)arena, xp, t, p.ne);
         BEM_CUDA_TRY(cudaGetLastError());
     }
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[3], st));
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[4], st));
-    k_rows<R, NR><<<p.nleaf * p.parts, ROW_THREADS, 0, st>>>(p, (const cx<R>*)near_entries, (const cx<R>*)arena, xp,
-                                                              t, y, (cx<R>*)p.ypart, p.arrive);
+    k_rows<R, NS, FS, NR><<<p.nleaf * p.parts, ROW_THREADS, 0, st>>>(p, (const NS*)near_entries, (const FS*)arena,
+                                                                      xp, t, y, (cx<R>*)p.ypart, p.arrive);
     BEM_CUDA_TRY(cudaGetLastError());
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[5], st));
     return cudaSuccess;
@@ -429,9 +446,9 @@ static cudaError_t product_chunk(const MatvecPlan& p, const void* near_entries, 
 
 // Right-hand sides are processed in chunks of 8, 4, 2, 1: every chunk streams the
 // operator once and applies each loaded entry to all of its right-hand sides.
-template <typename R>
-cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x, cx<R>* y,
-                       cx<R>* xp, cx<R>* t, int nrhs, int64_t t_len, cudaStream_t st, const cudaEvent_t* ev) {
+template <typename R, typename NS, typename FS>
+static cudaError_t matvec_chunks(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x,
+                                 cx<R>* y, cx<R>* xp, cx<R>* t, int nrhs, cudaStream_t st, const cudaEvent_t* ev) {
     const int64_t nn = 2 * (int64_t)p.ne;
     int r = 0, chunk = 0;
     while (r < nrhs) {
@@ -442,22 +459,60 @@ cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void
         cx<R>* yr = y + r * nn;
         cudaError_t err;
         switch (nr) {
-            case 8: err = product_chunk<R, 8>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
-            case 4: err = product_chunk<R, 4>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
-            case 2: err = product_chunk<R, 2>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
-            default: err = product_chunk<R, 1>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
+            case 8: err = product_chunk<R, NS, FS, 8>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
+            case 4: err = product_chunk<R, NS, FS, 4>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
+            case 2: err = product_chunk<R, NS, FS, 2>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
+            default: err = product_chunk<R, NS, FS, 1>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
         }
         if (err != cudaSuccess) return err;
         r += nr;
         ++chunk;
     }
-    (void)t_len;
     return cudaSuccess;
 }
 
+template <typename R>
+cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x, cx<R>* y,
+                       cx<R>* xp, cx<R>* t, int nrhs, int64_t t_len, cudaStream_t st, const cudaEvent_t* ev,
+                       int form) {
+    (void)t_len;
+    if constexpr (sizeof(R) == 4) {
+        if (form == BEM_FORM_BF16F)
+            return matvec_chunks<float, c64, bf16c>(p, near_entries, arena, x, y, xp, t, nrhs, st, ev);
+        if (form != BEM_FORM_NATIVE) return cudaErrorInvalidValue;
+    } else {
+        if (form == BEM_FORM_C64_IN_FP64) {
+            // complex64 operator applied in FP64 (residuals of iterative refinement);
+            // one right-hand side per pass
+            const int64_t nn = 2 * (int64_t)p.ne;
+            for (int r = 0; r < nrhs; ++r) {
+                cudaError_t e = product_chunk<double, c64, c64, 1>(p, near_entries, arena, x + r * nn, y + r * nn,
+                                                                   xp, t, st, ev ? ev + 6 * r : nullptr);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        }
+        if (form != BEM_FORM_NATIVE) return cudaErrorInvalidValue;
+    }
+    return matvec_chunks<R, cx<R>, cx<R>>(p, near_entries, arena, x, y, xp, t, nrhs, st, ev);
+}
+
+// BF16 copy of complex64 factors (round to nearest even per component)
+__global__ void k_to_bf16(const c64* __restrict__ in, bf16c* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = float2_to_bf16c(in[i].re, in[i].im);
+}
+
+cudaError_t factors_to_bf16(const c64* in, bf16c* out, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+    k_to_bf16<<<(unsigned)blocks, 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
 template cudaError_t matvec_run<float>(const MatvecPlan&, const void*, const void*, const c64*, c64*, c64*, c64*, int,
-                                       int64_t, cudaStream_t, const cudaEvent_t*);
+                                       int64_t, cudaStream_t, const cudaEvent_t*, int);
 template cudaError_t matvec_run<double>(const MatvecPlan&, const void*, const void*, const c128*, c128*, c128*,
-                                        c128*, int, int64_t, cudaStream_t, const cudaEvent_t*);
+                                        c128*, int, int64_t, cudaStream_t, const cudaEvent_t*, int);
 
 }  // namespace bem
