@@ -373,7 +373,8 @@ cudaError_t eval_entries(GeomDev g, const int* rows, const int* cols, int64_t co
 // ---------------------------------------------------------------------------
 #define ACA_THREADS 256
 #define ACA_THREADS_WIDE 1024
-#define ACA_MAX_CHECKS 8  // sampled-row checks per task before the stopping test is accepted
+#define ACA_MAX_CHECKS 8      // sampled-row checks per task before the stopping test is accepted
+#define ACA_CHECK_FACTOR 4.0  // a checked row resumes the iteration above 4x its share of the tolerance
 #define ACA_RMAX 128
 
 // block-wide argmax of val with smallest index on ties; returns (val, idx) to all threads
@@ -587,8 +588,8 @@ __device__ void aca_task(const GeomDev& g, const int64_t* __restrict__ perm, con
             // coplanar faces of a box, say) can look converged while a whole group
             // of rows is still missing.  Before stopping, the residual of the unvisited
             // row farthest (in tree order) from every visited row is computed; if
-            // its energy exceeds the per-row share tol^2 |S|^2 / m of the tolerance,
-            // that row becomes the next pivot row.
+            // its energy exceeds ACA_CHECK_FACTOR times the per-row share
+            // tol^2 |S|^2 / m of the tolerance, that row becomes the next pivot row.
             int resume = -1;
             while (resume < 0 && checks < ACA_MAX_CHECKS) {
                 if (tid == 0) {
@@ -615,7 +616,7 @@ __device__ void aca_task(const GeomDev& g, const int64_t* __restrict__ perm, con
                 double cv;
                 int ci;
                 const double e2 = residual_row(ic, k, cv, ci);
-                if (e2 > tol * tol * fmax(norm2, 0.0) / m) resume = ic;
+                if (e2 > ACA_CHECK_FACTOR * tol * tol * fmax(norm2, 0.0) / m) resume = ic;
             }
             if (resume < 0) {
                 converged = true;

@@ -44,8 +44,9 @@ struct Operator {
     int64_t n_far_split = 0;           // far blocks split because their rank passed the cap
     int64_t n_far_dense = 0;           // partition far blocks stored densely (rank above break-even)
     int64_t near_stride = 0;
-    int parts = 1;                     // CTAs per leaf in the rows kernel
+    int nslot = 0, pmax = 1;           // rows-kernel CTAs; most slots of one leaf
     DevBuf d_work_ptr, d_work_item, d_near_c0, d_near_n, d_near_off, d_farp_blk, d_farp_row, d_ypart, d_arrive;
+    DevBuf d_leaf_parts, d_slot_order, d_slot_leaf, d_slot_part;
     DevBuf near;          // 3 * near_stride complex
     DevBuf arena;         // low-rank factors
     DevBuf arena_bf16;    // BF16 copy of the factors (complex64 operator, BEM_PREC_BF16F)
@@ -200,8 +201,9 @@ static c128 csqrt_principal(c128 z) {
 }
 
 static void release_operator(Operator& o) {
-    DevBuf* plan[] = {&o.d_work_ptr, &o.d_work_item, &o.d_near_c0, &o.d_near_n, &o.d_near_off,
-                      &o.d_farp_blk, &o.d_farp_row, &o.d_ypart, &o.d_arrive};
+    DevBuf* plan[] = {&o.d_work_ptr,  &o.d_work_item,  &o.d_near_c0,   &o.d_near_n,    &o.d_near_off,
+                      &o.d_farp_blk,  &o.d_farp_row,   &o.d_ypart,     &o.d_arrive,    &o.d_leaf_parts,
+                      &o.d_slot_order, &o.d_slot_leaf, &o.d_slot_part};
     for (DevBuf* b : plan) dfree(*b);
     o.items.clear();
     o.far_desc.clear();
@@ -727,7 +729,6 @@ static bem_status build_leaves(bem_ctx* c, cudaStream_t st) {
 // groups of a leaf stream about the same number of bytes.
 static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaStream_t st) {
     const int nleaf = (int)c->leaf_lo.size();
-    const int G = BEM_ROW_GROUPS;  // groups per CTA in the rows kernel
     std::vector<int> leaf_of(c->ne + 1, -1);
     for (int l = 0; l < nleaf; ++l) leaf_of[c->leaf_lo[l]] = l;
     // dense items
@@ -762,16 +763,27 @@ static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaSt
             items[l].push_back({(int64_t)c->leaf_m[l] * kp2, -1 - id});
         }
     }
-    // parts per leaf: aim at BEM_ROW_TARGET_CTAS CTAs in total (a few per SM resident at once)
-    const int target = BEM_ROW_TARGET_CTAS;
-    o.parts = std::max(1, std::min(32, (target + nleaf - 1) / std::max(1, nleaf)));
-    const int S = o.parts * G;
-    std::vector<int> wptr(1, 0), witem;
+    // Slots: a leaf's items are split into parts proportional to its share of the
+    // work (about BEM_ROW_TARGET_CTAS slots in total, at most 32 per leaf), by
+    // longest-processing-time assignment; CTAs take the slots heaviest first.
+    int64_t total = 0;
+    std::vector<int64_t> lw(nleaf, 0);
+    for (int l = 0; l < nleaf; ++l)
+        for (auto& it : items[l]) lw[l] += it.first;
+    for (int l = 0; l < nleaf; ++l) total += lw[l];
+    const double per_slot = std::max(1.0, (double)total / BEM_ROW_TARGET_CTAS);
+    std::vector<int> wptr(1, 0), witem, lparts(nleaf), sleaf, spart;
+    std::vector<int64_t> scost;
+    o.pmax = 1;
     for (int l = 0; l < nleaf; ++l) {
         auto& v = items[l];
         std::stable_sort(v.begin(), v.end(), [](const std::pair<int64_t, int>& x, const std::pair<int64_t, int>& y) {
             return x.first > y.first;
         });
+        const int S = (int)std::max<int64_t>(
+            1, std::min<int64_t>({32, (int64_t)v.size(), (int64_t)std::ceil((double)lw[l] / per_slot)}));
+        lparts[l] = S;
+        o.pmax = std::max(o.pmax, S);
         std::vector<int64_t> load(S, 0);
         std::vector<std::vector<int>> slot(S);
         for (auto& it : v) {
@@ -784,8 +796,19 @@ static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaSt
         for (int q = 0; q < S; ++q) {
             for (int e : slot[q]) witem.push_back(e);
             wptr.push_back((int)witem.size());
+            sleaf.push_back(l);
+            spart.push_back(q);
+            scost.push_back(load[q]);
         }
     }
+    o.nslot = (int)sleaf.size();
+    std::vector<int> sorder(o.nslot);
+    std::iota(sorder.begin(), sorder.end(), 0);
+    std::stable_sort(sorder.begin(), sorder.end(), [&](int x, int y) { return scost[x] > scost[y]; });
+    CK(upload(o.d_leaf_parts, lparts, st));
+    CK(upload(o.d_slot_order, sorder, st));
+    CK(upload(o.d_slot_leaf, sleaf, st));
+    CK(upload(o.d_slot_part, spart, st));
     CK(upload(o.d_work_ptr, wptr, st));
     CK(upload(o.d_work_item, witem, st));
     CK(upload(o.d_near_c0, nc0, st));
@@ -793,7 +816,7 @@ static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaSt
     CK(upload(o.d_near_off, noff, st));
     CK(upload(o.d_farp_blk, fblk, st));
     CK(upload(o.d_farp_row, frow, st));
-    CK(dalloc(o.d_ypart, es * 2 * c->ne * (o.parts > 1 ? o.parts : 1) * BEM_MAX_NR));
+    CK(dalloc(o.d_ypart, es * 2 * c->ne * (o.pmax > 1 ? o.pmax : 1) * BEM_MAX_NR));
     CK(dalloc(o.d_arrive, sizeof(unsigned int) * std::max(1, nleaf)));
     CK(cudaMemsetAsync(o.d_arrive.p, 0, sizeof(unsigned int) * std::max(1, nleaf), st));
     CK(cudaStreamSynchronize(st));
@@ -1216,7 +1239,12 @@ static MatvecPlan make_plan(const bem_ctx* c, const Operator& o) {
     p.perm = (const int64_t*)c->d_perm.p;
     p.leaf_r0 = (const int*)c->d_leaf_r0.p;
     p.leaf_m = (const int*)c->d_leaf_m.p;
-    p.parts = o.parts;
+    p.nslot = o.nslot;
+    p.pmax = o.pmax;
+    p.leaf_parts = (const int*)o.d_leaf_parts.p;
+    p.slot_order = (const int*)o.d_slot_order.p;
+    p.slot_leaf = (const int*)o.d_slot_leaf.p;
+    p.slot_part = (const int*)o.d_slot_part.p;
     p.work_ptr = (const int*)o.d_work_ptr.p;
     p.work_item = (const int*)o.d_work_item.p;
     p.ypart = o.d_ypart.p;

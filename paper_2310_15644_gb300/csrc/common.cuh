@@ -227,11 +227,16 @@ cudaError_t aca_compact(const AcaTask* tasks, int ntasks, const cx<R>* scratch, 
 // matvec.cu
 struct MatvecPlan {
     int ne, nleaf, nfar;
-    int parts;                   // CTAs per leaf in the rows kernel
+    int nslot;                   // CTAs of the rows kernel (work slots)
+    int pmax;                    // largest number of slots of one leaf
     const int64_t* perm;         // tree position -> edge
     const int* leaf_r0;          // nleaf
     const int* leaf_m;           // nleaf
-    const int* work_ptr;         // nleaf * parts * 4 + 1: work slot -> range of work_item
+    const int* leaf_parts;       // nleaf: slots of each leaf
+    const int* slot_order;       // nslot: slot handled by CTA b, heaviest slot first
+    const int* slot_leaf;        // nslot
+    const int* slot_part;        // nslot: index of the slot within its leaf
+    const int* work_ptr;         // nslot + 1: work slot -> range of work_item
     const int* work_item;        // >= 0: dense item; < 0: far piece -1 - item
     const int* near_c0;          // per dense item: column start
     const int* near_n;           // per dense item: columns
@@ -242,7 +247,7 @@ struct MatvecPlan {
     const FarRec* far;           // nfar
     const int2* vhx_units;       // nvhx units of the V^H x kernel: (far block, group of 8 items), largest first
     int nvhx;
-    void* ypart;                 // parts x 2ne partial rows (parts > 1)
+    void* ypart;                 // pmax x 2ne partial rows (pmax > 1)
     unsigned int* arrive;        // nleaf arrival counters, zero between products
 };
 // ev: NULL, or 6 events per right-hand side recorded around the three kernels

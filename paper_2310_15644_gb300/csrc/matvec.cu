@@ -289,8 +289,8 @@ __device__ __forceinline__ void far_slice(const F* __restrict__ U, int kpc, int 
                                           const cx<R>* __restrict__ tv, const cx<R>* __restrict__ tv2,
                                           cx<R> (&aJ)[NR], cx<R> (&aM)[NR]) {
     // MODE 0: aJ += U tv; 1: aJ += U tv (tBM), aM -= U tv2 (tBJ); 2: aM += U tv
-    // BF16 factors move half the bytes per load: twice as many loads in flight
-    constexpr int UN = (NR == 1 ? 4 : (NR == 2 ? 2 : 1)) * (sizeof(F) == 4 ? 2 : 1);
+    // (slices are short runs: eight loads in flight per thread for one right-hand side)
+    constexpr int UN = NR == 1 ? 8 : (NR == 2 ? 4 : (NR == 4 ? 2 : 1));
     auto apply = [&](const cx<R>& u0, const cx<R>& u1, int kp) {
         const int k2 = 2 * kp;
         cx<R> p0[NR], p1[NR];
@@ -344,11 +344,12 @@ __device__ __forceinline__ void far_piece(const FarRec& F, int ro, int ms, int i
     far_slice<R, FS, NR, 2>(arena + F.off_u[2] + 2 * (int64_t)ro * kpC, kpC, ms, i, tC, nullptr, aJ, aM);
 }
 
-// Grid: one 64-thread CTA per work slot (nleaf x parts; a balanced split of the
-// leaf's dense items and far pieces made at assembly).  With one part the CTA
-// writes y; with several, each writes its partial rows, and the last CTA of the
-// leaf to finish (arrival counter, after a memory fence) adds the parts in index
-// order and writes y -- the sum does not depend on which CTA finishes last.
+// Grid: one 64-thread CTA per work slot (a leaf's dense items and far pieces are
+// split at assembly into parts proportional to its share of the work; CTAs take
+// the slots heaviest first).  With one part the CTA writes y; with several, each
+// writes its partial rows, and the last CTA of the leaf to finish (arrival
+// counter, after a memory fence) adds the parts in index order and writes y -- the
+// sum does not depend on which CTA finishes last.
 // y is in the caller's layout: right-hand side r at y + r * 2ne.
 template <typename R, typename NS, typename FS, int NR>
 __global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const NS* __restrict__ near,
@@ -357,8 +358,9 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const NS* __
                                                       cx<R>* __restrict__ y, cx<R>* __restrict__ ypart,
                                                       unsigned int* __restrict__ arrive) {
     __shared__ bool s_last;
-    const int P = p.parts;
-    const int leaf = blockIdx.x / P, part = blockIdx.x % P;
+    const int slot = p.slot_order[blockIdx.x];
+    const int leaf = p.slot_leaf[slot], part = p.slot_part[slot];
+    const int P = p.leaf_parts[leaf];
     const int r0 = p.leaf_r0[leaf], m = p.leaf_m[leaf];
     const int i = threadIdx.x & 63;
     const bool act = i < m;
@@ -367,7 +369,6 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const NS* __
     cx<R> aJ[NR], aM[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) aJ[r] = aM[r] = mk<R>(0, 0);
-    const int slot = leaf * P + part;
     const int w0 = p.work_ptr[slot], w1 = p.work_ptr[slot + 1];
     if (act) {
         for (int w = w0; w < w1; ++w) {
@@ -437,7 +438,7 @@ static cudaError_t product_chunk(const MatvecPlan& p, const void* near_entries, 
     }
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[3], st));
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[4], st));
-    k_rows<R, NS, FS, NR><<<p.nleaf * p.parts, ROW_THREADS, 0, st>>>(p, (const NS*)near_entries, (const FS*)arena,
+    k_rows<R, NS, FS, NR><<<p.nslot, ROW_THREADS, 0, st>>>(p, (const NS*)near_entries, (const FS*)arena,
                                                                       xp, t, y, (cx<R>*)p.ypart, p.arrive);
     BEM_CUDA_TRY(cudaGetLastError());
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[5], st));
