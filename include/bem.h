@@ -212,6 +212,18 @@ bem_status bem_eval_entries(bem_ctx* ctx, const int32_t* rows, const int32_t* co
  * given nrhs.  The product reads each dense entry and each factor once per call. */
 bem_status bem_matvec(bem_ctx* ctx, const void* x, void* y, int nrhs, int dtype, void* stream);
 
+/* y = Z^H x, the conjugate transpose of the assembled operator (adjoint solves
+ * and gradients; the paper gives no adjoint).  Exact for the stored operator: the
+ * transposed dense entries and, for every far block U V^H, the product V (U^H x)
+ * through the same factors.  The matrix is complex symmetric only up to
+ * quadrature and compression, so Z^T is not used in its place.
+ * x, y: device 2ne x nrhs complex of type `dtype` (BEM_C64 or BEM_C128; the
+ * BF16-factor form has no adjoint).  The first call for a precision builds the
+ * transposed dense entries (as much memory as the dense entries) and their work
+ * schedule, allocates and synchronises `stream`; later calls are asynchronous.
+ * Errors as bem_matvec. */
+bem_status bem_matvec_adjoint(bem_ctx* ctx, const void* x, void* y, int nrhs, int dtype, void* stream);
+
 /* Kernel timing of bem_matvec.  After bem_profile_begin, every bem_matvec on ctx
  * records a CUDA event pair around each of its kernels on the caller's stream
  * (a few microseconds of overhead per product); bem_profile_end synchronises those
@@ -241,6 +253,14 @@ bem_status bem_rhs_planewave(bem_ctx* ctx, const double* khat, const bem_c128* e
  * right-hand side misses its tolerance. */
 bem_status bem_solve(bem_ctx* ctx, const void* b, void* x, int nrhs, void* stream, int* iters, double* relres);
 
+/* Solve Z^H lambda = g (the adjoint system of gradient computations) for nrhs
+ * right-hand sides, g and lambda device complex128 2ne x nrhs.  Same solver,
+ * options and outputs as bem_solve with every product replaced by
+ * bem_matvec_adjoint (inner GMRES on complex64 when assembled, else complex128;
+ * BF16 factors are not used); lambda is used as the initial guess. */
+bem_status bem_solve_adjoint(bem_ctx* ctx, const void* g, void* lambda, int nrhs, void* stream, int* iters,
+                             double* relres);
+
 /* Powers of a solution x (device complex128 2ne x nrhs) for its right-hand side b,
  * in units of 1/(2 eta0) (efficiency Q = value / (pi a^2 |E0|^2)):
  *   p_abs = Re(xJ^H X xM),  X[m,n] = int f_m . (n x f_n)   (absorbed, -Re oint E x H* . n)
@@ -250,6 +270,26 @@ bem_status bem_solve(bem_ctx* ctx, const void* b, void* x, int nrhs, void* strea
  * Host outputs of nrhs doubles each (any may be NULL).  Synchronises `stream`. */
 bem_status bem_power(bem_ctx* ctx, const void* x, const void* b, int nrhs, double* p_abs, double* p_ext,
                      double* p_sca, void* stream);
+
+/* Gradient of the absorbed power with respect to the conjugate coefficients:
+ * g = dP_abs/d conj(x) = (1/2) [X xM ; X^T xJ] (X as in bem_power; P_abs = x^H H x
+ * with H Hermitian, so g = H x).  x, g: device complex128 2ne x nrhs, distinct.
+ * Asynchronous on `stream`.  No paper counterpart (the source term of the
+ * adjoint solve of a gradient). */
+bem_status bem_absorbed_power_gradient(bem_ctx* ctx, const void* x, void* g, int nrhs, void* stream);
+
+/* Absorbed power of a weighted sum of excitations and its gradient with respect to
+ * the weights, by one forward and one adjoint solve.  bm: device complex128
+ * 2ne x nw, column i the right-hand side of excitation i (e.g. from
+ * bem_rhs_planewave); w: host nw complex weights; b = bm w, Z x = b,
+ * P = Re(xJ^H X xM) (host *p_abs), Z^H lambda = dP/d conj(x), and
+ * grad[i] = dP/d conj(w_i) = bm_i^H lambda (host nw complex; the real gradient is
+ * (2 Re grad, 2 Im grad) with respect to (Re w, Im w)).  x_out, lambda_out: device
+ * complex128 2ne, or NULL.  iters (host, may be NULL): inner iterations of both
+ * solves.  Solver options as bem_solve.  Allocates scratch; synchronises `stream`.
+ * No paper counterpart. */
+bem_status bem_grad_weights(bem_ctx* ctx, const void* bm, int nw, const bem_c128* w, double* p_abs,
+                            bem_c128* grad, void* x_out, void* lambda_out, void* stream, int* iters);
 
 /* Absorbed power density per triangle for the first right-hand side of x
  * (device complex128): per_tri (device, nt doubles) = Re(sum_ij conj(xJ_i) X_t[i,j] xM_j) / area_t,

@@ -27,6 +27,7 @@ EXPORTS = [
     "bem_debye_eps", "bem_assemble", "bem_num_edges", "bem_num_unknowns", "bem_edges", "bem_stats_get",
     "bem_partition", "bem_eval_entries", "bem_matvec", "bem_rhs_planewave", "bem_solve", "bem_power",
     "bem_power_density", "bem_profile_begin", "bem_profile_end", "bem_absorbed_power_static",
+    "bem_matvec_adjoint", "bem_solve_adjoint", "bem_absorbed_power_gradient", "bem_grad_weights",
 ]
 KERNEL_NAMES = ["k_gather", "k_vhx", "k_rows"]   # BEM_KERNEL_GATHER, _VHX, _ROWS
 
@@ -90,6 +91,11 @@ def _load():
         "bem_partition": (ctypes.c_int, [ctx, i64p, i32p, i32p]),
         "bem_eval_entries": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int64, vp, ctypes.c_int, vp]),
         "bem_matvec": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
+        "bem_matvec_adjoint": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
+        "bem_solve_adjoint": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int), dp]),
+        "bem_absorbed_power_gradient": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, vp]),
+        "bem_grad_weights": (ctypes.c_int, [ctx, vp, ctypes.c_int, ctypes.POINTER(bem_c128), dp,
+                                            ctypes.POINTER(bem_c128), vp, vp, vp, ctypes.POINTER(ctypes.c_int)]),
         "bem_rhs_planewave": (ctypes.c_int, [ctx, dp, ctypes.POINTER(bem_c128), ctypes.c_int, vp, ctypes.c_int, vp]),
         "bem_solve": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int), dp]),
         "bem_power": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, dp, dp, dp, vp]),
@@ -208,6 +214,11 @@ def bem_matvec(ctx, x_ptr: int, y_ptr: int, nrhs: int, dtype: int, stream: int =
                                ctypes.c_void_p(stream)))
 
 
+def bem_matvec_adjoint(ctx, x_ptr: int, y_ptr: int, nrhs: int, dtype: int, stream: int = 0) -> None:
+    _check(ctx, lib.bem_matvec_adjoint(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), int(nrhs), int(dtype),
+                                       ctypes.c_void_p(stream)))
+
+
 def bem_rhs_planewave(ctx, khat, e0, b_ptr: int, dtype: int, stream: int = 0) -> None:
     kh = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
     e = np.ascontiguousarray(np.atleast_2d(e0), dtype=np.complex128)
@@ -224,6 +235,36 @@ def bem_solve(ctx, b_ptr: int, x_ptr: int, nrhs: int, stream: int = 0, raise_on_
     if st != BEM_OK and not (st == BEM_ENOCONV and not raise_on_noconv):
         _check(ctx, st)
     return it.value, rel, st
+
+
+def bem_solve_adjoint(ctx, g_ptr: int, lam_ptr: int, nrhs: int, stream: int = 0, raise_on_noconv: bool = True):
+    """Solve Z^H lambda = g.  Returns (iterations, relative residual per right-hand side, status)."""
+    it = ctypes.c_int(0)
+    rel = np.zeros(nrhs, dtype=np.float64)
+    st = lib.bem_solve_adjoint(ctx, ctypes.c_void_p(g_ptr), ctypes.c_void_p(lam_ptr), int(nrhs),
+                               ctypes.c_void_p(stream), ctypes.byref(it), _np_ptr(rel, ctypes.c_double))
+    if st != BEM_OK and not (st == BEM_ENOCONV and not raise_on_noconv):
+        _check(ctx, st)
+    return it.value, rel, st
+
+
+def bem_absorbed_power_gradient(ctx, x_ptr: int, g_ptr: int, nrhs: int, stream: int = 0) -> None:
+    _check(ctx, lib.bem_absorbed_power_gradient(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(g_ptr), int(nrhs),
+                                                ctypes.c_void_p(stream)))
+
+
+def bem_grad_weights(ctx, bm_ptr: int, w, x_ptr: int = 0, lam_ptr: int = 0, stream: int = 0):
+    """Returns (P_abs, dP/d conj(w) as a complex128 array, inner iterations)."""
+    w = np.ascontiguousarray(w, dtype=np.complex128)
+    nw = len(w)
+    grad = np.zeros(nw, dtype=np.complex128)
+    p = ctypes.c_double(0.0)
+    it = ctypes.c_int(0)
+    _check(ctx, lib.bem_grad_weights(ctx, ctypes.c_void_p(bm_ptr), nw, w.ctypes.data_as(ctypes.POINTER(bem_c128)),
+                                     ctypes.byref(p), grad.ctypes.data_as(ctypes.POINTER(bem_c128)),
+                                     ctypes.c_void_p(x_ptr or None), ctypes.c_void_p(lam_ptr or None),
+                                     ctypes.c_void_p(stream), ctypes.byref(it)))
+    return p.value, grad, it.value
 
 
 def bem_power(ctx, x_ptr: int, b_ptr: int, nrhs: int, stream: int = 0):

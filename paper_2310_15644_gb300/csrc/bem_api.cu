@@ -36,6 +36,24 @@ using namespace bem;
 
 namespace {
 
+// Work schedule of the rows kernel, for the forward or the adjoint product
+struct RowsPlan {
+    int64_t near_stride = 0;           // complex elements per operator array of the dense items
+    int nslot = 0, pmax = 1;           // rows-kernel CTAs; most slots of one leaf
+    DevBuf d_work_ptr, d_work_item, d_near_c0, d_near_n, d_near_off, d_farp_blk, d_farp_row, d_ypart, d_arrive;
+    DevBuf d_leaf_parts, d_slot_order, d_slot_leaf, d_slot_part;
+};
+
+static void release_rows_plan(RowsPlan& r) {
+    DevBuf* plan[] = {&r.d_work_ptr,   &r.d_work_item, &r.d_near_c0,  &r.d_near_n,     &r.d_near_off,
+                      &r.d_farp_blk,   &r.d_farp_row,  &r.d_ypart,    &r.d_arrive,     &r.d_leaf_parts,
+                      &r.d_slot_order, &r.d_slot_leaf, &r.d_slot_part};
+    for (DevBuf* b : plan) dfree(*b);
+    r.near_stride = 0;
+    r.nslot = 0;
+    r.pmax = 1;
+}
+
 struct Operator {
     bool built = false;
     // product plan of this precision: dense items (leaf row x column range) and far pieces
@@ -43,11 +61,11 @@ struct Operator {
     std::vector<BlockDesc> far_desc;   // blocks stored as factors (partition far blocks, or their splits)
     int64_t n_far_split = 0;           // far blocks split because their rank passed the cap
     int64_t n_far_dense = 0;           // partition far blocks stored densely (rank above break-even)
-    int64_t near_stride = 0;
-    int nslot = 0, pmax = 1;           // rows-kernel CTAs; most slots of one leaf
-    DevBuf d_work_ptr, d_work_item, d_near_c0, d_near_n, d_near_off, d_farp_blk, d_farp_row, d_ypart, d_arrive;
-    DevBuf d_leaf_parts, d_slot_order, d_slot_leaf, d_slot_part;
-    DevBuf near;          // 3 * near_stride complex
+    RowsPlan fwd;         // rows kernel of Z x (items by row leaf)
+    RowsPlan adj;         // rows kernel of Z^H x (transposed items, by column leaf); built on first use
+    bool adj_built = false;
+    DevBuf near;          // 3 * fwd.near_stride complex
+    DevBuf nearT;         // transposed dense items, 3 * adj.near_stride complex (adjoint)
     DevBuf arena;         // low-rank factors
     DevBuf arena_bf16;    // BF16 copy of the factors (complex64 operator, BEM_PREC_BF16F)
     int64_t arena_len = 0;
@@ -201,15 +219,14 @@ static c128 csqrt_principal(c128 z) {
 }
 
 static void release_operator(Operator& o) {
-    DevBuf* plan[] = {&o.d_work_ptr,  &o.d_work_item,  &o.d_near_c0,   &o.d_near_n,    &o.d_near_off,
-                      &o.d_farp_blk,  &o.d_farp_row,   &o.d_ypart,     &o.d_arrive,    &o.d_leaf_parts,
-                      &o.d_slot_order, &o.d_slot_leaf, &o.d_slot_part};
-    for (DevBuf* b : plan) dfree(*b);
+    release_rows_plan(o.fwd);
+    release_rows_plan(o.adj);
+    o.adj_built = false;
+    dfree(o.nearT);
     o.items.clear();
     o.far_desc.clear();
     o.n_far_dense = 0;
     o.n_far_split = 0;
-    o.near_stride = 0;
     dfree(o.near);
     dfree(o.arena);
     dfree(o.arena_bf16);
@@ -723,11 +740,14 @@ static bem_status build_leaves(bem_ctx* c, cudaStream_t st) {
     return BEM_OK;
 }
 
-// Work schedule of the rows kernel for one operator.  Every leaf's dense items
-// and far pieces are split over parts x BEM_ROW_GROUPS work slots (one 64-thread group each),
-// largest item first to the least loaded slot (ties: lowest slot), so that the
-// groups of a leaf stream about the same number of bytes.
-static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaStream_t st) {
+// Work schedule of the rows kernel.  Every row leaf's dense items and far pieces
+// are split over work slots (one 64-thread CTA each), largest item first to the
+// least loaded slot (ties: lowest slot), so that the CTAs of a leaf stream about
+// the same number of bytes.  Forward: items are (row leaf x column range) and a
+// far block gives a piece to every leaf of its rows; adjoint: items are the
+// transposed items and a far block gives a piece to every leaf of its columns.
+static bem_status build_rows_plan(bem_ctx* c, const Operator& o, const std::vector<BlockDesc>& dense, bool adjoint,
+                                  RowsPlan& rp, size_t es, cudaStream_t st) {
     const int nleaf = (int)c->leaf_lo.size();
     std::vector<int> leaf_of(c->ne + 1, -1);
     for (int l = 0; l < nleaf; ++l) leaf_of[c->leaf_lo[l]] = l;
@@ -736,8 +756,8 @@ static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaSt
     std::vector<int64_t> noff;
     std::vector<std::vector<std::pair<int64_t, int>>> items(nleaf);  // (cost, encoded item)
     int64_t off = 0;
-    for (size_t k = 0; k < o.items.size(); ++k) {
-        const BlockDesc& b = o.items[k];
+    for (size_t k = 0; k < dense.size(); ++k) {
+        const BlockDesc& b = dense[k];
         int l = leaf_of[b.r0];
         if (l < 0 || c->leaf_m[l] != b.m) return fail(c, BEM_ECUDA, "dense item rows are not a leaf");
         nc0.push_back(b.c0);
@@ -747,19 +767,20 @@ static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaSt
         off += cost;
         items[l].push_back({3 * cost, (int)k});
     }
-    o.near_stride = off;
-    // far pieces: every leaf inside a far block's row range
+    rp.near_stride = off;
+    // far pieces: every leaf inside a far block's row range (adjoint: column range)
     std::vector<int> fblk, frow;
     for (size_t k = 0; k < o.far_desc.size(); ++k) {
         const BlockDesc& F = o.far_desc[k];
         const FarRec& R = o.recs[k];
         int64_t kp2 = 2 * (int64_t)((R.rk[0] + 1) / 2 + (R.rk[1] + 1) / 2 + (R.rk[2] + 1) / 2);
-        int l = leaf_of[F.r0];
+        const int lo = adjoint ? F.c0 : F.r0, sz = adjoint ? F.n : F.m;
+        int l = leaf_of[lo];
         if (l < 0) return fail(c, BEM_ECUDA, "far block does not start at a leaf");
-        for (; l < nleaf && c->leaf_lo[l] < F.r0 + F.m; ++l) {
+        for (; l < nleaf && c->leaf_lo[l] < lo + sz; ++l) {
             int id = (int)fblk.size();
             fblk.push_back((int)k);
-            frow.push_back(c->leaf_lo[l] - F.r0);
+            frow.push_back(c->leaf_lo[l] - lo);
             items[l].push_back({(int64_t)c->leaf_m[l] * kp2, -1 - id});
         }
     }
@@ -774,7 +795,7 @@ static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaSt
     const double per_slot = std::max(1.0, (double)total / BEM_ROW_TARGET_CTAS);
     std::vector<int> wptr(1, 0), witem, lparts(nleaf), sleaf, spart;
     std::vector<int64_t> scost;
-    o.pmax = 1;
+    rp.pmax = 1;
     for (int l = 0; l < nleaf; ++l) {
         auto& v = items[l];
         std::stable_sort(v.begin(), v.end(), [](const std::pair<int64_t, int>& x, const std::pair<int64_t, int>& y) {
@@ -783,7 +804,7 @@ static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaSt
         const int S = (int)std::max<int64_t>(
             1, std::min<int64_t>({32, (int64_t)v.size(), (int64_t)std::ceil((double)lw[l] / per_slot)}));
         lparts[l] = S;
-        o.pmax = std::max(o.pmax, S);
+        rp.pmax = std::max(rp.pmax, S);
         std::vector<int64_t> load(S, 0);
         std::vector<std::vector<int>> slot(S);
         for (auto& it : v) {
@@ -801,24 +822,24 @@ static bem_status build_operator_plan(bem_ctx* c, Operator& o, size_t es, cudaSt
             scost.push_back(load[q]);
         }
     }
-    o.nslot = (int)sleaf.size();
-    std::vector<int> sorder(o.nslot);
+    rp.nslot = (int)sleaf.size();
+    std::vector<int> sorder(rp.nslot);
     std::iota(sorder.begin(), sorder.end(), 0);
     std::stable_sort(sorder.begin(), sorder.end(), [&](int x, int y) { return scost[x] > scost[y]; });
-    CK(upload(o.d_leaf_parts, lparts, st));
-    CK(upload(o.d_slot_order, sorder, st));
-    CK(upload(o.d_slot_leaf, sleaf, st));
-    CK(upload(o.d_slot_part, spart, st));
-    CK(upload(o.d_work_ptr, wptr, st));
-    CK(upload(o.d_work_item, witem, st));
-    CK(upload(o.d_near_c0, nc0, st));
-    CK(upload(o.d_near_n, nn, st));
-    CK(upload(o.d_near_off, noff, st));
-    CK(upload(o.d_farp_blk, fblk, st));
-    CK(upload(o.d_farp_row, frow, st));
-    CK(dalloc(o.d_ypart, es * 2 * c->ne * (o.pmax > 1 ? o.pmax : 1) * BEM_MAX_NR));
-    CK(dalloc(o.d_arrive, sizeof(unsigned int) * std::max(1, nleaf)));
-    CK(cudaMemsetAsync(o.d_arrive.p, 0, sizeof(unsigned int) * std::max(1, nleaf), st));
+    CK(upload(rp.d_leaf_parts, lparts, st));
+    CK(upload(rp.d_slot_order, sorder, st));
+    CK(upload(rp.d_slot_leaf, sleaf, st));
+    CK(upload(rp.d_slot_part, spart, st));
+    CK(upload(rp.d_work_ptr, wptr, st));
+    CK(upload(rp.d_work_item, witem, st));
+    CK(upload(rp.d_near_c0, nc0, st));
+    CK(upload(rp.d_near_n, nn, st));
+    CK(upload(rp.d_near_off, noff, st));
+    CK(upload(rp.d_farp_blk, fblk, st));
+    CK(upload(rp.d_farp_row, frow, st));
+    CK(dalloc(rp.d_ypart, es * 2 * c->ne * (rp.pmax > 1 ? rp.pmax : 1) * BEM_MAX_NR));
+    CK(dalloc(rp.d_arrive, sizeof(unsigned int) * std::max(1, nleaf)));
+    CK(cudaMemsetAsync(rp.d_arrive.p, 0, sizeof(unsigned int) * std::max(1, nleaf), st));
     CK(cudaStreamSynchronize(st));
     return BEM_OK;
 }
@@ -1108,7 +1129,7 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
     CK(upload(o.far_rec, o.recs, st));
     CK(upload(o.far_order, units, st));
     bem_status s;
-    if ((s = build_operator_plan(c, o, es, st)) != BEM_OK) return s;
+    if ((s = build_rows_plan(c, o, o.items, false, o.fwd, es, st)) != BEM_OK) return s;
     CK(dalloc(o.xp, es * 2 * c->ne * BEM_MAX_NR));
     CK(dalloc(o.t, es * std::max<int64_t>(1, o.t_len) * BEM_MAX_NR));
     lap(BEM_PHASE_PLAN);
@@ -1231,7 +1252,8 @@ extern "C" bem_status bem_eval_entries(bem_ctx* c, const int32_t* rows, const in
     return BEM_OK;
 }
 
-static MatvecPlan make_plan(const bem_ctx* c, const Operator& o) {
+static MatvecPlan make_plan(const bem_ctx* c, const Operator& o, bool adjoint = false) {
+    const RowsPlan& rp = adjoint ? o.adj : o.fwd;
     MatvecPlan p;
     p.ne = (int)c->ne;
     p.nleaf = (int)c->leaf_lo.size();
@@ -1239,30 +1261,77 @@ static MatvecPlan make_plan(const bem_ctx* c, const Operator& o) {
     p.perm = (const int64_t*)c->d_perm.p;
     p.leaf_r0 = (const int*)c->d_leaf_r0.p;
     p.leaf_m = (const int*)c->d_leaf_m.p;
-    p.nslot = o.nslot;
-    p.pmax = o.pmax;
-    p.leaf_parts = (const int*)o.d_leaf_parts.p;
-    p.slot_order = (const int*)o.d_slot_order.p;
-    p.slot_leaf = (const int*)o.d_slot_leaf.p;
-    p.slot_part = (const int*)o.d_slot_part.p;
-    p.work_ptr = (const int*)o.d_work_ptr.p;
-    p.work_item = (const int*)o.d_work_item.p;
-    p.ypart = o.d_ypart.p;
-    p.arrive = (unsigned int*)o.d_arrive.p;
-    p.near_c0 = (const int*)o.d_near_c0.p;
-    p.near_n = (const int*)o.d_near_n.p;
-    p.near_off = (const int64_t*)o.d_near_off.p;
-    p.near_op_stride = o.near_stride;
-    p.farp_blk = (const int*)o.d_farp_blk.p;
-    p.farp_row = (const int*)o.d_farp_row.p;
+    p.nslot = rp.nslot;
+    p.pmax = rp.pmax;
+    p.leaf_parts = (const int*)rp.d_leaf_parts.p;
+    p.slot_order = (const int*)rp.d_slot_order.p;
+    p.slot_leaf = (const int*)rp.d_slot_leaf.p;
+    p.slot_part = (const int*)rp.d_slot_part.p;
+    p.work_ptr = (const int*)rp.d_work_ptr.p;
+    p.work_item = (const int*)rp.d_work_item.p;
+    p.ypart = rp.d_ypart.p;
+    p.arrive = (unsigned int*)rp.d_arrive.p;
+    p.near_c0 = (const int*)rp.d_near_c0.p;
+    p.near_n = (const int*)rp.d_near_n.p;
+    p.near_off = (const int64_t*)rp.d_near_off.p;
+    p.near_op_stride = rp.near_stride;
+    p.farp_blk = (const int*)rp.d_farp_blk.p;
+    p.farp_row = (const int*)rp.d_farp_row.p;
     p.far = (const FarRec*)o.far_rec.p;
     p.vhx_units = (const int2*)o.far_order.p;
     p.nvhx = o.nvhx;
+    p.pos_leaf_lo = (const int*)c->d_pos_leaf_lo.p;
+    p.pos_leaf_m = (const int*)c->d_pos_leaf_m.p;
     return p;
 }
 
+// Transposed dense items and the adjoint rows plan of operator o (first adjoint use)
+template <typename R>
+static bem_status ensure_adjoint(bem_ctx* c, Operator& o, cudaStream_t st) {
+    if (o.adj_built) return BEM_OK;
+    const size_t es = sizeof(cx<R>);
+    const size_t ni = o.items.size();
+    std::vector<BlockDesc> itemsT(ni);
+    std::vector<int64_t> offF(ni), offT(ni);
+    int64_t oF = 0, oT = 0;
+    for (size_t k = 0; k < ni; ++k) {
+        const BlockDesc& b = o.items[k];
+        offF[k] = oF;
+        oF += (int64_t)b.m * 2 * ((b.n + 1) / 2);
+        itemsT[k] = {b.c0, b.n, b.r0, b.m};
+        offT[k] = oT;
+        oT += (int64_t)b.n * 2 * ((b.m + 1) / 2);
+    }
+    bem_status s;
+    if ((s = build_rows_plan(c, o, itemsT, true, o.adj, es, st)) != BEM_OK) return s;
+    if (o.adj.near_stride != oT || o.fwd.near_stride != oF) return fail(c, BEM_ECUDA, "adjoint item layout");
+    DevBuf d_items, d_offF, d_offT;
+    struct G {
+        DevBuf* b[3];
+        ~G() {
+            for (DevBuf* x : b) dfree(*x);
+        }
+    } guard{{&d_items, &d_offF, &d_offT}};
+    CK(upload(d_items, o.items, st));
+    CK(upload(d_offF, offF, st));
+    CK(upload(d_offT, offT, st));
+    CK(dalloc(o.nearT, es * 3 * std::max<int64_t>(1, oT)));
+    CK(transpose_items<R>((const BlockDesc*)d_items.p, (const int64_t*)d_offF.p, (const int64_t*)d_offT.p, (int)ni,
+                          (const cx<R>*)o.near.p, oF, (cx<R>*)o.nearT.p, oT, st));
+    CK(cudaStreamSynchronize(st));
+    o.adj_built = true;
+    return BEM_OK;
+}
+
+static bem_status ensure_adjoint_for(bem_ctx* c, int dtype, cudaStream_t st) {
+    if (dtype == BEM_C64 || dtype == DT_C64_IN_FP64) return ensure_adjoint<float>(c, c->op[0], st);
+    if (dtype == BEM_C128) return ensure_adjoint<double>(c, c->op[1], st);
+    return fail(c, BEM_EINVAL, "the adjoint product exists for BEM_C64 and BEM_C128");
+}
+
+// y = Z x (adjoint: y = Z^H x, after ensure_adjoint_for)
 static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int nrhs, cudaStream_t st,
-                              bool record = false) {
+                              bool record = false, bool adjoint = false) {
     const cudaEvent_t* ev = nullptr;
     if (record && c->prof) {
         size_t need = c->ev_used + 6 * (size_t)nrhs;
@@ -1278,20 +1347,22 @@ static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int
     if (dtype == BEM_C64 || dtype == BEM_C64_BF16F) {
         Operator& o = c->op[0];
         const bool bf = dtype == BEM_C64_BF16F;
-        return matvec_run<float>(make_plan(c, o), o.near.p, bf ? o.arena_bf16.p : o.arena.p, (const c64*)x, (c64*)y,
-                                 (c64*)o.xp.p, (c64*)o.t.p, nrhs, o.t_len, st, ev,
-                                 bf ? BEM_FORM_BF16F : BEM_FORM_NATIVE);
+        if (bf && adjoint) return cudaErrorInvalidValue;
+        return matvec_run<float>(make_plan(c, o, adjoint), adjoint ? o.nearT.p : o.near.p,
+                                 bf ? o.arena_bf16.p : o.arena.p, (const c64*)x, (c64*)y, (c64*)o.xp.p, (c64*)o.t.p,
+                                 nrhs, o.t_len, st, ev, bf ? BEM_FORM_BF16F : BEM_FORM_NATIVE, adjoint);
     }
     if (dtype == DT_C64_IN_FP64) {
         // complex128 vectors through the complex64 operator (its workspaces hold one
         // complex128 right-hand side)
         Operator& o = c->op[0];
-        return matvec_run<double>(make_plan(c, o), o.near.p, o.arena.p, (const c128*)x, (c128*)y, (c128*)o.xp.p,
-                                  (c128*)o.t.p, nrhs, o.t_len, st, ev, BEM_FORM_C64_IN_FP64);
+        return matvec_run<double>(make_plan(c, o, adjoint), adjoint ? o.nearT.p : o.near.p, o.arena.p,
+                                  (const c128*)x, (c128*)y, (c128*)o.xp.p, (c128*)o.t.p, nrhs, o.t_len, st, ev,
+                                  BEM_FORM_C64_IN_FP64, adjoint);
     }
     Operator& o = c->op[1];
-    return matvec_run<double>(make_plan(c, o), o.near.p, o.arena.p, (const c128*)x, (c128*)y, (c128*)o.xp.p,
-                              (c128*)o.t.p, nrhs, o.t_len, st, ev);
+    return matvec_run<double>(make_plan(c, o, adjoint), adjoint ? o.nearT.p : o.near.p, o.arena.p, (const c128*)x,
+                              (c128*)y, (c128*)o.xp.p, (c128*)o.t.p, nrhs, o.t_len, st, ev, BEM_FORM_NATIVE, adjoint);
 }
 
 extern "C" bem_status bem_profile_begin(bem_ctx* c) {
@@ -1331,6 +1402,23 @@ extern "C" bem_status bem_matvec(bem_ctx* c, const void* x, void* y, int nrhs, i
     const char* ya = (const char*)y;
     if (xa < ya + bytes && ya < xa + bytes) return fail(c, BEM_EINVAL, "x and y overlap");
     CK(matvec_any(c, dtype, x, y, nrhs, (cudaStream_t)stream, true));
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_matvec_adjoint(bem_ctx* c, const void* x, void* y, int nrhs, int dtype, void* stream) {
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "bem_matvec_adjoint needs bem_assemble");
+    if (dtype != BEM_C64 && dtype != BEM_C128) return fail(c, BEM_EINVAL, "dtype: BEM_C64 or BEM_C128");
+    if (!dtype_ok(c, dtype)) return fail(c, BEM_EINVAL, "no operator of that precision was assembled");
+    if (nrhs < 1 || !x || !y) return fail(c, BEM_EINVAL, "bad arguments");
+    int64_t bytes = (int64_t)esize_of(dtype) * 2 * c->ne * nrhs;
+    const char* xa = (const char*)x;
+    const char* ya = (const char*)y;
+    if (xa < ya + bytes && ya < xa + bytes) return fail(c, BEM_EINVAL, "x and y overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    bem_status s;
+    if ((s = ensure_adjoint_for(c, dtype, st)) != BEM_OK) return s;
+    CK(matvec_any(c, dtype, x, y, nrhs, st, true, true));
     return BEM_OK;
 }
 
@@ -1395,7 +1483,7 @@ static bem_status gmres_work(bem_ctx* c, int dtype, int restart) {
 
 // solve Z x = rhs (dtype vectors in gw.rin / gw.xin), x starts at zero; absolute tolerance
 static bem_status gmres(bem_ctx* c, int pdt, double tol_abs, int maxit, int* iters, double* final_res,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool adjoint = false) {
     const int dtype = vec_dtype(pdt);  // vectors; pdt selects the product
     GmresWork& w = c->gw;
     const int64_t n = w.n;
@@ -1417,7 +1505,7 @@ static bem_status gmres(bem_ctx* c, int pdt, double tol_abs, int maxit, int* ite
         g[0] = mk<double>(beta, 0);
         int jl = -1;
         for (int j = 0; j < m; ++j) {
-            CK(matvec_any(c, pdt, V + es * n * j, w.w.p, 1, st));
+            CK(matvec_any(c, pdt, V + es * n * j, w.w.p, 1, st, false, adjoint));
             for (int pass = 0; pass < 2; ++pass) {
                 CK(kv_multidot(V, dtype, n, j + 1, w.w.p, n, (c128*)w.hpart.p, NPART, st));
                 CK(kv_reduce_partials((const c128*)w.hpart.p, NPART, j + 1, (c128*)w.hdev.p, st));
@@ -1466,7 +1554,7 @@ static bem_status gmres(bem_ctx* c, int pdt, double tol_abs, int maxit, int* ite
         CK(cudaMemcpyAsync(w.hdev.p, y.data(), sizeof(c128) * k, cudaMemcpyHostToDevice, st));
         CK(kv_update(w.xin.p, V, dtype, n, k, (const c128*)w.hdev.p, 1.0, n, st));
         // true residual
-        CK(matvec_any(c, pdt, w.xin.p, w.z.p, 1, st));
+        CK(matvec_any(c, pdt, w.xin.p, w.z.p, 1, st, false, adjoint));
         CK(kv_sub(w.rin.p, w.z.p, w.r.p, dtype, n, st));
     }
     *iters += it;
@@ -1474,15 +1562,22 @@ static bem_status gmres(bem_ctx* c, int pdt, double tol_abs, int maxit, int* ite
     return BEM_OK;
 }
 
-extern "C" bem_status bem_solve(bem_ctx* c, const void* b, void* x, int nrhs, void* stream, int* iters,
-                                double* relres) {
+static bem_status solve_impl(bem_ctx* c, const void* b, void* x, int nrhs, void* stream, int* iters, double* relres,
+                             bool adjoint) {
     if (!c) return BEM_EINVAL;
     if (!c->assembled) return fail(c, BEM_ESTATE, "bem_solve needs bem_assemble");
     if (nrhs < 1 || !b || !x) return fail(c, BEM_EINVAL, "bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    const int din = dtype_ok(c, BEM_C64_BF16F) ? BEM_C64_BF16F : (c->op[0].built ? BEM_C64 : BEM_C128);
+    // the BF16-factor product has no adjoint form
+    const int din = (!adjoint && dtype_ok(c, BEM_C64_BF16F)) ? BEM_C64_BF16F : (c->op[0].built ? BEM_C64 : BEM_C128);
     const int vin = vec_dtype(din);
     const bool out128 = c->op[1].built;
+    const int dres = out128 ? BEM_C128 : DT_C64_IN_FP64;
+    if (adjoint) {
+        bem_status s0;
+        if ((s0 = ensure_adjoint_for(c, din, st)) != BEM_OK) return s0;
+        if ((s0 = ensure_adjoint_for(c, dres, st)) != BEM_OK) return s0;
+    }
     bem_status s;
     if ((s = gmres_work(c, vin, c->opt.gmres_restart)) != BEM_OK) return s;
     const int64_t n = 2 * c->ne;
@@ -1516,7 +1611,7 @@ extern "C" bem_status bem_solve(bem_ctx* c, const void* b, void* x, int nrhs, vo
         bool inner_ok = true;
         for (int step = 0;; ++step) {
             // r = b - Z x with the most accurate operator
-            CK(matvec_any(c, out128 ? BEM_C128 : DT_C64_IN_FP64, xr, zr.p, 1, st));
+            CK(matvec_any(c, dres, xr, zr.p, 1, st, false, adjoint));
             CK(kv_sub(br, zr.p, rr.p, BEM_C128, n, st));
             double rn;
             if ((s = norm_dev(c, BEM_C128, rr.p, n, &rn, st)) != BEM_OK) return s;
@@ -1530,13 +1625,14 @@ extern "C" bem_status bem_solve(bem_ctx* c, const void* b, void* x, int nrhs, vo
                 CK(cudaMemcpyAsync(c->gw.rin.p, rr.p, sizeof(c128) * n, cudaMemcpyDeviceToDevice, st));
             double fres;
             int before = total_it;
-            if ((s = gmres(c, din, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st)) != BEM_OK)
+            if ((s = gmres(c, din, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st, adjoint)) !=
+                BEM_OK)
                 return s;
             inner_ok = fres <= c->opt.tol * rn * 1.0000001;
             CK(kv_axpy_c128(xr, c->gw.xin.p, vin, (const c128*)c->d_one.p, 1.0, n, 1, n, st));
             if (total_it >= c->opt.maxit || total_it == before) {
                 // out of iterations (or no progress possible): measure and stop
-                CK(matvec_any(c, out128 ? BEM_C128 : DT_C64_IN_FP64, xr, zr.p, 1, st));
+                CK(matvec_any(c, dres, xr, zr.p, 1, st, false, adjoint));
                 CK(kv_sub(br, zr.p, rr.p, BEM_C128, n, st));
                 if ((s = norm_dev(c, BEM_C128, rr.p, n, &rn, st)) != BEM_OK) return s;
                 rel = rn / bn;
@@ -1551,6 +1647,16 @@ extern "C" bem_status bem_solve(bem_ctx* c, const void* b, void* x, int nrhs, vo
     if (iters) *iters = total_it;
     if (!all_ok) return fail(c, BEM_ENOCONV, "solver did not reach its tolerance");
     return BEM_OK;
+}
+
+extern "C" bem_status bem_solve(bem_ctx* c, const void* b, void* x, int nrhs, void* stream, int* iters,
+                                double* relres) {
+    return solve_impl(c, b, x, nrhs, stream, iters, relres, false);
+}
+
+extern "C" bem_status bem_solve_adjoint(bem_ctx* c, const void* g, void* lambda, int nrhs, void* stream, int* iters,
+                                        double* relres) {
+    return solve_impl(c, g, lambda, nrhs, stream, iters, relres, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -1619,6 +1725,76 @@ extern "C" bem_status bem_power(bem_ctx* c, const void* x, const void* b, int nr
         memcpy(p_sca, host.data(), sizeof(double) * nrhs);
     }
     CK(cudaStreamSynchronize(st));
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_absorbed_power_gradient(bem_ctx* c, const void* x, void* g, int nrhs, void* stream) {
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "bem_absorbed_power_gradient needs bem_assemble");
+    if (nrhs < 1 || !x || !g || x == g) return fail(c, BEM_EINVAL, "bad arguments");
+    CK(power_abs_grad(geom_view(c), (const c128*)x, nrhs, (c128*)g, (cudaStream_t)stream));
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_grad_weights(bem_ctx* c, const void* bm, int nw, const bem_c128* w, double* p_abs,
+                                       bem_c128* grad, void* x_out, void* lambda_out, void* stream, int* iters) {
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "bem_grad_weights needs bem_assemble");
+    if (nw < 1 || !bm || !w || !p_abs || !grad) return fail(c, BEM_EINVAL, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = 2 * c->ne;
+    GeomDev gv = geom_view(c);
+    DevBuf d_w, d_b, d_x, d_lam, d_g, d_part, d_red;
+    struct G {
+        DevBuf* b[7];
+        ~G() {
+            for (DevBuf* x : b) dfree(*x);
+        }
+    } guard{{&d_w, &d_b, &d_x, &d_lam, &d_g, &d_part, &d_red}};
+    std::vector<c128> wh(nw);
+    for (int i = 0; i < nw; ++i) wh[i] = mk<double>(w[i].re, w[i].im);
+    CK(upload(d_w, wh, st));
+    CK(dalloc(d_b, sizeof(c128) * n));
+    CK(dalloc(d_g, sizeof(c128) * n));
+    c128* x = (c128*)x_out;
+    c128* lam = (c128*)lambda_out;
+    if (!x) {
+        CK(dalloc(d_x, sizeof(c128) * n));
+        x = (c128*)d_x.p;
+    }
+    if (!lam) {
+        CK(dalloc(d_lam, sizeof(c128) * n));
+        lam = (c128*)d_lam.p;
+    }
+    // b = Bm w
+    CK(cudaMemsetAsync(d_b.p, 0, sizeof(c128) * n, st));
+    CK(kv_update(d_b.p, bm, BEM_C128, n, nw, (const c128*)d_w.p, 1.0, n, st));
+    // x = Z^-1 b
+    CK(cudaMemsetAsync(x, 0, sizeof(c128) * n, st));
+    int it1 = 0, it2 = 0;
+    double rr;
+    bem_status s = solve_impl(c, d_b.p, x, 1, stream, &it1, &rr, false);
+    if (s != BEM_OK) return s;
+    // P = Re(xJ^H X xM)
+    const int npa = (int)((c->nt + 255) / 256);
+    CK(dalloc(d_part, sizeof(c128) * std::max<int64_t>(npa, (int64_t)NPART * nw)));
+    CK(dalloc(d_red, sizeof(c128) * nw));
+    CK(power_abs(gv, x, 1, nullptr, (double*)d_part.p, npa, st));
+    CK(kv_reduce_real((const double*)d_part.p, npa, 1, (double*)d_red.p, st));
+    CK(cudaMemcpyAsync(p_abs, d_red.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    // g = dP/dconj(x); Z^H lambda = g
+    CK(power_abs_grad(gv, x, 1, (c128*)d_g.p, st));
+    CK(cudaMemsetAsync(lam, 0, sizeof(c128) * n, st));
+    s = solve_impl(c, d_g.p, lam, 1, stream, &it2, &rr, true);
+    if (s != BEM_OK) return s;
+    // dP/dconj(w_i) = Bm_i^H lambda
+    CK(kv_multidot(bm, BEM_C128, n, nw, lam, n, (c128*)d_part.p, NPART, st));
+    CK(kv_reduce_partials((const c128*)d_part.p, NPART, nw, (c128*)d_red.p, st));
+    std::vector<c128> gh(nw);
+    CK(cudaMemcpyAsync(gh.data(), d_red.p, sizeof(c128) * nw, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < nw; ++i) grad[i] = {gh[i].re, gh[i].im};
+    if (iters) *iters = it1 + it2;
     return BEM_OK;
 }
 

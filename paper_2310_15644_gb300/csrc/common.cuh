@@ -247,6 +247,8 @@ struct MatvecPlan {
     const FarRec* far;           // nfar
     const int2* vhx_units;       // nvhx units of the V^H x kernel: (far block, group of 8 items), largest first
     int nvhx;
+    const int* pos_leaf_lo;      // ne: first tree position of each position's leaf (adjoint U^T x pass)
+    const int* pos_leaf_m;       // ne: size of each position's leaf
     void* ypart;                 // pmax x 2ne partial rows (pmax > 1)
     unsigned int* arrive;        // nleaf arrival counters, zero between products
 };
@@ -254,7 +256,11 @@ struct MatvecPlan {
 template <typename R>
 cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x,
                        cx<R>* y, cx<R>* xp, cx<R>* t, int nrhs, int64_t t_len, cudaStream_t st,
-                       const cudaEvent_t* ev, int form = BEM_FORM_NATIVE);
+                       const cudaEvent_t* ev, int form = BEM_FORM_NATIVE, bool adjoint = false);
+// Transposed copy of the dense items (adjoint product); layouts as k_transpose_items
+template <typename R>
+cudaError_t transpose_items(const BlockDesc* items, const int64_t* offF, const int64_t* offT, int nitems,
+                            const cx<R>* near, int64_t strideF, cx<R>* nearT, int64_t strideT, cudaStream_t st);
 // BF16 copy of n complex64 factor values
 cudaError_t factors_to_bf16(const c64* in, bf16c* out, int64_t n, cudaStream_t st);
 
@@ -263,6 +269,8 @@ template <typename R>
 cudaError_t rhs_planewave(GeomDev g, const double* khat, const c128* e0, int nrhs, cx<R>* b, cudaStream_t st);
 cudaError_t power_abs(GeomDev g, const c128* x, int nrhs, double* per_tri, double* partial, int npart,
                       cudaStream_t st);
+// out = d P_abs / d conj(x) = (1/2) [X xM ; X^T xJ] (device complex128, 2ne x nrhs)
+cudaError_t power_abs_grad(GeomDev g, const c128* x, int nrhs, c128* out, cudaStream_t st);
 cudaError_t power_sca(GeomDev g, const c128* x, int nrhs, double* partial, int ntheta, int nphi,
                       const double* ct, const double* wt, cudaStream_t st);
 cudaError_t dot_real_parts(const c128* a, const c128* b, int64_t n, int nrhs, double* partial, int npart,

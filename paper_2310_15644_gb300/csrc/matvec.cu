@@ -86,8 +86,9 @@ __device__ __forceinline__ void ldv(const cx<R>* __restrict__ q, cx<R> (&v)[NR])
     }
 }
 
-// xp[(pos) * NR + r] = x[r * 2ne + edge(pos)] for both halves (J: pos < ne, M: ne + pos)
-template <typename R, int NR>
+// xp[(pos) * NR + r] = x[r * 2ne + edge(pos)] for both halves (J: pos < ne, M: ne + pos),
+// conjugated for the adjoint product
+template <typename R, int NR, bool CONJ>
 __global__ void k_gather(const cx<R>* __restrict__ x, const int64_t* __restrict__ perm, cx<R>* __restrict__ xp,
                          int ne) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -96,8 +97,13 @@ __global__ void k_gather(const cx<R>* __restrict__ x, const int64_t* __restrict_
     const int64_t nn = 2 * (int64_t)ne;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        xp[(int64_t)i * NR + r] = x[r * nn + e];
-        xp[(int64_t)(ne + i) * NR + r] = x[r * nn + ne + e];
+        cx<R> a = x[r * nn + e], b = x[r * nn + ne + e];
+        if (CONJ) {
+            a.im = -a.im;
+            b.im = -b.im;
+        }
+        xp[(int64_t)i * NR + r] = a;
+        xp[(int64_t)(ne + i) * NR + r] = b;
     }
 }
 
@@ -208,12 +214,108 @@ __global__ void __launch_bounds__(VHX_THREADS) k_vhx(const FarRec* __restrict__ 
     if ((int)blockIdx.x < nunits) vhx_unit<R, F, NR>(far, units[blockIdx.x], arena, xp, t, ne);
 }
 
+// Adjoint product, first pass: t' = U^T xp over the block's rows (A and C use x_J
+// and x_M of the row cluster; B gives both segments), the same units and t layout
+// as vhx.  U is slice-major, so each row's pair index depends on its leaf: the leaf
+// start and size of every tree position come from pos_leaf_lo / pos_leaf_m.
+template <typename R, typename F, int NR>
+__device__ __forceinline__ void uhx_unit(const FarRec* __restrict__ far, int2 un, const F* __restrict__ arena,
+                                         const cx<R>* __restrict__ xp, cx<R>* __restrict__ t, int ne,
+                                         const int* __restrict__ pos_leaf_lo, const int* __restrict__ pos_leaf_m) {
+    const FarRec* Fp = far + un.x;
+    const int m = Fp->m, r0 = Fp->r0;
+    const int kpA = (Fp->rk[0] + 1) >> 1, kpB = (Fp->rk[1] + 1) >> 1, kpC = (Fp->rk[2] + 1) >> 1;
+    const int it = un.y * 8 + (threadIdx.x >> 3);
+    const int jj = threadIdx.x & 7;
+    if (it >= kpA + kpB + kpC) return;  // whole 8-lane group leaves this unit together
+    int op, kp, kpc;
+    if (it < kpA) {
+        op = 0;
+        kp = it;
+        kpc = kpA;
+    } else if (it < kpA + kpB) {
+        op = 1;
+        kp = it - kpA;
+        kpc = kpB;
+    } else {
+        op = 2;
+        kp = it - kpA - kpB;
+        kpc = kpC;
+    }
+    const F* Ub = arena + Fp->off_u[op];
+    const cx<R>* xs = xp + ((int64_t)((op == 2) ? ne : 0) + r0) * NR;  // J for A and B, M for C
+    const cx<R>* xm = xp + ((int64_t)ne + r0) * NR;
+    cx<R> a0[NR], a1[NR], b0[NR], b1[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) a0[r] = a1[r] = b0[r] = b1[r] = mk<R>(0, 0);
+    for (int i = jj; i < m; i += 8) {
+        const int ro = pos_leaf_lo[r0 + i] - r0, ms = pos_leaf_m[r0 + i];
+        cx<R> u0, u1;
+        FPair<F>::template ld<R>(Ub, (int64_t)ro * kpc + (int64_t)kp * ms + (i - ro), u0, u1);
+        cx<R> xv[NR];
+        ldv<R, NR>(xs + (int64_t)i * NR, xv);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            cfma(a0[r], u0, xv[r]);
+            cfma(a1[r], u1, xv[r]);
+        }
+        if (op == 1) {
+            ldv<R, NR>(xm + (int64_t)i * NR, xv);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                cfma(b0[r], u0, xv[r]);
+                cfma(b1[r], u1, xv[r]);
+            }
+        }
+    }
+    const unsigned mask = 0xffu << (threadIdx.x & 24);
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+        for (int o = 4; o > 0; o >>= 1) {
+            a0[r].re += __shfl_xor_sync(mask, a0[r].re, o);
+            a0[r].im += __shfl_xor_sync(mask, a0[r].im, o);
+            a1[r].re += __shfl_xor_sync(mask, a1[r].re, o);
+            a1[r].im += __shfl_xor_sync(mask, a1[r].im, o);
+            if (op == 1) {
+                b0[r].re += __shfl_xor_sync(mask, b0[r].re, o);
+                b0[r].im += __shfl_xor_sync(mask, b0[r].im, o);
+                b1[r].re += __shfl_xor_sync(mask, b1[r].re, o);
+                b1[r].im += __shfl_xor_sync(mask, b1[r].im, o);
+            }
+        }
+    if (jj == 0) {
+        cx<R>* tb = t + Fp->off_t * NR;
+        const int seg = (op == 0) ? 0 : ((op == 1) ? 2 * kpA : 2 * (kpA + 2 * kpB));
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            tb[(seg + 2 * kp) * NR + r] = a0[r];
+            tb[(seg + 2 * kp + 1) * NR + r] = a1[r];
+            if (op == 1) {
+                tb[(2 * (kpA + kpB) + 2 * kp) * NR + r] = b0[r];
+                tb[(2 * (kpA + kpB) + 2 * kp + 1) * NR + r] = b1[r];
+            }
+        }
+    }
+}
+
+template <typename R, typename F, int NR>
+__global__ void __launch_bounds__(VHX_THREADS) k_uhx(const FarRec* __restrict__ far, const int2* __restrict__ units,
+                                                     int nunits, const F* __restrict__ arena,
+                                                     const cx<R>* __restrict__ xp, cx<R>* __restrict__ t, int ne,
+                                                     const int* __restrict__ pos_leaf_lo,
+                                                     const int* __restrict__ pos_leaf_m) {
+    if ((int)blockIdx.x < nunits)
+        uhx_unit<R, F, NR>(far, units[blockIdx.x], arena, xp, t, ne, pos_leaf_lo, pos_leaf_m);
+}
+
 #define ROW_THREADS (64 * BEM_ROW_GROUPS)
 #define ROW_GROUPS BEM_ROW_GROUPS
 
 // One dense item (leaf rows x n columns): y_J += A xJ + B xM, y_M += C xM - B xJ
-// for NR right-hand sides (xJ, xM: NR values per column).
-template <typename R, typename NS, int NR>
+// for NR right-hand sides (xJ, xM: NR values per column).  ADJ: the item holds the
+// transposed blocks and B enters with the opposite signs (Z^T = [[A^T, -B^T],
+// [B^T, C^T]]).
+template <typename R, typename NS, int NR, bool ADJ>
 __device__ __forceinline__ void dense_item(const NS* __restrict__ A, int64_t stride, int m, int i, int n,
                                            const cx<R>* __restrict__ xJ, const cx<R>* __restrict__ xM,
                                            cx<R> (&aJ)[NR], cx<R> (&aM)[NR]) {
@@ -232,13 +334,22 @@ __device__ __forceinline__ void dense_item(const NS* __restrict__ A, int64_t str
         for (int r = 0; r < NR; ++r) {
             cfma(aJ[r], a0, xj0[r]);
             cfma(aJ[r], a1, xj1[r]);
-            cfma(aJ[r], b0, xm0[r]);
-            cfma(aJ[r], b1, xm1[r]);
             cfma(aM[r], c0, xm0[r]);
             cfma(aM[r], c1, xm1[r]);
-            cx<R> bx = b0 * xj0[r];
-            cfma(bx, b1, xj1[r]);
-            aM[r] = aM[r] - bx;
+            if (ADJ) {
+                cx<R> bm = b0 * xm0[r];
+                cfma(bm, b1, xm1[r]);
+                cx<R> bx = b0 * xj0[r];
+                cfma(bx, b1, xj1[r]);
+                aJ[r] = aJ[r] - bm;
+                aM[r] = aM[r] + bx;
+            } else {
+                cfma(aJ[r], b0, xm0[r]);
+                cfma(aJ[r], b1, xm1[r]);
+                cx<R> bx = b0 * xj0[r];
+                cfma(bx, b1, xj1[r]);
+                aM[r] = aM[r] - bx;
+            }
         }
     };
     int cp = 0;
@@ -274,17 +385,24 @@ __device__ __forceinline__ void dense_item(const NS* __restrict__ A, int64_t str
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             cfma(aJ[r], a0, xj0[r]);
-            cfma(aJ[r], b0, xm0[r]);
             cfma(aM[r], c0, xm0[r]);
-            aM[r] = aM[r] - b0 * xj0[r];
+            if (ADJ) {
+                aJ[r] = aJ[r] - b0 * xm0[r];
+                aM[r] = aM[r] + b0 * xj0[r];
+            } else {
+                cfma(aJ[r], b0, xm0[r]);
+                aM[r] = aM[r] - b0 * xj0[r];
+            }
         }
     }
 }
 
 // y_J += U_A tA + U_B tBM, y_M += U_C tC - U_B tBJ for rows ro + i of one far block.
 // U is slice-major: the leaf's slice (ms rows starting at ro) of operator q is one
-// contiguous run, pair (kp, i) at ro * kpc + kp * ms + i.  t values: NR per column.
-template <typename R, typename F, int NR, int MODE>
+// contiguous run, pair (kp, i) at ro * kpc + kp * ms + i (stride ms).  t values: NR
+// per column.  ADJ (rows of the block's column cluster): the factor is W, pair
+// (kp, i) at kp * n + so + i (stride n), and the B terms change sign.
+template <typename R, typename F, int NR, int MODE, bool ADJ>
 __device__ __forceinline__ void far_slice(const F* __restrict__ U, int kpc, int ms, int i,
                                           const cx<R>* __restrict__ tv, const cx<R>* __restrict__ tv2,
                                           cx<R> (&aJ)[NR], cx<R> (&aM)[NR]) {
@@ -302,6 +420,8 @@ __device__ __forceinline__ void far_slice(const F* __restrict__ U, int kpc, int 
             cfma(sum, u1, p1[r]);
             if (MODE == 2)
                 aM[r] = aM[r] + sum;
+            else if (MODE == 1 && ADJ)
+                aJ[r] = aJ[r] - sum;
             else
                 aJ[r] = aJ[r] + sum;
         }
@@ -312,7 +432,7 @@ __device__ __forceinline__ void far_slice(const F* __restrict__ U, int kpc, int 
             for (int r = 0; r < NR; ++r) {
                 cx<R> bx = u0 * p0[r];
                 cfma(bx, u1, p1[r]);
-                aM[r] = aM[r] - bx;
+                aM[r] = ADJ ? aM[r] + bx : aM[r] - bx;
             }
         }
     };
@@ -331,7 +451,8 @@ __device__ __forceinline__ void far_slice(const F* __restrict__ U, int kpc, int 
     }
 }
 
-template <typename R, typename FS, int NR>
+// ro: offset of the leaf inside the block's rows (forward) or columns (ADJ)
+template <typename R, typename FS, int NR, bool ADJ>
 __device__ __forceinline__ void far_piece(const FarRec& F, int ro, int ms, int i, const FS* __restrict__ arena,
                                           const cx<R>* __restrict__ t, cx<R> (&aJ)[NR], cx<R> (&aM)[NR]) {
     const int kpA = (F.rk[0] + 1) >> 1, kpB = (F.rk[1] + 1) >> 1, kpC = (F.rk[2] + 1) >> 1;
@@ -339,9 +460,15 @@ __device__ __forceinline__ void far_piece(const FarRec& F, int ro, int ms, int i
     const cx<R>* tBJ = tA + 2 * kpA * NR;
     const cx<R>* tBM = tBJ + 2 * kpB * NR;
     const cx<R>* tC = tBM + 2 * kpB * NR;
-    far_slice<R, FS, NR, 0>(arena + F.off_u[0] + 2 * (int64_t)ro * kpA, kpA, ms, i, tA, nullptr, aJ, aM);
-    far_slice<R, FS, NR, 1>(arena + F.off_u[1] + 2 * (int64_t)ro * kpB, kpB, ms, i, tBM, tBJ, aJ, aM);
-    far_slice<R, FS, NR, 2>(arena + F.off_u[2] + 2 * (int64_t)ro * kpC, kpC, ms, i, tC, nullptr, aJ, aM);
+    if (ADJ) {
+        far_slice<R, FS, NR, 0, true>(arena + F.off_v[0] + 2 * (int64_t)ro, kpA, F.n, i, tA, nullptr, aJ, aM);
+        far_slice<R, FS, NR, 1, true>(arena + F.off_v[1] + 2 * (int64_t)ro, kpB, F.n, i, tBM, tBJ, aJ, aM);
+        far_slice<R, FS, NR, 2, true>(arena + F.off_v[2] + 2 * (int64_t)ro, kpC, F.n, i, tC, nullptr, aJ, aM);
+    } else {
+        far_slice<R, FS, NR, 0, false>(arena + F.off_u[0] + 2 * (int64_t)ro * kpA, kpA, ms, i, tA, nullptr, aJ, aM);
+        far_slice<R, FS, NR, 1, false>(arena + F.off_u[1] + 2 * (int64_t)ro * kpB, kpB, ms, i, tBM, tBJ, aJ, aM);
+        far_slice<R, FS, NR, 2, false>(arena + F.off_u[2] + 2 * (int64_t)ro * kpC, kpC, ms, i, tC, nullptr, aJ, aM);
+    }
 }
 
 // Grid: one 64-thread CTA per work slot (a leaf's dense items and far pieces are
@@ -351,7 +478,7 @@ __device__ __forceinline__ void far_piece(const FarRec& F, int ro, int ms, int i
 // counter, after a memory fence) adds the parts in index order and writes y -- the
 // sum does not depend on which CTA finishes last.
 // y is in the caller's layout: right-hand side r at y + r * 2ne.
-template <typename R, typename NS, typename FS, int NR>
+template <typename R, typename NS, typename FS, int NR, bool ADJ>
 __global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const NS* __restrict__ near,
                                                       const FS* __restrict__ arena,
                                                       const cx<R>* __restrict__ xp, const cx<R>* __restrict__ t,
@@ -375,12 +502,12 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const NS* __
             const int item = p.work_item[w];
             if (item >= 0) {
                 const int c0 = p.near_c0[item];
-                dense_item<R, NS, NR>(near + p.near_off[item], p.near_op_stride, m, i, p.near_n[item],
+                dense_item<R, NS, NR, ADJ>(near + p.near_off[item], p.near_op_stride, m, i, p.near_n[item],
                                   xp + (int64_t)c0 * NR, xp + ((int64_t)ne + c0) * NR, aJ, aM);
             } else {
                 const int fp = -1 - item;
                 const FarRec F = p.far[p.farp_blk[fp]];
-                far_piece<R, FS, NR>(F, p.farp_row[fp], m, i, arena, t, aJ, aM);
+                far_piece<R, FS, NR, ADJ>(F, p.farp_row[fp], m, i, arena, t, aJ, aM);
             }
         }
     }
@@ -389,6 +516,10 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const NS* __
             const int64_t e = p.perm[r0 + i];
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
+                if (ADJ) {
+                    aJ[r].im = -aJ[r].im;
+                    aM[r].im = -aM[r].im;
+                }
                 y[r * nn + e] = aJ[r];
                 y[r * nn + ne + e] = aM[r];
             }
@@ -417,6 +548,10 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const NS* __
                 sj = sj + ld_cg(ypart + (q * nn + r0 + i) * NR + r);
                 sm = sm + ld_cg(ypart + (q * nn + ne + r0 + i) * NR + r);
             }
+            if (ADJ) {
+                sj.im = -sj.im;
+                sm.im = -sm.im;
+            }
             y[r * nn + e] = sj;
             y[r * nn + ne + e] = sm;
         }
@@ -424,22 +559,26 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const NS* __
     if (threadIdx.x == 0) arrive[leaf] = 0u;  // ready for the next product
 }
 
-template <typename R, typename NS, typename FS, int NR>
+template <typename R, typename NS, typename FS, int NR, bool ADJ>
 static cudaError_t product_chunk(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x,
                                  cx<R>* y, cx<R>* xp, cx<R>* t, cudaStream_t st, const cudaEvent_t* e) {
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[0], st));
-    k_gather<R, NR><<<(p.ne + 255) / 256, 256, 0, st>>>(x, p.perm, xp, p.ne);
+    k_gather<R, NR, ADJ><<<(p.ne + 255) / 256, 256, 0, st>>>(x, p.perm, xp, p.ne);
     BEM_CUDA_TRY(cudaGetLastError());
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[1], st));
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[2], st));
     if (p.nvhx > 0) {
-        k_vhx<R, FS, NR><<<p.nvhx, VHX_THREADS, 0, st>>>(p.far, p.vhx_units, p.nvhx, (const FS*)arena, xp, t, p.ne);
+        if (ADJ)
+            k_uhx<R, FS, NR><<<p.nvhx, VHX_THREADS, 0, st>>>(p.far, p.vhx_units, p.nvhx, (const FS*)arena, xp, t, p.ne,
+                                                             p.pos_leaf_lo, p.pos_leaf_m);
+        else
+            k_vhx<R, FS, NR><<<p.nvhx, VHX_THREADS, 0, st>>>(p.far, p.vhx_units, p.nvhx, (const FS*)arena, xp, t, p.ne);
         BEM_CUDA_TRY(cudaGetLastError());
     }
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[3], st));
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[4], st));
-    k_rows<R, NS, FS, NR><<<p.nslot, ROW_THREADS, 0, st>>>(p, (const NS*)near_entries, (const FS*)arena,
-                                                                      xp, t, y, (cx<R>*)p.ypart, p.arrive);
+    k_rows<R, NS, FS, NR, ADJ><<<p.nslot, ROW_THREADS, 0, st>>>(p, (const NS*)near_entries, (const FS*)arena, xp, t,
+                                                                 y, (cx<R>*)p.ypart, p.arrive);
     BEM_CUDA_TRY(cudaGetLastError());
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[5], st));
     return cudaSuccess;
@@ -447,7 +586,7 @@ static cudaError_t product_chunk(const MatvecPlan& p, const void* near_entries, 
 
 // Right-hand sides are processed in chunks of 8, 4, 2, 1: every chunk streams the
 // operator once and applies each loaded entry to all of its right-hand sides.
-template <typename R, typename NS, typename FS>
+template <typename R, typename NS, typename FS, bool ADJ>
 static cudaError_t matvec_chunks(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x,
                                  cx<R>* y, cx<R>* xp, cx<R>* t, int nrhs, cudaStream_t st, const cudaEvent_t* ev) {
     const int64_t nn = 2 * (int64_t)p.ne;
@@ -460,10 +599,10 @@ static cudaError_t matvec_chunks(const MatvecPlan& p, const void* near_entries, 
         cx<R>* yr = y + r * nn;
         cudaError_t err;
         switch (nr) {
-            case 8: err = product_chunk<R, NS, FS, 8>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
-            case 4: err = product_chunk<R, NS, FS, 4>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
-            case 2: err = product_chunk<R, NS, FS, 2>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
-            default: err = product_chunk<R, NS, FS, 1>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
+            case 8: err = product_chunk<R, NS, FS, 8, ADJ>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
+            case 4: err = product_chunk<R, NS, FS, 4, ADJ>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
+            case 2: err = product_chunk<R, NS, FS, 2, ADJ>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
+            default: err = product_chunk<R, NS, FS, 1, ADJ>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
         }
         if (err != cudaSuccess) return err;
         r += nr;
@@ -475,11 +614,13 @@ static cudaError_t matvec_chunks(const MatvecPlan& p, const void* near_entries, 
 template <typename R>
 cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x, cx<R>* y,
                        cx<R>* xp, cx<R>* t, int nrhs, int64_t t_len, cudaStream_t st, const cudaEvent_t* ev,
-                       int form) {
+                       int form, bool adjoint) {
     (void)t_len;
     if constexpr (sizeof(R) == 4) {
-        if (form == BEM_FORM_BF16F)
-            return matvec_chunks<float, c64, bf16c>(p, near_entries, arena, x, y, xp, t, nrhs, st, ev);
+        if (form == BEM_FORM_BF16F) {
+            if (adjoint) return cudaErrorInvalidValue;
+            return matvec_chunks<float, c64, bf16c, false>(p, near_entries, arena, x, y, xp, t, nrhs, st, ev);
+        }
         if (form != BEM_FORM_NATIVE) return cudaErrorInvalidValue;
     } else {
         if (form == BEM_FORM_C64_IN_FP64) {
@@ -487,15 +628,49 @@ cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void
             // one right-hand side per pass
             const int64_t nn = 2 * (int64_t)p.ne;
             for (int r = 0; r < nrhs; ++r) {
-                cudaError_t e = product_chunk<double, c64, c64, 1>(p, near_entries, arena, x + r * nn, y + r * nn,
-                                                                   xp, t, st, ev ? ev + 6 * r : nullptr);
-                if (e != cudaSuccess) return e;
+                const cudaEvent_t* e = ev ? ev + 6 * r : nullptr;
+                cudaError_t err =
+                    adjoint ? product_chunk<double, c64, c64, 1, true>(p, near_entries, arena, x + r * nn, y + r * nn,
+                                                                       xp, t, st, e)
+                            : product_chunk<double, c64, c64, 1, false>(p, near_entries, arena, x + r * nn,
+                                                                        y + r * nn, xp, t, st, e);
+                if (err != cudaSuccess) return err;
             }
             return cudaSuccess;
         }
         if (form != BEM_FORM_NATIVE) return cudaErrorInvalidValue;
     }
-    return matvec_chunks<R, cx<R>, cx<R>>(p, near_entries, arena, x, y, xp, t, nrhs, st, ev);
+    if (adjoint) return matvec_chunks<R, cx<R>, cx<R>, true>(p, near_entries, arena, x, y, xp, t, nrhs, st, ev);
+    return matvec_chunks<R, cx<R>, cx<R>, false>(p, near_entries, arena, x, y, xp, t, nrhs, st, ev);
+}
+
+// Transposed copy of the dense items for the adjoint product: item k (m rows x n
+// columns at offF[k], element (i, j) at 2 ((j / 2) m + i) + j mod 2, an odd n padded
+// with a zero column) becomes an item of n rows x m columns at offT[k] in the same
+// layout (an odd m padded with a zero column).  One CTA per item.
+template <typename R>
+__global__ void k_transpose_items(const BlockDesc* __restrict__ items, const int64_t* __restrict__ offF,
+                                  const int64_t* __restrict__ offT, const cx<R>* __restrict__ near, int64_t strideF,
+                                  cx<R>* __restrict__ nearT, int64_t strideT) {
+    const BlockDesc b = items[blockIdx.x];
+    const int m = b.m, n = b.n, mpad = m + (m & 1);
+    for (int q = 0; q < 3; ++q) {
+        const cx<R>* src = near + q * strideF + offF[blockIdx.x];
+        cx<R>* dst = nearT + q * strideT + offT[blockIdx.x];
+        for (int e = threadIdx.x; e < n * mpad; e += blockDim.x) {
+            const int j = e % n, i = e / n;  // destination row j (a column of the item), column i
+            const cx<R> v = i < m ? src[2 * ((int64_t)(j >> 1) * m + i) + (j & 1)] : mk<R>(0, 0);
+            dst[2 * ((int64_t)(i >> 1) * n + j) + (i & 1)] = v;
+        }
+    }
+}
+
+template <typename R>
+cudaError_t transpose_items(const BlockDesc* items, const int64_t* offF, const int64_t* offT, int nitems,
+                            const cx<R>* near, int64_t strideF, cx<R>* nearT, int64_t strideT, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    k_transpose_items<R><<<nitems, 256, 0, st>>>(items, offF, offT, near, strideF, nearT, strideT);
+    return cudaGetLastError();
 }
 
 // BF16 copy of complex64 factors (round to nearest even per component)
@@ -512,8 +687,12 @@ cudaError_t factors_to_bf16(const c64* in, bf16c* out, int64_t n, cudaStream_t s
 }
 
 template cudaError_t matvec_run<float>(const MatvecPlan&, const void*, const void*, const c64*, c64*, c64*, c64*, int,
-                                       int64_t, cudaStream_t, const cudaEvent_t*, int);
+                                       int64_t, cudaStream_t, const cudaEvent_t*, int, bool);
 template cudaError_t matvec_run<double>(const MatvecPlan&, const void*, const void*, const c128*, c128*, c128*,
-                                        c128*, int, int64_t, cudaStream_t, const cudaEvent_t*, int);
+                                        c128*, int, int64_t, cudaStream_t, const cudaEvent_t*, int, bool);
+template cudaError_t transpose_items<float>(const BlockDesc*, const int64_t*, const int64_t*, int, const c64*, int64_t,
+                                            c64*, int64_t, cudaStream_t);
+template cudaError_t transpose_items<double>(const BlockDesc*, const int64_t*, const int64_t*, int, const c128*,
+                                             int64_t, c128*, int64_t, cudaStream_t);
 
 }  // namespace bem

@@ -113,6 +113,56 @@ __global__ void k_pabs(GeomDev g, const c128* __restrict__ x, double* __restrict
     if (threadIdx.x == 0 && partial) partial[(int64_t)r * gridDim.x + blockIdx.x] = s;
 }
 
+// Local 3 x 3 twisted Gram matrix of triangle t: X[i][j] = int_t f_i . (n x f_j) dS
+// (7-point rule, exact for this quadratic integrand), FP64.
+__device__ void twisted_gram_local(const GeomDev& g, int t, double X[3][3]) {
+    d3 v[3];
+    for (int i = 0; i < 3; ++i) v[i] = ld3(g.tv + 9 * t + 3 * i);
+    d3 n = ld3(g.nrm + 3 * t);
+    double A = g.area[t];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) X[i][j] = 0.0;
+    for (int q = 0; q < 7; ++q) {
+        double l0, l1, l2, w;
+        rule7_d(q, l0, l1, l2, w);
+        d3 rq = l0 * v[0] + l1 * v[1] + l2 * v[2];
+        d3 f[3];
+        for (int i = 0; i < 3; ++i) f[i] = (g.tri_coef[3 * t + i] / (2.0 * A)) * (rq - v[i]);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) X[i][j] += w * A * dot(f[i], cross(n, f[j]));
+    }
+}
+
+// Gradient of the absorbed power P = Re(xJ^H X xM) = x^H H x, H = (1/2)[[0, X], [X^T, 0]]
+// (X real), with respect to conj(x): out = H x = (1/2) [X xM ; X^T xJ].  One thread per
+// edge gathers the contributions of its two triangles (no atomics); grid.y = rhs.
+__global__ void k_pabs_grad(GeomDev g, const c128* __restrict__ x, c128* __restrict__ out) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (m >= g.ne) return;
+    const c128* xr = x + (int64_t)r * 2 * g.ne;
+    c128 gJ = mk<double>(0, 0), gM = gJ;
+    for (int s = 0; s < 2; ++s) {
+        const int t = g.edge_tri[2 * m + s], li = g.edge_loc[2 * m + s];
+        double X[3][3];
+        twisted_gram_local(g, t, X);
+        for (int j = 0; j < 3; ++j) {
+            const int e = g.tri_edge[3 * t + j];
+            gJ = gJ + X[li][j] * xr[g.ne + e];
+            gM = gM + X[j][li] * xr[e];
+        }
+    }
+    c128* o = out + (int64_t)r * 2 * g.ne;
+    o[m] = 0.5 * gJ;
+    o[g.ne + m] = 0.5 * gM;
+}
+
+cudaError_t power_abs_grad(GeomDev g, const c128* x, int nrhs, c128* out, cudaStream_t st) {
+    dim3 grid((g.ne + 127) / 128, nrhs);
+    k_pabs_grad<<<grid, 128, 0, st>>>(g, x, out);
+    return cudaGetLastError();
+}
+
 cudaError_t power_abs(GeomDev g, const c128* x, int nrhs, double* per_tri, double* partial, int npart,
                       cudaStream_t st) {
     (void)npart;
