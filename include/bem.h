@@ -291,6 +291,19 @@ bem_status bem_absorbed_power_gradient(bem_ctx* ctx, const void* x, void* g, int
 bem_status bem_grad_weights(bem_ctx* ctx, const void* bm, int nw, const bem_c128* w, double* p_abs,
                             bem_c128* grad, void* x_out, void* lambda_out, void* stream, int* iters);
 
+/* Gradient of the absorbed power with respect to the interior permittivity,
+ * given the forward solution x (Z x = b) and the adjoint solution lambda
+ * (Z^H lambda = dP/d conj(x), e.g. the x_out and lambda_out of bem_grad_weights):
+ * dp[0] = dP/d Re(eps_r), dp[1] = dP/d Im(eps_r) (host), from
+ * dP = -2 Re(lambda^H (dZ/d eps_r) x d eps_r).  The derivative of the interior
+ * blocks is applied between lambda and x by an O(nt^2) pass over all triangle
+ * pairs in FP64 (the k-derivative of the quadrature: dG/dk = -j e^{-jkR}/(4 pi),
+ * and of the singular-pair extraction), so it is exact for the uncompressed
+ * discretisation; meant for the moderate meshes of design problems.  x, lambda:
+ * device complex128 2ne.  Allocates scratch; synchronises `stream`.  No paper
+ * counterpart. */
+bem_status bem_grad_eps(bem_ctx* ctx, const void* x, const void* lambda, double* dp, void* stream);
+
 /* Absorbed power density per triangle for the first right-hand side of x
  * (device complex128): per_tri (device, nt doubles) = Re(sum_ij conj(xJ_i) X_t[i,j] xM_j) / area_t,
  * same units as bem_power. */

@@ -15,6 +15,12 @@ power is a Hermitian quadratic form in the weights,
 so its gradient with respect to conj(w) is Q w -- written out here with a dense
 LU solve and no adjoint system.  Parity of this function is pinned in the tests
 by central finite differences of P(w) and by the Hermitian structure of Q.
+
+The gradient with respect to the interior permittivity is taken by central
+differences of the dense solution (absorbed_eps_gradient), pinned in the tests by
+the lossless limit (P = 0 for every real eps_r, so dP/d Re eps_r = 0 there and
+dP/d Im eps_r < 0) and by the Mie series of the sphere (same derivative of the
+absorption efficiency, to the discretisation error).
 """
 from __future__ import annotations
 
@@ -42,3 +48,18 @@ def absorbed_and_weight_gradient(rwg: RWG, Z, Bm, w):
     Q = weight_form(rwg, Z, Bm)
     w = np.asarray(w, dtype=np.complex128)
     return float(np.real(np.vdot(w, Q @ w))), Q @ w
+
+
+def absorbed_eps_gradient(rwg: RWG, k0: float, eps_r: complex, b, h: float = 1e-6):
+    """(dP/d Re eps_r, dP/d Im eps_r) of P = Re(xJ^H X xM), x = Z(eps_r)^-1 b, by
+    central differences of the dense LU solution (the plain definition; b does not
+    depend on eps_r: the excitation lives in the exterior medium)."""
+    from . import operators
+
+    def p_of(e):
+        Z = operators.pmchwt_matrix(rwg, k0, e)
+        return power.absorbed(rwg, np.linalg.solve(Z, b))
+
+    d_re = (p_of(eps_r + h) - p_of(eps_r - h)) / (2 * h)
+    d_im = (p_of(eps_r + 1j * h) - p_of(eps_r - 1j * h)) / (2 * h)
+    return np.array([d_re, d_im])

@@ -27,7 +27,7 @@ EXPORTS = [
     "bem_debye_eps", "bem_assemble", "bem_num_edges", "bem_num_unknowns", "bem_edges", "bem_stats_get",
     "bem_partition", "bem_eval_entries", "bem_matvec", "bem_rhs_planewave", "bem_solve", "bem_power",
     "bem_power_density", "bem_profile_begin", "bem_profile_end", "bem_absorbed_power_static",
-    "bem_matvec_adjoint", "bem_solve_adjoint", "bem_absorbed_power_gradient", "bem_grad_weights",
+    "bem_matvec_adjoint", "bem_solve_adjoint", "bem_absorbed_power_gradient", "bem_grad_weights", "bem_grad_eps",
 ]
 KERNEL_NAMES = ["k_gather", "k_vhx", "k_rows"]   # BEM_KERNEL_GATHER, _VHX, _ROWS
 
@@ -94,6 +94,7 @@ def _load():
         "bem_matvec_adjoint": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
         "bem_solve_adjoint": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int), dp]),
         "bem_absorbed_power_gradient": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, vp]),
+        "bem_grad_eps": (ctypes.c_int, [ctx, vp, vp, dp, vp]),
         "bem_grad_weights": (ctypes.c_int, [ctx, vp, ctypes.c_int, ctypes.POINTER(bem_c128), dp,
                                             ctypes.POINTER(bem_c128), vp, vp, vp, ctypes.POINTER(ctypes.c_int)]),
         "bem_rhs_planewave": (ctypes.c_int, [ctx, dp, ctypes.POINTER(bem_c128), ctypes.c_int, vp, ctypes.c_int, vp]),
@@ -265,6 +266,14 @@ def bem_grad_weights(ctx, bm_ptr: int, w, x_ptr: int = 0, lam_ptr: int = 0, stre
                                      ctypes.c_void_p(x_ptr or None), ctypes.c_void_p(lam_ptr or None),
                                      ctypes.c_void_p(stream), ctypes.byref(it)))
     return p.value, grad, it.value
+
+
+def bem_grad_eps(ctx, x_ptr: int, lam_ptr: int, stream: int = 0):
+    """(dP/d Re eps_r, dP/d Im eps_r) from the forward and adjoint solutions."""
+    out = np.zeros(2, dtype=np.float64)
+    _check(ctx, lib.bem_grad_eps(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(lam_ptr), _np_ptr(out, ctypes.c_double),
+                                 ctypes.c_void_p(stream)))
+    return out
 
 
 def bem_power(ctx, x_ptr: int, b_ptr: int, nrhs: int, stream: int = 0):

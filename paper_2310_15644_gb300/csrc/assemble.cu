@@ -24,19 +24,6 @@
 
 namespace bem {
 
-__device__ __forceinline__ int find_singular(const GeomDev& g, int a, int b) {
-    int lo = g.sing_ptr[a], hi = g.sing_ptr[a + 1];
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        int v = g.sing_b[mid];
-        if (v == b) return mid;
-        if (v < b)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    return -1;
-}
 
 template <typename R>
 __device__ __forceinline__ R r_sqrt(R x);

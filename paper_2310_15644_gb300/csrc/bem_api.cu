@@ -1798,6 +1798,50 @@ extern "C" bem_status bem_grad_weights(bem_ctx* c, const void* bm, int nw, const
     return BEM_OK;
 }
 
+extern "C" bem_status bem_grad_eps(bem_ctx* c, const void* x, const void* lambda, double* dp, void* stream) {
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "bem_grad_eps needs bem_assemble");
+    if (!x || !lambda || !dp) return fail(c, BEM_EINVAL, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nsing = c->n_sing;
+    DevBuf d_pair_a, d_dvals, d_part, d_out;
+    struct G {
+        DevBuf* b[4];
+        ~G() {
+            for (DevBuf* z : b) dfree(*z);
+        }
+    } guard{{&d_pair_a, &d_dvals, &d_part, &d_out}};
+    // k-derivatives of the singular-pair tables at k1
+    std::vector<int> ptr(c->nt + 1);
+    CK(cudaMemcpyAsync(ptr.data(), c->d_sing_ptr.p, sizeof(int) * (c->nt + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<int> pa(std::max<int64_t>(1, nsing));
+    for (int64_t t = 0; t < c->nt; ++t)
+        for (int k = ptr[t]; k < ptr[t + 1]; ++k) pa[k] = (int)t;
+    CK(upload(d_pair_a, pa, st));
+    CK(dalloc(d_dvals, sizeof(c128) * 18 * std::max<int64_t>(1, nsing)));
+    GeomDev g = geom_view(c);
+    CK(singular_dvalues(g, (int)nsing, (const int*)d_pair_a.p, (c128*)d_dvals.p, st));
+    CK(dalloc(d_part, sizeof(c128) * 6 * c->nt));
+    CK(dalloc(d_out, sizeof(c128) * 6));
+    CK(interior_forms(g, (const c128*)d_dvals.p, (const c128*)x, (const c128*)lambda, (c128*)d_part.p,
+                      (c128*)d_out.p, st));
+    c128 f[6];
+    CK(cudaMemcpyAsync(f, d_out.p, sizeof(f), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    // dZ/d eps_r applied between lambda and x: k1' = k1 / (2 eps_r), eta_r' = -eta_r / (2 eps_r),
+    // dA = eta_r' T1 + eta_r k1' T1', dB = k1' K1', dC = k1' T1' / eta_r - (eta_r' / eta_r^2) T1
+    const c128 two_eps = 2.0 * c->eps;
+    const c128 dk1 = cdiv(c->k1, two_eps);
+    const c128 der = cdiv(mk<double>(-c->eta_r.re, -c->eta_r.im), two_eps);
+    const c128 s = der * f[0] + (c->eta_r * dk1) * f[2] + dk1 * (f[4] - f[5]) + cdiv(dk1, c->eta_r) * f[3] -
+                   cdiv(der, c->eta_r * c->eta_r) * f[1];
+    // dP = -2 Re(lambda^H dZ x), dZ = (dZ/d eps_r) d eps_r, d eps_r = d eps' + j d eps''
+    dp[0] = -2.0 * s.re;
+    dp[1] = 2.0 * s.im;
+    return BEM_OK;
+}
+
 extern "C" bem_status bem_power_density(bem_ctx* c, const void* x, double* per_tri, void* stream) {
     if (!c) return BEM_EINVAL;
     if (!c->assembled) return fail(c, BEM_ESTATE, "bem_power_density needs bem_assemble");

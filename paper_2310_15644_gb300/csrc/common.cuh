@@ -201,6 +201,13 @@ struct SingGrid {
 cudaError_t singular_count(GeomDev g, SingGrid G, int* counts, cudaStream_t st);
 cudaError_t singular_fill(GeomDev g, SingGrid G, const int* ptr, int* partners, cudaStream_t st);
 cudaError_t singular_values(GeomDev g, int npairs, const int* pair_a, c128* vals, cudaStream_t st);
+// k-derivatives (k = k1) of the singular-pair tables: 18 complex per pair, dT^_1 then dK_1
+cudaError_t singular_dvalues(GeomDev g, int npairs, const int* pair_a, c128* dvals, cudaStream_t st);
+// Bilinear forms of the interior operators for the permittivity gradient, summed
+// over all triangle pairs (FP64, O(nt^2)): out[6] = {lJ^H T1 xJ, lM^H T1 xM,
+// lJ^H T1' xJ, lM^H T1' xM, lJ^H K1' xM, lM^H K1' xJ} (' = d/dk at k1)
+cudaError_t interior_forms(GeomDev g, const c128* dvals, const c128* x, const c128* lam, c128* partial, c128* out,
+                           cudaStream_t st);
 
 // assemble.cu
 template <typename R>

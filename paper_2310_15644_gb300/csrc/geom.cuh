@@ -5,6 +5,21 @@
 
 namespace bem {
 
+// slot of the singular pair (a, b) in the table (partners of a sorted ascending), or -1
+__device__ __forceinline__ int find_singular(const GeomDev& g, int a, int b) {
+    int lo = g.sing_ptr[a], hi = g.sing_ptr[a + 1];
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        int v = g.sing_b[mid];
+        if (v == b) return mid;
+        if (v < b)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return -1;
+}
+
 // 7-point degree-5 rule: barycentric points and weights (closed form with sqrt(15))
 __device__ __forceinline__ void rule7_d(int q, double& l0, double& l1, double& l2, double& w) {
     const double s = 3.872983346207416885;  // sqrt(15)

@@ -291,6 +291,163 @@ __global__ void __launch_bounds__(128) k_sing_values(GeomDev g, int npairs, cons
     }
 }
 
+// ---------------------------------------------------------------------------
+// k-derivatives of the singular-pair local matrices (gradient with respect to the
+// interior permittivity).  The extraction splits G = 1/(4 pi R) - k^2 R/(8 pi) + G_s and
+// g = -1/(4 pi R^3) - k^2/(8 pi R) + g_s; differentiating the same split,
+//   dG/dk = -k R/(4 pi) + dG_s/dk,   dG_s/dk = -j e^{-jkR}/(4 pi) + k R/(4 pi),
+//   dg/dk = -k/(4 pi R) + dg_s/dk,   dg_s/dk = -k (e^{-jkR} - 1)/(4 pi R),
+// so the analytic parts only keep their R (resp. grad R) integrals, with factor
+// -k/(4 pi), and the smooth parts are integrated by the same 7 x 7 rule.  This is
+// the exact derivative of the stored T^_k and K_k of the pair.
+// ---------------------------------------------------------------------------
+__device__ c128 smooth_dG(c128 k, double R) {
+    c128 e = expmjkr(k, R);
+    c128 mje = mk<double>(e.im, -e.re);  // -j e
+    return (1.0 / (4.0 * BEM_PI)) * (mje + R * k);
+}
+
+__device__ c128 smooth_dg(c128 k, double R) {
+    double x = sqrt(cabs2(k)) * R;
+    c128 em1;  // e^{-jkR} - 1
+    if (x < 1.0) {
+        c128 z = R * mk<double>(k.im, -k.re);  // -j k R
+        c128 term = z, sum = z;
+        for (int n = 2; n < 30; ++n) {
+            term = (1.0 / n) * (term * z);
+            sum = sum + term;
+        }
+        em1 = sum;
+    } else {
+        em1 = expmjkr(k, R) - mk<double>(1.0, 0.0);
+    }
+    return (-1.0 / (4.0 * BEM_PI * R)) * (k * em1);
+}
+
+// dT^_1/dk and dK_1/dk (k = k1) of every singular pair: 18 complex per pair, the
+// same [i][j] layout and coefficients as the values table.  One warp per pair,
+// lanes 0..6 = outer points.
+__global__ void __launch_bounds__(128) k_sing_dvalues(GeomDev g, int npairs, const int* __restrict__ pair_a,
+                                                      c128* __restrict__ dvals) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= npairs) return;
+    int a = pair_a[warp];
+    int b = g.sing_b[warp];
+    const int p = lane;
+    const bool act = p < 7;
+    const c128 k = g.k1;
+    d3 va[3], vb[3];
+    for (int i = 0; i < 3; ++i) {
+        va[i] = ld3(g.tv + 9 * a + 3 * i);
+        vb[i] = ld3(g.tv + 9 * b + 3 * i);
+    }
+    double Aa = g.area[a], Ab = g.area[b];
+    d3 nb = ld3(g.nrm + 3 * b);
+    const c128 z0 = mk<double>(0, 0);
+    c128 Iff[3][3], dIff[3][3], dIk[3][3], I0 = z0, dI0 = z0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Iff[i][j] = dIff[i][j] = dIk[i][j] = z0;
+    if (act) {
+        double l0, l1, l2, wp;
+        rule7_d(p, l0, l1, l2, wp);
+        wp *= Aa;
+        d3 r = l0 * va[0] + l1 * va[1] + l2 * va[2];
+        Analytic an = triangle_integrals(r, vb, nb, a == b);
+        z3 F[3], dF[3];
+        z3 zz = Z3(z0, z0, z0);
+        c128 Phi = z0, dPhi = z0, dS0 = z0;
+        z3 dS1 = zz;
+        for (int j = 0; j < 3; ++j) F[j] = dF[j] = zz;
+        for (int q = 0; q < 7; ++q) {
+            double m0, m1, m2, wq;
+            rule7_d(q, m0, m1, m2, wq);
+            wq *= Ab;
+            d3 rq = m0 * vb[0] + m1 * vb[1] + m2 * vb[2];
+            d3 d = r - rq;
+            double R = sqrt(dot(d, d));
+            c128 Gs = wq * smooth_G(k, R);
+            c128 dGs = wq * smooth_dG(k, R);
+            c128 dgs = wq * smooth_dg(k, R);
+            for (int j = 0; j < 3; ++j) {
+                F[j] = zadd(F[j], zscale(Gs, rq - vb[j]));
+                dF[j] = zadd(dF[j], zscale(dGs, rq - vb[j]));
+            }
+            Phi = Phi + Gs;
+            dPhi = dPhi + dGs;
+            dS0 = dS0 + dgs;
+            dS1 = zadd(dS1, zscale(dgs, rq));
+        }
+        const c128 c1 = mk<double>(1.0 / (4.0 * BEM_PI), 0.0);
+        const c128 c2 = (-1.0 / (8.0 * BEM_PI)) * (k * k);
+        const c128 dc2 = (-1.0 / (4.0 * BEM_PI)) * k;
+        for (int j = 0; j < 3; ++j) {
+            d3 rv = an.rho - vb[j];
+            F[j] = zadd(F[j], zscale(c1, an.V_m1 + an.S_m1 * rv));
+            F[j] = zadd(F[j], zscale(c2, an.V_1 + an.S_1 * rv));
+            dF[j] = zadd(dF[j], zscale(dc2, an.V_1 + an.S_1 * rv));
+        }
+        Phi = Phi + an.S_m1 * c1 + an.S_1 * c2;
+        dPhi = dPhi + an.S_1 * dc2;
+        z3 dgvec = zscale(dc2, an.G_1);
+        for (int j = 0; j < 3; ++j) {
+            z3 inner = zsub(dS1, zscale(dS0, vb[j]));
+            z3 H = zadd(rzcross(r, inner), zrcross(dS1, vb[j]));
+            H = zadd(H, zrcross(dgvec, r - vb[j]));
+            for (int i = 0; i < 3; ++i) {
+                d3 u = r - va[i];
+                Iff[i][j] = wp * zdot(u, F[j]);
+                dIff[i][j] = wp * zdot(u, dF[j]);
+                dIk[i][j] = wp * zdot(u, H);
+            }
+        }
+        I0 = wp * Phi;
+        dI0 = wp * dPhi;
+    }
+    for (int o = 4; o > 0; o >>= 1) {
+        const unsigned m = 0xffffffffu;
+        I0.re += __shfl_xor_sync(m, I0.re, o);
+        I0.im += __shfl_xor_sync(m, I0.im, o);
+        dI0.re += __shfl_xor_sync(m, dI0.re, o);
+        dI0.im += __shfl_xor_sync(m, dI0.im, o);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                Iff[i][j].re += __shfl_xor_sync(m, Iff[i][j].re, o);
+                Iff[i][j].im += __shfl_xor_sync(m, Iff[i][j].im, o);
+                dIff[i][j].re += __shfl_xor_sync(m, dIff[i][j].re, o);
+                dIff[i][j].im += __shfl_xor_sync(m, dIff[i][j].im, o);
+                dIk[i][j].re += __shfl_xor_sync(m, dIk[i][j].re, o);
+                dIk[i][j].im += __shfl_xor_sync(m, dIk[i][j].im, o);
+            }
+    }
+    if (lane == 0) {
+        // T^ = jk/(4AA') Iff - (j/k)/(AA') I0, so
+        // dT^/dk = j/(4AA') Iff + jk/(4AA') dIff + j/(k^2 AA') I0 - (j/k)/(AA') dI0
+        const c128 j1 = mk<double>(0.0, 1.0);
+        const c128 jk = mk<double>(-k.im, k.re);
+        const c128 j_over_k = cdiv(j1, k);
+        const c128 j_over_k2 = cdiv(j1, k * k);
+        const double AA = Aa * Ab;
+        c128* out = dvals + (int64_t)warp * 18;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double cc = g.tri_coef[3 * a + i] * g.tri_coef[3 * b + j];
+                c128 t = j1 * ((1.0 / (4.0 * AA)) * Iff[i][j]) + jk * ((1.0 / (4.0 * AA)) * dIff[i][j]) +
+                         j_over_k2 * ((1.0 / AA) * I0) - j_over_k * ((1.0 / AA) * dI0);
+                out[3 * i + j] = cc * t;
+                out[9 + 3 * i + j] = (cc / (4.0 * AA)) * dIk[i][j];
+            }
+    }
+}
+
+cudaError_t singular_dvalues(GeomDev g, int npairs, const int* pair_a, c128* dvals, cudaStream_t st) {
+    if (npairs <= 0) return cudaSuccess;
+    const int warps_per_block = 4;
+    const int blocks = (npairs + warps_per_block - 1) / warps_per_block;
+    k_sing_dvalues<<<blocks, 32 * warps_per_block, 0, st>>>(g, npairs, pair_a, dvals);
+    return cudaGetLastError();
+}
+
 cudaError_t singular_values(GeomDev g, int npairs, const int* pair_a, c128* vals, cudaStream_t st) {
     if (npairs <= 0) return cudaSuccess;
     int warps_per_block = 4;

@@ -196,3 +196,64 @@ def test_autograd_function_compressed_complex64(B, sphere2_weights):
         assert np.abs(got - 2 * g_ref).max() <= 1e-4 * np.abs(2 * g_ref).max()
     finally:
         B.bem_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def sphere2_eps():
+    v, t = W.icosphere(2)
+    g = R.build(v, t)
+    b = E.rhs_planewave(g, 2.0, [0.0, 0.0, 1.0], [1.0, 0.0, 0.0])
+    ref = G.absorbed_eps_gradient(g, 2.0, 3.2 - 1.9j, b)
+    return v, t, g, b, ref
+
+
+def _p_and_eps_grad(B, h, b):
+    bd = torch.from_numpy(np.ascontiguousarray(b[None, :])).to(DEV)
+    n = bd.shape[1]
+    x = torch.empty(n, dtype=torch.complex128, device=DEV)
+    lam = torch.empty_like(x)
+    p, _, _ = B.bem_grad_weights(h, bd.data_ptr(), np.array([1.0 + 0j]), x.data_ptr(), lam.data_ptr(), _stream())
+    return p, B.bem_grad_eps(h, x.data_ptr(), lam.data_ptr(), _stream())
+
+
+def test_eps_gradient_dense_complex128(B, sphere2_eps):
+    """dP/d eps_r by the adjoint solve and the dG/dk pass against central
+    differences of the oracle's dense solution (1e-5; operator entries agree to
+    1e-11) and against central differences of the library's own P (1e-3)."""
+    v, t, g, b, ref = sphere2_eps
+    kw = dict(eta=0.0, tol=1e-10, refine_tol=1e-13, maxit=3000)
+    h = make(B, v, t, 2.0, 3.2 - 1.9j, 2, 1e-6, **kw)
+    try:
+        p0, d = _p_and_eps_grad(B, h, b)
+        assert np.abs(d - ref).max() <= 1e-5 * np.abs(ref).max(), (d, ref)
+        step = 1e-5
+        fd = []
+        for de in (step, 1j * step):
+            pp = []
+            for sgn in (1, -1):
+                B.bem_set_media(h, 2.0, 3.2 - 1.9j + sgn * de)
+                B.bem_assemble(h, _stream())
+                pp.append(_p_and_eps_grad(B, h, b)[0])
+            fd.append((pp[0] - pp[1]) / (2 * step))
+        assert np.abs(d - np.array(fd)).max() <= 1e-3 * np.abs(d).max(), (d, fd)
+    finally:
+        B.bem_destroy(h)
+
+
+def test_eps_gradient_compressed_complex64_autograd(B, sphere2_eps):
+    """Through torch.autograd with the compressed complex64 operator (FP64
+    refinement): eps.grad against the oracle's dense gradient to 1e-3."""
+    from paper_2310_15644_gb300.autograd import absorbed_power
+
+    v, t, g, b, ref = sphere2_eps
+    h = make(B, v, t, 2.0, 3.2 - 1.9j, 1, 1e-6, leaf=16, tol=1e-4, refine_tol=1e-10, maxit=3000)
+    try:
+        bm = torch.from_numpy(np.ascontiguousarray(b[None, :])).to(DEV)
+        w = torch.tensor([1.0 + 0j], dtype=torch.complex128, requires_grad=True)
+        eps = torch.tensor([3.2, -1.9], dtype=torch.float64, requires_grad=True)
+        p = absorbed_power(w, h, bm, eps=eps, k0=2.0)
+        p.backward()
+        got = eps.grad.numpy()
+        assert np.abs(got - ref).max() <= 1e-3 * np.abs(ref).max(), (got, ref)
+    finally:
+        B.bem_destroy(h)
