@@ -309,19 +309,22 @@ __device__ c128 smooth_dG(c128 k, double R) {
 
 __device__ c128 smooth_dg(c128 k, double R) {
     double x = sqrt(cabs2(k)) * R;
-    c128 em1;  // e^{-jkR} - 1
+    const c128 mjk = mk<double>(k.im, -k.re);  // -j k
+    c128 em1_R;                                // (e^{-jkR} - 1) / R
     if (x < 1.0) {
-        c128 z = R * mk<double>(k.im, -k.re);  // -j k R
-        c128 term = z, sum = z;
+        // (e^z - 1) / R = -j k sum_{n>=1} z^{n-1} / n!, z = -j k R: finite at R = 0
+        // (the coincident outer and inner points of a self pair)
+        c128 z = R * mjk;
+        c128 term = mk<double>(1.0, 0.0), sum = term;
         for (int n = 2; n < 30; ++n) {
             term = (1.0 / n) * (term * z);
             sum = sum + term;
         }
-        em1 = sum;
+        em1_R = mjk * sum;
     } else {
-        em1 = expmjkr(k, R) - mk<double>(1.0, 0.0);
+        em1_R = (1.0 / R) * (expmjkr(k, R) - mk<double>(1.0, 0.0));
     }
-    return (-1.0 / (4.0 * BEM_PI * R)) * (k * em1);
+    return (-1.0 / (4.0 * BEM_PI)) * (k * em1_R);
 }
 
 // dT^_1/dk and dK_1/dk (k = k1) of every singular pair: 18 complex per pair, the
