@@ -96,7 +96,16 @@ typedef struct {
     double tol;          /* inner GMRES relative residual tolerance (default 1e-6) */
     double refine_tol;   /* outer FP64 iterative-refinement target; 0 disables refinement (default 0) */
     int refine_maxit;    /* maximum outer refinement steps (default 10) */
+    int solver;          /* inner Krylov solver, BEM_SOLVER_* (default GMRES) */
 } bem_options;
+
+/* Inner Krylov solvers (bem_options.solver).  maxit counts iterations: one product
+ * per GMRES iteration, two per CGS, BiCGStab and CGNR iteration. */
+#define BEM_SOLVER_GMRES 0     /* restarted GMRES, classical Gram-Schmidt with reorthogonalisation */
+#define BEM_SOLVER_CGS 1       /* conjugate gradient squared */
+#define BEM_SOLVER_BICGSTAB 2  /* stabilised bi-conjugate gradient */
+#define BEM_SOLVER_CGNR 3      /* conjugate gradient on Z^H Z x = Z^H b (uses the adjoint product; not with
+                                  BF16 factors, whose solves then use the complex64 operator) */
 
 /* Parts of bem_assemble timed in bem_stats.assemble_phase_ms (host wall time, milliseconds). */
 #define BEM_PHASE_TREE 0     /* geometry upload, cluster tree, block partition, leaf tables */

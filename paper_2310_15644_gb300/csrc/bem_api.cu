@@ -120,6 +120,11 @@ struct bem_ctx {
     // reductions and small transfers
     DevBuf d_part, d_red, d_tmp_in, d_one, d_gl;
     GmresWork gw;
+    struct {
+        int dtype = -1;
+        int64_t n = 0;
+        DevBuf v[8];
+    } cgw;  // vectors of the CG-type solvers
     // kernel timing of bem_matvec
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;   // created once, reused
@@ -262,6 +267,7 @@ extern "C" void bem_default_options(bem_options* o) {
     o->tol = 1e-6;
     o->refine_tol = 0.0;
     o->refine_maxit = 10;
+    o->solver = BEM_SOLVER_GMRES;
 }
 
 extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
@@ -272,7 +278,8 @@ extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
     if (opt) o = *opt;
     if (o.leaf_size < 2 || o.leaf_size > BEM_MAX_LEAF || (o.precision & 7) == 0 || (o.precision & ~7) != 0 ||
         o.aca_tol <= 0 || o.aca_max_rank < 1 || o.aca_max_rank > 128 || o.gmres_restart < 1 || o.gmres_restart > 200 || o.maxit < 1 ||
-        o.tol <= 0 || o.refine_tol < 0 || o.refine_maxit < 1)
+        o.tol <= 0 || o.refine_tol < 0 || o.refine_maxit < 1 || o.solver < BEM_SOLVER_GMRES ||
+        o.solver > BEM_SOLVER_CGNR)
         return BEM_EINVAL;
     bem_ctx* c = new (std::nothrow) bem_ctx();
     if (!c) return BEM_ENOMEM;
@@ -290,7 +297,9 @@ extern "C" void bem_destroy(bem_ctx* c) {
                       &c->d_sing_val, &c->d_perm, &c->d_leaf_r0, &c->d_leaf_m, &c->d_pos_leaf_lo,
                       &c->d_pos_leaf_m, &c->d_part, &c->d_trif,
                       &c->d_red, &c->d_tmp_in, &c->d_one, &c->d_gl, &c->gw.V, &c->gw.w, &c->gw.z, &c->gw.r,
-                      &c->gw.xin, &c->gw.rin, &c->gw.hpart, &c->gw.hdev, &c->gw.npart};
+                      &c->gw.xin, &c->gw.rin, &c->gw.hpart, &c->gw.hdev, &c->gw.npart, &c->cgw.v[0],
+                      &c->cgw.v[1], &c->cgw.v[2], &c->cgw.v[3], &c->cgw.v[4], &c->cgw.v[5], &c->cgw.v[6],
+                      &c->cgw.v[7]};
     for (DevBuf* b : bufs) dfree(*b);
     delete c;
 }
@@ -1562,6 +1571,144 @@ static bem_status gmres(bem_ctx* c, int pdt, double tol_abs, int maxit, int* ite
     return BEM_OK;
 }
 
+// a^H b with FP64 sums (host result; synchronises)
+static bem_status dotc(bem_ctx* c, int dtype, const void* a, const void* b, int64_t n, c128* out, cudaStream_t st) {
+    CK(ensure(c->d_part, sizeof(c128) * (NPART + 1)));
+    c128* part = (c128*)c->d_part.p;
+    CK(kv_multidot(a, dtype, n, 1, b, n, part, NPART, st));
+    CK(kv_reduce_partials(part, NPART, 1, part + NPART, st));
+    CK(cudaMemcpyAsync(out, part + NPART, sizeof(c128), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return BEM_OK;
+}
+
+static bem_status cg_work(bem_ctx* c, int dtype) {
+    const int64_t n = 2 * c->ne;
+    if (c->cgw.dtype == dtype && c->cgw.n == n && c->cgw.v[0].p) return BEM_OK;
+    for (DevBuf& b : c->cgw.v) CK(dalloc(b, esize_of(dtype) * n));
+    c->cgw.dtype = dtype;
+    c->cgw.n = n;
+    return BEM_OK;
+}
+
+// CGS, BiCGStab or CGNR on A x = rin (A = Z, or Z^H when adjoint), x = xin from zero;
+// stops when the recurred residual norm reaches tol_abs.  Scalars on the host from
+// FP64 inner products; vector updates fused in kv_lincomb.
+static bem_status cg_family(bem_ctx* c, int pdt, int solver, double tol_abs, int maxit, int* iters,
+                            double* final_res, cudaStream_t st, bool adjoint) {
+    const int dtype = vec_dtype(pdt);
+    const int64_t n = 2 * c->ne;
+    bem_status s;
+    if ((s = cg_work(c, dtype)) != BEM_OK) return s;
+    GmresWork& gw = c->gw;
+    void* x = gw.xin.p;
+    void *r = c->cgw.v[0].p, *rt = c->cgw.v[1].p, *p = c->cgw.v[2].p, *q = c->cgw.v[3].p, *u = c->cgw.v[4].p,
+         *v = c->cgw.v[5].p, *w = c->cgw.v[6].p, *t = c->cgw.v[7].p;
+    const c128 one = mk<double>(1, 0), zero = mk<double>(0, 0);
+    auto A = [&](const void* in, void* out, bool adj) { return matvec_any(c, pdt, in, out, 1, st, false, adj); };
+    CK(cudaMemsetAsync(x, 0, esize_of(dtype) * n, st));
+    CK(cudaMemcpyAsync(r, gw.rin.p, esize_of(dtype) * n, cudaMemcpyDeviceToDevice, st));
+    double rn;
+    if ((s = norm_dev(c, dtype, r, n, &rn, st)) != BEM_OK) return s;
+    int it = 0;
+    if (solver == BEM_SOLVER_CGS) {
+        CK(cudaMemcpyAsync(rt, r, esize_of(dtype) * n, cudaMemcpyDeviceToDevice, st));
+        c128 rho_prev = one;
+        while (rn > tol_abs && it < maxit) {
+            c128 rho;
+            if ((s = dotc(c, dtype, rt, r, n, &rho, st)) != BEM_OK) return s;
+            if (cabs2(rho) == 0.0) break;
+            if (it == 0) {
+                CK(kv_lincomb(u, dtype, one, r, zero, nullptr, zero, nullptr, n, st));
+                CK(kv_lincomb(p, dtype, one, u, zero, nullptr, zero, nullptr, n, st));
+            } else {
+                const c128 beta = cdiv(rho, rho_prev);
+                CK(kv_lincomb(u, dtype, one, r, beta, q, zero, nullptr, n, st));        // u = r + beta q
+                CK(kv_lincomb(p, dtype, one, u, beta, q, beta * beta, p, n, st));      // p = u + beta q + beta^2 p
+            }
+            CK(A(p, v, adjoint));
+            c128 sigma;
+            if ((s = dotc(c, dtype, rt, v, n, &sigma, st)) != BEM_OK) return s;
+            if (cabs2(sigma) == 0.0) break;
+            const c128 alpha = cdiv(rho, sigma);
+            const c128 malpha = mk<double>(-alpha.re, -alpha.im);
+            CK(kv_lincomb(q, dtype, one, u, malpha, v, zero, nullptr, n, st));         // q = u - alpha v
+            CK(kv_lincomb(w, dtype, one, u, one, q, zero, nullptr, n, st));            // w = u + q
+            CK(kv_lincomb(x, dtype, one, x, alpha, w, zero, nullptr, n, st));          // x += alpha w
+            CK(A(w, t, adjoint));
+            CK(kv_lincomb(r, dtype, one, r, malpha, t, zero, nullptr, n, st));         // r -= alpha A w
+            rho_prev = rho;
+            ++it;
+            if ((s = norm_dev(c, dtype, r, n, &rn, st)) != BEM_OK) return s;
+        }
+    } else if (solver == BEM_SOLVER_BICGSTAB) {
+        CK(cudaMemcpyAsync(rt, r, esize_of(dtype) * n, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemsetAsync(p, 0, esize_of(dtype) * n, st));
+        CK(cudaMemsetAsync(v, 0, esize_of(dtype) * n, st));
+        c128 rho = one, alpha = one, omega = one;
+        while (rn > tol_abs && it < maxit) {
+            c128 rho_new;
+            if ((s = dotc(c, dtype, rt, r, n, &rho_new, st)) != BEM_OK) return s;
+            if (cabs2(rho_new) == 0.0 || cabs2(omega) == 0.0) break;
+            const c128 beta = cdiv(rho_new, rho) * cdiv(alpha, omega);
+            const c128 mbo = mk<double>(-(beta * omega).re, -(beta * omega).im);
+            CK(kv_lincomb(p, dtype, one, r, beta, p, mbo, v, n, st));                 // p = r + beta (p - omega v)
+            CK(A(p, v, adjoint));
+            c128 rv;
+            if ((s = dotc(c, dtype, rt, v, n, &rv, st)) != BEM_OK) return s;
+            if (cabs2(rv) == 0.0) break;
+            alpha = cdiv(rho_new, rv);
+            const c128 malpha = mk<double>(-alpha.re, -alpha.im);
+            CK(kv_lincomb(q, dtype, one, r, malpha, v, zero, nullptr, n, st));        // s = r - alpha v (in q)
+            double sn;
+            if ((s = norm_dev(c, dtype, q, n, &sn, st)) != BEM_OK) return s;
+            ++it;
+            if (sn <= tol_abs) {
+                CK(kv_lincomb(x, dtype, one, x, alpha, p, zero, nullptr, n, st));
+                CK(cudaMemcpyAsync(r, q, esize_of(dtype) * n, cudaMemcpyDeviceToDevice, st));
+                rn = sn;
+                break;
+            }
+            CK(A(q, t, adjoint));
+            c128 ts, tt;
+            if ((s = dotc(c, dtype, t, q, n, &ts, st)) != BEM_OK) return s;
+            if ((s = dotc(c, dtype, t, t, n, &tt, st)) != BEM_OK) return s;
+            if (tt.re == 0.0) break;
+            omega = cdiv(ts, tt);
+            CK(kv_lincomb(x, dtype, one, x, alpha, p, omega, q, n, st));              // x += alpha p + omega s
+            const c128 momega = mk<double>(-omega.re, -omega.im);
+            CK(kv_lincomb(r, dtype, one, q, momega, t, zero, nullptr, n, st));        // r = s - omega t
+            rho = rho_new;
+            if ((s = norm_dev(c, dtype, r, n, &rn, st)) != BEM_OK) return s;
+        }
+    } else {  // CGNR: CG on A^H A x = A^H b
+        CK(A(r, u, !adjoint));  // z = A^H r (in u)
+        CK(cudaMemcpyAsync(p, u, esize_of(dtype) * n, cudaMemcpyDeviceToDevice, st));
+        double zn;
+        if ((s = norm_dev(c, dtype, u, n, &zn, st)) != BEM_OK) return s;
+        while (rn > tol_abs && it < maxit && zn > 0.0) {
+            CK(A(p, w, adjoint));
+            double wn;
+            if ((s = norm_dev(c, dtype, w, n, &wn, st)) != BEM_OK) return s;
+            if (wn == 0.0) break;
+            const c128 alpha = mk<double>((zn * zn) / (wn * wn), 0.0);
+            CK(kv_lincomb(x, dtype, one, x, alpha, p, zero, nullptr, n, st));
+            CK(kv_lincomb(r, dtype, one, r, mk<double>(-alpha.re, 0.0), w, zero, nullptr, n, st));
+            CK(A(r, u, !adjoint));
+            double zn_new;
+            if ((s = norm_dev(c, dtype, u, n, &zn_new, st)) != BEM_OK) return s;
+            const c128 beta = mk<double>((zn_new * zn_new) / (zn * zn), 0.0);
+            CK(kv_lincomb(p, dtype, one, u, beta, p, zero, nullptr, n, st));
+            zn = zn_new;
+            ++it;
+            if ((s = norm_dev(c, dtype, r, n, &rn, st)) != BEM_OK) return s;
+        }
+    }
+    *iters += it;
+    *final_res = rn;
+    return BEM_OK;
+}
+
 static bem_status solve_impl(bem_ctx* c, const void* b, void* x, int nrhs, void* stream, int* iters, double* relres,
                              bool adjoint) {
     if (!c) return BEM_EINVAL;
@@ -1569,11 +1716,13 @@ static bem_status solve_impl(bem_ctx* c, const void* b, void* x, int nrhs, void*
     if (nrhs < 1 || !b || !x) return fail(c, BEM_EINVAL, "bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
     // the BF16-factor product has no adjoint form
-    const int din = (!adjoint && dtype_ok(c, BEM_C64_BF16F)) ? BEM_C64_BF16F : (c->op[0].built ? BEM_C64 : BEM_C128);
+    // the BF16-factor product has no adjoint form (nor does CGNR run on it)
+    const bool bf_ok = !adjoint && c->opt.solver != BEM_SOLVER_CGNR && dtype_ok(c, BEM_C64_BF16F);
+    const int din = bf_ok ? BEM_C64_BF16F : (c->op[0].built ? BEM_C64 : BEM_C128);
     const int vin = vec_dtype(din);
     const bool out128 = c->op[1].built;
     const int dres = out128 ? BEM_C128 : DT_C64_IN_FP64;
-    if (adjoint) {
+    if (adjoint || c->opt.solver == BEM_SOLVER_CGNR) {
         bem_status s0;
         if ((s0 = ensure_adjoint_for(c, din, st)) != BEM_OK) return s0;
         if ((s0 = ensure_adjoint_for(c, dres, st)) != BEM_OK) return s0;
@@ -1625,8 +1774,12 @@ static bem_status solve_impl(bem_ctx* c, const void* b, void* x, int nrhs, void*
                 CK(cudaMemcpyAsync(c->gw.rin.p, rr.p, sizeof(c128) * n, cudaMemcpyDeviceToDevice, st));
             double fres;
             int before = total_it;
-            if ((s = gmres(c, din, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st, adjoint)) !=
-                BEM_OK)
+            if (c->opt.solver == BEM_SOLVER_GMRES)
+                s = gmres(c, din, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st, adjoint);
+            else
+                s = cg_family(c, din, c->opt.solver, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st,
+                              adjoint);
+            if (s != BEM_OK)
                 return s;
             inner_ok = fres <= c->opt.tol * rn * 1.0000001;
             CK(kv_axpy_c128(xr, c->gw.xin.p, vin, (const c128*)c->d_one.p, 1.0, n, 1, n, st));

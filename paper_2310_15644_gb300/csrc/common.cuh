@@ -297,6 +297,9 @@ cudaError_t kv_scale_copy(const void* w, int dtype, double s, int64_t n, void* v
 cudaError_t kv_axpy_c128(c128* y, const void* x, int dtype, const c128* coef, double sign, int64_t n, int k,
                          int64_t ld, cudaStream_t st);
 cudaError_t kv_sub(const void* b, const void* zx, void* r, int dtype, int64_t n, cudaStream_t st);
+// z = a x + b y + c w (null operands skipped; z may alias them)
+cudaError_t kv_lincomb(void* z, int dtype, c128 a, const void* x, c128 b, const void* y, c128 c, const void* w,
+                       int64_t n, cudaStream_t st);
 
 }  // namespace bem
 

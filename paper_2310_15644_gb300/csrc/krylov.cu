@@ -209,4 +209,30 @@ cudaError_t kv_sub(const void* b, const void* zx, void* r, int dtype, int64_t n,
     return cudaGetLastError();
 }
 
+// z = a x + b y + c w (complex coefficients, FP64 arithmetic, any of x, y, w may be
+// null; z may alias them): the fused vector update of the CG-type solvers.
+template <typename R>
+__global__ void k_lincomb(cx<R>* z, c128 a, const cx<R>* x, c128 b, const cx<R>* y, c128 c, const cx<R>* w,
+                          int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        c128 acc = mk<double>(0, 0);
+        if (x) acc = acc + a * to128(x[i]);
+        if (y) acc = acc + b * to128(y[i]);
+        if (w) acc = acc + c * to128(w[i]);
+        z[i] = mk<R>((R)acc.re, (R)acc.im);
+    }
+}
+
+cudaError_t kv_lincomb(void* z, int dtype, c128 a, const void* x, c128 b, const void* y, c128 c, const void* w,
+                       int64_t n, cudaStream_t st) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (dtype == BEM_C64)
+        k_lincomb<float><<<blocks, 256, 0, st>>>((c64*)z, a, (const c64*)x, b, (const c64*)y, c, (const c64*)w, n);
+    else
+        k_lincomb<double><<<blocks, 256, 0, st>>>((c128*)z, a, (const c128*)x, b, (const c128*)y, c, (const c128*)w,
+                                                  n);
+    return cudaGetLastError();
+}
+
 }  // namespace bem
