@@ -233,6 +233,30 @@ bem_status bem_matvec(bem_ctx* ctx, const void* x, void* y, int nrhs, int dtype,
  * Errors as bem_matvec. */
 bem_status bem_matvec_adjoint(bem_ctx* ctx, const void* x, void* y, int nrhs, int dtype, void* stream);
 
+/* Autotuner of the product's block-to-CTA schedule: times the product of the
+ * operator of `dtype` (10 products after 3 warm-ups, CUDA events on `stream`)
+ * for rows-kernel schedules of 4 to 96 slots per SM in total, and keeps the
+ * fastest (the sums of a leaf's slots are taken in a different grouping, so
+ * results change at rounding level).  chosen (host, may be NULL): slots chosen;
+ * ms_best (host, may be NULL): its time per product.  Allocates two vectors;
+ * synchronises `stream`; drops the adjoint schedule, rebuilt on next use.
+ * No paper counterpart. */
+bem_status bem_autotune(bem_ctx* ctx, int dtype, void* stream, int* chosen, double* ms_best);
+
+/* Several operators' products as one CUDA graph (many meshes of uneven size in
+ * one launch).  bem_batch_create captures y[i] = Z_i x[i] (nrhs[i] vectors, type
+ * `dtype`) of every context, each on its own branch of the graph so that small
+ * meshes run side by side, and instantiates it; contexts must be distinct
+ * (their workspaces are per context), assembled, not profiling, and they, x and
+ * y must stay alive and unchanged (no re-assembly or autotuning) while the batch
+ * exists.  bem_batch_launch runs the whole graph on `stream` (asynchronous);
+ * bem_batch_destroy frees it.  No paper counterpart. */
+typedef struct bem_batch bem_batch;
+bem_status bem_batch_create(bem_ctx* const* ctxs, int n, const void* const* x, void* const* y, const int* nrhs,
+                            int dtype, void* stream, bem_batch** out);
+bem_status bem_batch_launch(bem_batch* batch, void* stream);
+void bem_batch_destroy(bem_batch* batch);
+
 /* Kernel timing of bem_matvec.  After bem_profile_begin, every bem_matvec on ctx
  * records a CUDA event pair around each of its kernels on the caller's stream
  * (a few microseconds of overhead per product); bem_profile_end synchronises those

@@ -29,6 +29,7 @@ EXPORTS = [
     "bem_partition", "bem_eval_entries", "bem_matvec", "bem_rhs_planewave", "bem_solve", "bem_power",
     "bem_power_density", "bem_profile_begin", "bem_profile_end", "bem_absorbed_power_static",
     "bem_matvec_adjoint", "bem_solve_adjoint", "bem_absorbed_power_gradient", "bem_grad_weights", "bem_grad_eps",
+    "bem_autotune", "bem_batch_create", "bem_batch_launch", "bem_batch_destroy",
 ]
 KERNEL_NAMES = ["k_gather", "k_vhx", "k_rows"]   # BEM_KERNEL_GATHER, _VHX, _ROWS
 
@@ -96,6 +97,11 @@ def _load():
         "bem_solve_adjoint": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int), dp]),
         "bem_absorbed_power_gradient": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, vp]),
         "bem_grad_eps": (ctypes.c_int, [ctx, vp, vp, dp, vp]),
+        "bem_autotune": (ctypes.c_int, [ctx, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int), dp]),
+        "bem_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int, vp, ctypes.POINTER(vp)]),
+        "bem_batch_launch": (ctypes.c_int, [vp, vp]),
+        "bem_batch_destroy": (None, [vp]),
         "bem_grad_weights": (ctypes.c_int, [ctx, vp, ctypes.c_int, ctypes.POINTER(bem_c128), dp,
                                             ctypes.POINTER(bem_c128), vp, vp, vp, ctypes.POINTER(ctypes.c_int)]),
         "bem_rhs_planewave": (ctypes.c_int, [ctx, dp, ctypes.POINTER(bem_c128), ctypes.c_int, vp, ctypes.c_int, vp]),
@@ -275,6 +281,35 @@ def bem_grad_eps(ctx, x_ptr: int, lam_ptr: int, stream: int = 0):
     _check(ctx, lib.bem_grad_eps(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(lam_ptr), _np_ptr(out, ctypes.c_double),
                                  ctypes.c_void_p(stream)))
     return out
+
+
+def bem_autotune(ctx, dtype: int, stream: int = 0):
+    """Returns (slots chosen, ms per product)."""
+    ch = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    _check(ctx, lib.bem_autotune(ctx, int(dtype), ctypes.c_void_p(stream), ctypes.byref(ch), ctypes.byref(ms)))
+    return ch.value, ms.value
+
+
+def bem_batch_create(ctxs, x_ptrs, y_ptrs, nrhs, dtype: int, stream: int = 0):
+    n = len(ctxs)
+    arr = lambda vals: (ctypes.c_void_p * n)(*[ctypes.c_void_p(int(v.value) if hasattr(v, "value") else int(v))  # noqa: E731
+                                                for v in vals])
+    out = ctypes.c_void_p()
+    st = lib.bem_batch_create(arr(ctxs), n, arr(x_ptrs), arr(y_ptrs), (ctypes.c_int * n)(*[int(r) for r in nrhs]),
+                              int(dtype), ctypes.c_void_p(stream), ctypes.byref(out))
+    _check(ctxs[0], st)
+    return out
+
+
+def bem_batch_launch(batch, stream: int = 0) -> None:
+    st = lib.bem_batch_launch(batch, ctypes.c_void_p(stream))
+    if st != BEM_OK:
+        raise BemError(st, "bem_batch_launch failed")
+
+
+def bem_batch_destroy(batch) -> None:
+    lib.bem_batch_destroy(batch)
 
 
 def bem_power(ctx, x_ptr: int, b_ptr: int, nrhs: int, stream: int = 0):

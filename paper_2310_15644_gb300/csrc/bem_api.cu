@@ -61,6 +61,7 @@ struct Operator {
     std::vector<BlockDesc> far_desc;   // blocks stored as factors (partition far blocks, or their splits)
     int64_t n_far_split = 0;           // far blocks split because their rank passed the cap
     int64_t n_far_dense = 0;           // partition far blocks stored densely (rank above break-even)
+    int row_target = BEM_ROW_TARGET_CTAS;  // rows-kernel slots aimed at (bem_autotune may change it)
     RowsPlan fwd;         // rows kernel of Z x (items by row leaf)
     RowsPlan adj;         // rows kernel of Z^H x (transposed items, by column leaf); built on first use
     bool adj_built = false;
@@ -226,6 +227,7 @@ static c128 csqrt_principal(c128 z) {
 static void release_operator(Operator& o) {
     release_rows_plan(o.fwd);
     release_rows_plan(o.adj);
+    o.row_target = BEM_ROW_TARGET_CTAS;
     o.adj_built = false;
     dfree(o.nearT);
     o.items.clear();
@@ -757,6 +759,7 @@ static bem_status build_leaves(bem_ctx* c, cudaStream_t st) {
 // transposed items and a far block gives a piece to every leaf of its columns.
 static bem_status build_rows_plan(bem_ctx* c, const Operator& o, const std::vector<BlockDesc>& dense, bool adjoint,
                                   RowsPlan& rp, size_t es, cudaStream_t st) {
+    const int target = o.row_target;
     const int nleaf = (int)c->leaf_lo.size();
     std::vector<int> leaf_of(c->ne + 1, -1);
     for (int l = 0; l < nleaf; ++l) leaf_of[c->leaf_lo[l]] = l;
@@ -794,14 +797,14 @@ static bem_status build_rows_plan(bem_ctx* c, const Operator& o, const std::vect
         }
     }
     // Slots: a leaf's items are split into parts proportional to its share of the
-    // work (about BEM_ROW_TARGET_CTAS slots in total, at most 32 per leaf), by
+    // work (about o.row_target slots in total, at most 32 per leaf), by
     // longest-processing-time assignment; CTAs take the slots heaviest first.
     int64_t total = 0;
     std::vector<int64_t> lw(nleaf, 0);
     for (int l = 0; l < nleaf; ++l)
         for (auto& it : items[l]) lw[l] += it.first;
     for (int l = 0; l < nleaf; ++l) total += lw[l];
-    const double per_slot = std::max(1.0, (double)total / BEM_ROW_TARGET_CTAS);
+    const double per_slot = std::max(1.0, (double)total / target);
     std::vector<int> wptr(1, 0), witem, lparts(nleaf), sleaf, spart;
     std::vector<int64_t> scost;
     rp.pmax = 1;
@@ -1372,6 +1375,154 @@ static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int
     Operator& o = c->op[1];
     return matvec_run<double>(make_plan(c, o, adjoint), adjoint ? o.nearT.p : o.near.p, o.arena.p, (const c128*)x,
                               (c128*)y, (c128*)o.xp.p, (c128*)o.t.p, nrhs, o.t_len, st, ev, BEM_FORM_NATIVE, adjoint);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner of the rows-kernel schedule
+// ---------------------------------------------------------------------------
+extern "C" bem_status bem_autotune(bem_ctx* c, int dtype, void* stream, int* chosen, double* ms_best) {
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "bem_autotune needs bem_assemble");
+    if (dtype != BEM_C64 && dtype != BEM_C128 && dtype != BEM_C64_BF16F) return fail(c, BEM_EINVAL, "dtype");
+    if (!dtype_ok(c, dtype)) return fail(c, BEM_EINVAL, "no operator of that precision was assembled");
+    cudaStream_t st = (cudaStream_t)stream;
+    Operator& o = c->op[dtype == BEM_C128 ? 1 : 0];
+    const size_t es = esize_of(dtype);
+    const int64_t n = 2 * c->ne;
+    DevBuf x, y;
+    struct G {
+        DevBuf* b[2];
+        ~G() {
+            for (DevBuf* z : b) dfree(*z);
+        }
+    } guard{{&x, &y}};
+    CK(dalloc(x, es * n));
+    CK(dalloc(y, es * n));
+    CK(cudaMemsetAsync(x.p, 0, es * n, st));  // the schedule's time does not depend on the values
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    struct GE {
+        cudaEvent_t a, b;
+        ~GE() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } gev{e0, e1};
+    // candidate slot counts: multiples of the SM count (4 .. 96 CTAs per SM over the product)
+    const int cand[] = {4 * 152, 8 * 152, 16 * 152, 32 * 152, 48 * 152, 64 * 152, 96 * 152};
+    int best = o.row_target;
+    double best_ms = 1e300;
+    bem_status s;
+    for (int target : cand) {
+        release_rows_plan(o.fwd);
+        o.row_target = target;
+        if ((s = build_rows_plan(c, o, o.items, false, o.fwd, es, st)) != BEM_OK) return s;
+        for (int w = 0; w < 3; ++w) CK(matvec_any(c, dtype, x.p, y.p, 1, st));
+        CK(cudaEventRecord(e0, st));
+        const int reps = 10;
+        for (int r = 0; r < reps; ++r) CK(matvec_any(c, dtype, x.p, y.p, 1, st));
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms / reps < best_ms) {
+            best_ms = ms / reps;
+            best = target;
+        }
+    }
+    release_rows_plan(o.fwd);
+    o.row_target = best;
+    if ((s = build_rows_plan(c, o, o.items, false, o.fwd, es, st)) != BEM_OK) return s;
+    if (o.adj_built) {  // the adjoint plan follows the same target
+        release_rows_plan(o.adj);
+        o.adj_built = false;
+        dfree(o.nearT);
+    }
+    CK(cudaStreamSynchronize(st));
+    if (chosen) *chosen = best;
+    if (ms_best) *ms_best = best_ms;
+    return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// several operators' products in one CUDA graph
+// ---------------------------------------------------------------------------
+struct bem_batch {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int n = 0;
+};
+
+extern "C" bem_status bem_batch_create(bem_ctx* const* ctxs, int n, const void* const* x, void* const* y,
+                                       const int* nrhs, int dtype, void* stream, bem_batch** out) {
+    if (!out || n < 1 || !ctxs || !x || !y || !nrhs) return BEM_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        bem_ctx* c = ctxs[i];
+        if (!c || !c->assembled || !dtype_ok(c, dtype) || nrhs[i] < 1 || !x[i] || !y[i]) return BEM_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return fail(c, BEM_EINVAL, "a context appears twice in a batch (shared workspaces)");
+        if (c->prof) return fail(c, BEM_ESTATE, "bem_batch_create during bem_profile_begin");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // capture on a private stream: one forked branch per operator, joined at the end
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    std::vector<cudaStream_t> br(n, nullptr);
+    std::vector<cudaEvent_t> ev(n + 1, nullptr);
+    bem_batch* b = new (std::nothrow) bem_batch();
+    cudaError_t e = b ? cudaSuccess : cudaErrorMemoryAllocation;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+    for (int i = 0; i <= n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    bool capturing = false;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        capturing = true;
+        e = cudaEventRecord(ev[n], cap);
+    }
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaStreamWaitEvent(br[i], ev[n], 0);
+        if (e == cudaSuccess) e = matvec_any(ctxs[i], dtype, x[i], y[i], nrhs[i], br[i]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[i], br[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, ev[i], 0);
+    }
+    if (capturing) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess) e = e2;
+        if (b) b->graph = g;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e == cudaSuccess) e = cudaGraphUpload(b->exec, st);
+    for (int i = 0; i < n; ++i)
+        if (br[i]) cudaStreamDestroy(br[i]);
+    for (cudaEvent_t v : ev)
+        if (v) cudaEventDestroy(v);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        if (b) {
+            if (b->exec) cudaGraphExecDestroy(b->exec);
+            if (b->graph) cudaGraphDestroy(b->graph);
+            delete b;
+        }
+        return fail(ctxs[0], e == cudaErrorMemoryAllocation ? BEM_ENOMEM : BEM_ECUDA, cudaGetErrorString(e));
+    }
+    b->n = n;
+    *out = b;
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_batch_launch(bem_batch* b, void* stream) {
+    if (!b || !b->exec) return BEM_EINVAL;
+    return cudaGraphLaunch(b->exec, (cudaStream_t)stream) == cudaSuccess ? BEM_OK : BEM_ECUDA;
+}
+
+extern "C" void bem_batch_destroy(bem_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
 }
 
 extern "C" bem_status bem_profile_begin(bem_ctx* c) {
