@@ -1468,6 +1468,7 @@ extern "C" bem_status bem_batch_create(bem_ctx* const* ctxs, int n, const void* 
     cudaStream_t st = (cudaStream_t)stream;
     // capture on a private stream: one forked branch per operator, joined at the end
     cudaStream_t cap;
+    bem_ctx* c = ctxs[0];  // errors are reported on the first context
     CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     std::vector<cudaStream_t> br(n, nullptr);
     std::vector<cudaEvent_t> ev(n + 1, nullptr);
