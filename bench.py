@@ -20,7 +20,9 @@ Reported beside the headline value:
                 with complex64 and with BF16 factors, their error on oracle rows,
                 a BF16-inner solve refined in FP64, and the 1/8-scale copy's
                 currents and absorbed power density against the stored oracle
-                solution.
+                solution;
+  multi_mesh    16 spheres of uneven size: one product each per step, as separate
+                calls, as one CUDA-graph launch, and after autotuning.
 `--impl reference` times the oracle alone (the reference arm).
 """
 from __future__ import annotations
@@ -410,6 +412,8 @@ def run_native(args, rank, world, dist):
                                    "error_metric": "max |y_gpu - y_oracle| over sampled rows / rms(y_gpu)"}
         if not args.no_large:
             out["large"] = run_large(args, dev, stream, B, W, peak, not args.no_cpu_baseline)
+        if not args.no_multi:
+            out["multi_mesh"] = run_multi_mesh(args, dev, stream, B, W)
     return out
 
 
@@ -539,6 +543,77 @@ def run_large(args, dev, stream, B, W, peak, with_oracle):
 
 
 # ---------------------------------------------------------------------------
+# many meshes of uneven size in one graph launch
+# ---------------------------------------------------------------------------
+def run_multi_mesh(args, dev, stream, B, W, count=16):
+    """16 geodesic spheres of uneven size (1280-20480 triangles, random radius, k0
+    and eps_r; workloads.uneven_sphere_batch, seed 1): one product of every mesh
+    per step, issued as 16 bem_matvec calls on one stream, as one CUDA-graph launch
+    (bem_batch_launch), and as one graph launch after bem_autotune of each mesh."""
+    import torch
+
+    sp = stream.cuda_stream
+    specs = W.uneven_sphere_batch(count, seed=1)
+    hs, xs, ys, tris, unk = [], [], [], [], []
+    t0 = time.perf_counter()
+    for i, sp_ in enumerate(specs):
+        v, t = W.geodesic_sphere(sp_["freq"], sp_["radius"])
+        opt = B.bem_default_options()
+        opt.precision = B.BEM_PREC_C64
+        opt.leaf_size, opt.eta, opt.aca_tol = LEAF, ETA, ACA_TOL
+        h = B.bem_create(opt)
+        B.bem_set_mesh(h, v, t)
+        B.bem_set_media(h, sp_["k0"], sp_["eps_r"])
+        B.bem_assemble(h, sp)
+        n = B.bem_num_unknowns(h)
+        hs.append(h)
+        xs.append(torch.from_numpy(W.complex_normal(n, seed=100 + i).astype(np.complex64)).to(dev))
+        ys.append(torch.empty_like(xs[-1]))
+        tris.append(len(t))
+        unk.append(n)
+    torch.cuda.synchronize(dev)
+    asm_s = time.perf_counter() - t0
+    K = max(10, args.steps // 20)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / K
+
+    def seq():
+        for h, x, y in zip(hs, xs, ys):
+            B.bem_matvec(h, x.data_ptr(), y.data_ptr(), 1, B.BEM_C64, sp)
+
+    out = {"meshes": count, "triangles": tris, "unknowns_total": int(sum(unk)), "assembly_s": round(asm_s, 2),
+           "steps": K}
+    ms_seq = timed(seq)
+    batch = B.bem_batch_create(hs, [x.data_ptr() for x in xs], [y.data_ptr() for y in ys], [1] * count,
+                               B.BEM_C64, sp)
+    ms_graph = timed(lambda: B.bem_batch_launch(batch, sp))
+    B.bem_batch_destroy(batch)
+    chosen = [B.bem_autotune(h, B.BEM_C64, sp)[0] for h in hs]
+    batch = B.bem_batch_create(hs, [x.data_ptr() for x in xs], [y.data_ptr() for y in ys], [1] * count,
+                               B.BEM_C64, sp)
+    ms_tuned = timed(lambda: B.bem_batch_launch(batch, sp))
+    B.bem_batch_destroy(batch)
+    for h in hs:
+        B.bem_destroy(h)
+    out.update({"ms_per_step_sequential": round(ms_seq, 4), "ms_per_step_graph": round(ms_graph, 4),
+                "ms_per_step_graph_autotuned": round(ms_tuned, 4),
+                "meshes_per_s_graph_autotuned": round(count / (ms_tuned * 1e-3), 1),
+                "autotuned_slots_per_sm": [c // 152 for c in chosen]})
+    return out
+
+
+# ---------------------------------------------------------------------------
 # reference arm: the oracle alone on host cores
 # ---------------------------------------------------------------------------
 def run_reference(args):
@@ -578,6 +653,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the complex128 GPU comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")
     ap.add_argument("--no-large", action="store_true", help="skip the 602,208-unknown slab")
+    ap.add_argument("--no-multi", action="store_true", help="skip the 16-mesh graph batch")
     ap.add_argument("--level", type=int, default=5,
                     help="icosphere level (5 = the 61440-unknown workload; smaller levels for profiling captures)")
     args = ap.parse_args()
