@@ -1346,7 +1346,18 @@ static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int
                               bool record = false, bool adjoint = false) {
     const cudaEvent_t* ev = nullptr;
     if (record && c->prof) {
-        size_t need = c->ev_used + 6 * (size_t)nrhs;
+        // 6 events per operator pass: chunks of 8, 4, 2, 1 right-hand sides (one pass
+        // per right-hand side for the FP64-sum form)
+        size_t passes = 0;
+        if (dtype == DT_C64_IN_FP64) {
+            passes = (size_t)nrhs;
+        } else {
+            for (int left = nrhs; left > 0;) {
+                left -= left >= 8 ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1));
+                ++passes;
+            }
+        }
+        size_t need = c->ev_used + 6 * passes;
         while (c->ev_pool.size() < need) {
             cudaEvent_t e;
             cudaError_t err = cudaEventCreate(&e);

@@ -125,3 +125,21 @@ def test_autotune_keeps_the_product(B):
         assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
     finally:
         B.bem_destroy(h)
+
+
+def test_profile_counts_operator_passes(B):
+    """Kernel timing with 13 right-hand sides: three operator passes (8 + 4 + 1),
+    so three launches of each kernel per product."""
+    v, t = W.icosphere(3)
+    h = make(B, v, t, 6.0, 3.2 - 1.9j)
+    try:
+        n = B.bem_num_unknowns(h)
+        X = torch.zeros((13, n), dtype=torch.complex64, device=DEV)
+        Y = torch.empty_like(X)
+        B.bem_profile_begin(h)
+        for _ in range(2):
+            B.bem_matvec(h, X.data_ptr(), Y.data_ptr(), 13, 0, _stream())
+        ms, cnt = B.bem_profile_end(h)
+        assert list(cnt) == [6, 6, 6] and all(m > 0 for m in ms)
+    finally:
+        B.bem_destroy(h)
