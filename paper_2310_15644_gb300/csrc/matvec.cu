@@ -208,12 +208,112 @@ __device__ __forceinline__ void vhx_unit(const FarRec* __restrict__ far, int2 un
     }
 }
 
+// The same for 4 or 8 right-hand sides, with lanes over right-hand sides: lane l
+// of an item's 8 handles right-hand side l mod NR over the rows j = l / NR,
+// l / NR + 8 / NR, ...; the W pair of a row is
+// one broadcast load for the lanes that share it, each lane keeps four complex
+// sums, and the lanes of one right-hand side are summed by shuffles.
+template <typename R, typename F, int NR>
+__device__ __forceinline__ void vhx_unit_rhs(const FarRec* __restrict__ far, int2 un, const F* __restrict__ arena,
+                                             const cx<R>* __restrict__ xp, cx<R>* __restrict__ t, int ne) {
+    constexpr int LPR = 8 / NR;  // lanes per right-hand side (rows split among them)
+    constexpr int UN = 4;
+    const FarRec* Fp = far + un.x;
+    const int n = Fp->n;
+    const int kpA = (Fp->rk[0] + 1) >> 1, kpB = (Fp->rk[1] + 1) >> 1, kpC = (Fp->rk[2] + 1) >> 1;
+    const int it = un.y * 8 + (threadIdx.x >> 3);
+    const int ll = threadIdx.x & 7;
+    const int r = ll % NR, j0 = ll / NR;
+    if (it >= kpA + kpB + kpC) return;  // whole 8-lane group leaves this unit together
+    int op, kp;
+    if (it < kpA) {
+        op = 0;
+        kp = it;
+    } else if (it < kpA + kpB) {
+        op = 1;
+        kp = it - kpA;
+    } else {
+        op = 2;
+        kp = it - kpA - kpB;
+    }
+    const F* V = arena + Fp->off_v[op] + 2 * (int64_t)kp * n;
+    const cx<R>* xs = xp + ((int64_t)((op == 2) ? ne : 0) + Fp->c0) * NR + r;
+    const cx<R>* xm = xp + ((int64_t)ne + Fp->c0) * NR + r;
+    cx<R> a0 = mk<R>(0, 0), a1 = a0, b0 = a0, b1 = a0;
+    int j = j0;
+    for (; j + LPR * (UN - 1) < n; j += LPR * UN) {
+        cx<R> w0[UN], w1[UN], xv[UN];
+#pragma unroll
+        for (int q = 0; q < UN; ++q) {
+            FPair<F>::template ld<R>(V, j + LPR * q, w0[q], w1[q]);
+            xv[q] = xs[(int64_t)(j + LPR * q) * NR];
+        }
+#pragma unroll
+        for (int q = 0; q < UN; ++q) {
+            cfma(a0, w0[q], xv[q]);
+            cfma(a1, w1[q], xv[q]);
+        }
+        if (op == 1) {
+#pragma unroll
+            for (int q = 0; q < UN; ++q) {
+                const cx<R> xw = xm[(int64_t)(j + LPR * q) * NR];
+                cfma(b0, w0[q], xw);
+                cfma(b1, w1[q], xw);
+            }
+        }
+    }
+    for (; j < n; j += LPR) {
+        cx<R> w0, w1;
+        FPair<F>::template ld<R>(V, j, w0, w1);
+        const cx<R> xv = xs[(int64_t)j * NR];
+        cfma(a0, w0, xv);
+        cfma(a1, w1, xv);
+        if (op == 1) {
+            const cx<R> xw = xm[(int64_t)j * NR];
+            cfma(b0, w0, xw);
+            cfma(b1, w1, xw);
+        }
+    }
+    if (LPR > 1) {
+        // lanes of one right-hand side differ in the bits above log2(NR)
+        const unsigned mask = 0xffu << (threadIdx.x & 24);
+#pragma unroll
+        for (int o = NR; o < 8; o <<= 1) {
+            a0.re += __shfl_xor_sync(mask, a0.re, o);
+            a0.im += __shfl_xor_sync(mask, a0.im, o);
+            a1.re += __shfl_xor_sync(mask, a1.re, o);
+            a1.im += __shfl_xor_sync(mask, a1.im, o);
+            if (op == 1) {
+                b0.re += __shfl_xor_sync(mask, b0.re, o);
+                b0.im += __shfl_xor_sync(mask, b0.im, o);
+                b1.re += __shfl_xor_sync(mask, b1.re, o);
+                b1.im += __shfl_xor_sync(mask, b1.im, o);
+            }
+        }
+    }
+    if (j0 == 0) {
+        cx<R>* tb = t + Fp->off_t * NR;
+        const int seg = (op == 0) ? 0 : ((op == 1) ? 2 * kpA : 2 * (kpA + 2 * kpB));
+        tb[(seg + 2 * kp) * NR + r] = a0;
+        tb[(seg + 2 * kp + 1) * NR + r] = a1;
+        if (op == 1) {
+            tb[(2 * (kpA + kpB) + 2 * kp) * NR + r] = b0;
+            tb[(2 * (kpA + kpB) + 2 * kp + 1) * NR + r] = b1;
+        }
+    }
+}
+
 // one CTA per unit; the hardware scheduler balances the (largest-first) units
 template <typename R, typename F, int NR>
 __global__ void __launch_bounds__(VHX_THREADS) k_vhx(const FarRec* __restrict__ far, const int2* __restrict__ units,
                                                      int nunits, const F* __restrict__ arena,
                                                      const cx<R>* __restrict__ xp, cx<R>* __restrict__ t, int ne) {
-    if ((int)blockIdx.x < nunits) vhx_unit<R, F, NR>(far, units[blockIdx.x], arena, xp, t, ne);
+    if ((int)blockIdx.x < nunits) {
+        if constexpr (NR >= 4)
+            vhx_unit_rhs<R, F, NR>(far, units[blockIdx.x], arena, xp, t, ne);
+        else
+            vhx_unit<R, F, NR>(far, units[blockIdx.x], arena, xp, t, ne);
+    }
 }
 
 // Adjoint product, first pass: t' = U^T xp over the block's rows (A and C use x_J
