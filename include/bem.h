@@ -97,15 +97,7 @@ typedef struct {
     double refine_tol;   /* outer FP64 iterative-refinement target; 0 disables refinement (default 0) */
     int refine_maxit;    /* maximum outer refinement steps (default 10) */
     int solver;          /* inner Krylov solver, BEM_SOLVER_* (default GMRES) */
-    int precond;         /* BEM_PRECOND_* for the GMRES inner solve (default none) */
 } bem_options;
-
-/* Preconditioners (bem_options.precond), right-applied in GMRES on the complex64 or
- * BF16-factor operator (other inner solvers and complex128-only contexts ignore
- * them).  They change the iteration count, not the solution. */
-#define BEM_PRECOND_NONE 0
-#define BEM_PRECOND_BLOCK_JACOBI 1 /* exact inverse of every leaf's 2m x 2m self block [[A, B], [-B, C]],
-                                      built on first use (4 (2m)^2 bytes per leaf) */
 
 /* Inner Krylov solvers (bem_options.solver).  maxit counts iterations: one product
  * per GMRES iteration, two per CGS, BiCGStab and CGNR iteration. */

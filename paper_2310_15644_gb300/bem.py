@@ -19,7 +19,6 @@ BEM_OK, BEM_EINVAL, BEM_ENOMEM, BEM_ECUDA, BEM_ENOCONV, BEM_ETIMEOUT, BEM_ESTATE
 BEM_PREC_C64, BEM_PREC_C128, BEM_PREC_BF16F = 1, 2, 4
 BEM_C64, BEM_C128, BEM_C64_BF16F = 0, 1, 2
 BEM_SOLVER_GMRES, BEM_SOLVER_CGS, BEM_SOLVER_BICGSTAB, BEM_SOLVER_CGNR = 0, 1, 2, 3
-BEM_PRECOND_NONE, BEM_PRECOND_BLOCK_JACOBI = 0, 1
 STATUS_NAMES = {0: "BEM_OK", 1: "BEM_EINVAL", 2: "BEM_ENOMEM", 3: "BEM_ECUDA", 4: "BEM_ENOCONV",
                 5: "BEM_ETIMEOUT", 6: "BEM_ESTATE"}
 
@@ -40,7 +39,7 @@ class bem_options(ctypes.Structure):
         ("precision", ctypes.c_int), ("leaf_size", ctypes.c_int), ("eta", ctypes.c_double),
         ("aca_tol", ctypes.c_double), ("aca_max_rank", ctypes.c_int), ("gmres_restart", ctypes.c_int),
         ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("refine_tol", ctypes.c_double),
-        ("refine_maxit", ctypes.c_int), ("solver", ctypes.c_int), ("precond", ctypes.c_int),
+        ("refine_maxit", ctypes.c_int), ("solver", ctypes.c_int),
     ]
 
 

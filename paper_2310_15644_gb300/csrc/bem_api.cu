@@ -67,8 +67,6 @@ struct Operator {
     bool adj_built = false;
     DevBuf near;          // 3 * fwd.near_stride complex
     DevBuf nearT;         // transposed dense items, 3 * adj.near_stride complex (adjoint)
-    DevBuf bj, bj_off;    // block-Jacobi inverses (complex64 operator), per-leaf offsets
-    bool bj_built = false;
     DevBuf arena;         // low-rank factors
     DevBuf arena_bf16;    // BF16 copy of the factors (complex64 operator, BEM_PREC_BF16F)
     int64_t arena_len = 0;
@@ -230,9 +228,6 @@ static void release_operator(Operator& o) {
     release_rows_plan(o.fwd);
     release_rows_plan(o.adj);
     o.row_target = BEM_ROW_TARGET_CTAS;
-    dfree(o.bj);
-    dfree(o.bj_off);
-    o.bj_built = false;
     o.adj_built = false;
     dfree(o.nearT);
     o.items.clear();
@@ -275,7 +270,6 @@ extern "C" void bem_default_options(bem_options* o) {
     o->refine_tol = 0.0;
     o->refine_maxit = 10;
     o->solver = BEM_SOLVER_GMRES;
-    o->precond = BEM_PRECOND_NONE;
 }
 
 extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
@@ -287,7 +281,7 @@ extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
     if (o.leaf_size < 2 || o.leaf_size > BEM_MAX_LEAF || (o.precision & 7) == 0 || (o.precision & ~7) != 0 ||
         o.aca_tol <= 0 || o.aca_max_rank < 1 || o.aca_max_rank > 128 || o.gmres_restart < 1 || o.gmres_restart > 200 || o.maxit < 1 ||
         o.tol <= 0 || o.refine_tol < 0 || o.refine_maxit < 1 || o.solver < BEM_SOLVER_GMRES ||
-        o.solver > BEM_SOLVER_CGNR || o.precond < BEM_PRECOND_NONE || o.precond > BEM_PRECOND_BLOCK_JACOBI)
+        o.solver > BEM_SOLVER_CGNR)
         return BEM_EINVAL;
     bem_ctx* c = new (std::nothrow) bem_ctx();
     if (!c) return BEM_ENOMEM;
@@ -1660,59 +1654,8 @@ static bem_status gmres_work(bem_ctx* c, int dtype, int restart) {
 }
 
 // solve Z x = rhs (dtype vectors in gw.rin / gw.xin), x starts at zero; absolute tolerance
-// block-Jacobi inverses of the complex64 operator's leaf self blocks (first use)
-static bem_status ensure_bj(bem_ctx* c, cudaStream_t st) {
-    Operator& o = c->op[0];
-    if (o.bj_built) return BEM_OK;
-    const int nleaf = (int)c->leaf_lo.size();
-    // the self block of leaf l is the dense item with r0 == c0 == leaf start
-    std::vector<int64_t> item_off(nleaf, -1), inv_off(nleaf);
-    int64_t off = 0, ioff = 0;
-    std::vector<int> leaf_of(c->ne + 1, -1);
-    for (int l = 0; l < nleaf; ++l) leaf_of[c->leaf_lo[l]] = l;
-    for (const BlockDesc& b : o.items) {
-        if (b.r0 == b.c0 && leaf_of[b.r0] >= 0) item_off[leaf_of[b.r0]] = off;
-        off += (int64_t)b.m * 2 * ((b.n + 1) / 2);
-    }
-    int max_m = 1;
-    for (int l = 0; l < nleaf; ++l) {
-        if (item_off[l] < 0) return fail(c, BEM_ECUDA, "a leaf has no self block");
-        inv_off[l] = ioff;
-        ioff += 4 * (int64_t)c->leaf_m[l] * c->leaf_m[l];
-        max_m = std::max(max_m, c->leaf_m[l]);
-    }
-    DevBuf d_item, d_flag;
-    struct G {
-        DevBuf* b[2];
-        ~G() {
-            for (DevBuf* z : b) dfree(*z);
-        }
-    } guard{{&d_item, &d_flag}};
-    CK(upload(d_item, item_off, st));
-    CK(upload(o.bj_off, inv_off, st));
-    CK(dalloc(o.bj, sizeof(c64) * std::max<int64_t>(1, ioff)));
-    CK(dalloc(d_flag, sizeof(int)));
-    CK(cudaMemsetAsync(d_flag.p, 0, sizeof(int), st));
-    CK(bj_build((const int*)c->d_leaf_r0.p, (const int*)c->d_leaf_m.p, (const int64_t*)d_item.p, nleaf, max_m,
-                (const c64*)o.near.p, o.fwd.near_stride, (const int64_t*)o.bj_off.p, (c64*)o.bj.p, (int*)d_flag.p,
-                st));
-    int flag = 0;
-    CK(cudaMemcpyAsync(&flag, d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (flag) return fail(c, BEM_ECUDA, "block-Jacobi: a leaf self block is singular");
-    o.bj_built = true;
-    return BEM_OK;
-}
-
-static cudaError_t bj_apply_ctx(bem_ctx* c, const void* x, void* z, bool adjoint, cudaStream_t st) {
-    const Operator& o = c->op[0];
-    return bj_apply((const int*)c->d_leaf_r0.p, (const int*)c->d_leaf_m.p, (const int64_t*)c->d_perm.p,
-                    (int)c->leaf_lo.size(), (const int64_t*)o.bj_off.p, (const c64*)o.bj.p, (const c64*)x, (c64*)z,
-                    (int)c->ne, adjoint, st);
-}
-
 static bem_status gmres(bem_ctx* c, int pdt, double tol_abs, int maxit, int* iters, double* final_res,
-                        cudaStream_t st, bool adjoint = false, bool precond = false) {
+                        cudaStream_t st, bool adjoint = false) {
     const int dtype = vec_dtype(pdt);  // vectors; pdt selects the product
     GmresWork& w = c->gw;
     const int64_t n = w.n;
@@ -1734,12 +1677,7 @@ static bem_status gmres(bem_ctx* c, int pdt, double tol_abs, int maxit, int* ite
         g[0] = mk<double>(beta, 0);
         int jl = -1;
         for (int j = 0; j < m; ++j) {
-            if (precond) {  // right preconditioning: w = Z P^-1 v_j
-                CK(bj_apply_ctx(c, V + es * n * j, w.z.p, adjoint, st));
-                CK(matvec_any(c, pdt, w.z.p, w.w.p, 1, st, false, adjoint));
-            } else {
-                CK(matvec_any(c, pdt, V + es * n * j, w.w.p, 1, st, false, adjoint));
-            }
+            CK(matvec_any(c, pdt, V + es * n * j, w.w.p, 1, st, false, adjoint));
             for (int pass = 0; pass < 2; ++pass) {
                 CK(kv_multidot(V, dtype, n, j + 1, w.w.p, n, (c128*)w.hpart.p, NPART, st));
                 CK(kv_reduce_partials((const c128*)w.hpart.p, NPART, j + 1, (c128*)w.hdev.p, st));
@@ -1786,15 +1724,7 @@ static bem_status gmres(bem_ctx* c, int pdt, double tol_abs, int maxit, int* ite
             y[i] = cdiv(acc, H[i * m + i]);
         }
         CK(cudaMemcpyAsync(w.hdev.p, y.data(), sizeof(c128) * k, cudaMemcpyHostToDevice, st));
-        if (precond) {  // x += P^-1 (V y)
-            CK(cudaMemsetAsync(w.r.p, 0, es * n, st));
-            CK(kv_update(w.r.p, V, dtype, n, k, (const c128*)w.hdev.p, 1.0, n, st));
-            CK(bj_apply_ctx(c, w.r.p, w.z.p, adjoint, st));
-            const c128 one = mk<double>(1, 0), zero = mk<double>(0, 0);
-            CK(kv_lincomb(w.xin.p, dtype, one, w.xin.p, one, w.z.p, zero, nullptr, n, st));
-        } else {
-            CK(kv_update(w.xin.p, V, dtype, n, k, (const c128*)w.hdev.p, 1.0, n, st));
-        }
+        CK(kv_update(w.xin.p, V, dtype, n, k, (const c128*)w.hdev.p, 1.0, n, st));
         // true residual
         CK(matvec_any(c, pdt, w.xin.p, w.z.p, 1, st, false, adjoint));
         CK(kv_sub(w.rin.p, w.z.p, w.r.p, dtype, n, st));
@@ -1955,12 +1885,6 @@ static bem_status solve_impl(bem_ctx* c, const void* b, void* x, int nrhs, void*
     const int vin = vec_dtype(din);
     const bool out128 = c->op[1].built;
     const int dres = out128 ? BEM_C128 : DT_C64_IN_FP64;
-    const bool use_bj =
-        c->opt.precond == BEM_PRECOND_BLOCK_JACOBI && c->opt.solver == BEM_SOLVER_GMRES && vin == BEM_C64;
-    if (use_bj) {
-        bem_status s0;
-        if ((s0 = ensure_bj(c, st)) != BEM_OK) return s0;
-    }
     if (adjoint || c->opt.solver == BEM_SOLVER_CGNR) {
         bem_status s0;
         if ((s0 = ensure_adjoint_for(c, din, st)) != BEM_OK) return s0;
@@ -2014,7 +1938,7 @@ static bem_status solve_impl(bem_ctx* c, const void* b, void* x, int nrhs, void*
             double fres;
             int before = total_it;
             if (c->opt.solver == BEM_SOLVER_GMRES)
-                s = gmres(c, din, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st, adjoint, use_bj);
+                s = gmres(c, din, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st, adjoint);
             else
                 s = cg_family(c, din, c->opt.solver, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st,
                               adjoint);

@@ -271,13 +271,6 @@ cudaError_t transpose_items(const BlockDesc* items, const int64_t* offF, const i
 // BF16 copy of n complex64 factor values
 cudaError_t factors_to_bf16(const c64* in, bf16c* out, int64_t n, cudaStream_t st);
 
-// precond.cu: near-field block-Jacobi preconditioner (complex64 self blocks)
-cudaError_t bj_build(const int* leaf_r0, const int* leaf_m, const int64_t* item_off, int nleaf, int max_m,
-                     const c64* near, int64_t op_stride, const int64_t* inv_off, c64* inv, int* flag,
-                     cudaStream_t st);
-cudaError_t bj_apply(const int* leaf_r0, const int* leaf_m, const int64_t* perm, int nleaf, const int64_t* inv_off,
-                     const c64* inv, const c64* x, c64* z, int ne, bool adjoint, cudaStream_t st);
-
 // rhs_power.cu
 template <typename R>
 cudaError_t rhs_planewave(GeomDev g, const double* khat, const c128* e0, int nrhs, cx<R>* b, cudaStream_t st);
