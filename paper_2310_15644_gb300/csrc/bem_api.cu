@@ -40,13 +40,13 @@ namespace {
 struct RowsPlan {
     int64_t near_stride = 0;           // complex elements per operator array of the dense items
     int nslot = 0, pmax = 1;           // rows-kernel CTAs; most slots of one leaf
-    DevBuf d_work_ptr, d_work_item, d_near_c0, d_near_n, d_near_off, d_farp_blk, d_farp_row, d_ypart, d_arrive;
+    DevBuf d_work_ptr, d_work_item, d_near_c0, d_near_n, d_near_off, d_pieces, d_ypart, d_arrive;
     DevBuf d_leaf_parts, d_slot_order, d_slot_leaf, d_slot_part;
 };
 
 static void release_rows_plan(RowsPlan& r) {
     DevBuf* plan[] = {&r.d_work_ptr,   &r.d_work_item, &r.d_near_c0,  &r.d_near_n,     &r.d_near_off,
-                      &r.d_farp_blk,   &r.d_farp_row,  &r.d_ypart,    &r.d_arrive,     &r.d_leaf_parts,
+                      &r.d_pieces,     &r.d_ypart,     &r.d_arrive,   &r.d_leaf_parts,
                       &r.d_slot_order, &r.d_slot_leaf, &r.d_slot_part};
     for (DevBuf* b : plan) dfree(*b);
     r.near_stride = 0;
@@ -847,8 +847,23 @@ static bem_status build_rows_plan(bem_ctx* c, const Operator& o, const std::vect
     CK(upload(rp.d_near_c0, nc0, st));
     CK(upload(rp.d_near_n, nn, st));
     CK(upload(rp.d_near_off, noff, st));
-    CK(upload(rp.d_farp_blk, fblk, st));
-    CK(upload(rp.d_farp_row, frow, st));
+    // flat piece descriptors
+    std::vector<PieceDesc> pieces(fblk.size());
+    for (size_t q = 0; q < fblk.size(); ++q) {
+        const FarRec& R = o.recs[fblk[q]];
+        const int ro = frow[q];
+        PieceDesc& d = pieces[q];
+        for (int k = 0; k < 3; ++k) {
+            d.kp[k] = (R.rk[k] + 1) / 2;
+            // forward: U slice of the leaf (pair (kp, i) at ro kpc + kp ms + i, stride ms);
+            // adjoint: W rows so + i (pair (kp, j) at kp n + j, stride n)
+            d.base[k] = adjoint ? R.off_v[k] + 2 * (int64_t)ro : R.off_u[k] + 2 * (int64_t)ro * d.kp[k];
+        }
+        const int l = leaf_of[(adjoint ? R.c0 : R.r0) + ro];
+        d.ld = adjoint ? R.n : c->leaf_m[l];
+        d.t_off = R.off_t;
+    }
+    CK(upload(rp.d_pieces, pieces, st));
     CK(dalloc(rp.d_ypart, es * 2 * c->ne * (rp.pmax > 1 ? rp.pmax : 1) * BEM_MAX_NR));
     CK(dalloc(rp.d_arrive, sizeof(unsigned int) * std::max(1, nleaf)));
     CK(cudaMemsetAsync(rp.d_arrive.p, 0, sizeof(unsigned int) * std::max(1, nleaf), st));
@@ -1287,8 +1302,7 @@ static MatvecPlan make_plan(const bem_ctx* c, const Operator& o, bool adjoint = 
     p.near_n = (const int*)rp.d_near_n.p;
     p.near_off = (const int64_t*)rp.d_near_off.p;
     p.near_op_stride = rp.near_stride;
-    p.farp_blk = (const int*)rp.d_farp_blk.p;
-    p.farp_row = (const int*)rp.d_farp_row.p;
+    p.pieces = (const PieceDesc*)rp.d_pieces.p;
     p.far = (const FarRec*)o.far_rec.p;
     p.vhx_units = (const int2*)o.far_order.p;
     p.nvhx = o.nvhx;

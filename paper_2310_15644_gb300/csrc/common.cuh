@@ -232,6 +232,18 @@ cudaError_t aca_compact(const AcaTask* tasks, int ntasks, const cx<R>* scratch, 
                         const int* pos_leaf_m, cudaStream_t st);
 
 // matvec.cu
+// One far piece of the rows kernel (a leaf's rows of one factored block): the
+// complex offsets in the arena of the three factor slices it streams (U slices in
+// the forward product, W rows in the adjoint), their pair stride, the column-pair
+// counts of A, B, C and the offset of the block's t values, so that a piece costs
+// one 48-byte descriptor load instead of a chain of lookups.
+struct __align__(16) PieceDesc {
+    int64_t base[3];
+    int64_t t_off;
+    int kp[3];
+    int ld;
+};
+
 struct MatvecPlan {
     int ne, nleaf, nfar;
     int nslot;                   // CTAs of the rows kernel (work slots)
@@ -249,8 +261,7 @@ struct MatvecPlan {
     const int* near_n;           // per dense item: columns
     const int64_t* near_off;     // per dense item: offset (complex elements) of its A entries
     int64_t near_op_stride;      // distance between the A, B, C arrays
-    const int* farp_blk;         // per far piece: far block index
-    const int* farp_row;         // per far piece: row offset of the leaf inside the far block
+    const PieceDesc* pieces;     // per far piece: factor bases, strides, ranks and t offset
     const FarRec* far;           // nfar
     const int2* vhx_units;       // nvhx units of the V^H x kernel: (far block, group of 8 items), largest first
     int nvhx;

@@ -553,24 +553,19 @@ __device__ __forceinline__ void far_slice(const F* __restrict__ U, int kpc, int 
     }
 }
 
-// ro: offset of the leaf inside the block's rows (forward) or columns (ADJ)
+// One far piece: the three factor slices of a leaf's rows with the 2 x 2 PMCHWT
+// structure (ADJ: the factors are W rows and the B terms change sign).
 template <typename R, typename FS, int NR, bool ADJ>
-__device__ __forceinline__ void far_piece(const FarRec& F, int ro, int ms, int i, const FS* __restrict__ arena,
+__device__ __forceinline__ void far_piece(const PieceDesc& d, int i, const FS* __restrict__ arena,
                                           const cx<R>* __restrict__ t, cx<R> (&aJ)[NR], cx<R> (&aM)[NR]) {
-    const int kpA = (F.rk[0] + 1) >> 1, kpB = (F.rk[1] + 1) >> 1, kpC = (F.rk[2] + 1) >> 1;
-    const cx<R>* tA = t + F.off_t * NR;
+    const int kpA = d.kp[0], kpB = d.kp[1], kpC = d.kp[2];
+    const cx<R>* tA = t + d.t_off * NR;
     const cx<R>* tBJ = tA + 2 * kpA * NR;
     const cx<R>* tBM = tBJ + 2 * kpB * NR;
     const cx<R>* tC = tBM + 2 * kpB * NR;
-    if (ADJ) {
-        far_slice<R, FS, NR, 0, true>(arena + F.off_v[0] + 2 * (int64_t)ro, kpA, F.n, i, tA, nullptr, aJ, aM);
-        far_slice<R, FS, NR, 1, true>(arena + F.off_v[1] + 2 * (int64_t)ro, kpB, F.n, i, tBM, tBJ, aJ, aM);
-        far_slice<R, FS, NR, 2, true>(arena + F.off_v[2] + 2 * (int64_t)ro, kpC, F.n, i, tC, nullptr, aJ, aM);
-    } else {
-        far_slice<R, FS, NR, 0, false>(arena + F.off_u[0] + 2 * (int64_t)ro * kpA, kpA, ms, i, tA, nullptr, aJ, aM);
-        far_slice<R, FS, NR, 1, false>(arena + F.off_u[1] + 2 * (int64_t)ro * kpB, kpB, ms, i, tBM, tBJ, aJ, aM);
-        far_slice<R, FS, NR, 2, false>(arena + F.off_u[2] + 2 * (int64_t)ro * kpC, kpC, ms, i, tC, nullptr, aJ, aM);
-    }
+    far_slice<R, FS, NR, 0, ADJ>(arena + d.base[0], kpA, d.ld, i, tA, nullptr, aJ, aM);
+    far_slice<R, FS, NR, 1, ADJ>(arena + d.base[1], kpB, d.ld, i, tBM, tBJ, aJ, aM);
+    far_slice<R, FS, NR, 2, ADJ>(arena + d.base[2], kpC, d.ld, i, tC, nullptr, aJ, aM);
 }
 
 // Grid: one 64-thread CTA per work slot (a leaf's dense items and far pieces are
@@ -607,9 +602,8 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const NS* __
                 dense_item<R, NS, NR, ADJ>(near + p.near_off[item], p.near_op_stride, m, i, p.near_n[item],
                                   xp + (int64_t)c0 * NR, xp + ((int64_t)ne + c0) * NR, aJ, aM);
             } else {
-                const int fp = -1 - item;
-                const FarRec F = p.far[p.farp_blk[fp]];
-                far_piece<R, FS, NR, ADJ>(F, p.farp_row[fp], m, i, arena, t, aJ, aM);
+                const PieceDesc d = p.pieces[-1 - item];
+                far_piece<R, FS, NR, ADJ>(d, i, arena, t, aJ, aM);
             }
         }
     }
