@@ -467,13 +467,24 @@ __device__ __forceinline__ void dense_item(const NS* __restrict__ A, int64_t str
 #pragma unroll
         for (int u = 0; u < UN; ++u) apply(a0[u], a1[u], b0[u], b1[u], c0[u], c1[u], 2 * (cp + u));
     }
-    for (; cp < nfull; ++cp) {
-        cx<R> a0, a1, b0, b1, c0, c1;
-        const int64_t idx = (int64_t)cp * m + i;
-        FPair<NS>::template ld<R>(A, idx, a0, a1);
-        FPair<NS>::template ld<R>(B, idx, b0, b1);
-        FPair<NS>::template ld<R>(C, idx, c0, c1);
-        apply(a0, a1, b0, b1, c0, c1, 2 * cp);
+    if (cp < nfull) {
+        // the remaining (< UN) column pairs: all loads issued before any is used
+        cx<R> a0[UN], a1[UN], b0[UN], b1[UN], c0[UN], c1[UN];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            if (cp + u < nfull) {
+                const int64_t idx = (int64_t)(cp + u) * m + i;
+                FPair<NS>::template ld<R>(A, idx, a0[u], a1[u]);
+                FPair<NS>::template ld<R>(B, idx, b0[u], b1[u]);
+                FPair<NS>::template ld<R>(C, idx, c0[u], c1[u]);
+            } else {
+                a0[u] = a1[u] = b0[u] = b1[u] = c0[u] = c1[u] = mk<R>(0, 0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UN; ++u)
+            if (cp + u < nfull) apply(a0[u], a1[u], b0[u], b1[u], c0[u], c1[u], 2 * (cp + u));
+        cp = nfull;
     }
     if (n & 1) {  // last column; its pair partner is a stored zero column
         cx<R> a0, a1, b0, b1, c0, c1;
@@ -546,10 +557,21 @@ __device__ __forceinline__ void far_slice(const F* __restrict__ U, int kpc, int 
 #pragma unroll
         for (int u = 0; u < UN; ++u) apply(u0[u], u1[u], kp + u);
     }
-    for (; kp < kpc; ++kp) {
-        cx<R> u0, u1;
-        FPair<F>::template ld<R>(U, (int64_t)kp * ms + i, u0, u1);
-        apply(u0, u1, kp);
+    if (kp < kpc) {
+        // the remaining (< UN) pairs: all loads issued before any is used (short
+        // slices, e.g. low-rank blocks of small leaves, are mostly tail)
+        cx<R> u0[UN], u1[UN];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            if (kp + u < kpc) {
+                FPair<F>::template ld<R>(U, (int64_t)(kp + u) * ms + i, u0[u], u1[u]);
+            } else {
+                u0[u] = u1[u] = mk<R>(0, 0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UN; ++u)
+            if (kp + u < kpc) apply(u0[u], u1[u], kp + u);
     }
 }
 
