@@ -171,10 +171,20 @@ __device__ __forceinline__ void vhx_unit(const FarRec* __restrict__ far, int2 un
 #pragma unroll
         for (int q = 0; q < UN; ++q) step(w0[q], w1[q], j + 8 * q);
     }
-    for (; j < n; j += 8) {
-        cx<R> w0, w1;
-        FPair<F>::template ld<R>(V, j, w0, w1);
-        step(w0, w1, j);
+    if (j < n) {
+        // the remaining (< UN) rows of this lane: loads first, then the sums
+        cx<R> w0[UN], w1[UN];
+#pragma unroll
+        for (int q = 0; q < UN; ++q) {
+            if (j + 8 * q < n) {
+                FPair<F>::template ld<R>(V, j + 8 * q, w0[q], w1[q]);
+            } else {
+                w0[q] = w1[q] = mk<R>(0, 0);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < UN; ++q)
+            if (j + 8 * q < n) step(w0[q], w1[q], j + 8 * q);
     }
     // sum over the 8 lanes of the group (xor offsets stay inside the group)
     const unsigned mask = 0xffu << (threadIdx.x & 24);
@@ -262,16 +272,30 @@ __device__ __forceinline__ void vhx_unit_rhs(const FarRec* __restrict__ far, int
             }
         }
     }
-    for (; j < n; j += LPR) {
-        cx<R> w0, w1;
-        FPair<F>::template ld<R>(V, j, w0, w1);
-        const cx<R> xv = xs[(int64_t)j * NR];
-        cfma(a0, w0, xv);
-        cfma(a1, w1, xv);
+    if (j < n) {
+        cx<R> w0[UN], w1[UN], xv[UN];
+#pragma unroll
+        for (int q = 0; q < UN; ++q) {
+            if (j + LPR * q < n) {
+                FPair<F>::template ld<R>(V, j + LPR * q, w0[q], w1[q]);
+                xv[q] = xs[(int64_t)(j + LPR * q) * NR];
+            } else {
+                w0[q] = w1[q] = xv[q] = mk<R>(0, 0);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < UN; ++q) {
+            cfma(a0, w0[q], xv[q]);
+            cfma(a1, w1[q], xv[q]);
+        }
         if (op == 1) {
-            const cx<R> xw = xm[(int64_t)j * NR];
-            cfma(b0, w0, xw);
-            cfma(b1, w1, xw);
+#pragma unroll
+            for (int q = 0; q < UN; ++q)
+                if (j + LPR * q < n) {
+                    const cx<R> xw = xm[(int64_t)(j + LPR * q) * NR];
+                    cfma(b0, w0[q], xw);
+                    cfma(b1, w1[q], xw);
+                }
         }
     }
     if (LPR > 1) {
