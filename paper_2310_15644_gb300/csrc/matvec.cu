@@ -118,10 +118,8 @@ __global__ void k_gather(const cx<R>* __restrict__ x, const int64_t* __restrict_
 template <typename R, typename F, int NR>
 __device__ __forceinline__ void vhx_unit(const FarRec* __restrict__ far, int2 un, const F* __restrict__ arena,
                                          const cx<R>* __restrict__ xp, cx<R>* __restrict__ t, int ne) {
-    // BF16 factors move half the bytes per load: four times as many loads in flight
-    // for one right-hand side (measured: 3.28 -> 3.65 TB/s; complex64 gains nothing
-    // beyond four)
-    constexpr int UN = sizeof(F) == 4 ? (NR == 1 ? 16 : (NR == 2 ? 4 : 2)) : (NR == 1 ? 4 : (NR == 2 ? 2 : 1));
+    // BF16 factors move half the bytes per load: twice as many loads in flight
+    constexpr int UN = (NR == 1 ? 4 : (NR == 2 ? 2 : 1)) * (sizeof(F) == 4 ? 2 : 1);
     const FarRec* Fp = far + un.x;
     const int n = Fp->n;
     const int kpA = (Fp->rk[0] + 1) >> 1, kpB = (Fp->rk[1] + 1) >> 1, kpC = (Fp->rk[2] + 1) >> 1;
@@ -374,23 +372,38 @@ __device__ __forceinline__ void uhx_unit(const FarRec* __restrict__ far, int2 un
     cx<R> a0[NR], a1[NR], b0[NR], b1[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) a0[r] = a1[r] = b0[r] = b1[r] = mk<R>(0, 0);
-    for (int i = jj; i < m; i += 8) {
-        const int ro = pos_leaf_lo[r0 + i] - r0, ms = pos_leaf_m[r0 + i];
-        cx<R> u0, u1;
-        FPair<F>::template ld<R>(Ub, (int64_t)ro * kpc + (int64_t)kp * ms + (i - ro), u0, u1);
-        cx<R> xv[NR];
-        ldv<R, NR>(xs + (int64_t)i * NR, xv);
+    constexpr int UN = NR == 1 ? 4 : (NR == 2 ? 2 : 1);
+    for (int i0 = jj; i0 < m; i0 += 8 * UN) {
+        // UN rows of this lane: loads first (predicated at the end of the block)
+        cx<R> u0[UN], u1[UN];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            cfma(a0[r], u0, xv[r]);
-            cfma(a1[r], u1, xv[r]);
+        for (int q = 0; q < UN; ++q) {
+            const int i = i0 + 8 * q;
+            if (i < m) {
+                const int ro = pos_leaf_lo[r0 + i] - r0, ms = pos_leaf_m[r0 + i];
+                FPair<F>::template ld<R>(Ub, (int64_t)ro * kpc + (int64_t)kp * ms + (i - ro), u0[q], u1[q]);
+            } else {
+                u0[q] = u1[q] = mk<R>(0, 0);
+            }
         }
-        if (op == 1) {
-            ldv<R, NR>(xm + (int64_t)i * NR, xv);
+#pragma unroll
+        for (int q = 0; q < UN; ++q) {
+            const int i = i0 + 8 * q;
+            if (i >= m) continue;
+            cx<R> xv[NR];
+            ldv<R, NR>(xs + (int64_t)i * NR, xv);
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                cfma(b0[r], u0, xv[r]);
-                cfma(b1[r], u1, xv[r]);
+                cfma(a0[r], u0[q], xv[r]);
+                cfma(a1[r], u1[q], xv[r]);
+            }
+            if (op == 1) {
+                ldv<R, NR>(xm + (int64_t)i * NR, xv);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    cfma(b0[r], u0[q], xv[r]);
+                    cfma(b1[r], u1[q], xv[r]);
+                }
             }
         }
     }
