@@ -120,3 +120,33 @@ def test_struct_layout_matches_header(B, tmp_path):
         cls = structs[sname]
         got = ctypes.sizeof(cls) if what == "size" else getattr(cls, what).offset
         assert got == int(val), (sname, what, got, val)
+
+
+def test_new_entry_points_check_state_and_arguments(B):
+    """Adjoint, gradient, autotuning and batch calls refuse a context that is not
+    assembled, and bad options, before touching the GPU."""
+    v, t = W.icosphere(1)
+    h = B.bem_create()
+    try:
+        B.bem_set_mesh(h, v, t)
+        for call in (lambda: B.bem_matvec_adjoint(h, 0, 0, 1, B.BEM_C64),
+                     lambda: B.bem_solve_adjoint(h, 0, 0, 1),
+                     lambda: B.bem_grad_eps(h, 0, 0),
+                     lambda: B.bem_grad_weights(h, 0, [1.0]),
+                     lambda: B.bem_autotune(h, B.BEM_C64),
+                     lambda: B.bem_absorbed_power_gradient(h, 0, 0, 1)):
+            with pytest.raises(B.BemError) as ei:
+                call()
+            assert ei.value.status == B.BEM_ESTATE
+        with pytest.raises(B.BemError) as ei:
+            B.bem_batch_create([h], [0], [0], [1], B.BEM_C64)
+        assert ei.value.status == B.BEM_EINVAL
+    finally:
+        B.bem_destroy(h)
+    opt = B.bem_default_options()
+    assert opt.solver == B.BEM_SOLVER_GMRES
+    for field, value in (("solver", 4), ("solver", -1), ("precision", 8)):
+        o = B.bem_default_options()
+        setattr(o, field, value)
+        with pytest.raises(B.BemError):
+            B.bem_create(o)
