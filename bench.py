@@ -176,7 +176,7 @@ def kernel_traffic(name):
         return None
     for line in open(p):
         parts = line.split()
-        if len(parts) >= 3 and parts[0] == name and parts[2] == digest:
+        if len(parts) >= 4 and parts[0] == name and parts[2] == digest and parts[3] == workload_name(LEVEL):
             return float(parts[1])
     return None
 
