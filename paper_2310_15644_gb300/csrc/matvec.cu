@@ -327,7 +327,7 @@ __device__ __forceinline__ void vhx_unit_rhs(const FarRec* __restrict__ far, int
 
 // one CTA per unit; the hardware scheduler balances the (largest-first) units
 template <typename R, typename F, int NR>
-__global__ void __launch_bounds__(VHX_THREADS) k_vhx(const FarRec* __restrict__ far, const int2* __restrict__ units,
+__global__ void __launch_bounds__(VHX_THREADS, (NR == 1 && sizeof(R) == 4 && sizeof(F) == 8) ? 24 : 1) k_vhx(const FarRec* __restrict__ far, const int2* __restrict__ units,
                                                      int nunits, const F* __restrict__ arena,
                                                      const cx<R>* __restrict__ xp, cx<R>* __restrict__ t, int ne) {
     if ((int)blockIdx.x < nunits) {
@@ -635,7 +635,7 @@ __device__ __forceinline__ void far_piece(const PieceDesc& d, int i, const FS* _
 // sum does not depend on which CTA finishes last.
 // y is in the caller's layout: right-hand side r at y + r * 2ne.
 template <typename R, typename NS, typename FS, int NR, bool ADJ>
-__global__ void __launch_bounds__(ROW_THREADS) k_rows(MatvecPlan p, const NS* __restrict__ near,
+__global__ void __launch_bounds__(ROW_THREADS, (NR == 1 && sizeof(R) == 4) ? 16 : 1) k_rows(MatvecPlan p, const NS* __restrict__ near,
                                                       const FS* __restrict__ arena,
                                                       const cx<R>* __restrict__ xp, const cx<R>* __restrict__ t,
                                                       cx<R>* __restrict__ y, cx<R>* __restrict__ ypart,
