@@ -26,7 +26,8 @@ Modules:
   operators   -- dense T_k, K_k, PMCHWT matrix, on-the-fly rows
   excitation  -- plane-wave right-hand sides
   power       -- absorbed / extinguished / scattered power
-  mie         -- Mie series of a homogeneous sphere (closed-form pin)
+  mie         -- Mie series of a homogeneous and of a coated sphere (closed-form pins)
+  multiregion -- layered bodies: PMCHWT written region by region
   tree        -- cluster tree and block partition
   aca         -- partial-pivot adaptive cross approximation
   debye       -- double-Debye permittivity (Eq. 5)

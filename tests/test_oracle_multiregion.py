@@ -1,0 +1,140 @@
+"""Pins of the multi-region oracle: the coated-sphere series and the layered PMCHWT system.
+
+The coated-sphere coefficients (interface conditions solved order by order)
+are pinned by three limits that reduce them to the homogeneous-sphere series:
+equal indices, a vanishing core and a vanishing coating (the last one checks
+the inner interface with two different indices), and by energy conservation
+of a lossless coated sphere.  The dense layered PMCHWT solve is then pinned to
+the coated-sphere series (k0 a = 2, shell eps 3.2 - 1.9j, core eps 2.5 - 1.2j,
+core radius a / 2): the error must fall as both icospheres are refined.  An
+inner interface between two copies of one medium must be transparent (the
+homogeneous-sphere series), and one surface between regions 0 and 1 must
+give the single-body matrix.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mie
+from oracle import multiregion as MR
+from oracle import operators as O
+from oracle import power as P
+from oracle import rwg as R
+
+K0 = 2.0
+EPS_SHELL = 3.2 - 1.9j
+EPS_CORE = 2.5 - 1.2j
+
+
+def _two_layer(level_outer, level_inner, radius_inner=0.5):
+    (vo, to), (vi, ti) = W.concentric_spheres(level_outer, 1.0, level_inner, radius_inner)
+    v, t, s = MR.union_mesh([(vo, to), (vi, ti)])
+    g = R.build(v, t)
+    regions = np.where(s[:, None] == 0, np.array([0, 1]), np.array([1, 2]))
+    return g, regions
+
+
+def _efficiencies(g, regions, eps_core, k0=K0):
+    Z = MR.pmchwt_regions(g, regions, k0, [1.0, EPS_SHELL, eps_core])
+    b = MR.rhs_planewave(g, regions, k0, [0.0, 0.0, 1.0], [1.0, 0.0, 0.0])
+    x = np.linalg.solve(Z, b)
+    return P.efficiencies(g, k0, MR.exterior_currents(g, regions, x), b, radius=1.0)
+
+
+def test_coated_equal_indices_is_homogeneous():
+    m = np.sqrt(np.conj(EPS_SHELL))
+    n, a, b = mie.coefficients(2.0, m)
+    _, a2, b2 = mie.coated_coefficients(1.0, 2.0, m, m, nmax=len(n))
+    assert np.abs(a - a2).max() < 1e-13
+    assert np.abs(b - b2).max() < 1e-13
+
+
+def test_coated_vanishing_core_and_vanishing_coating():
+    m_core = np.sqrt(np.conj(EPS_CORE))
+    m_shell = np.sqrt(np.conj(EPS_SHELL))
+    n, a_s, b_s = mie.coefficients(2.0, m_shell)
+    _, a0, b0 = mie.coated_coefficients(1e-4, 2.0, m_core, m_shell, nmax=len(n))
+    assert np.abs(a0 - a_s).max() < 1e-10 and np.abs(b0 - b_s).max() < 1e-10
+    # a coating of thickness d -> 0 leaves the core-material sphere, with an O(d) error
+    _, a_c, b_c = mie.coefficients(2.0, m_core)
+    errs = []
+    for d in (1e-3, 1e-5):
+        _, a1, b1 = mie.coated_coefficients(2.0 - d, 2.0, m_core, m_shell, nmax=len(n))
+        errs.append(max(np.abs(a1 - a_c).max(), np.abs(b1 - b_c).max()))
+    assert errs[0] < 1e-3 and errs[1] < 1e-5
+    assert 50 < errs[0] / errs[1] < 200
+
+
+def test_coated_lossless_conserves_energy():
+    q = mie.coated_efficiencies(1.0, 3.0, 1.7, 1.3)
+    assert q["ext"] > 0.5
+    assert abs(q["ext"] - q["sca"]) < 1e-12 * q["ext"]
+
+
+def test_one_surface_is_the_single_body_matrix():
+    v, t = W.icosphere(1)
+    g = R.build(v, t)
+    regions = np.tile([0, 1], (g.nt, 1))
+    Z = MR.pmchwt_regions(g, regions, K0, [1.0, EPS_SHELL])
+    Z1 = O.pmchwt_matrix(g, K0, EPS_SHELL)
+    assert np.abs(Z - Z1).max() < 1e-13 * np.abs(Z1).max()
+
+
+def test_region_boundaries_and_reciprocity():
+    g, regions = _two_layer(1, 0)
+    ne_outer = 30 * 4
+    # region 0 sees the outer surface, region 2 the inner one, region 1 both (inner ones negated)
+    for r, lo, hi in ((0, 0, ne_outer), (2, ne_outer, g.ne)):
+        sub, edges, sigma = MR.region_boundary(g, regions, r)
+        assert np.array_equal(edges, np.arange(lo, hi)) and np.all(sigma == 1.0)
+    sub, edges, sigma = MR.region_boundary(g, regions, 1)
+    assert np.array_equal(edges, np.arange(g.ne))
+    assert np.all(sigma[:ne_outer] == -1.0) and np.all(sigma[ne_outer:] == 1.0)
+    assert np.array_equal(sub.edges, g.edges)
+    # Z^T = J Z J with J = diag(I, -I), each region's T and K being symmetric: exactly
+    # for the regular pairs between the surfaces (an inner sphere of radius 0.3 has
+    # no near-singular pair with the outer one), to the 7-point outer rule's error
+    # for the singular pairs on each surface
+    g, regions = _two_layer(2, 0, radius_inner=0.3)
+    Z = MR.pmchwt_regions(g, regions, K0, [1.0, EPS_SHELL, EPS_CORE])
+    J = np.concatenate([np.ones(g.ne), -np.ones(g.ne)])
+    D = Z.T - J[:, None] * Z * J[None, :]
+    na = 30 * 16
+    ia = np.r_[0:na, g.ne:g.ne + na]
+    ib = np.r_[na:g.ne, g.ne + na:2 * g.ne]
+    assert np.abs(D[np.ix_(ia, ib)]).max() < 1e-13 * np.abs(Z).max()
+    assert np.linalg.norm(D) < 5e-3 * np.linalg.norm(Z)
+
+
+def test_exterior_normals_must_point_out():
+    g, regions = _two_layer(1, 0)
+    flipped = regions[:, ::-1].copy()
+    with pytest.raises(ValueError):
+        MR.exterior_mask(g, flipped)
+
+
+@pytest.fixture(scope="module")
+def coated_results():
+    ref = mie.coated_efficiencies_eps(K0, 0.5, 1.0, EPS_CORE, EPS_SHELL)
+    out = {}
+    for lo, li in ((2, 1), (3, 2)):
+        g, regions = _two_layer(lo, li)
+        q = _efficiencies(g, regions, EPS_CORE)
+        out[(lo, li)] = {k: abs(q[k] - ref[k]) / ref[k] for k in ("ext", "abs", "sca")}
+    return out
+
+
+def test_layered_solve_converges_to_coated_series(coated_results):
+    coarse, fine = coated_results[(2, 1)], coated_results[(3, 2)]
+    for q in ("ext", "abs", "sca"):
+        assert fine[q] < coarse[q], (q, coarse, fine)
+        assert coarse[q] < 0.06, (q, coarse)
+        assert fine[q] < 0.02, (q, fine)
+
+
+def test_interface_between_equal_media_is_transparent():
+    g, regions = _two_layer(2, 1)
+    q = _efficiencies(g, regions, EPS_SHELL)
+    ref = mie.efficiencies_eps(K0, EPS_SHELL)
+    for k in ("ext", "abs", "sca"):
+        assert abs(q[k] - ref[k]) / ref[k] < 0.06, (k, q, ref)
