@@ -83,10 +83,11 @@ def test_one_surface_is_the_single_body_matrix():
 def test_region_boundaries_and_reciprocity():
     g, regions = _two_layer(1, 0)
     ne_outer = 30 * 4
-    # region 0 sees the outer surface, region 2 the inner one, region 1 both (inner ones negated)
-    for r, lo, hi in ((0, 0, ne_outer), (2, ne_outer, g.ne)):
+    # region 0 sees the outer surface from its normal side, region 2 the inner one from
+    # behind, region 1 both (the outer one from behind)
+    for r, lo, hi, sg in ((0, 0, ne_outer, 1.0), (2, ne_outer, g.ne, -1.0)):
         sub, edges, sigma = MR.region_boundary(g, regions, r)
-        assert np.array_equal(edges, np.arange(lo, hi)) and np.all(sigma == 1.0)
+        assert np.array_equal(edges, np.arange(lo, hi)) and np.all(sigma == sg)
     sub, edges, sigma = MR.region_boundary(g, regions, 1)
     assert np.array_equal(edges, np.arange(g.ne))
     assert np.all(sigma[:ne_outer] == -1.0) and np.all(sigma[ne_outer:] == 1.0)
