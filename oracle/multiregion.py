@@ -129,10 +129,55 @@ def exterior_mask(rwg: RWG, tri_regions):
 def rhs_planewave(rwg: RWG, tri_regions, k0: float, khat, e0):
     """Right-hand side of a plane wave incident in region 0."""
     b = excitation.rhs_planewave(rwg, k0, khat, e0)
-    return b * exterior_mask(rwg, tri_regions)
+    m = exterior_mask(rwg, tri_regions)
+    return b * (m if np.ndim(b) == 1 else m[:, None])
 
 
 def exterior_currents(rwg: RWG, tri_regions, x):
     """The currents of region 0's boundary (other surfaces zeroed)."""
     m = exterior_mask(rwg, tri_regions)
     return x * (m if np.ndim(x) == 1 else m[:, None])
+
+
+def pmchwt_regions_rows_apply(rwg: RWG, tri_regions, k0: float, eps_r, x, rows, mu_r=None):
+    """Entries ``rows`` (indices into the 2 ne unknowns) of Z @ x, Z never stored.
+
+    Each region whose boundary holds a row's edge contributes sigma times the
+    row of its single-medium operator (``operators.operator_rows`` on the
+    region's boundary mesh) applied to that boundary's signed currents.
+    """
+    ne = rwg.ne
+    rows = np.asarray(rows, dtype=np.int64)
+    out = np.zeros(len(rows), dtype=np.complex128)
+    for r, (k, eta_r) in enumerate(region_media(k0, eps_r, mu_r)):
+        sub, edges, sigma = region_boundary(rwg, tri_regions, r)
+        where = {int(e): i for i, e in enumerate(edges)}
+        hit = [(j, where[int(row % ne)]) for j, row in enumerate(rows) if int(row % ne) in where]
+        if not hit:
+            continue
+        T, K = operators.operator_rows(sub, k, [i for _, i in hit])
+        xJ = sigma * x[edges]
+        xM = sigma * x[ne + edges]
+        for n, (j, i) in enumerate(hit):
+            if rows[j] < ne:
+                v = eta_r * (T[n] @ xJ) + K[n] @ xM
+            else:
+                v = -(K[n] @ xJ) + (T[n] @ xM) / eta_r
+            out[j] += sigma[i] * v
+    return out
+
+
+def absorbed_and_weight_gradient(rwg: RWG, tri_regions, Z, Bm, w):
+    """(P(w), dP/d conj(w)) of the power absorbed by a layered body, b = Bm w.
+
+    P = xe^H H xe with xe the currents of region 0's boundary (the power that
+    leaves region 0), x = Z^-1 b: a Hermitian form w^H Q w in the weights,
+    Q = (E Z^-1 Bm)^H H (E Z^-1 Bm), E the mask of ``exterior_mask``; its
+    gradient with respect to conj(w) is Q w (dense LU, no adjoint system).
+    """
+    from . import gradient
+
+    Y = np.linalg.solve(Z, Bm) * exterior_mask(rwg, tri_regions)[:, None]
+    Q = Y.conj().T @ (gradient.hermitian_form(rwg) @ Y)
+    w = np.asarray(w, dtype=np.complex128)
+    return float(np.real(np.vdot(w, Q @ w))), Q @ w

@@ -139,3 +139,34 @@ def test_interface_between_equal_media_is_transparent():
     ref = mie.efficiencies_eps(K0, EPS_SHELL)
     for k in ("ext", "abs", "sca"):
         assert abs(q[k] - ref[k]) / ref[k] < 0.06, (k, q, ref)
+
+
+def test_rows_on_the_fly_equal_dense():
+    g, regions = _two_layer(2, 1)
+    Z = MR.pmchwt_regions(g, regions, K0, [1.0, EPS_SHELL, EPS_CORE])
+    x = W.complex_normal(2 * g.ne, seed=4)
+    rows = np.random.default_rng(5).choice(2 * g.ne, 24, replace=False)
+    got = MR.pmchwt_regions_rows_apply(g, regions, K0, [1.0, EPS_SHELL, EPS_CORE], x, rows)
+    ref = Z[rows] @ x
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_layered_weight_gradient_by_finite_differences():
+    g, regions = _two_layer(1, 0)
+    Z = MR.pmchwt_regions(g, regions, K0, [1.0, EPS_SHELL, EPS_CORE])
+    kh, e0 = W.plane_wave_batch(3, seed=2)
+    Bm = MR.rhs_planewave(g, regions, K0, kh, e0)
+    w = W.complex_normal(3, seed=6)
+    p, grad = MR.absorbed_and_weight_gradient(g, regions, Z, Bm, w)
+    xe = MR.exterior_currents(g, regions, np.linalg.solve(Z, Bm @ w))
+    assert abs(p - P.absorbed(g, xe)) < 1e-12 * abs(p)
+    h = 1e-6
+    for i in range(3):
+        d = np.zeros(3, dtype=np.complex128)
+        d[i] = h
+        fd_re = (MR.absorbed_and_weight_gradient(g, regions, Z, Bm, w + d)[0]
+                 - MR.absorbed_and_weight_gradient(g, regions, Z, Bm, w - d)[0]) / (2 * h)
+        fd_im = (MR.absorbed_and_weight_gradient(g, regions, Z, Bm, w + 1j * d)[0]
+                 - MR.absorbed_and_weight_gradient(g, regions, Z, Bm, w - 1j * d)[0]) / (2 * h)
+        # dP/d conj(w) = (dP/d Re w + j dP/d Im w) / 2
+        assert abs(0.5 * (fd_re + 1j * fd_im) - grad[i]) < 1e-6 * np.abs(grad).max()
