@@ -35,11 +35,8 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "coated_sphere_or
 
 
 def mesh():
-    """Union mesh and per-triangle (region on the normal side, region behind)."""
-    (vo, to), (vi, ti) = W.concentric_spheres(LEVELS[0], RADII[0], LEVELS[1], RADII[1])
-    v, t, s = multiregion.union_mesh([(vo, to), (vi, ti)])
-    regions = np.where(s[:, None] == 0, np.array([0, 1]), np.array([1, 2]))
-    return v, t, regions
+    """Both surfaces in one mesh and per-triangle (region on the normal side, region behind)."""
+    return W.coated_sphere(LEVELS[0], RADII[0], LEVELS[1], RADII[1])
 
 
 def main():

@@ -170,3 +170,26 @@ def test_layered_weight_gradient_by_finite_differences():
                  - MR.absorbed_and_weight_gradient(g, regions, Z, Bm, w - 1j * d)[0]) / (2 * h)
         # dP/d conj(w) = (dP/d Re w + j dP/d Im w) / 2
         assert abs(0.5 * (fd_re + 1j * fd_im) - grad[i]) < 1e-6 * np.abs(grad).max()
+
+
+def test_coated_sphere_workload_is_the_union_of_its_surfaces():
+    v, t, regions = W.coated_sphere(2, 1.0, 1, 0.5)
+    (vo, to), (vi, ti) = W.concentric_spheres(2, 1.0, 1, 0.5)
+    v2, t2, s2 = MR.union_mesh([(vo, to), (vi, ti)])
+    assert np.array_equal(v, v2) and np.array_equal(t, t2)
+    assert np.array_equal(regions, np.where(s2[:, None] == 0, np.array([0, 1]), np.array([1, 2])))
+
+
+def test_coated_sphere_golden_against_series():
+    """The stored dense solution of the 19,200-unknown coated sphere (k0 a = 6) is
+    within its discretisation error of the coated-sphere series."""
+    import os
+
+    d = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "coated_sphere_oracle.npz"))
+    q = mie.coated_efficiencies_eps(float(d["k0"]), float(d["radii"][1]), float(d["radii"][0]),
+                                    complex(d["eps"][2]), complex(d["eps"][1]))
+    assert np.allclose(d["mie"], [q["ext"], q["abs"], q["sca"]], rtol=1e-12)
+    a2 = np.pi * float(d["radii"][0]) ** 2
+    for key, ref in (("p_ext", q["ext"]), ("p_abs", q["abs"]), ("p_sca", q["sca"])):
+        assert abs(float(d[key]) / a2 - ref) / ref < 0.01, key
+    assert d["x"].shape == (19200,)

@@ -24,6 +24,7 @@ __all__ = [
     "icosphere",
     "geodesic_sphere",
     "concentric_spheres",
+    "coated_sphere",
     "box_mesh",
     "fibonacci_directions",
     "plane_wave_batch",
@@ -156,6 +157,21 @@ def geodesic_sphere(freq: int, radius: float = 1.0, center=(0.0, 0.0, 0.0)):
 def concentric_spheres(level_outer: int, radius_outer: float, level_inner: int, radius_inner: float):
     """Two nested icospheres; the inner one is returned as a separate mesh."""
     return icosphere(level_outer, radius_outer), icosphere(level_inner, radius_inner)
+
+
+def coated_sphere(level_outer: int, radius_outer: float, level_inner: int, radius_inner: float):
+    """A coated sphere as one mesh of two surfaces, with the regions each triangle separates.
+
+    Returns (verts, tris, tri_regions): the outer icosphere's vertices and
+    triangles first, then the inner one's (indices shifted), and tri_regions
+    (nt, 2) int32 = (region on the normal side, region behind): (0, 1) on the
+    outer surface (exterior / coating), (1, 2) on the inner one (coating / core).
+    """
+    (vo, to), (vi, ti) = concentric_spheres(level_outer, radius_outer, level_inner, radius_inner)
+    verts = np.concatenate([vo, vi])
+    tris = np.concatenate([to, ti + len(vo)]).astype(np.int32)
+    regions = np.concatenate([np.tile([0, 1], (len(to), 1)), np.tile([1, 2], (len(ti), 1))]).astype(np.int32)
+    return verts, tris, regions
 
 
 def box_mesh(lx: float, ly: float, lz: float, nx: int, ny: int, nz: int):
