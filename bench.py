@@ -22,7 +22,12 @@ Reported beside the headline value:
                 currents and absorbed power density against the stored oracle
                 solution;
   multi_mesh    16 spheres of uneven size: one product each per step, as separate
-                calls, as one CUDA-graph launch, and after autotuning.
+                calls, as one CUDA-graph launch, and after autotuning;
+  layered       a coated lossy sphere (two surfaces, three regions, 19,200
+                unknowns): product and adjoint product of the region-by-region
+                operator, a solve against the stored dense oracle solution and the
+                coated-sphere series, and the absorbed-power gradient with respect
+                to the weights of 64 plane waves.
 `--impl reference` times the oracle alone (the reference arm).
 """
 from __future__ import annotations
@@ -414,6 +419,8 @@ def run_native(args, rank, world, dist):
             out["large"] = run_large(args, dev, stream, B, W, peak, not args.no_cpu_baseline)
         if not args.no_multi:
             out["multi_mesh"] = run_multi_mesh(args, dev, stream, B, W)
+        if not args.no_layered:
+            out["layered"] = run_layered(args, dev, stream, B, W)
     return out
 
 
@@ -554,6 +561,101 @@ def run_large(args, dev, stream, B, W, peak, with_oracle):
 
 
 # ---------------------------------------------------------------------------
+# layered body: the coated sphere of the gradient workload
+# ---------------------------------------------------------------------------
+COATED = (4, 1.0, 3, 0.5)          # outer icosphere level and radius, inner level and radius
+COATED_K0 = 6.0
+COATED_EPS = [1.0, 3.2 - 1.9j, 2.5 - 1.2j]   # exterior (ignored), coating, core
+
+
+def run_layered(args, dev, stream, B, W):
+    """Coated lossy sphere (5,120 + 1,280 triangles, 19,200 unknowns, k0 a = 6): the
+    product of the region-by-region operator (three single-medium operators), its
+    adjoint, a mixed-precision solve against the stored dense oracle solution and
+    the coated-sphere series, and the gradient of the absorbed power with respect
+    to the weights of 64 plane waves (w ~ CN(0, 1/64), seed 2)."""
+    import torch
+
+    sp = stream.cuda_stream
+    v, t, regions = W.coated_sphere(*COATED)
+    opt = B.bem_default_options()
+    opt.precision = B.BEM_PREC_C64
+    opt.leaf_size, opt.eta, opt.aca_tol = LEAF, ETA, ACA_TOL
+    opt.tol, opt.maxit = 1e-6, 4000
+    h = B.bem_create(opt)
+    B.bem_set_mesh(h, v, t)
+    B.bem_set_regions(h, COATED_K0, COATED_EPS, regions)
+    t0 = time.perf_counter()
+    B.bem_assemble(h, sp)
+    torch.cuda.synchronize(dev)
+    asm = time.perf_counter() - t0
+    st = B.bem_stats_get(h)
+    n = B.bem_num_unknowns(h)
+    out = {"workload": "coated-sphere-ico4r1-ico3r0.5-6400tri-19200unk-k0a6-shell3.2-1.9j-core2.5-1.2j-"
+                       "leaf64-eta2-aca1e-4",
+           "unknowns": n, "regions": 3, "assembly_ms": round(asm * 1e3, 1),
+           "bytes_per_product": st["matvec_bytes_c64"], "max_rank": st["max_rank"]}
+    x = torch.from_numpy(W.complex_normal(n, seed=0).astype(np.complex64)).to(dev)
+    y = torch.empty_like(x)
+    K = max(20, args.steps // 10)
+    for adj in (False, True):
+        f = B.bem_matvec_adjoint if adj else B.bem_matvec
+        for _ in range(3):
+            f(h, x.data_ptr(), y.data_ptr(), 1, B.BEM_C64, sp)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            f(h, x.data_ptr(), y.data_ptr(), 1, B.BEM_C64, sp)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / K
+        out["adjoint_product" if adj else "product"] = {
+            "ms": round(ms, 4), "matvecs_per_s": round(1e3 / ms, 1),
+            "hbm_gbps_algorithmic": round(st["matvec_bytes_c64"] / (ms * 1e-3) / 1e9, 1), "steps": K}
+    gold = os.path.join(ROOT, "tests", "golden", "coated_sphere_oracle.npz")
+    if os.path.exists(gold):
+        d = np.load(gold)
+        b = torch.empty(n, dtype=torch.complex128, device=dev)
+        B.bem_rhs_planewave(h, d["khat"].tolist(), d["e0"].tolist(), b.data_ptr(), B.BEM_C128, sp)
+        xs = torch.zeros_like(b)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        it, relres, status = B.bem_solve(h, b.data_ptr(), xs.data_ptr(), 1, sp, raise_on_noconv=False)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        pa, pe, ps = B.bem_power(h, xs.data_ptr(), b.data_ptr(), 1, sp)
+        xh = xs.cpu().numpy()
+        ne = n // 2
+        relv = lambda a, c: float(np.linalg.norm(a - c) / np.linalg.norm(c))  # noqa: E731
+        area = math.pi * COATED[1] ** 2
+        q = {"ext": pe[0] / area, "abs": pa[0] / area, "sca": ps[0] / area}
+        series = dict(zip(("ext", "abs", "sca"), d["mie"].tolist()))
+        oracle = {"ext": float(d["p_ext"]) / area, "abs": float(d["p_abs"]) / area, "sca": float(d["p_sca"]) / area}
+        out["solve"] = {"form": "complex64 GMRES(50) to 1e-6, ACA 1e-4", "seconds": round(dt, 3), "iterations": it,
+                        "relative_residual": float(relres[0]), "converged": status == 0,
+                        "err_J_vs_dense_oracle": relv(xh[:ne], d["x"][:ne]),
+                        "err_M_vs_dense_oracle": relv(xh[ne:], d["x"][ne:]),
+                        "Q": {k: round(q[k], 6) for k in q},
+                        "Q_dense_oracle": {k: round(oracle[k], 6) for k in oracle},
+                        "Q_coated_sphere_series": {k: round(series[k], 6) for k in series}}
+    kh, e0 = W.plane_wave_batch(64, seed=0)
+    bm = torch.empty(64, n, dtype=torch.complex128, device=dev)
+    B.bem_rhs_planewave(h, kh, e0, bm.data_ptr(), B.BEM_C128, sp)
+    w = W.complex_normal(64, seed=2) / 8.0
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    p, grad, itg = B.bem_grad_weights(h, bm.data_ptr(), w, stream=sp)
+    torch.cuda.synchronize(dev)
+    out["weight_gradient"] = {"plane_waves": 64, "seconds": round(time.perf_counter() - t0, 3),
+                              "iterations_forward_plus_adjoint": itg, "p_abs": p,
+                              "grad_norm": float(np.linalg.norm(grad))}
+    B.bem_destroy(h)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # many meshes of uneven size in one graph launch
 # ---------------------------------------------------------------------------
 def run_multi_mesh(args, dev, stream, B, W, count=16):
@@ -665,6 +767,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")
     ap.add_argument("--no-large", action="store_true", help="skip the 602,208-unknown slab")
     ap.add_argument("--no-multi", action="store_true", help="skip the 16-mesh graph batch")
+    ap.add_argument("--no-layered", action="store_true", help="skip the coated (two-region) sphere")
     ap.add_argument("--level", type=int, default=5,
                     help="icosphere level (5 = the 61440-unknown workload; smaller levels for profiling captures)")
     args = ap.parse_args()

@@ -176,6 +176,52 @@ bem_status bem_set_mesh(bem_ctx* ctx, const double* verts, int64_t nv, const int
  * Invalidates any assembled operator. */
 bem_status bem_set_media(bem_ctx* ctx, double k0, bem_c128 eps_r, bem_c128 mu_r);
 
+/* Layered bodies: several closed surfaces, each between two homogeneous regions
+ * (a coated sphere, a body with inclusions).  The two rows of Eq. 7 hold on every
+ * surface, with the field of each region radiated by the currents on that
+ * region's own boundary; written region by region the operator is
+ *
+ *     Z = sum_r Q_r^T Z_r Q_r,   Z_r = [[ eta_r T_r , K_r ], [ -K_r , T_r / eta_r ]],
+ *
+ * Z_r the single-medium operator of region r (k_r = k0 sqrt(eps_r mu_r),
+ * eta_r = sqrt(mu_r / eps_r); region 0: k0, 1) between the surfaces of its
+ * boundary, Q_r selecting those surfaces' unknowns with the sign +1 where region
+ * r lies on the normal side and -1 behind.  One surface between regions 0 and 1
+ * gives the single-body operator above.  No paper counterpart (the paper treats
+ * one homogeneous body).
+ *
+ * The mesh of bem_set_mesh holds every surface; the unknowns are as for one body
+ * (x = [eta0 J ; M] over all edges, J and M taken on each surface's normal side).
+ * tri_regions: host, nt x 2 int32, for each triangle the region its normal points
+ * into and the region behind it: two different values in [0, n_regions); the two
+ * triangles of every edge must carry the same pair; region 0 is the exterior
+ * (free space, wavenumber k0 > 0) and must lie on the normal side of every
+ * surface bounding it; every region needs a boundary.  eps_r, mu_r: host,
+ * n_regions values for e^{+j w t} (Im <= 0, nonzero; entries 0 are ignored).
+ * Else BEM_EINVAL (the context keeps its previous media).  Requires
+ * bem_set_mesh; replaces bem_set_media (calling bem_set_media or bem_set_mesh
+ * afterwards returns to one body).  Invalidates any assembled operator.  Host only.
+ *
+ * On such a context bem_assemble builds one compressed single-medium operator per
+ * region on the region's boundary (same options); bem_matvec, bem_matvec_adjoint,
+ * bem_solve and bem_solve_adjoint apply Z or Z^H through them; bem_rhs_planewave
+ * gives the incident field of region 0 (zero on the surfaces that do not bound
+ * it); bem_power, bem_power_density, bem_absorbed_power_gradient and
+ * bem_grad_weights use the currents of region 0's boundary alone, i.e. the power
+ * absorbed, extinguished and scattered by the whole body; bem_stats_get and
+ * bem_profile_end report sums over the regions' operators.  bem_eval_entries,
+ * bem_partition, bem_autotune, bem_grad_eps and bem_absorbed_power_static return
+ * BEM_ESTATE, bem_batch_create BEM_EINVAL. */
+bem_status bem_set_regions(bem_ctx* ctx, double k0, int n_regions, const bem_c128* eps_r, const bem_c128* mu_r,
+                           const int32_t* tri_regions);
+
+/* Boundary of region r of a layered context (after bem_set_regions; host only).
+ * *n_edges receives the number of RWG edges on it; edges and sign (host, room for
+ * *n_edges values, or NULL) receive, in the order of the region's own operator,
+ * the context's index of each of those edges and +1 / -1 (region r on the normal
+ * side of the edge's surface / behind it).  BEM_ESTATE on a single body. */
+bem_status bem_region_boundary(const bem_ctx* ctx, int r, int64_t* n_edges, int32_t* edges, int8_t* sign);
+
 /* Double-Debye permittivity of Eq. 5 at freq_hz >= 0:
  * params = {eps_inf, eps_s, eps_2, tau1 [s], tau2 [s]}; NULL selects the skin
  * values given after Eq. 5 (3, 60, 3.6, 10 ps, 0.2 ps).  Host only, no context. */

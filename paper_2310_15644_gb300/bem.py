@@ -29,7 +29,8 @@ EXPORTS = [
     "bem_partition", "bem_eval_entries", "bem_matvec", "bem_rhs_planewave", "bem_solve", "bem_power",
     "bem_power_density", "bem_profile_begin", "bem_profile_end", "bem_absorbed_power_static",
     "bem_matvec_adjoint", "bem_solve_adjoint", "bem_absorbed_power_gradient", "bem_grad_weights", "bem_grad_eps",
-    "bem_autotune", "bem_batch_create", "bem_batch_launch", "bem_batch_destroy",
+    "bem_autotune", "bem_batch_create", "bem_batch_launch", "bem_batch_destroy", "bem_set_regions",
+    "bem_region_boundary",
 ]
 KERNEL_NAMES = ["k_gather", "k_vhx", "k_rows"]   # BEM_KERNEL_GATHER, _VHX, _ROWS
 
@@ -84,6 +85,9 @@ def _load():
         "bem_last_error": (ctypes.c_char_p, [ctx]),
         "bem_set_mesh": (ctypes.c_int, [ctx, dp, ctypes.c_int64, i32p, ctypes.c_int64]),
         "bem_set_media": (ctypes.c_int, [ctx, ctypes.c_double, bem_c128, bem_c128]),
+        "bem_set_regions": (ctypes.c_int, [ctx, ctypes.c_double, ctypes.c_int, ctypes.POINTER(bem_c128),
+                                           ctypes.POINTER(bem_c128), i32p]),
+        "bem_region_boundary": (ctypes.c_int, [ctx, ctypes.c_int, i64p, i32p, ctypes.POINTER(ctypes.c_int8)]),
         "bem_debye_eps": (ctypes.c_int, [ctypes.c_double, dp, ctypes.POINTER(bem_c128)]),
         "bem_assemble": (ctypes.c_int, [ctx, vp]),
         "bem_num_edges": (ctypes.c_int64, [ctx]),
@@ -164,6 +168,30 @@ def bem_set_mesh(ctx, verts, tris) -> None:
 def bem_set_media(ctx, k0: float, eps_r: complex, mu_r: complex = 1.0) -> None:
     e, m = complex(eps_r), complex(mu_r)
     _check(ctx, lib.bem_set_media(ctx, float(k0), bem_c128(e.real, e.imag), bem_c128(m.real, m.imag)))
+
+
+def bem_set_regions(ctx, k0: float, eps_r, tri_regions, mu_r=None) -> None:
+    """Layered body: eps_r / mu_r per region (entry 0, the exterior, ignored),
+    tri_regions (nt, 2) = (region on the normal side, region behind) per triangle."""
+    n = len(eps_r)
+    mu_r = [1.0] * n if mu_r is None else mu_r
+    if len(mu_r) != n:
+        raise ValueError("eps_r and mu_r need one value per region")
+    eps = (bem_c128 * n)(*[bem_c128(complex(e).real, complex(e).imag) for e in eps_r])
+    mu = (bem_c128 * n)(*[bem_c128(complex(m).real, complex(m).imag) for m in mu_r])
+    tr = np.ascontiguousarray(tri_regions, dtype=np.int32)
+    _check(ctx, lib.bem_set_regions(ctx, float(k0), n, eps, mu, _np_ptr(tr, ctypes.c_int32)))
+
+
+def bem_region_boundary(ctx, r: int):
+    """(edges, sign) of region r's boundary: the context's edge indices and +1 / -1."""
+    n = ctypes.c_int64()
+    _check(ctx, lib.bem_region_boundary(ctx, int(r), ctypes.byref(n), None, None))
+    edges = np.zeros(n.value, dtype=np.int32)
+    sign = np.zeros(n.value, dtype=np.int8)
+    _check(ctx, lib.bem_region_boundary(ctx, int(r), ctypes.byref(n), _np_ptr(edges, ctypes.c_int32),
+                                        _np_ptr(sign, ctypes.c_int8)))
+    return edges, sign
 
 
 def bem_debye_eps(freq_hz: float, params=None) -> complex:

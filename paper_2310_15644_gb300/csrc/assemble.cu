@@ -243,11 +243,18 @@ __device__ __forceinline__ void pair_terms(const GeomDev& g, int a, int li, int 
     }
 }
 
-// A = T^_0 + eta_r T^_1, B = K_0 + K_1, C = T^_0 + T^_1 / eta_r
+// A = T^_0 + eta_r T^_1, B = K_0 + K_1, C = T^_0 + T^_1 / eta_r; for one region of a
+// layered body (w0 = 0) the k1 medium alone: A = eta_r T^_1, B = K_1, C = T^_1 / eta_r
 template <typename R>
 __device__ __forceinline__ void combine_ops(const GeomDev& g, int ops, cx<R> T0, cx<R> T1, cx<R> K0, cx<R> K1,
                                             cx<R> out[3]) {
     const MediaConst<R>& M = media<R>(g);
+    if (M.w0 == (R)0) {
+        if (ops & 1) out[0] = M.er * T1;
+        if (ops & 2) out[1] = K1;
+        if (ops & 4) out[2] = M.ie * T1;
+        return;
+    }
     if (ops & 1) out[0] = T0 + M.er * T1;
     if (ops & 2) out[1] = K0 + K1;
     if (ops & 4) out[2] = T0 + M.ie * T1;

@@ -130,6 +130,20 @@ struct bem_ctx {
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;   // created once, reused
     size_t ev_used = 0;
+    // one medium only (k1): the operator of one region of a layered body
+    bool single = false;
+    // layered body (bem_set_regions): one single-medium context per region, on the
+    // region's boundary; edges[e] is the edge of this context that boundary edge e is,
+    // sign[e] = +1 if the region lies on the normal side of that edge's surface
+    struct Region {
+        bem_ctx* sub = nullptr;
+        std::vector<int> edges;
+        std::vector<signed char> sign;
+        DevBuf d_edges, d_sign;
+    };
+    std::vector<Region> regions;
+    DevBuf d_rx, d_ry;   // one region's operand and product
+    DevBuf d_xext;       // the currents of the exterior boundary (powers)
 };
 
 // ---------------------------------------------------------------------------
@@ -202,6 +216,7 @@ static GeomDev geom_view(const bem_ctx* c) {
     md.jok1 = cdiv(mk<double>(0.0, 1.0), c->k1);
     md.er = c->eta_r;
     md.ie = cdiv(mk<double>(1.0, 0.0), c->eta_r);
+    md.w0 = c->single ? 0.0 : 1.0;
     g.md = md;
     auto f = [](c128 z) { return mk<float>((float)z.re, (float)z.im); };
     g.mf.k0 = (float)md.k0;
@@ -213,6 +228,7 @@ static GeomDev geom_view(const bem_ctx* c) {
     g.mf.jok1 = f(md.jok1);
     g.mf.er = f(md.er);
     g.mf.ie = f(md.ie);
+    g.mf.w0 = (float)md.w0;
     return g;
 }
 
@@ -254,6 +270,23 @@ static void invalidate(bem_ctx* c) {
     for (int i = 0; i < 2; ++i) release_operator(c->op[i]);
 }
 
+extern "C" void bem_destroy(bem_ctx* c);
+
+// back to one body: drop the regions' contexts
+static void clear_regions(bem_ctx* c) {
+    for (auto& r : c->regions) {
+        bem_destroy(r.sub);
+        dfree(r.d_edges);
+        dfree(r.d_sign);
+    }
+    c->regions.clear();
+    dfree(c->d_rx);
+    dfree(c->d_ry);
+    dfree(c->d_xext);
+}
+
+static bool layered(const bem_ctx* c) { return !c->regions.empty(); }
+
 // ---------------------------------------------------------------------------
 // options, context
 // ---------------------------------------------------------------------------
@@ -293,6 +326,7 @@ extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
 extern "C" void bem_destroy(bem_ctx* c) {
     if (!c) return;
     invalidate(c);
+    clear_regions(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     DevBuf* bufs[] = {&c->d_tv, &c->d_area, &c->d_nrm, &c->d_cen, &c->d_diam, &c->d_tvid, &c->d_tri_edge,
                       &c->d_tri_coef, &c->d_edge_tri, &c->d_edge_loc, &c->d_mid, &c->d_sing_ptr, &c->d_sing_b,
@@ -319,6 +353,7 @@ extern "C" bem_status bem_set_mesh(bem_ctx* c, const double* verts, int64_t nv, 
     if (!verts || !tris || nv <= 0 || nt <= 0) return fail(c, BEM_EINVAL, "empty mesh");
     if (nt > (1 << 29) || nv > (1 << 30)) return fail(c, BEM_EINVAL, "mesh too large");
     invalidate(c);
+    clear_regions(c);
     c->has_mesh = false;
     for (int64_t t = 0; t < nt; ++t)
         for (int i = 0; i < 3; ++i) {
@@ -432,6 +467,7 @@ extern "C" bem_status bem_set_media(bem_ctx* c, double k0, bem_c128 eps_r, bem_c
     if (eps_r.re == 0 && eps_r.im == 0) return fail(c, BEM_EINVAL, "eps_r must be nonzero");
     if (mu_r.re == 0 && mu_r.im == 0) return fail(c, BEM_EINVAL, "mu_r must be nonzero");
     invalidate(c);
+    clear_regions(c);
     c->k0 = k0;
     c->eps = mk<double>(eps_r.re, eps_r.im);
     c->mu = mk<double>(mu_r.re, mu_r.im);
@@ -439,6 +475,134 @@ extern "C" bem_status bem_set_media(bem_ctx* c, double k0, bem_c128 eps_r, bem_c
     c->eta_r = csqrt_principal(cdiv(c->mu, c->eps));
     c->has_media = true;
     c->err.clear();
+    return BEM_OK;
+}
+
+// Layered body: surfaces between homogeneous regions (see bem.h).  Host only: the
+// regions' boundary meshes, their edge maps and signs, and one context per region
+// holding that region's medium alone.
+extern "C" bem_status bem_set_regions(bem_ctx* c, double k0, int nreg, const bem_c128* eps_r, const bem_c128* mu_r,
+                                      const int32_t* tri_regions) {
+    if (!c) return BEM_EINVAL;
+    if (!c->has_mesh) return fail(c, BEM_ESTATE, "bem_set_regions needs bem_set_mesh");
+    if (!(k0 > 0) || !std::isfinite(k0)) return fail(c, BEM_EINVAL, "k0 must be positive");
+    if (nreg < 2 || nreg > 4096 || !eps_r || !mu_r || !tri_regions) return fail(c, BEM_EINVAL, "bad arguments");
+    for (int r = 1; r < nreg; ++r) {
+        if (!std::isfinite(eps_r[r].re) || !std::isfinite(eps_r[r].im) || !std::isfinite(mu_r[r].re) ||
+            !std::isfinite(mu_r[r].im))
+            return fail(c, BEM_EINVAL, "eps_r and mu_r must be finite");
+        if (eps_r[r].im > 0 || mu_r[r].im > 0)
+            return fail(c, BEM_EINVAL, "Im eps_r and Im mu_r must be <= 0 (e^{+jwt})");
+        if ((eps_r[r].re == 0 && eps_r[r].im == 0) || (mu_r[r].re == 0 && mu_r[r].im == 0))
+            return fail(c, BEM_EINVAL, "eps_r and mu_r must be nonzero");
+    }
+    const int64_t nt = c->nt, ne = c->ne;
+    for (int64_t t = 0; t < nt; ++t) {
+        const int o = tri_regions[2 * t], i = tri_regions[2 * t + 1];
+        if (o < 0 || o >= nreg || i < 0 || i >= nreg) return fail(c, BEM_EINVAL, "region index out of range");
+        if (o == i) return fail(c, BEM_EINVAL, "a triangle must separate two different regions");
+        if (i == 0) return fail(c, BEM_EINVAL, "normals of the surfaces bounding region 0 must point into it");
+    }
+    for (int64_t e = 0; e < ne; ++e) {
+        const int a = c->edge_tri[2 * e], b = c->edge_tri[2 * e + 1];
+        if (tri_regions[2 * a] != tri_regions[2 * b] || tri_regions[2 * a + 1] != tri_regions[2 * b + 1])
+            return fail(c, BEM_EINVAL, "the two triangles of an edge bound different regions");
+    }
+    invalidate(c);
+    clear_regions(c);
+    c->has_media = false;
+    c->regions.resize(nreg);
+    std::vector<int> newid(c->nv);
+    for (int r = 0; r < nreg; ++r) {
+        bem_ctx::Region& R = c->regions[r];
+        std::vector<int> tsel;
+        for (int64_t t = 0; t < nt; ++t)
+            if (tri_regions[2 * t] == r || tri_regions[2 * t + 1] == r) tsel.push_back((int)t);
+        if (tsel.empty()) {
+            clear_regions(c);
+            return fail(c, BEM_EINVAL, "region " + std::to_string(r) + " has no boundary");
+        }
+        // vertices of the boundary, renumbered in increasing order (so the boundary's
+        // edges keep the body's relative order and T+ / T- roles)
+        std::fill(newid.begin(), newid.end(), -1);
+        for (int t : tsel)
+            for (int k = 0; k < 3; ++k) newid[c->tris[3 * t + k]] = 0;
+        std::vector<int> vsel;
+        for (int64_t v = 0; v < c->nv; ++v)
+            if (newid[v] == 0) {
+                newid[v] = (int)vsel.size();
+                vsel.push_back((int)v);
+            }
+        std::vector<double> sv(3 * vsel.size());
+        for (size_t v = 0; v < vsel.size(); ++v)
+            for (int d = 0; d < 3; ++d) sv[3 * v + d] = c->verts[3 * (size_t)vsel[v] + d];
+        std::vector<int32_t> stris(3 * tsel.size());
+        for (size_t t = 0; t < tsel.size(); ++t)
+            for (int k = 0; k < 3; ++k) stris[3 * t + k] = newid[c->tris[3 * (size_t)tsel[t] + k]];
+        bem_status s = bem_create(&c->opt, &R.sub);
+        if (s == BEM_OK) {
+            s = bem_set_mesh(R.sub, sv.data(), (int64_t)vsel.size(), stris.data(), (int64_t)tsel.size());
+            if (s != BEM_OK) c->err = "region " + std::to_string(r) + ": " + R.sub->err;
+        } else {
+            c->err = "region context";
+        }
+        if (s != BEM_OK) {
+            clear_regions(c);
+            return s;
+        }
+        bem_ctx* q = R.sub;
+        // the region's medium alone, in the k1 slot (region 0: free space)
+        q->k0 = k0;
+        q->eps = r == 0 ? mk<double>(1, 0) : mk<double>(eps_r[r].re, eps_r[r].im);
+        q->mu = r == 0 ? mk<double>(1, 0) : mk<double>(mu_r[r].re, mu_r[r].im);
+        q->k1 = k0 * csqrt_principal(q->eps * q->mu);
+        q->eta_r = csqrt_principal(cdiv(q->mu, q->eps));
+        q->single = true;
+        q->has_media = true;
+        // boundary edge -> body edge: the body's edges are sorted by (min, max) vertex
+        R.edges.resize(q->ne);
+        R.sign.resize(q->ne);
+        for (int64_t e = 0; e < q->ne; ++e) {
+            const int lo = vsel[q->edge_v[2 * e]], hi = vsel[q->edge_v[2 * e + 1]];
+            int64_t a = 0, b = ne;
+            while (a < b) {
+                const int64_t m = (a + b) / 2;
+                const int ml = c->edge_v[2 * m], mh = c->edge_v[2 * m + 1];
+                if (ml < lo || (ml == lo && mh < hi))
+                    a = m + 1;
+                else
+                    b = m;
+            }
+            if (a >= ne || c->edge_v[2 * a] != lo || c->edge_v[2 * a + 1] != hi) {
+                clear_regions(c);
+                return fail(c, BEM_EINVAL, "boundary edge not found in the mesh");
+            }
+            R.edges[e] = (int)a;
+            const int tb = tsel[q->edge_tri[2 * e]];
+            R.sign[e] = tri_regions[2 * tb] == r ? 1 : -1;
+        }
+    }
+    c->k0 = k0;
+    c->eps = mk<double>(1, 0);
+    c->mu = mk<double>(1, 0);
+    c->k1 = mk<double>(k0, 0);
+    c->eta_r = mk<double>(1, 0);
+    c->has_media = true;
+    c->err.clear();
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_region_boundary(const bem_ctx* cc, int r, int64_t* n_edges, int32_t* edges, int8_t* sign) {
+    bem_ctx* c = const_cast<bem_ctx*>(cc);
+    if (!c || !n_edges) return BEM_EINVAL;
+    if (!layered(c)) return fail(c, BEM_ESTATE, "not a layered context (bem_set_regions)");
+    if (r < 0 || r >= (int)c->regions.size()) return fail(c, BEM_EINVAL, "region index out of range");
+    const bem_ctx::Region& R = c->regions[r];
+    *n_edges = (int64_t)R.edges.size();
+    for (size_t e = 0; e < R.edges.size(); ++e) {
+        if (edges) edges[e] = R.edges[e];
+        if (sign) sign[e] = R.sign[e];
+    }
     return BEM_OK;
 }
 
@@ -1164,9 +1328,34 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
     return BEM_OK;
 }
 
+// Layered body: the body's geometry (right-hand sides and powers) and one operator
+// per region, each assembled by its own context on the region's boundary.
+static bem_status assemble_layered(bem_ctx* c, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    invalidate(c);
+    for (double& p : c->phase_ms) p = 0.0;
+    bem_status s;
+    if ((s = upload_geometry(c, st)) != BEM_OK) return s;
+    for (size_t r = 0; r < c->regions.size(); ++r) {
+        bem_ctx::Region& R = c->regions[r];
+        if ((s = bem_assemble(R.sub, stream)) != BEM_OK)
+            return fail(c, s, "region " + std::to_string(r) + ": " + R.sub->err);
+        CK(upload(R.d_edges, R.edges, st));
+        CK(upload(R.d_sign, R.sign, st));
+        for (int i = 0; i < BEM_PHASES; ++i) c->phase_ms[i] += R.sub->phase_ms[i];
+    }
+    CK(cudaStreamSynchronize(st));
+    c->assemble_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    c->assembled = true;
+    c->err.clear();
+    return BEM_OK;
+}
+
 extern "C" bem_status bem_assemble(bem_ctx* c, void* stream) {
     if (!c) return BEM_EINVAL;
     if (!c->has_mesh || !c->has_media) return fail(c, BEM_ESTATE, "bem_assemble needs bem_set_mesh and bem_set_media");
+    if (layered(c)) return assemble_layered(c, stream);
     cudaStream_t st = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     invalidate(c);
@@ -1198,6 +1387,38 @@ extern "C" bem_status bem_stats_get(const bem_ctx* cc, bem_stats* out) {
     if (!c || !out) return BEM_EINVAL;
     if (!c->assembled) return fail(c, BEM_ESTATE, "not assembled");
     memset(out, 0, sizeof(*out));
+    if (layered(c)) {
+        // sums over the regions' operators (max_rank: their maximum)
+        for (auto& R : c->regions) {
+            bem_stats q;
+            bem_status s = bem_stats_get(R.sub, &q);
+            if (s != BEM_OK) return fail(c, s, R.sub->err);
+            out->n_clusters += q.n_clusters;
+            out->n_leaves += q.n_leaves;
+            out->n_near += q.n_near;
+            out->n_far += q.n_far;
+            out->n_far_dense += q.n_far_dense;
+            out->n_far_split += q.n_far_split;
+            out->n_far_factored += q.n_far_factored;
+            out->near_entries += q.near_entries;
+            for (int k = 0; k < 3; ++k) {
+                out->factor_entries[k] += q.factor_entries[k];
+                out->kernel_bytes_c64[k] += q.kernel_bytes_c64[k];
+                out->kernel_bytes_c128[k] += q.kernel_bytes_c128[k];
+                out->kernel_bytes_bf16f[k] += q.kernel_bytes_bf16f[k];
+            }
+            out->max_rank = std::max(out->max_rank, q.max_rank);
+            out->singular_pairs += q.singular_pairs;
+            out->matvec_bytes_c64 += q.matvec_bytes_c64;
+            out->matvec_bytes_c128 += q.matvec_bytes_c128;
+            out->matvec_bytes_bf16f += q.matvec_bytes_bf16f;
+        }
+        out->ne = c->ne;
+        out->nt = c->nt;
+        out->assemble_ms = c->assemble_ms;
+        for (int i = 0; i < BEM_PHASES; ++i) out->assemble_phase_ms[i] = c->phase_ms[i];
+        return BEM_OK;
+    }
     out->ne = c->ne;
     out->nt = c->nt;
     out->n_clusters = (int64_t)c->node_lo.size();
@@ -1251,16 +1472,36 @@ extern "C" bem_status bem_partition(const bem_ctx* cc, int64_t* perm, int32_t* n
     bem_ctx* c = const_cast<bem_ctx*>(cc);
     if (!c) return BEM_EINVAL;
     if (!c->assembled) return fail(c, BEM_ESTATE, "not assembled");
+    if (layered(c)) return fail(c, BEM_ESTATE, "bem_partition is not available on a layered context");
     if (perm) memcpy(perm, c->perm.data(), sizeof(int64_t) * c->ne);
     if (nearo) memcpy(nearo, c->near_blocks.data(), sizeof(BlockDesc) * c->near_blocks.size());
     if (faro) memcpy(faro, c->far_blocks.data(), sizeof(BlockDesc) * c->far_blocks.size());
     return BEM_OK;
 }
 
+// operator p (0: complex64, 1: complex128) built (for a layered body: in every region)
+static bool op_built(const bem_ctx* c, int p) {
+    if (layered(c)) {
+        for (const auto& R : c->regions)
+            if (!R.sub->op[p].built) return false;
+        return c->assembled;
+    }
+    return c->op[p].built;
+}
+
+static bool bf16_built(const bem_ctx* c) {
+    if (layered(c)) {
+        for (const auto& R : c->regions)
+            if (!R.sub->op[0].built || !R.sub->op[0].arena_bf16.p) return false;
+        return c->assembled;
+    }
+    return c->op[0].built && c->op[0].arena_bf16.p != nullptr;
+}
+
 static bool dtype_ok(const bem_ctx* c, int dtype) {
-    if (dtype == BEM_C64) return c->op[0].built;
-    if (dtype == BEM_C128) return c->op[1].built;
-    if (dtype == BEM_C64_BF16F) return c->op[0].built && c->op[0].arena_bf16.p != nullptr;
+    if (dtype == BEM_C64) return op_built(c, 0);
+    if (dtype == BEM_C128) return op_built(c, 1);
+    if (dtype == BEM_C64_BF16F) return bf16_built(c);
     return false;
 }
 
@@ -1268,6 +1509,7 @@ extern "C" bem_status bem_eval_entries(bem_ctx* c, const int32_t* rows, const in
                                        int dtype, void* stream) {
     if (!c) return BEM_EINVAL;
     if (!c->assembled) return fail(c, BEM_ESTATE, "bem_eval_entries needs bem_assemble");
+    if (layered(c)) return fail(c, BEM_ESTATE, "bem_eval_entries is not available on a layered context");
     if (count < 0 || (count > 0 && (!rows || !cols || !out))) return fail(c, BEM_EINVAL, "bad arguments");
     if (dtype != BEM_C64 && dtype != BEM_C128) return fail(c, BEM_EINVAL, "dtype");
     GeomDev g = geom_view(c);
@@ -1350,14 +1592,48 @@ static bem_status ensure_adjoint(bem_ctx* c, Operator& o, cudaStream_t st) {
 }
 
 static bem_status ensure_adjoint_for(bem_ctx* c, int dtype, cudaStream_t st) {
+    if (layered(c)) {
+        for (auto& R : c->regions) {
+            bem_status s = ensure_adjoint_for(R.sub, dtype, st);
+            if (s != BEM_OK) return fail(c, s, R.sub->err);
+        }
+        return BEM_OK;
+    }
     if (dtype == BEM_C64 || dtype == DT_C64_IN_FP64) return ensure_adjoint<float>(c, c->op[0], st);
     if (dtype == BEM_C128) return ensure_adjoint<double>(c, c->op[1], st);
     return fail(c, BEM_EINVAL, "the adjoint product exists for BEM_C64 and BEM_C128");
 }
 
+static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int nrhs, cudaStream_t st,
+                              bool record = false, bool adjoint = false);
+
+// Layered body: y = sum_r Q_r^T Z_r Q_r x (adjoint: Z_r^H), Q_r taking region r's
+// boundary unknowns with their signs (the continuity conditions of Eq. 7 written
+// for every surface, each region's field radiated by its own boundary's currents)
+static cudaError_t matvec_layered(bem_ctx* c, int dtype, const void* x, void* y, int nrhs, cudaStream_t st,
+                                  bool record, bool adjoint) {
+    const int es = esize_of(dtype);
+    int64_t nmax = 0;
+    for (const auto& R : c->regions) nmax = std::max<int64_t>(nmax, (int64_t)R.edges.size());
+    const size_t need = (size_t)es * 2 * nmax * nrhs;
+    BEM_CUDA_TRY(ensure(c->d_rx, need));
+    BEM_CUDA_TRY(ensure(c->d_ry, need));
+    BEM_CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)es * 2 * c->ne * nrhs, st));
+    for (auto& R : c->regions) {
+        const int64_t ns = (int64_t)R.edges.size();
+        const int* ed = (const int*)R.d_edges.p;
+        const signed char* sg = (const signed char*)R.d_sign.p;
+        BEM_CUDA_TRY(region_gather(x, es, c->ne, ed, sg, ns, nrhs, c->d_rx.p, st));
+        BEM_CUDA_TRY(matvec_any(R.sub, dtype, c->d_rx.p, c->d_ry.p, nrhs, st, record, adjoint));
+        BEM_CUDA_TRY(region_scatter_add(c->d_ry.p, es, c->ne, ed, sg, ns, nrhs, y, st));
+    }
+    return cudaSuccess;
+}
+
 // y = Z x (adjoint: y = Z^H x, after ensure_adjoint_for)
 static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int nrhs, cudaStream_t st,
-                              bool record = false, bool adjoint = false) {
+                              bool record, bool adjoint) {
+    if (layered(c)) return matvec_layered(c, dtype, x, y, nrhs, st, record, adjoint);
     const cudaEvent_t* ev = nullptr;
     if (record && c->prof) {
         // 6 events per operator pass: chunks of 8, 4, 2, 1 right-hand sides (one pass
@@ -1408,6 +1684,7 @@ static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int
 extern "C" bem_status bem_autotune(bem_ctx* c, int dtype, void* stream, int* chosen, double* ms_best) {
     if (!c) return BEM_EINVAL;
     if (!c->assembled) return fail(c, BEM_ESTATE, "bem_autotune needs bem_assemble");
+    if (layered(c)) return fail(c, BEM_ESTATE, "bem_autotune is not available on a layered context");
     if (dtype != BEM_C64 && dtype != BEM_C128 && dtype != BEM_C64_BF16F) return fail(c, BEM_EINVAL, "dtype");
     if (!dtype_ok(c, dtype)) return fail(c, BEM_EINVAL, "no operator of that precision was assembled");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1485,7 +1762,8 @@ extern "C" bem_status bem_batch_create(bem_ctx* const* ctxs, int n, const void* 
     *out = nullptr;
     for (int i = 0; i < n; ++i) {
         bem_ctx* c = ctxs[i];
-        if (!c || !c->assembled || !dtype_ok(c, dtype) || nrhs[i] < 1 || !x[i] || !y[i]) return BEM_EINVAL;
+        if (!c || !c->assembled || layered(c) || !dtype_ok(c, dtype) || nrhs[i] < 1 || !x[i] || !y[i])
+            return BEM_EINVAL;
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == c) return fail(c, BEM_EINVAL, "a context appears twice in a batch (shared workspaces)");
         if (c->prof) return fail(c, BEM_ESTATE, "bem_batch_create during bem_profile_begin");
@@ -1555,6 +1833,7 @@ extern "C" bem_status bem_profile_begin(bem_ctx* c) {
     if (!c) return BEM_EINVAL;
     c->prof = true;
     c->ev_used = 0;
+    for (auto& R : c->regions) bem_profile_begin(R.sub);  // a layered body times its regions' products
     return BEM_OK;
 }
 
@@ -1563,6 +1842,17 @@ extern "C" bem_status bem_profile_end(bem_ctx* c, double* ms_sum, int64_t* launc
     if (!c->prof) return fail(c, BEM_ESTATE, "bem_profile_end without bem_profile_begin");
     double ms[3] = {0, 0, 0};
     int64_t cnt[3] = {0, 0, 0};
+    for (auto& R : c->regions) {
+        if (!R.sub->prof) continue;
+        double m2[3];
+        int64_t n2[3];
+        bem_status s = bem_profile_end(R.sub, m2, n2);
+        if (s != BEM_OK) return fail(c, s, R.sub->err);
+        for (int k = 0; k < 3; ++k) {
+            ms[k] += m2[k];
+            cnt[k] += n2[k];
+        }
+    }
     for (size_t i = 0; i + 6 <= c->ev_used; i += 6)
         for (int k = 0; k < 3; ++k) {
             CK(cudaEventSynchronize(c->ev_pool[i + 2 * k + 1]));
@@ -1627,6 +1917,18 @@ extern "C" bem_status bem_rhs_planewave(bem_ctx* c, const double* khat, const be
         CK(rhs_planewave<float>(g, kd, ed, nrhs, (c64*)b, st));
     else
         CK(rhs_planewave<double>(g, kd, ed, nrhs, (c128*)b, st));
+    if (layered(c)) {
+        // the incident field lives in region 0: zero on the surfaces that do not bound it
+        const bem_ctx::Region& R = c->regions[0];
+        const int es = dtype == BEM_C64 ? 8 : 16;
+        const int64_t ns = (int64_t)R.edges.size();
+        CK(ensure(c->d_rx, (size_t)es * 2 * ns * nrhs));
+        CK(region_gather(b, es, c->ne, (const int*)R.d_edges.p, (const signed char*)R.d_sign.p, ns, nrhs, c->d_rx.p,
+                         st));
+        CK(cudaMemsetAsync(b, 0, (size_t)es * 2 * c->ne * nrhs, st));
+        CK(region_scatter_add(c->d_rx.p, es, c->ne, (const int*)R.d_edges.p, (const signed char*)R.d_sign.p, ns,
+                              nrhs, b, st));
+    }
     CK(cudaStreamSynchronize(st));
     return BEM_OK;
 }
@@ -1892,12 +2194,11 @@ static bem_status solve_impl(bem_ctx* c, const void* b, void* x, int nrhs, void*
     if (!c->assembled) return fail(c, BEM_ESTATE, "bem_solve needs bem_assemble");
     if (nrhs < 1 || !b || !x) return fail(c, BEM_EINVAL, "bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    // the BF16-factor product has no adjoint form
     // the BF16-factor product has no adjoint form (nor does CGNR run on it)
     const bool bf_ok = !adjoint && c->opt.solver != BEM_SOLVER_CGNR && dtype_ok(c, BEM_C64_BF16F);
-    const int din = bf_ok ? BEM_C64_BF16F : (c->op[0].built ? BEM_C64 : BEM_C128);
+    const int din = bf_ok ? BEM_C64_BF16F : (op_built(c, 0) ? BEM_C64 : BEM_C128);
     const int vin = vec_dtype(din);
-    const bool out128 = c->op[1].built;
+    const bool out128 = op_built(c, 1);
     const int dres = out128 ? BEM_C128 : DT_C64_IN_FP64;
     if (adjoint || c->opt.solver == BEM_SOLVER_CGNR) {
         bem_status s0;
@@ -2015,6 +2316,28 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
     }
 }
 
+// The currents that radiate into region 0: x itself for one body; for a layered
+// body a copy with every surface that does not bound region 0 zeroed (the power
+// leaving region 0 -- absorbed, extinguished, scattered by the whole body --
+// depends on those alone; region 0's boundary signs are all +1)
+static bem_status exterior_view(bem_ctx* c, const void* x, int nrhs, const c128** out, cudaStream_t st) {
+    if (!layered(c)) {
+        *out = (const c128*)x;
+        return BEM_OK;
+    }
+    const bem_ctx::Region& R = c->regions[0];
+    const int64_t ns = (int64_t)R.edges.size();
+    const size_t n = sizeof(c128) * 2 * c->ne * nrhs;
+    CK(ensure(c->d_xext, n));
+    CK(ensure(c->d_rx, sizeof(c128) * 2 * ns * nrhs));
+    CK(cudaMemsetAsync(c->d_xext.p, 0, n, st));
+    CK(region_gather(x, 16, c->ne, (const int*)R.d_edges.p, (const signed char*)R.d_sign.p, ns, nrhs, c->d_rx.p, st));
+    CK(region_scatter_add(c->d_rx.p, 16, c->ne, (const int*)R.d_edges.p, (const signed char*)R.d_sign.p, ns, nrhs,
+                          c->d_xext.p, st));
+    *out = (const c128*)c->d_xext.p;
+    return BEM_OK;
+}
+
 extern "C" bem_status bem_power(bem_ctx* c, const void* x, const void* b, int nrhs, double* p_abs, double* p_ext,
                                 double* p_sca, void* stream) {
     if (!c) return BEM_EINVAL;
@@ -2022,6 +2345,9 @@ extern "C" bem_status bem_power(bem_ctx* c, const void* x, const void* b, int nr
     if (nrhs < 1 || !x || (p_ext && !b)) return fail(c, BEM_EINVAL, "bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
     GeomDev g = geom_view(c);
+    const c128* xe;
+    bem_status s0;
+    if ((s0 = exterior_view(c, x, nrhs, &xe, st)) != BEM_OK) return s0;
     const int nta = 64, nph = 128;
     int npa = (int)((c->nt + 255) / 256);
     size_t need = sizeof(double) * (size_t)nrhs * std::max(npa, std::max(NPART, nta * nph));
@@ -2029,12 +2355,12 @@ extern "C" bem_status bem_power(bem_ctx* c, const void* x, const void* b, int nr
     CK(ensure(c->d_red, sizeof(double) * nrhs));
     std::vector<double> host(nrhs);
     if (p_abs) {
-        CK(power_abs(g, (const c128*)x, nrhs, nullptr, (double*)c->d_part.p, npa, st));
+        CK(power_abs(g, xe, nrhs, nullptr, (double*)c->d_part.p, npa, st));
         CK(kv_reduce_real((const double*)c->d_part.p, npa, nrhs, (double*)c->d_red.p, st));
         CK(cudaMemcpyAsync(p_abs, c->d_red.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
     }
     if (p_ext) {
-        CK(dot_real_parts((const c128*)x, (const c128*)b, c->ne, nrhs, (double*)c->d_part.p, NPART, st));
+        CK(dot_real_parts(xe, (const c128*)b, c->ne, nrhs, (double*)c->d_part.p, NPART, st));
         CK(kv_reduce_real((const double*)c->d_part.p, NPART, nrhs, (double*)c->d_red.p, st));
         CK(cudaMemcpyAsync(host.data(), c->d_red.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -2047,7 +2373,7 @@ extern "C" bem_status bem_power(bem_ctx* c, const void* x, const void* b, int nr
             gx.insert(gx.end(), gw.begin(), gw.end());
             CK(upload(c->d_gl, gx, st));
         }
-        CK(power_sca(g, (const c128*)x, nrhs, (double*)c->d_part.p, nta, nph, (const double*)c->d_gl.p,
+        CK(power_sca(g, xe, nrhs, (double*)c->d_part.p, nta, nph, (const double*)c->d_gl.p,
                      (const double*)c->d_gl.p + nta, st));
         CK(kv_reduce_real((const double*)c->d_part.p, nta * nph, nrhs, (double*)c->d_red.p, st));
         CK(cudaMemcpyAsync(host.data(), c->d_red.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
@@ -2062,7 +2388,10 @@ extern "C" bem_status bem_absorbed_power_gradient(bem_ctx* c, const void* x, voi
     if (!c) return BEM_EINVAL;
     if (!c->assembled) return fail(c, BEM_ESTATE, "bem_absorbed_power_gradient needs bem_assemble");
     if (nrhs < 1 || !x || !g || x == g) return fail(c, BEM_EINVAL, "bad arguments");
-    CK(power_abs_grad(geom_view(c), (const c128*)x, nrhs, (c128*)g, (cudaStream_t)stream));
+    const c128* xe;
+    bem_status s0;
+    if ((s0 = exterior_view(c, x, nrhs, &xe, (cudaStream_t)stream)) != BEM_OK) return s0;
+    CK(power_abs_grad(geom_view(c), xe, nrhs, (c128*)g, (cudaStream_t)stream));
     return BEM_OK;
 }
 
@@ -2109,11 +2438,13 @@ extern "C" bem_status bem_grad_weights(bem_ctx* c, const void* bm, int nw, const
     const int npa = (int)((c->nt + 255) / 256);
     CK(dalloc(d_part, sizeof(c128) * std::max<int64_t>(npa, (int64_t)NPART * nw)));
     CK(dalloc(d_red, sizeof(c128) * nw));
-    CK(power_abs(gv, x, 1, nullptr, (double*)d_part.p, npa, st));
+    const c128* xe;
+    if ((s = exterior_view(c, x, 1, &xe, st)) != BEM_OK) return s;
+    CK(power_abs(gv, xe, 1, nullptr, (double*)d_part.p, npa, st));
     CK(kv_reduce_real((const double*)d_part.p, npa, 1, (double*)d_red.p, st));
     CK(cudaMemcpyAsync(p_abs, d_red.p, sizeof(double), cudaMemcpyDeviceToHost, st));
     // g = dP/dconj(x); Z^H lambda = g
-    CK(power_abs_grad(gv, x, 1, (c128*)d_g.p, st));
+    CK(power_abs_grad(gv, xe, 1, (c128*)d_g.p, st));
     CK(cudaMemsetAsync(lam, 0, sizeof(c128) * n, st));
     s = solve_impl(c, d_g.p, lam, 1, stream, &it2, &rr, true);
     if (s != BEM_OK) return s;
@@ -2131,6 +2462,7 @@ extern "C" bem_status bem_grad_weights(bem_ctx* c, const void* bm, int nw, const
 extern "C" bem_status bem_grad_eps(bem_ctx* c, const void* x, const void* lambda, double* dp, void* stream) {
     if (!c) return BEM_EINVAL;
     if (!c->assembled) return fail(c, BEM_ESTATE, "bem_grad_eps needs bem_assemble");
+    if (layered(c)) return fail(c, BEM_ESTATE, "bem_grad_eps is not available on a layered context");
     if (!x || !lambda || !dp) return fail(c, BEM_EINVAL, "bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nsing = c->n_sing;
@@ -2180,7 +2512,10 @@ extern "C" bem_status bem_power_density(bem_ctx* c, const void* x, double* per_t
     GeomDev g = geom_view(c);
     int npa = (int)((c->nt + 255) / 256);
     CK(ensure(c->d_part, sizeof(double) * std::max(npa, NPART)));
-    CK(power_abs(g, (const c128*)x, 1, per_tri, (double*)c->d_part.p, npa, st));
+    const c128* xe;
+    bem_status s0;
+    if ((s0 = exterior_view(c, x, 1, &xe, st)) != BEM_OK) return s0;
+    CK(power_abs(g, xe, 1, per_tri, (double*)c->d_part.p, npa, st));
     return BEM_OK;
 }
 
@@ -2189,4 +2524,5 @@ extern "C" bem_status bem_power_density(bem_ctx* c, const void* x, double* per_t
 // ---------------------------------------------------------------------------
 GeomDev bem_geom_view_for_static(const bem_ctx* c) { return geom_view(c); }
 bool bem_ctx_has_geometry(const bem_ctx* c) { return c->assembled; }
+bool bem_ctx_is_layered(const bem_ctx* c) { return layered(c); }
 void bem_ctx_set_error(bem_ctx* c, const char* msg) { c->err = msg; }

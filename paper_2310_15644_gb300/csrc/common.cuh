@@ -101,6 +101,7 @@ struct MediaConst {
     cx<R> jk0, jk1;          // j k0, j k1
     cx<R> jok0, jok1;        // j / k0, j / k1
     cx<R> er, ie;            // eta_r = eta1 / eta0 and 1 / eta_r
+    R w0;                    // 1: both media (one body); 0: the k1 medium alone (a region of a layered body)
 };
 
 // One triangle for the FP32 quadrature: the centroid split into a high and a low
@@ -311,6 +312,12 @@ cudaError_t kv_sub(const void* b, const void* zx, void* r, int dtype, int64_t n,
 // z = a x + b y + c w (null operands skipped; z may alias them)
 cudaError_t kv_lincomb(void* z, int dtype, c128 a, const void* x, c128 b, const void* y, c128 c, const void* w,
                        int64_t n, cudaStream_t st);
+// layered bodies: xs = sign * x[edges] (both halves [J ; M] of every column) and
+// y[edges] += sign * ys; esize 8 (complex64) or 16 (complex128); edges distinct
+cudaError_t region_gather(const void* x, int esize, int64_t ne, const int* edges, const signed char* sign,
+                          int64_t ns, int nrhs, void* xs, cudaStream_t st);
+cudaError_t region_scatter_add(const void* ys, int esize, int64_t ne, const int* edges, const signed char* sign,
+                               int64_t ns, int nrhs, void* y, cudaStream_t st);
 
 }  // namespace bem
 

@@ -235,4 +235,69 @@ cudaError_t kv_lincomb(void* z, int dtype, c128 a, const void* x, c128 b, const 
     return cudaGetLastError();
 }
 
+// Layered bodies (several closed surfaces between homogeneous regions): the
+// product is a sum over regions of each region's single-medium operator acting
+// on the currents of that region's boundary, taken with the sign +1 where the
+// region lies on the surface's normal side and -1 behind it.  These two kernels
+// move a vector between the body's unknowns and one region's: element e of the
+// region's boundary is edge edges[e] of the body, in both halves [J ; M] of each
+// of the nrhs columns (column-major, 2 ne and 2 ns long).
+template <typename R>
+__global__ void k_region_gather(const cx<R>* __restrict__ x, int64_t ne, const int* __restrict__ edges,
+                                const signed char* __restrict__ sign, int64_t ns, int64_t total,
+                                cx<R>* __restrict__ xs) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t col = i / (2 * ns), rem = i - col * 2 * ns;
+        const int64_t h = rem >= ns ? 1 : 0, e = rem - h * ns;
+        cx<R> v = x[col * 2 * ne + h * ne + edges[e]];
+        if (sign[e] < 0) v = mk<R>(-v.re, -v.im);
+        xs[i] = v;
+    }
+}
+
+template <typename R>
+__global__ void k_region_scatter_add(const cx<R>* __restrict__ ys, int64_t ne, const int* __restrict__ edges,
+                                     const signed char* __restrict__ sign, int64_t ns, int64_t total,
+                                     cx<R>* __restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t col = i / (2 * ns), rem = i - col * 2 * ns;
+        const int64_t h = rem >= ns ? 1 : 0, e = rem - h * ns;
+        cx<R> v = ys[i];
+        if (sign[e] < 0) v = mk<R>(-v.re, -v.im);
+        cx<R>& d = y[col * 2 * ne + h * ne + edges[e]];
+        d = d + v;
+    }
+}
+
+static int region_blocks(int64_t total) {
+    int64_t b = (total + 255) / 256;
+    return (int)(b > 16 * 152 ? 16 * 152 : b);
+}
+
+cudaError_t region_gather(const void* x, int esize, int64_t ne, const int* edges, const signed char* sign,
+                          int64_t ns, int nrhs, void* xs, cudaStream_t st) {
+    const int64_t total = 2 * ns * (int64_t)nrhs;
+    if (total <= 0) return cudaSuccess;
+    if (esize == 16)
+        k_region_gather<double><<<region_blocks(total), 256, 0, st>>>((const c128*)x, ne, edges, sign, ns, total,
+                                                                      (c128*)xs);
+    else
+        k_region_gather<float><<<region_blocks(total), 256, 0, st>>>((const c64*)x, ne, edges, sign, ns, total,
+                                                                     (c64*)xs);
+    return cudaGetLastError();
+}
+
+cudaError_t region_scatter_add(const void* ys, int esize, int64_t ne, const int* edges, const signed char* sign,
+                               int64_t ns, int nrhs, void* y, cudaStream_t st) {
+    const int64_t total = 2 * ns * (int64_t)nrhs;
+    if (total <= 0) return cudaSuccess;
+    if (esize == 16)
+        k_region_scatter_add<double><<<region_blocks(total), 256, 0, st>>>((const c128*)ys, ne, edges, sign, ns,
+                                                                           total, (c128*)y);
+    else
+        k_region_scatter_add<float><<<region_blocks(total), 256, 0, st>>>((const c64*)ys, ne, edges, sign, ns,
+                                                                          total, (c64*)y);
+    return cudaGetLastError();
+}
+
 }  // namespace bem

@@ -49,12 +49,17 @@ cudaError_t partials_address(double** out) {
 // Helper shared with bem_api.cu: the context's device geometry (no allocation).
 GeomDev bem_geom_view_for_static(const bem_ctx* c);
 bool bem_ctx_has_geometry(const bem_ctx* c);
+bool bem_ctx_is_layered(const bem_ctx* c);
 void bem_ctx_set_error(bem_ctx* c, const char* msg);
 
 extern "C" bem_status bem_absorbed_power_static(bem_ctx* c, const void* x, int nrhs, double* p_abs, void* stream) {
     if (!c) return BEM_EINVAL;
     if (!bem_ctx_has_geometry(c)) {
         bem_ctx_set_error(c, "bem_absorbed_power_static needs bem_assemble");
+        return BEM_ESTATE;
+    }
+    if (bem_ctx_is_layered(c)) {
+        bem_ctx_set_error(c, "bem_absorbed_power_static is not available on a layered context");
         return BEM_ESTATE;
     }
     if (nrhs < 1 || !x || !p_abs) {

@@ -150,3 +150,76 @@ def test_new_entry_points_check_state_and_arguments(B):
         setattr(o, field, value)
         with pytest.raises(B.BemError):
             B.bem_create(o)
+
+
+def _layered_mesh(level_outer=2, level_inner=1, radius_inner=0.5):
+    from oracle import multiregion as MR
+
+    (vo, to), (vi, ti) = W.concentric_spheres(level_outer, 1.0, level_inner, radius_inner)
+    v, t, s = MR.union_mesh([(vo, to), (vi, ti)])
+    regions = np.where(s[:, None] == 0, np.array([0, 1]), np.array([1, 2]))
+    return v, t, regions
+
+
+def test_layered_boundaries_match_oracle(B):
+    """bem_set_regions (host only): each region's boundary edges and signs are the
+    oracle's, for a coated sphere and for two spheres side by side in free space."""
+    from oracle import multiregion as MR
+
+    cases = [_layered_mesh()]
+    (va, ta), (vb, tb) = W.icosphere(1, 0.6, (-1.0, 0.0, 0.0)), W.icosphere(2, 0.5, (1.0, 0.2, 0.0))
+    v2, t2, s2 = MR.union_mesh([(va, ta), (vb, tb)])
+    cases.append((v2, t2, np.where(s2[:, None] == 0, np.array([0, 1]), np.array([0, 2]))))
+    for v, t, regions in cases:
+        g = rwg.build(v, t)
+        h = B.bem_create()
+        try:
+            B.bem_set_mesh(h, v, t)
+            B.bem_set_regions(h, 2.0, [1.0, 3.2 - 1.9j, 2.5 - 1.2j], regions)
+            for r in range(3):
+                edges, sign = B.bem_region_boundary(h, r)
+                _, e_o, s_o = MR.region_boundary(g, regions, r)
+                assert np.array_equal(edges, e_o), r
+                assert np.array_equal(sign.astype(np.float64), s_o), r
+            # bem_set_media returns to one body
+            B.bem_set_media(h, 2.0, 3.2 - 1.9j)
+            with pytest.raises(B.BemError) as ei:
+                B.bem_region_boundary(h, 0)
+            assert ei.value.status == B.BEM_ESTATE
+        finally:
+            B.bem_destroy(h)
+
+
+def test_layered_regions_rejected_when_inconsistent(B):
+    v, t, regions = _layered_mesh(1, 0)
+    eps = [1.0, 3.2 - 1.9j, 2.5 - 1.2j]
+    h = B.bem_create()
+    try:
+        with pytest.raises(B.BemError) as ei:       # no mesh yet
+            B.bem_set_regions(h, 2.0, eps, regions)
+        assert ei.value.status == B.BEM_ESTATE
+        B.bem_set_mesh(h, v, t)
+        bad = []
+        r = regions.copy(); r[:, :] = r[:, ::-1]; bad.append(r)          # exterior normals point inward
+        r = regions.copy(); r[0] = [1, 1]; bad.append(r)                  # same region on both sides
+        r = regions.copy(); r[0] = [0, 5]; bad.append(r)                  # region index out of range
+        r = regions.copy(); r[0] = [0, 2]; bad.append(r)                  # an edge between two region pairs
+        for r in bad:
+            with pytest.raises(B.BemError) as ei:
+                B.bem_set_regions(h, 2.0, eps, r)
+            assert ei.value.status == B.BEM_EINVAL
+        with pytest.raises(B.BemError):                                   # region 3 has no boundary
+            B.bem_set_regions(h, 2.0, eps + [2.0], regions)
+        with pytest.raises(B.BemError):                                   # gain medium
+            B.bem_set_regions(h, 2.0, [1.0, 3.2 + 1.0j, 2.5], regions)
+        with pytest.raises(B.BemError):
+            B.bem_set_regions(h, -1.0, eps, regions)
+        # a valid call, then the calls that a layered context refuses before any launch
+        B.bem_set_regions(h, 2.0, eps, regions)
+        for call in (lambda: B.bem_matvec(h, 0, 0, 1, B.BEM_C64),
+                     lambda: B.bem_solve(h, 0, 0, 1)):
+            with pytest.raises(B.BemError) as ei:
+                call()
+            assert ei.value.status == B.BEM_ESTATE
+    finally:
+        B.bem_destroy(h)
