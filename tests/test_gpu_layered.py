@@ -8,9 +8,11 @@ Small cases, dense oracle:
     2.5 - 1.2j), k0 = 2; 600 edges, 1,200 unknowns;
   * two spheres side by side in free space (80 and 320 triangles), coupled
     through the exterior region.
-Leaf 16, so that every region's operator has compressed blocks.  Tolerances
-are those of one body: compressed products 2e-5 (complex64, ACA 1e-6) and 1e-8
-(complex128, ACA 1e-10); refined solves 1e-8; powers 1e-8 relative.
+Leaf 16, so that every region's partition has far blocks (stored as ACA
+factors, or densely where the rank passes break-even).  Tolerances are those of
+one body: compressed products 2e-5 (complex64, ACA 1e-6), 1e-3 (complex64, ACA
+1e-4) and 1e-8 (complex128, ACA 1e-10); refined solves 1e-8; powers 1e-8
+relative.
 
 Full size: the coated sphere of the gradient workload (5,120 + 1,280
 triangles, radii 1 and 0.5, k0 = 6; 19,200 unknowns), leaf 64, eta 2: sampled
@@ -107,13 +109,14 @@ def small():
 
 
 @pytest.mark.parametrize("case", ["coated", "side_by_side"])
-@pytest.mark.parametrize("dtype,aca_tol,tol", [(0, 1e-6, 2e-5), (1, 1e-10, 1e-8)], ids=["c64", "c128"])
+@pytest.mark.parametrize("dtype,aca_tol,tol", [(0, 1e-6, 2e-5), (0, 1e-4, 1e-3), (1, 1e-10, 1e-8)],
+                         ids=["c64", "c64_aca1e-4", "c128"])
 def test_layered_product_equals_oracle(B, small, case, dtype, aca_tol, tol):
     v, t, regions, g, Z = small[case]
     h = make(B, v, t, regions, prec=1 if dtype == 0 else 2, aca_tol=aca_tol)
     try:
         st = B.bem_stats_get(h)
-        assert st["ne"] == g.ne and st["n_far_factored"] > 0
+        assert st["ne"] == g.ne and st["n_far"] > 0
         X = W.complex_normal(2 * g.ne, seed=1, nrhs=3)
         if dtype == 0:
             X = X.astype(np.complex64).astype(np.complex128)
@@ -241,6 +244,7 @@ def test_coated_sphere_full_size_sampled_rows(B, full):
     v, t, regions, g = full
     h = make(B, v, t, regions, k0=6.0, prec=1, leaf=64, aca_tol=1e-4)
     try:
+        assert B.bem_stats_get(h)["n_far_factored"] > 0
         x = W.complex_normal(2 * g.ne, seed=0).astype(np.complex64).astype(np.complex128)
         y = apply(B, h, x, B.BEM_C64)
         rows = np.random.default_rng(12).choice(2 * g.ne, 12, replace=False)
