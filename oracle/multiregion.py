@@ -181,3 +181,21 @@ def absorbed_and_weight_gradient(rwg: RWG, tri_regions, Z, Bm, w):
     Q = Y.conj().T @ (gradient.hermitian_form(rwg) @ Y)
     w = np.asarray(w, dtype=np.complex128)
     return float(np.real(np.vdot(w, Q @ w))), Q @ w
+
+
+def absorbed_eps_gradient(rwg: RWG, tri_regions, k0: float, eps_r, region: int, b, h: float = 1e-6):
+    """(dP/d Re eps, dP/d Im eps) of the region's permittivity, P = Re(xeJ^H X xeM)
+    the power absorbed by the layered body (region 0's boundary currents), by
+    central differences of the dense LU solution (b does not depend on eps)."""
+    from . import power
+
+    def p_of(e):
+        eps = list(eps_r)
+        eps[region] = e
+        Z = pmchwt_regions(rwg, tri_regions, k0, eps)
+        return power.absorbed(rwg, exterior_currents(rwg, tri_regions, np.linalg.solve(Z, b)))
+
+    e0 = complex(eps_r[region])
+    d_re = (p_of(e0 + h) - p_of(e0 - h)) / (2 * h)
+    d_im = (p_of(e0 + 1j * h) - p_of(e0 - 1j * h)) / (2 * h)
+    return np.array([d_re, d_im])
