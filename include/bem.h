@@ -199,8 +199,9 @@ bem_status bem_set_media(bem_ctx* ctx, double k0, bem_c128 eps_r, bem_c128 mu_r)
  * surface bounding it; every region needs a boundary.  eps_r, mu_r: host,
  * n_regions values for e^{+j w t} (Im <= 0, nonzero; entries 0 are ignored).
  * Else BEM_EINVAL (the context keeps its previous media).  Requires
- * bem_set_mesh; replaces bem_set_media (calling bem_set_media or bem_set_mesh
- * afterwards returns to one body).  Invalidates any assembled operator.  Host only.
+ * bem_set_mesh; replaces bem_set_media (bem_set_media afterwards returns to one
+ * body; bem_set_mesh afterwards drops the regions, and the media or regions must
+ * be set again).  Invalidates any assembled operator.  Host only.
  *
  * On such a context bem_assemble builds one compressed single-medium operator per
  * region on the region's boundary (same options); bem_matvec, bem_matvec_adjoint,
@@ -209,8 +210,9 @@ bem_status bem_set_media(bem_ctx* ctx, double k0, bem_c128 eps_r, bem_c128 mu_r)
  * it); bem_power, bem_power_density, bem_absorbed_power_gradient and
  * bem_grad_weights use the currents of region 0's boundary alone, i.e. the power
  * absorbed, extinguished and scattered by the whole body; bem_stats_get and
- * bem_profile_end report sums over the regions' operators.  bem_eval_entries,
- * bem_partition, bem_autotune, bem_grad_eps and bem_absorbed_power_static return
+ * bem_profile_end report sums over the regions' operators; bem_grad_eps gives
+ * one pair of derivatives per region r >= 1.  bem_eval_entries,
+ * bem_partition, bem_autotune and bem_absorbed_power_static return
  * BEM_ESTATE, bem_batch_create BEM_EINVAL. */
 bem_status bem_set_regions(bem_ctx* ctx, double k0, int n_regions, const bem_c128* eps_r, const bem_c128* mu_r,
                            const int32_t* tri_regions);
@@ -379,9 +381,16 @@ bem_status bem_grad_weights(bem_ctx* ctx, const void* bm, int nw, const bem_c128
  * pairs in FP64 (the k-derivative of the quadrature: dG/dk = -j e^{-jkR}/(4 pi),
  * and of the singular-pair extraction), so it is exact for the uncompressed
  * discretisation; meant for the moderate meshes of design problems.  x, lambda:
- * device complex128 2ne.  Allocates scratch; synchronises `stream`.  No paper
- * counterpart. */
+ * device complex128 2ne.  On a layered context (bem_set_regions) dp holds
+ * 2 (bem_num_regions - 1) values, the pair for region 1, then region 2, ...: only
+ * region r's operator depends on its permittivity, so its pair is the same form
+ * of region r's operator between the signed currents of its boundary.
+ * Allocates scratch; synchronises `stream`.  No paper counterpart. */
 bem_status bem_grad_eps(bem_ctx* ctx, const void* x, const void* lambda, double* dp, void* stream);
+
+/* Number of regions: 2 for one body (exterior and interior), n_regions after
+ * bem_set_regions, -1 before the media are set.  Host only. */
+int bem_num_regions(const bem_ctx* ctx);
 
 /* Absorbed power density per triangle for the first right-hand side of x
  * (device complex128): per_tri (device, nt doubles) = Re(sum_ij conj(xJ_i) X_t[i,j] xM_j) / area_t,

@@ -30,7 +30,7 @@ EXPORTS = [
     "bem_power_density", "bem_profile_begin", "bem_profile_end", "bem_absorbed_power_static",
     "bem_matvec_adjoint", "bem_solve_adjoint", "bem_absorbed_power_gradient", "bem_grad_weights", "bem_grad_eps",
     "bem_autotune", "bem_batch_create", "bem_batch_launch", "bem_batch_destroy", "bem_set_regions",
-    "bem_region_boundary",
+    "bem_region_boundary", "bem_num_regions",
 ]
 KERNEL_NAMES = ["k_gather", "k_vhx", "k_rows"]   # BEM_KERNEL_GATHER, _VHX, _ROWS
 
@@ -88,6 +88,7 @@ def _load():
         "bem_set_regions": (ctypes.c_int, [ctx, ctypes.c_double, ctypes.c_int, ctypes.POINTER(bem_c128),
                                            ctypes.POINTER(bem_c128), i32p]),
         "bem_region_boundary": (ctypes.c_int, [ctx, ctypes.c_int, i64p, i32p, ctypes.POINTER(ctypes.c_int8)]),
+        "bem_num_regions": (ctypes.c_int, [ctx]),
         "bem_debye_eps": (ctypes.c_int, [ctypes.c_double, dp, ctypes.POINTER(bem_c128)]),
         "bem_assemble": (ctypes.c_int, [ctx, vp]),
         "bem_num_edges": (ctypes.c_int64, [ctx]),
@@ -304,11 +305,16 @@ def bem_grad_weights(ctx, bm_ptr: int, w, x_ptr: int = 0, lam_ptr: int = 0, stre
 
 
 def bem_grad_eps(ctx, x_ptr: int, lam_ptr: int, stream: int = 0):
-    """(dP/d Re eps_r, dP/d Im eps_r) from the forward and adjoint solutions."""
-    out = np.zeros(2, dtype=np.float64)
+    """(dP/d Re eps_r, dP/d Im eps_r) from the forward and adjoint solutions; for a
+    layered context the pairs of regions 1, 2, ... one after another."""
+    out = np.zeros(2 * max(1, bem_num_regions(ctx) - 1), dtype=np.float64)
     _check(ctx, lib.bem_grad_eps(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(lam_ptr), _np_ptr(out, ctypes.c_double),
                                  ctypes.c_void_p(stream)))
     return out
+
+
+def bem_num_regions(ctx) -> int:
+    return int(lib.bem_num_regions(ctx))
 
 
 def bem_autotune(ctx, dtype: int, stream: int = 0):

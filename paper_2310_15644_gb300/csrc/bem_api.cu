@@ -353,6 +353,7 @@ extern "C" bem_status bem_set_mesh(bem_ctx* c, const double* verts, int64_t nv, 
     if (!verts || !tris || nv <= 0 || nt <= 0) return fail(c, BEM_EINVAL, "empty mesh");
     if (nt > (1 << 29) || nv > (1 << 30)) return fail(c, BEM_EINVAL, "mesh too large");
     invalidate(c);
+    if (layered(c)) c->has_media = false;  // the regions belonged to the old mesh
     clear_regions(c);
     c->has_mesh = false;
     for (int64_t t = 0; t < nt; ++t)
@@ -2459,12 +2460,8 @@ extern "C" bem_status bem_grad_weights(bem_ctx* c, const void* bm, int nw, const
     return BEM_OK;
 }
 
-extern "C" bem_status bem_grad_eps(bem_ctx* c, const void* x, const void* lambda, double* dp, void* stream) {
-    if (!c) return BEM_EINVAL;
-    if (!c->assembled) return fail(c, BEM_ESTATE, "bem_grad_eps needs bem_assemble");
-    if (layered(c)) return fail(c, BEM_ESTATE, "bem_grad_eps is not available on a layered context");
-    if (!x || !lambda || !dp) return fail(c, BEM_EINVAL, "bad arguments");
-    cudaStream_t st = (cudaStream_t)stream;
+// dP/d eps_r of one body's interior medium (the k1 slot), from x and lambda
+static bem_status grad_eps_one(bem_ctx* c, const void* x, const void* lambda, double* dp, cudaStream_t st) {
     const int64_t nsing = c->n_sing;
     DevBuf d_pair_a, d_dvals, d_part, d_out;
     struct G {
@@ -2501,6 +2498,43 @@ extern "C" bem_status bem_grad_eps(bem_ctx* c, const void* x, const void* lambda
     // dP = -2 Re(lambda^H dZ x), dZ = (dZ/d eps_r) d eps_r, d eps_r = d eps' + j d eps''
     dp[0] = -2.0 * s.re;
     dp[1] = 2.0 * s.im;
+    return BEM_OK;
+}
+
+extern "C" int bem_num_regions(const bem_ctx* c) {
+    if (!c || !c->has_media) return -1;
+    return layered(c) ? (int)c->regions.size() : 2;
+}
+
+extern "C" bem_status bem_grad_eps(bem_ctx* c, const void* x, const void* lambda, double* dp, void* stream) {
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled) return fail(c, BEM_ESTATE, "bem_grad_eps needs bem_assemble");
+    if (!x || !lambda || !dp) return fail(c, BEM_EINVAL, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!layered(c)) return grad_eps_one(c, x, lambda, dp, st);
+    // layered body: only Z_r depends on eps_r, so lambda^H Q_r^T (dZ_r/d eps_r) Q_r x is
+    // region r's single-medium form between its signed boundary currents
+    int64_t nmax = 0;
+    for (const auto& R : c->regions) nmax = std::max<int64_t>(nmax, (int64_t)R.edges.size());
+    DevBuf xr, lr;
+    struct G {
+        DevBuf* b[2];
+        ~G() {
+            for (DevBuf* z : b) dfree(*z);
+        }
+    } guard{{&xr, &lr}};
+    CK(dalloc(xr, sizeof(c128) * 2 * nmax));
+    CK(dalloc(lr, sizeof(c128) * 2 * nmax));
+    for (size_t r = 1; r < c->regions.size(); ++r) {
+        bem_ctx::Region& R = c->regions[r];
+        const int64_t ns = (int64_t)R.edges.size();
+        const int* ed = (const int*)R.d_edges.p;
+        const signed char* sg = (const signed char*)R.d_sign.p;
+        CK(region_gather(x, 16, c->ne, ed, sg, ns, 1, xr.p, st));
+        CK(region_gather(lambda, 16, c->ne, ed, sg, ns, 1, lr.p, st));
+        bem_status s = grad_eps_one(R.sub, xr.p, lr.p, dp + 2 * (r - 1), st);
+        if (s != BEM_OK) return fail(c, s, "region " + std::to_string(r) + ": " + R.sub->err);
+    }
     return BEM_OK;
 }
 

@@ -175,14 +175,20 @@ def test_layered_boundaries_match_oracle(B):
         h = B.bem_create()
         try:
             B.bem_set_mesh(h, v, t)
+            assert B.bem_num_regions(h) == -1
             B.bem_set_regions(h, 2.0, [1.0, 3.2 - 1.9j, 2.5 - 1.2j], regions)
+            assert B.bem_num_regions(h) == 3
             for r in range(3):
                 edges, sign = B.bem_region_boundary(h, r)
                 _, e_o, s_o = MR.region_boundary(g, regions, r)
                 assert np.array_equal(edges, e_o), r
                 assert np.array_equal(sign.astype(np.float64), s_o), r
-            # bem_set_media returns to one body
+            # bem_set_media returns to one body; a new mesh drops the regions and the media
             B.bem_set_media(h, 2.0, 3.2 - 1.9j)
+            assert B.bem_num_regions(h) == 2
+            B.bem_set_regions(h, 2.0, [1.0, 3.2 - 1.9j, 2.5 - 1.2j], regions)
+            B.bem_set_mesh(h, v, t)
+            assert B.bem_num_regions(h) == -1
             with pytest.raises(B.BemError) as ei:
                 B.bem_region_boundary(h, 0)
             assert ei.value.status == B.BEM_ESTATE
