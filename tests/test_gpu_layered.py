@@ -217,7 +217,7 @@ def test_layered_eps_gradient_equals_oracle(B, small):
     v, t, regions, g, Z = small["coated"]
     b = MR.rhs_planewave(g, regions, K0, [0.0, 0.0, 1.0], [1.0, 0.0, 0.0])
     ref = np.concatenate([MR.absorbed_eps_gradient(g, regions, K0, EPS3, r, b) for r in (1, 2)])
-    h = make(B, v, t, regions, prec=3, eta=0.0, tol=1e-10, refine_tol=1e-13, maxit=3000)
+    h = make(B, v, t, regions, prec=2, eta=0.0, tol=1e-10, refine_tol=1e-13, maxit=3000)
     try:
         assert B.bem_num_regions(h) == 3
         bd = torch.from_numpy(np.ascontiguousarray(b[None, :])).to(DEV)
