@@ -10,8 +10,8 @@
  * the matrices P11..P22 after it).  The library works in three dimensions with
  * RWG bases on a closed triangle mesh and the kernel e^{-jkR}/(4 pi R) under the
  * e^{+j w t} convention (the paper's H0^(2) kernel and 1 + j w tau Debye terms of
- * Eq. 5 fix that convention).  The interior medium has a complex relative
- * permittivity (Eq. 5 gives the skin model) and the outputs are the currents and
+ * Eq. 6 fix that convention).  The interior medium has a complex relative
+ * permittivity (Eq. 6 gives the skin model) and the outputs are the currents and
  * the absorbed power, the dosimetric quantity the paper is after (Sec. I).
  *
  * Unknowns and scaling.  For a mesh with ne interior edges the unknown vector has
@@ -31,7 +31,7 @@
  *
  * Compression.  Edges are ordered by a cluster tree over their midpoints; blocks of
  * the operator whose clusters are well separated are stored as low-rank factors
- * U V^H computed by adaptive cross approximation (the skeleton U V^T of Eq. 10),
+ * U V^H computed by adaptive cross approximation (the skeleton U V^T of Eq. 17),
  * the other blocks densely.
  *
  * Conventions for every entry point:
@@ -224,9 +224,9 @@ bem_status bem_set_regions(bem_ctx* ctx, double k0, int n_regions, const bem_c12
  * side of the edge's surface / behind it).  BEM_ESTATE on a single body. */
 bem_status bem_region_boundary(const bem_ctx* ctx, int r, int64_t* n_edges, int32_t* edges, int8_t* sign);
 
-/* Double-Debye permittivity of Eq. 5 at freq_hz >= 0:
+/* Double-Debye permittivity of Eq. 6 at freq_hz >= 0:
  * params = {eps_inf, eps_s, eps_2, tau1 [s], tau2 [s]}; NULL selects the skin
- * values given after Eq. 5 (3, 60, 3.6, 10 ps, 0.2 ps).  Host only, no context. */
+ * values given after Eq. 6 (3, 60, 3.6, 10 ps, 0.2 ps).  Host only, no context. */
 bem_status bem_debye_eps(double freq_hz, const double* params, bem_c128* eps_out);
 
 /* Build the operator on the GPU: cluster and block trees, singular-pair table,

@@ -15,8 +15,8 @@ Method (lifted from the paper's 2-D TM system to three dimensions):
     rows, and the matrices P11..P22 listed after Eq. 8);
   * the free-space kernel, here the 3-D e^{-jkR}/(4 pi R) under the e^{+j w t}
     convention implied by H0^(2) in Sec. II and by the 1+j w tau Debye terms
-    of Eq. 5;
-  * a low-rank skeleton of well-separated blocks (the U V^T of Eq. 10), here by
+    of Eq. 6;
+  * a low-rank skeleton of well-separated blocks (the U V^T of Eq. 17), here by
     adaptive cross approximation.
 
 Modules:
@@ -30,5 +30,5 @@ Modules:
   multiregion -- layered bodies: PMCHWT written region by region
   tree        -- cluster tree and block partition
   aca         -- partial-pivot adaptive cross approximation
-  debye       -- double-Debye permittivity (Eq. 5)
+  debye       -- double-Debye permittivity (Eq. 6)
 """

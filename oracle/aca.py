@@ -1,7 +1,7 @@
 """Partial-pivot adaptive cross approximation (oracle, test infrastructure).
 
 The paper compresses the non-circulant part of its operator into a skeleton
-U V^T (Eq. 10) with a randomized range finder; the library compresses each
+U V^T (Eq. 17) with a randomized range finder; the library compresses each
 admissible block by adaptive cross approximation into U V^H.  This is the
 textbook partial-pivot form, in float64, on a block seen only through its
 rows and columns:

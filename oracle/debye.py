@@ -1,8 +1,8 @@
-"""Double-Debye skin permittivity, Eq. 5 (oracle, test infrastructure).
+"""Double-Debye skin permittivity, Eq. 6 (oracle, test infrastructure).
 
 eps_r(w) = eps_inf + (eps_s - eps_2)/(1 + j w tau1) + (eps_2 - eps_inf)/(1 + j w tau2)
 
-with the skin parameters given right after Eq. 5: eps_inf = 3, eps_s = 60,
+with the skin parameters given right after Eq. 6: eps_inf = 3, eps_s = 60,
 eps_2 = 3.6, tau1 = 10 ps, tau2 = 0.2 ps.
 """
 from __future__ import annotations

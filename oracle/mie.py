@@ -4,7 +4,7 @@ A closed-form solution against which the whole discrete chain (RWG, operators,
 PMCHWT signs, right-hand side, powers) is checked.  Textbook form (Bohren and
 Huffman, ch. 4) with Riccati-Bessel functions psi_n(z) = z j_n(z) and
 xi_n(z) = z h_n^(1)(z), in that book's e^{-i w t} convention: a permittivity
-eps_r written for e^{+j w t} (Im eps_r <= 0, Eq. 5) enters as the relative
+eps_r written for e^{+j w t} (Im eps_r <= 0, Eq. 6) enters as the relative
 index m = sqrt(conj(eps_r) conj(mu_r)).
 """
 from __future__ import annotations

@@ -1,6 +1,6 @@
 """Cluster tree and block partition (oracle, test infrastructure).
 
-The paper's compressed block (Eq. 10) is global; the library splits the
+The paper's compressed block (Eq. 17) is global; the library splits the
 operator into a hierarchy of blocks instead, each either stored densely (near)
 or compressed (far).  The partition is defined here exactly, so that the GPU
 builder can be checked for equality:

@@ -16,7 +16,7 @@
 // are A = T^_0 + eta_r T^_1, B = K_0 + K_1, C = T^_0 + T^_1 / eta_r.
 //
 // The far blocks are compressed into U V^H by partial-pivot ACA (the low-rank
-// skeleton of Eq. 10, built here per admissible block by cross approximation
+// skeleton of Eq. 17, built here per admissible block by cross approximation
 // instead of random sampling): one CTA per (block, operator), rows and columns
 // evaluated by the same entry routine.
 #include "common.cuh"

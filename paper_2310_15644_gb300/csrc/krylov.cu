@@ -2,7 +2,7 @@
 // norms with FP64 accumulation (fixed reduction trees, so results do not depend
 // on scheduling), basis updates, casts between complex64 and complex128, and the
 // residual r = b - Z x of the iterative refinement.  The Krylov solve itself is
-// not in the paper (its Eq. 11 inverts the compressed operator directly); it is
+// not in the paper (its Eq. 18 inverts the compressed operator directly); it is
 // the iterative counterpart applied to the same compressed product.
 #include "common.cuh"
 

@@ -1,7 +1,7 @@
 // Cluster tree and block tree on the GPU.
 //
 // The compressed product needs a partition of the operator into dense (near) and
-// low-rank (far) blocks; the paper's skeleton U V^T (Eq. 10) is the global form of
+// low-rank (far) blocks; the paper's skeleton U V^T (Eq. 17) is the global form of
 // the same idea.  The partition is defined exactly (so results can be compared for
 // equality):
 //   * clusters are contiguous ranges of a permutation of the RWG edges; a cluster

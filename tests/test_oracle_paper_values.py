@@ -1,4 +1,4 @@
-"""Pins against values the paper prints (Eq. 5 parameters, Table I)."""
+"""Pins against values the paper prints (Eq. 6 parameters, Table I)."""
 import json
 import math
 import os
