@@ -31,4 +31,6 @@ Modules:
   tree        -- cluster tree and block partition
   aca         -- partial-pivot adaptive cross approximation
   debye       -- double-Debye permittivity (Eq. 6)
+  planar      -- the paper's own two-dimensional TM pipeline: S, D, D*, N on a polygon,
+                 PMCHWT, CFIE and its Calderon form, circulant counterpart, skeleton, Woodbury
 """

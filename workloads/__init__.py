@@ -30,6 +30,9 @@ __all__ = [
     "plane_wave_batch",
     "complex_normal",
     "uneven_sphere_batch",
+    "circle_polygon",
+    "ellipse_polygon",
+    "airfoil_polygon",
 ]
 
 
@@ -277,3 +280,57 @@ def uneven_sphere_batch(count: int = 16, seed: int = 1):
         eps = complex(rng.uniform(2.0, 5.0), rng.uniform(-3.0, -1.0))
         out.append({"freq": freq, "radius": radius, "k0": k0, "eps_r": eps})
     return out
+
+
+# ---------------------------------------------------------------------------
+# closed curves of the two-dimensional (z-invariant) setting
+# ---------------------------------------------------------------------------
+def _equal_arc(points_of, n: int, samples: int = 1 << 18):
+    """n points equally spaced in arc length along the closed parametric curve
+    points_of(theta), theta in [0, 2 pi); returns (n, 2) float64, starting at theta = 0."""
+    th = np.linspace(0.0, 2.0 * math.pi, samples + 1)
+    p = points_of(th)
+    seg = np.hypot(np.diff(p[:, 0]), np.diff(p[:, 1]))
+    s = np.concatenate([[0.0], np.cumsum(seg)])
+    target = np.arange(n) * (s[-1] / n)
+    t = np.interp(target, s, th)
+    return points_of(t)
+
+
+def circle_polygon(n: int, radius: float = 1.0):
+    """Regular n-gon inscribed in the circle of the given radius, counter-clockwise,
+    first vertex on the +x axis."""
+    th = 2.0 * math.pi * np.arange(n) / n
+    return np.stack([radius * np.cos(th), radius * np.sin(th)], axis=1)
+
+
+def ellipse_polygon(n: int, aspect: float = 1.5, perimeter: float = 2.0 * math.pi):
+    """n vertices equally spaced in arc length on the ellipse with semi-axes
+    (aspect * b, b) whose perimeter is ``perimeter``; counter-clockwise."""
+    unit = lambda th: np.stack([aspect * np.cos(th), np.sin(th)], axis=-1)  # noqa: E731
+    th = np.linspace(0.0, 2.0 * math.pi, (1 << 18) + 1)
+    p = unit(th)
+    per1 = float(np.sum(np.hypot(np.diff(p[:, 0]), np.diff(p[:, 1]))))
+    b = perimeter / per1
+    return _equal_arc(lambda t: b * unit(t), n)
+
+
+def airfoil_polygon(n: int, perimeter: float = 2.0 * math.pi, center=(-0.08, 0.08), swell: float = 1.05):
+    """Joukowsky airfoil: the image w = z + 1/z of the circle of centre ``center``
+    and radius swell * |1 - center| (swell > 1 rounds the trailing edge), scaled
+    to the given perimeter, n vertices equally spaced in arc length,
+    counter-clockwise."""
+    c = complex(*center)
+    rho = swell * abs(1.0 - c)
+
+    def raw(th):
+        z = c + rho * np.exp(1j * th)
+        w = z + 1.0 / z
+        return np.stack([w.real, w.imag], axis=-1)
+
+    th = np.linspace(0.0, 2.0 * math.pi, (1 << 18) + 1)
+    p = raw(th)
+    per1 = float(np.sum(np.hypot(np.diff(p[:, 0]), np.diff(p[:, 1]))))
+    pts = _equal_arc(lambda t: raw(t) * (perimeter / per1), n)
+    area2 = float(np.sum(pts[:, 0] * np.roll(pts[:, 1], -1) - np.roll(pts[:, 0], -1) * pts[:, 1]))
+    return pts if area2 > 0 else pts[::-1].copy()
