@@ -4,7 +4,8 @@
 scalar tensor) of the excitation b = bm w.  With `eps` (a float64 tensor
 [Re eps_r, Im eps_r]) and `k0`, the interior permittivity is an input too: the
 context is re-assembled when eps changes, and eps gets its gradient from
-`bem_grad_eps`.  The forward pass already runs the adjoint solve, inside
+`bem_grad_eps` (single body; on a layered context, set up with bem_set_regions,
+only the weights are inputs).  The forward pass already runs the adjoint solve, inside
 `bem_grad_weights` (forward solve, adjoint solve Z^H lambda = dP/d conj(x),
 grad = bm^H lambda), so backward only scales stored gradients.  Argument
 marshalling only: every step runs in the library.
@@ -62,4 +63,7 @@ def absorbed_power(w, handle, bm, eps=None, k0=None):
     context whose media are changed outside this function must not be reused here."""
     if eps is not None and k0 is None:
         raise ValueError("k0 is needed with eps")
+    if eps is not None and B.bem_num_regions(handle) > 2:
+        raise ValueError("eps as an input needs a single-body context; a layered context gets "
+                         "one permittivity gradient per region from bem_grad_eps")
     return AbsorbedPower.apply(w, eps, handle, bm, k0)

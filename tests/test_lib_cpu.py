@@ -229,3 +229,21 @@ def test_layered_regions_rejected_when_inconsistent(B):
             assert ei.value.status == B.BEM_ESTATE
     finally:
         B.bem_destroy(h)
+
+
+def test_autograd_refuses_eps_on_a_layered_context(B):
+    torch = pytest.importorskip("torch")
+    from paper_2310_15644_gb300.autograd import absorbed_power
+
+    v, t, regions = _layered_mesh(1, 0)
+    h = B.bem_create()
+    try:
+        B.bem_set_mesh(h, v, t)
+        B.bem_set_regions(h, 2.0, [1.0, 3.2 - 1.9j, 2.5 - 1.2j], regions)
+        w = torch.ones(1, dtype=torch.complex128)
+        eps = torch.tensor([3.2, -1.9], dtype=torch.float64)
+        bm = torch.zeros(1, 2, dtype=torch.complex128)
+        with pytest.raises(ValueError, match="single-body"):
+            absorbed_power(w, h, bm, eps=eps, k0=2.0)
+    finally:
+        B.bem_destroy(h)
