@@ -27,7 +27,10 @@ Reported beside the headline value:
                 unknowns): product and adjoint product of the region-by-region
                 operator, a solve against the stored dense oracle solution and the
                 coated-sphere series, and the absorbed-power gradient with respect
-                to the weights of 64 plane waves.
+                to the weights of 64 plane waves;
+  planar        the paper's own 2-D operators: dense FP64 Galerkin S, D, N on the
+                ellipse of its rank study (aspect 1.5, perimeter 2 pi) at k0 = 64
+                and 128 (18 unknowns per wavelength).
 `--impl reference` times the oracle alone (the reference arm).
 """
 from __future__ import annotations
@@ -421,6 +424,8 @@ def run_native(args, rank, world, dist):
             out["multi_mesh"] = run_multi_mesh(args, dev, stream, B, W)
         if not args.no_layered:
             out["layered"] = run_layered(args, dev, stream, B, W)
+        if not args.no_planar:
+            out["planar"] = run_planar(args, dev, stream, B, W)
     return out
 
 
@@ -656,6 +661,37 @@ def run_layered(args, dev, stream, B, W):
 
 
 # ---------------------------------------------------------------------------
+# the paper's own two-dimensional operators
+# ---------------------------------------------------------------------------
+def run_planar(args, dev, stream, B, W):
+    """Dense 2-D Galerkin S, D and N (FP64) on the ellipse of the paper's rank study
+    (aspect 1.5, perimeter 2 pi, 18 unknowns per wavelength: N = 18 k0)."""
+    import torch
+
+    sp = stream.cuda_stream
+    out = {"curve": "ellipse aspect 1.5 perimeter 2pi, N = 18 k0", "cases": []}
+    for k0 in (64.0, 128.0):
+        n = int(round(18 * k0))
+        verts = W.ellipse_polygon(n, 1.5, 2 * math.pi)
+        mats = [torch.empty(n, n, dtype=torch.complex128, device=dev) for _ in range(3)]
+        call = lambda: B.bem_planar_operators(None, verts, k0, mats[0].data_ptr(), mats[1].data_ptr(),  # noqa: E731
+                                              mats[2].data_ptr(), sp)
+        call()
+        torch.cuda.synchronize(dev)
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            call()
+        torch.cuda.synchronize(dev)
+        ms = (time.perf_counter() - t0) / reps * 1e3
+        out["cases"].append({"k0": k0, "n": n, "ms": round(ms, 2),
+                             "segment_pairs_per_s": round(n * n / (ms * 1e-3), 1),
+                             "finite": bool(all(torch.isfinite(torch.view_as_real(m)).all().item() for m in mats))})
+        del mats
+    return out
+
+
+# ---------------------------------------------------------------------------
 # many meshes of uneven size in one graph launch
 # ---------------------------------------------------------------------------
 def run_multi_mesh(args, dev, stream, B, W, count=16):
@@ -768,6 +804,7 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the 602,208-unknown slab")
     ap.add_argument("--no-multi", action="store_true", help="skip the 16-mesh graph batch")
     ap.add_argument("--no-layered", action="store_true", help="skip the coated (two-region) sphere")
+    ap.add_argument("--no-planar", action="store_true", help="skip the 2-D operator assembly")
     ap.add_argument("--level", type=int, default=5,
                     help="icosphere level (5 = the 61440-unknown workload; smaller levels for profiling captures)")
     args = ap.parse_args()

@@ -416,6 +416,26 @@ bem_status bem_power_density(bem_ctx* ctx, const void* x, double* per_tri, void*
  * bem_assemble. */
 bem_status bem_absorbed_power_static(bem_ctx* ctx, const void* x, int nrhs, double* p_abs, void* stream);
 
+/* The paper's own two-dimensional setting (Sec. II: fields invariant along z):
+ * dense Galerkin matrices of the single-layer S, double-layer D and hypersingular
+ * N operators of Eqs. 1-4 with the kernel -(j/4) H0^(2)(k R) (Eq. 5), tested and
+ * expanded with hat functions on the closed polygon verts (host, n x 2 doubles,
+ * counter-clockwise, n >= 3): (O)_ij = (lambda_i, O lambda_j) with lambda_i the
+ * hat function of vertex i.  The adjoint double layer of Eq. 3 is D^T.  N uses
+ * the identity (lambda_i, N lambda_j) = int int G (lambda_i' lambda_j' -
+ * k^2 n.n' lambda_i lambda_j) (N = -d_n D).  Quadrature: 10 x 10 Gauss-Legendre
+ * points per segment pair after the static parts of the kernels are integrated
+ * over the source segment in closed form; the outer rule is 20 points graded
+ * toward the shared vertex of neighbouring segments; a segment with itself takes
+ * the logarithm over both copies in closed form.  k: complex wavenumber with
+ * Re k > 0 and Im k <= 0.  S, D, N: device complex128 n x n, row-major (element
+ * (i, j) at i * n + j), each may be NULL.  FP64 throughout (Hankel functions from
+ * their ascending series below |k R| = 12 and Hankel's expansion above).
+ * Allocates 128 n^2 bytes of scratch; synchronises `stream`.  ctx (may be NULL)
+ * only receives the error message.  No counterpart in the three-dimensional path. */
+bem_status bem_planar_operators(bem_ctx* ctx, const double* verts, int n, bem_c128 k, void* S, void* D, void* N,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ EXPORTS = [
     "bem_power_density", "bem_profile_begin", "bem_profile_end", "bem_absorbed_power_static",
     "bem_matvec_adjoint", "bem_solve_adjoint", "bem_absorbed_power_gradient", "bem_grad_weights", "bem_grad_eps",
     "bem_autotune", "bem_batch_create", "bem_batch_launch", "bem_batch_destroy", "bem_set_regions",
-    "bem_region_boundary", "bem_num_regions",
+    "bem_region_boundary", "bem_num_regions", "bem_planar_operators",
 ]
 KERNEL_NAMES = ["k_gather", "k_vhx", "k_rows"]   # BEM_KERNEL_GATHER, _VHX, _ROWS
 
@@ -89,6 +89,7 @@ def _load():
                                            ctypes.POINTER(bem_c128), i32p]),
         "bem_region_boundary": (ctypes.c_int, [ctx, ctypes.c_int, i64p, i32p, ctypes.POINTER(ctypes.c_int8)]),
         "bem_num_regions": (ctypes.c_int, [ctx]),
+        "bem_planar_operators": (ctypes.c_int, [ctx, dp, ctypes.c_int, bem_c128, vp, vp, vp, vp]),
         "bem_debye_eps": (ctypes.c_int, [ctypes.c_double, dp, ctypes.POINTER(bem_c128)]),
         "bem_assemble": (ctypes.c_int, [ctx, vp]),
         "bem_num_edges": (ctypes.c_int64, [ctx]),
@@ -193,6 +194,15 @@ def bem_region_boundary(ctx, r: int):
     _check(ctx, lib.bem_region_boundary(ctx, int(r), ctypes.byref(n), _np_ptr(edges, ctypes.c_int32),
                                         _np_ptr(sign, ctypes.c_int8)))
     return edges, sign
+
+
+def bem_planar_operators(ctx, verts, k: complex, s_ptr: int, d_ptr: int, n_ptr: int, stream: int = 0) -> None:
+    """Dense 2-D Galerkin S, D, N (device complex128 n x n, row-major) of a closed polygon."""
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    kk = complex(k)
+    _check(ctx, lib.bem_planar_operators(ctx, _np_ptr(v, ctypes.c_double), len(v), bem_c128(kk.real, kk.imag),
+                                    ctypes.c_void_p(s_ptr or None), ctypes.c_void_p(d_ptr or None),
+                                    ctypes.c_void_p(n_ptr or None), ctypes.c_void_p(stream)))
 
 
 def bem_debye_eps(freq_hz: float, params=None) -> complex:

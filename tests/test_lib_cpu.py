@@ -247,3 +247,12 @@ def test_autograd_refuses_eps_on_a_layered_context(B):
             absorbed_power(w, h, bm, eps=eps, k0=2.0)
     finally:
         B.bem_destroy(h)
+
+
+def test_planar_operators_reject_bad_input_before_any_launch(B):
+    sq = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+    for verts, k in ((sq[:2], 1.0), (sq[::-1].copy(), 1.0), (sq, 1.0 + 0.1j), (sq, -1.0),
+                     (np.array([[0.0, 0.0], [0.0, 0.0], [1.0, 1.0]]), 1.0)):
+        with pytest.raises(B.BemError) as ei:
+            B.bem_planar_operators(None, verts, k, 0, 0, 0)
+        assert ei.value.status == B.BEM_EINVAL
