@@ -185,6 +185,21 @@ P2_HD c128 dgreen_rem(c128 k, double R) {
     return (1.0 / R) * mul_mj(0.25 * (k * h1)) - mk<double>(1.0 / (P2_TWO_PI * R * R), 0.0);
 }
 
+// Both remainders at one distance (R > 0), sharing one Hankel evaluation above the
+// series range: gr = Gr_k(R), ar = Ar_k(R)
+P2_HD void kernel_rems(c128 k, double R, c128& gr, c128& ar) {
+    const c128 x = R * k;
+    if (cabs2d(x) < P2_SERIES_X) {
+        gr = green_rem(k, R);
+        ar = dgreen_rem(k, R);
+        return;
+    }
+    c128 h0, h1;
+    hankel2_01(x, h0, h1);
+    gr = mul_mj(0.25 * h0) + mk<double>(log(R) / P2_TWO_PI, 0.0);
+    ar = (1.0 / R) * mul_mj(0.25 * (k * h1)) - mk<double>(1.0 / (P2_TWO_PI * R * R), 0.0);
+}
+
 // Closed forms over a straight source segment of length L for a target at local
 // coordinates (u along the segment from its start, v along its outward normal):
 //   log moments  m0 = int_0^L ln R dt,  m1 = int_0^L t ln R dt,
@@ -261,8 +276,10 @@ P2_HD void pair_local(const double pa[2], const double ta[2], double La, const d
             const double R = sqrt(dx * dx + dy * dy);
             const double vv = dx * nb[0] + dy * nb[1];
             const double W = wi * Lb;
-            const c128 gr = (W) * green_rem(k, R);
-            const c128 ar = (W * vv) * dgreen_rem(k, R);
+            c128 g0, a0;
+            kernel_rems(k, R, g0, a0);
+            const c128 gr = W * g0;
+            const c128 ar = (W * vv) * a0;
             Sq[0] = Sq[0] + (1.0 - xi) * gr;
             Sq[1] = Sq[1] + xi * gr;
             Dq[0] = Dq[0] + (1.0 - xi) * ar;
