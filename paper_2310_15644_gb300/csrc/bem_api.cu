@@ -1987,6 +1987,8 @@ static bem_status gmres(bem_ctx* c, int pdt, double tol_abs, int maxit, int* ite
     int it = 0;
     while (true) {
         if ((s = norm_dev(c, dtype, w.r.p, n, &beta, st)) != BEM_OK) return s;
+        if (!std::isfinite(beta))
+            return fail(c, BEM_ENOCONV, "non-finite GMRES residual (NaN or Inf in the operator or the right-hand side)");
         if (beta <= tol_abs || it >= maxit) break;
         CK(kv_scale_copy(w.r.p, dtype, 1.0 / beta, n, V, st));
         std::fill(H.begin(), H.end(), mk<double>(0, 0));
@@ -2228,6 +2230,7 @@ static bem_status solve_impl(bem_ctx* c, const void* b, void* x, int nrhs, void*
         c128* xr = (c128*)x + r * n;
         double bn;
         if ((s = norm_dev(c, BEM_C128, br, n, &bn, st)) != BEM_OK) return s;
+        if (!std::isfinite(bn)) return fail(c, BEM_EINVAL, "the right-hand side has non-finite entries");
         if (bn == 0) {
             CK(cudaMemsetAsync(xr, 0, sizeof(c128) * n, st));
             if (relres) relres[r] = 0;

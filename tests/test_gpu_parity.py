@@ -331,3 +331,28 @@ def test_batched_product_equals_one_at_a_time(B, sphere3, dtype):
         assert rel(Y, Z @ X) <= 1e-3
     finally:
         B.bem_destroy(h)
+
+
+def test_solver_reports_nonconvergence_and_bad_input(B, sphere2):
+    """maxit = 1: BEM_ENOCONV with the residual of the last iterate reported (below 1,
+    one GMRES step); a non-finite right-hand side is refused (BEM_EINVAL)."""
+    v, t, g, _ = sphere2
+    b = E.rhs_planewave(g, K0, [0.0, 0.0, 1.0], [1.0, 0.0, 0.0])
+    h = make(B, v, t, prec=1, maxit=1, tol=1e-12)
+    try:
+        bd = torch.from_numpy(b).to(DEV)
+        xd = torch.zeros_like(bd)
+        it, relres, st = B.bem_solve(h, bd.data_ptr(), xd.data_ptr(), 1, _stream(), raise_on_noconv=False)
+        assert st == B.BEM_ENOCONV and it == 1
+        assert 0.0 < relres[0] < 1.0
+        with pytest.raises(B.BemError) as ei:
+            B.bem_solve(h, bd.data_ptr(), xd.data_ptr(), 1, _stream())
+        assert ei.value.status == B.BEM_ENOCONV
+        bad = b.copy()
+        bad[3] = np.nan
+        bdd = torch.from_numpy(bad).to(DEV)
+        with pytest.raises(B.BemError) as ei:
+            B.bem_solve(h, bdd.data_ptr(), xd.data_ptr(), 1, _stream())
+        assert ei.value.status == B.BEM_EINVAL
+    finally:
+        B.bem_destroy(h)
