@@ -509,6 +509,12 @@ extern "C" bem_status bem_set_regions(bem_ctx* c, double k0, int nreg, const bem
         if (tri_regions[2 * a] != tri_regions[2 * b] || tri_regions[2 * a + 1] != tri_regions[2 * b + 1])
             return fail(c, BEM_EINVAL, "the two triangles of an edge bound different regions");
     }
+    {
+        std::vector<char> bounded(nreg, 0);
+        for (int64_t t = 0; t < nt; ++t) bounded[tri_regions[2 * t]] = bounded[tri_regions[2 * t + 1]] = 1;
+        for (int r = 0; r < nreg; ++r)
+            if (!bounded[r]) return fail(c, BEM_EINVAL, "region " + std::to_string(r) + " has no boundary");
+    }
     invalidate(c);
     clear_regions(c);
     c->has_media = false;

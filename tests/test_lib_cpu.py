@@ -214,8 +214,10 @@ def test_layered_regions_rejected_when_inconsistent(B):
             with pytest.raises(B.BemError) as ei:
                 B.bem_set_regions(h, 2.0, eps, r)
             assert ei.value.status == B.BEM_EINVAL
+        B.bem_set_media(h, 2.0, 3.2 - 1.9j)
         with pytest.raises(B.BemError):                                   # region 3 has no boundary
             B.bem_set_regions(h, 2.0, eps + [2.0], regions)
+        assert B.bem_num_regions(h) == 2                                  # the media set before are kept
         with pytest.raises(B.BemError):                                   # gain medium
             B.bem_set_regions(h, 2.0, [1.0, 3.2 + 1.0j, 2.5], regions)
         with pytest.raises(B.BemError):
