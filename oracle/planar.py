@@ -513,3 +513,48 @@ def cylinder_pec_current(k0: float, a: float, theta, nmax: int | None = None):
     m = np.arange(-nmax, nmax + 1)
     coef = (-1j) ** m * 2.0 / (math.pi * k0 * a * hankel2(m, k0 * a))
     return np.exp(1j * np.outer(theta, m)) @ coef
+
+
+# ---------------------------------------------------------------------------
+# powers per unit length (TM), in the normalised units of the unknowns:
+# 2 eta0 P for x = [eta0 j_z ; m_t] and a unit incident field
+# ---------------------------------------------------------------------------
+def absorbed(poly: Polygon, x):
+    """2 eta0 P_abs = Re int m_t conj(eta0 j_z) dl = Re(xJ^H G xM): the power flowing
+    into the body, -1/2 Re oint (E x H*).n dl with (E x H*).n = -E_z conj(H_t)."""
+    n = poly.n
+    return float(np.real(np.vdot(x[:n], gram(poly) @ x[n:])))
+
+
+def extinguished(poly: Polygon, x, e, eta0_h):
+    """2 eta0 P_ext = Re(xJ^H e + (eta0 h)^H xM), from the surface fields
+    (P_abs + P_sca = -1/2 Re oint (E^i x H^s* + E^s x H^i*).n dl, the incident
+    field's own flux through the closed curve vanishing)."""
+    n = poly.n
+    return float(np.real(np.vdot(x[:n], e) + np.vdot(eta0_h, x[n:])))
+
+
+def far_field(poly: Polygon, k0: float, x, phi):
+    """F(phi) with E_z^s ~ -(j/4) sqrt(2/(pi k0 rho)) e^{-j(k0 rho - pi/4)} F(phi):
+    F = j k0 int [(rhat . n') m_t - eta0 j_z] e^{j k0 rhat . r'} dl'."""
+    n = poly.n
+    xg, wg = gauss01(N_OUTER)
+    pts = poly.points(xg)                                                          # (n, NG, 2)
+    W = wg[None, :] * poly.length[:, None]
+    phi_b = np.stack([1.0 - xg, xg], axis=-1)
+    idx = (np.arange(n)[:, None] + np.arange(2)[None, :]) % n                     # vertices of segment e
+    J = np.einsum("gp,ep->eg", phi_b, x[:n][idx])                                  # eta0 j_z at the points
+    M = np.einsum("gp,ep->eg", phi_b, x[n:][idx])
+    rhat = np.stack([np.cos(phi), np.sin(phi)], axis=-1)                           # (nphi, 2)
+    ph = np.exp(1j * k0 * np.einsum("fd,egd->feg", rhat, pts))
+    rn = rhat @ poly.normal.T                                                      # (nphi, n)
+    integrand = (rn[:, :, None] * M[None] - J[None]) * W[None]
+    return 1j * k0 * np.einsum("feg,feg->f", ph, integrand)
+
+
+def scattered(poly: Polygon, k0: float, x, nphi: int = 720):
+    """2 eta0 P_sca = (1 / (8 pi k0)) int_0^{2 pi} |F(phi)|^2 dphi (trapezoidal rule,
+    exponentially accurate for the periodic integrand)."""
+    phi = 2.0 * math.pi * np.arange(nphi) / nphi
+    F = far_field(poly, k0, x, phi)
+    return float(np.sum(np.abs(F) ** 2) * (2.0 * math.pi / nphi) / (8.0 * math.pi * k0))

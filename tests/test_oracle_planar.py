@@ -187,3 +187,47 @@ def test_skeleton_rank_grows_sublinearly(ellipse_calderon):
         sv = np.linalg.svd(Cp - Cc, compute_uv=False)
         ranks[k0] = int(np.sum(sv > 1e-3 * sv[0]))
     assert ranks[4.0] < ranks[8.0] < 1.8 * ranks[4.0], ranks
+
+
+def test_powers_balance_and_match_cylinder_series():
+    """2-D powers per unit length of the dielectric cylinder: extinction (surface
+    formula) = absorption + scattering (far-field integral) to the discretisation
+    error, falling under refinement; absorption against the series' surface fields
+    (Re oint E_z conj(eta0 H_t) dl on a fine angular grid); a lossless cylinder absorbs
+    (almost) nothing."""
+    th_f = 2 * np.pi * np.arange(4096) / 4096
+    bal, err = [], []
+    for n in (64, 128):
+        poly = PL.Polygon(W.circle_polygon(n, 1.0))
+        e, h = PL.rhs_tm(poly, K, [1.0, 0.0])
+        x = np.linalg.solve(PL.pmchwt_tm(poly, K, 3.2 - 1.9j), PL.rhs_pmchwt_tm(poly, K, [1.0, 0.0]))
+        pa, pe, ps = PL.absorbed(poly, x), PL.extinguished(poly, x, e, h), PL.scattered(poly, K, x)
+        bal.append(abs(pe - pa - ps) / pe)
+        jz, ez = PL.cylinder_tm_currents(K, 3.2 - 1.9j, 1.0, th_f)
+        ref = float(np.real(np.sum(ez * np.conj(jz))) * 2 * np.pi / len(th_f))
+        err.append(abs(pa - ref) / ref)
+    assert bal[0] < 1e-4 and bal[1] < bal[0] / 3
+    assert err[1] < 0.005 and err[0] / err[1] > 3.0, err
+    poly = PL.Polygon(W.circle_polygon(64, 1.0))
+    x = np.linalg.solve(PL.pmchwt_tm(poly, K, 3.2), PL.rhs_pmchwt_tm(poly, K, [1.0, 0.0]))
+    e, h = PL.rhs_tm(poly, K, [1.0, 0.0])
+    assert abs(PL.absorbed(poly, x)) < 1e-3 * PL.extinguished(poly, x, e, h)
+
+
+def test_skin_sample_golden_balances_energy():
+    """The stored 2-D skin-sample solution (ellipse of perimeter 5.85 mm, Debye skin at
+    1 THz, 654 hat functions): its powers recomputed from the stored currents satisfy
+    P_ext = P_abs + P_sca and absorb a positive share."""
+    import os
+
+    d = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "skin_2d_oracle.npz"))
+    n = int(d["n"])
+    poly = PL.Polygon(W.ellipse_polygon(n, float(d["aspect"]), float(d["perimeter"])))
+    khat = np.array([np.cos(float(d["angle"])), np.sin(float(d["angle"]))])
+    k0 = float(d["k0"])
+    e, h = PL.rhs_tm(poly, k0, khat)
+    x = d["x"]
+    pa, pe, ps = PL.absorbed(poly, x), PL.extinguished(poly, x, e, h), PL.scattered(poly, k0, x)
+    assert abs(pa - float(d["p_abs"])) < 1e-12 * abs(pa) and abs(pe - float(d["p_ext"])) < 1e-12 * abs(pe)
+    assert abs(pe - pa - ps) < 1e-4 * pe
+    assert 0.2 < pa / pe < 0.8
