@@ -558,3 +558,44 @@ def scattered(poly: Polygon, k0: float, x, nphi: int = 720):
     phi = 2.0 * math.pi * np.arange(nphi) / nphi
     F = far_field(poly, k0, x, phi)
     return float(np.sum(np.abs(F) ** 2) * (2.0 * math.pi / nphi) / (8.0 * math.pi * k0))
+
+
+def interior_field(poly: Polygon, k0: float, eps_r: complex, x, points, mu_r: complex = 1.0):
+    """E_z at points inside the body from its boundary currents: the interior
+    representation E_z(r) = oint [G_1 d_n' E_z - E_z d_n' G_1] dl' (n' outgoing) with
+    d_n E_z = j k1 eta1 j_z, i.e. E_z = j k1 eta_r S1[eta0 j_z] - D1[m_t], by the
+    10-point rule on every segment (points away from the boundary)."""
+    k1 = k0 * np.sqrt(complex(eps_r) * complex(mu_r))
+    eta_r = np.sqrt(complex(mu_r) / complex(eps_r))
+    n = poly.n
+    xg, wg = gauss01(N_OUTER)
+    pts = poly.points(xg).reshape(-1, 2)                                           # (n*NG, 2)
+    W = (wg[None, :] * poly.length[:, None]).reshape(-1)
+    phi_b = np.stack([1.0 - xg, xg], axis=-1)
+    idx = (np.arange(n)[:, None] + np.arange(2)[None, :]) % n
+    J = np.einsum("gp,ep->eg", phi_b, x[:n][idx]).reshape(-1)
+    M = np.einsum("gp,ep->eg", phi_b, x[n:][idx]).reshape(-1)
+    nrm = np.repeat(poly.normal, len(xg), axis=0)
+    d = np.asarray(points, dtype=np.float64)[:, None, :] - pts[None, :, :]         # r - r'
+    R = np.sqrt(np.einsum("pqd,pqd->pq", d, d))
+    G = green(k1, R)
+    dG = dgreen_coef(k1, R) * np.einsum("pqd,qd->pq", d, nrm)                      # d_n' G
+    return (1j * k1 * eta_r) * (G * W[None, :]) @ J - (dG * W[None, :]) @ M
+
+
+def cylinder_tm_interior(k0: float, eps_r: complex, a: float, r, theta, nmax: int | None = None):
+    """E_z inside the dielectric cylinder at polar points (r, theta) (series)."""
+    from scipy.special import h2vp, jv, jvp
+
+    k1 = k0 * np.sqrt(complex(eps_r))
+    if nmax is None:
+        nmax = int(abs(k1) * a + 4 * abs(k1 * a) ** (1 / 3) + 12)
+    m = np.arange(-nmax, nmax + 1)
+    x0, x1 = k0 * a, k1 * a
+    J0, J0p, H0, H0p = jv(m, x0), jvp(m, x0), hankel2(m, x0), h2vp(m, x0)
+    J1, J1p = jv(m, x1), jvp(m, x1)
+    det = H0 * k1 * J1p - k0 * H0p * J1
+    dm = (H0 * k0 * J0p - k0 * H0p * J0) / det
+    r = np.asarray(r, dtype=np.float64)
+    theta = np.asarray(theta, dtype=np.float64)
+    return np.sum((-1j) ** m * dm * jv(m, k1 * r[:, None]) * np.exp(1j * m * theta[:, None]), axis=1)

@@ -231,3 +231,37 @@ def test_skin_sample_golden_balances_energy():
     assert abs(pa - float(d["p_abs"])) < 1e-12 * abs(pa) and abs(pe - float(d["p_ext"])) < 1e-12 * abs(pe)
     assert abs(pe - pa - ps) < 1e-4 * pe
     assert 0.2 < pa / pe < 0.8
+
+
+def test_interior_field_matches_cylinder_series():
+    errs = []
+    r = np.array([0.0, 0.2, 0.5, 0.7, 0.5])
+    th = np.array([0.0, 1.0, 2.5, 4.0, -0.3])
+    pts = np.stack([r * np.cos(th), r * np.sin(th)], axis=1)
+    for n in (64, 128):
+        poly = PL.Polygon(W.circle_polygon(n, 1.0))
+        x = np.linalg.solve(PL.pmchwt_tm(poly, K, 3.2 - 1.9j), PL.rhs_pmchwt_tm(poly, K, [1.0, 0.0]))
+        ref = PL.cylinder_tm_interior(K, 3.2 - 1.9j, 1.0, r, th)
+        errs.append(np.max(np.abs(PL.interior_field(poly, K, 3.2 - 1.9j, x, pts) - ref) / np.abs(ref)))
+    assert errs[0] < 0.005 and errs[0] / errs[1] > 3.0, errs
+
+
+def test_skin_sample_field_decays_at_the_debye_rate():
+    """Inside the skin sample, along the inward normal at the illuminated point, |E_z|
+    decays with a 1/e length within 15 % of the plane-wave 1/alpha of Eq. 6 at 1 THz
+    (147 um; power: half of it)."""
+    import os
+
+    d = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "skin_2d_oracle.npz"))
+    poly = PL.Polygon(W.ellipse_polygon(int(d["n"]), float(d["aspect"]), float(d["perimeter"])))
+    khat = np.array([np.cos(float(d["angle"])), np.sin(float(d["angle"]))])
+    k0, eps = float(d["k0"]), complex(d["eps_r"])
+    vn = poly.normal + np.roll(poly.normal, 1, axis=0)
+    vn /= np.linalg.norm(vn, axis=1, keepdims=True)
+    i = int(np.argmin(vn @ khat))
+    depth = np.linspace(30e-6, 400e-6, 24)
+    pts = poly.verts[i][None, :] - depth[:, None] * vn[i][None, :]
+    E = PL.interior_field(poly, k0, eps, d["x"], pts)
+    length = -1.0 / np.polyfit(depth, np.log(np.abs(E)), 1)[0]
+    alpha = -(k0 * np.sqrt(eps)).imag
+    assert abs(length * alpha - 1.0) < 0.15, (length, 1 / alpha)
