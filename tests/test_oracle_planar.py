@@ -265,3 +265,20 @@ def test_skin_sample_field_decays_at_the_debye_rate():
     length = -1.0 / np.polyfit(depth, np.log(np.abs(E)), 1)[0]
     alpha = -(k0 * np.sqrt(eps)).imag
     assert abs(length * alpha - 1.0) < 0.15, (length, 1 / alpha)
+
+
+def test_stored_rank_study_is_sublinear():
+    """The stored epsilon-ranks of C_p - C_p,c on the ellipse (N = 18 k0, k0 = 4 ... 64,
+    written by tests/golden/make_rank_study.py from the oracle): they grow with k0,
+    but every doubling of k0 (and of N) less than doubles them at every tolerance."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ellipse_rank_study.json")) as f:
+        rows = json.load(f)["rows"]
+    assert [r["k0"] for r in rows] == [4.0, 8.0, 16.0, 32.0, 64.0]
+    assert [r["n"] for r in rows] == [72, 144, 288, 576, 1152]
+    for tol in ("0.01", "0.001", "0.0001"):
+        ranks = [r["ranks"][tol] for r in rows]
+        assert all(b > a for a, b in zip(ranks, ranks[1:])), (tol, ranks)
+        assert all(b < 2 * a for a, b in zip(ranks, ranks[1:])), (tol, ranks)
