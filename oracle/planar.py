@@ -599,3 +599,62 @@ def cylinder_tm_interior(k0: float, eps_r: complex, a: float, r, theta, nmax: in
     r = np.asarray(r, dtype=np.float64)
     theta = np.asarray(theta, dtype=np.float64)
     return np.sum((-1j) ** m * dm * jv(m, k1 * r[:, None]) * np.exp(1j * m * theta[:, None]), axis=1)
+
+
+# ---------------------------------------------------------------------------
+# TE polarisation (H_z) on the metal boundary
+# ---------------------------------------------------------------------------
+def rhs_te(poly: Polygon, k0: float, khat):
+    """(h, dh) with h_i = (lambda_i, H_z^inc), dh_i = (lambda_i, d_n H_z^inc) for
+    H_z^inc = exp(-j k0 khat . r) (unit amplitude), d_n H^inc = -j k0 (khat . n) H^inc."""
+    khat = np.asarray(khat, dtype=np.float64)
+    xg, wg = gauss01(N_OUTER)
+    pts = poly.points(xg)
+    H = np.exp(-1j * k0 * (pts @ khat))
+    dH = (-1j * k0 * (poly.normal @ khat))[:, None] * H
+    phi = np.stack([1.0 - xg, xg], axis=-1)
+    W = wg[None, :] * poly.length[:, None]
+    n = poly.n
+    h = np.zeros(n, dtype=np.complex128)
+    dh = np.zeros(n, dtype=np.complex128)
+    for p in range(2):
+        np.add.at(h, (np.arange(n) + p) % n, np.einsum("ng,ng,g->n", W, H, phi[:, p]))
+        np.add.at(dh, (np.arange(n) + p) % n, np.einsum("ng,ng,g->n", W, dH, phi[:, p]))
+    return h, dh
+
+
+def cfie_te(poly: Polygon, k0: float):
+    """TE combined field operator N/(j k0) + G/2 - D for the metal's tangential current
+    j_t = (n x H).t = -H_z (n outgoing, t = z x n); right-hand side
+    -(dh / (j k0) + h).  From the exterior representation
+    H_z = H^inc + oint [H_z d_n'G - G d_n'H_z] with d_n H_z = 0 on the metal (E_t = 0):
+    magnetic row (G/2 - D) j_t = -h, electric row N j_t = -dh (N = -d_n D)."""
+    S, D, Dt, N, G = operators(poly, k0)
+    return N / (1j * k0) + 0.5 * G - D
+
+
+def calderon_cfie_te(poly: Polygon, k0: float, a: float | None = None):
+    """(C_p, L_e, L_h) of the TE counterpart of Eq. 16: the electric row N j = -dh is
+    preconditioned by S~ (S N = 1/4 - D^2) and the magnetic row (G/2 - D) j = -h by
+    (G/2 + D~): C_p = S~ G^-1 N + (G/2 + D~) G^-1 (G/2 - D), right-hand side
+    L_e (-dh) + L_h (-h).  The paper prints only the TM form; this is its dual."""
+    a = curvature_radius(poly) if a is None else a
+    kt = k_tilde(k0, a)
+    S, D, Dt, N, G = operators(poly, k0)
+    St, Dtl, _, _, _ = operators(poly, kt)
+    Ginv = np.linalg.inv(G)
+    Le = St @ Ginv
+    Lh = (0.5 * G + Dtl) @ Ginv
+    return Le @ N + Lh @ (0.5 * G - D), Le, Lh
+
+
+def cylinder_pec_te_current(k0: float, a: float, theta, nmax: int | None = None):
+    """j_t = -H_z on a PEC cylinder of radius a under H_z = exp(-j k0 x) (series):
+    j_t = sum (-j)^m (2j / (pi k0 a H_m^(2)'(k0 a))) exp(j m theta)."""
+    from scipy.special import h2vp
+
+    if nmax is None:
+        nmax = int(k0 * a + 4 * (k0 * a) ** (1 / 3) + 12)
+    m = np.arange(-nmax, nmax + 1)
+    coef = (-1j) ** m * 2j / (math.pi * k0 * a * h2vp(m, k0 * a))
+    return np.exp(1j * np.outer(theta, m)) @ coef

@@ -282,3 +282,29 @@ def test_stored_rank_study_is_sublinear():
         ranks = [r["ranks"][tol] for r in rows]
         assert all(b > a for a, b in zip(ranks, ranks[1:])), (tol, ranks)
         assert all(b < 2 * a for a, b in zip(ranks, ranks[1:])), (tol, ranks)
+
+
+def test_te_cfie_and_calderon_match_pec_cylinder():
+    """TE metal boundary (H_z polarisation): the combined field operator and its
+    Calderon form give the series current j_t = -H_z with an O(h^2) error; the
+    Calderon form stays conditioned under refinement, the combined field operator
+    (with its hypersingular part) does not."""
+    errs = {"C": [], "Cp": []}
+    conds = {"C": [], "Cp": []}
+    for n in (64, 128):
+        poly = PL.Polygon(W.circle_polygon(n, 1.0))
+        th = 2 * np.pi * np.arange(n) / n
+        h, dh = PL.rhs_te(poly, K, [1.0, 0.0])
+        js = PL.cylinder_pec_te_current(K, 1.0, th)
+        C = PL.cfie_te(poly, K)
+        Cp, Le, Lh = PL.calderon_cfie_te(poly, K)
+        j = np.linalg.solve(C, -(dh / (1j * K) + h))
+        j2 = np.linalg.solve(Cp, Le @ (-dh) + Lh @ (-h))
+        errs["C"].append(np.linalg.norm(j - js) / np.linalg.norm(js))
+        errs["Cp"].append(np.linalg.norm(j2 - js) / np.linalg.norm(js))
+        conds["C"].append(np.linalg.cond(C))
+        conds["Cp"].append(np.linalg.cond(Cp))
+    for key in errs:
+        assert errs[key][1] < 0.003 and errs[key][0] / errs[key][1] > 3.0, errs
+    assert conds["Cp"][1] < 1.1 * conds["Cp"][0] < 10.0
+    assert conds["C"][1] > 1.8 * conds["C"][0]
