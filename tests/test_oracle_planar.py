@@ -308,3 +308,25 @@ def test_te_cfie_and_calderon_match_pec_cylinder():
         assert errs[key][1] < 0.003 and errs[key][0] / errs[key][1] > 3.0, errs
     assert conds["Cp"][1] < 1.1 * conds["Cp"][0] < 10.0
     assert conds["C"][1] > 1.8 * conds["C"][0]
+
+
+def test_planted_mistake_fails_the_eigenvalue_pin(monkeypatch):
+    """A wrong sign of the double layer's static part (the closed-form angle integral)
+    breaks agreement with the circle's eigenvalue by far more than the O(h^2) error.
+    (Slips in the self-segment logarithm table change S by O(h^2) as the
+    discretisation does; that table is pinned by direct quadrature instead.)"""
+    poly = PL.Polygon(W.circle_polygon(64, 1.0))
+    th = 2 * np.pi * np.arange(64) / 64
+    f = np.ones(64, dtype=np.complex128)      # m = 0: on a circle the static kernel is constant
+    _, d, _ = PL.circle_eigenvalues(K, 1.0, 0)
+
+    def err():
+        S, D, Dt, N, G = PL.operators(poly, K)
+        Gf = G @ f
+        return np.linalg.norm(D @ f - d * Gf) / np.linalg.norm(d * Gf)
+
+    base = err()
+    assert base < 0.01
+    orig = PL._angle_moments
+    monkeypatch.setattr(PL, "_angle_moments", lambda u, v, L: tuple(-m for m in orig(u, v, L)))
+    assert err() > 10 * base
