@@ -233,3 +233,23 @@ def test_layered_eps_gradient_matches_coated_series():
     for r in (1, 2):
         assert errs[r][1] < errs[r][0], errs
         assert errs[r][1] <= 0.10, errs
+
+
+def test_planted_media_swap_fails_the_coated_series(monkeypatch):
+    """Assigning the core's medium to the coating and vice versa (a plausible slip in
+    the region bookkeeping) moves the efficiencies far outside the discretisation
+    error of the coated-sphere pin."""
+    g, regions = _two_layer(2, 1)
+    ref = mie.coated_efficiencies_eps(K0, 0.5, 1.0, EPS_CORE, EPS_SHELL)
+    good = _efficiencies(g, regions, EPS_CORE)
+    orig = MR.region_media
+
+    def swapped(k0, eps_r, mu_r=None):
+        m = orig(k0, eps_r, mu_r)
+        return [m[0], m[2], m[1]]
+
+    monkeypatch.setattr(MR, "region_media", swapped)
+    bad = _efficiencies(g, regions, EPS_CORE)
+    e_good = max(abs(good[q] - ref[q]) / ref[q] for q in ("ext", "abs", "sca"))
+    e_bad = max(abs(bad[q] - ref[q]) / ref[q] for q in ("ext", "abs", "sca"))
+    assert e_good < 0.06 and e_bad > 3 * e_good, (e_good, e_bad)
