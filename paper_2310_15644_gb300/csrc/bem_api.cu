@@ -165,6 +165,13 @@ static bem_status cuda_fail(bem_ctx* c, cudaError_t e, const char* where) {
         if (_e != cudaSuccess) return cuda_fail(c, _e, #expr); \
     } while (0)
 
+// Kernels over right-hand sides put them on grid.y, whose limit is 65535
+static std::string nrhs_msg(const char* fn, int nrhs) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "%s: %d right-hand sides in one call; at most %d", fn, nrhs, BEM_MAX_NRHS);
+    return buf;
+}
+
 template <typename T>
 static cudaError_t upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
     cudaError_t e = dalloc(b, v.size() * sizeof(T));
@@ -1909,6 +1916,7 @@ extern "C" bem_status bem_rhs_planewave(bem_ctx* c, const double* khat, const be
                                         int dtype, void* stream) {
     if (!c) return BEM_EINVAL;
     if (!c->assembled) return fail(c, BEM_ESTATE, "bem_rhs_planewave needs bem_assemble");
+    if (nrhs > BEM_MAX_NRHS) return fail(c, BEM_EINVAL, nrhs_msg("bem_rhs_planewave", nrhs));
     if (nrhs < 1 || !khat || !e0 || !b || (dtype != BEM_C64 && dtype != BEM_C128))
         return fail(c, BEM_EINVAL, "bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
@@ -2353,6 +2361,7 @@ extern "C" bem_status bem_power(bem_ctx* c, const void* x, const void* b, int nr
     if (!c) return BEM_EINVAL;
     if (!c->assembled) return fail(c, BEM_ESTATE, "bem_power needs bem_assemble");
     if (nrhs < 1 || !x || (p_ext && !b)) return fail(c, BEM_EINVAL, "bad arguments");
+    if (nrhs > BEM_MAX_NRHS) return fail(c, BEM_EINVAL, nrhs_msg("bem_power", nrhs));
     cudaStream_t st = (cudaStream_t)stream;
     GeomDev g = geom_view(c);
     const c128* xe;
@@ -2398,6 +2407,7 @@ extern "C" bem_status bem_absorbed_power_gradient(bem_ctx* c, const void* x, voi
     if (!c) return BEM_EINVAL;
     if (!c->assembled) return fail(c, BEM_ESTATE, "bem_absorbed_power_gradient needs bem_assemble");
     if (nrhs < 1 || !x || !g || x == g) return fail(c, BEM_EINVAL, "bad arguments");
+    if (nrhs > BEM_MAX_NRHS) return fail(c, BEM_EINVAL, nrhs_msg("bem_absorbed_power_gradient", nrhs));
     const c128* xe;
     bem_status s0;
     if ((s0 = exterior_view(c, x, nrhs, &xe, (cudaStream_t)stream)) != BEM_OK) return s0;

@@ -21,6 +21,7 @@
 // SM (1024 threads) in the FP32 build
 #define BEM_ACA_WIDE_COST (1 << 19)
 #define BEM_MAX_NR 8   // right-hand sides applied per pass over the operator
+#define BEM_MAX_NRHS 65535  // right-hand sides per call of an entry point that launches one grid row per vector
 #define BEM_ROW_GROUPS 1     // 64-thread groups per CTA of the rows kernel (one work slot each)
 #define BEM_ROW_TARGET_CTAS (48 * 152)  // rows-kernel CTAs aimed at per product (about 3 waves)
 

@@ -1,5 +1,5 @@
 // The compressed PMCHWT product y = Z x (Eq. 8's system matrix applied to a
-// vector, with its far blocks in the skeleton form U V^H of Eq. 10).
+// vector, with its far blocks in the skeleton form U V^H of Eq. 17).
 //
 // Data layout (all in HBM, written once by assembly):
 //   near items   one per (leaf row cluster, dense column range); A, B, C arrays

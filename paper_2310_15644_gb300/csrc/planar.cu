@@ -6,6 +6,8 @@
 //   N_ab[p][q] = s_p s_q / (La Lb) sum_{p'q'} S_ab[p'][q'] - k^2 (n_a . n_b) S_ab[p][q],
 //   s = (-1, +1) (derivatives of the two hat functions along the curve).
 #include "common.cuh"
+#include <cstdio>
+
 #include "planar.cuh"
 
 using namespace bem2d;
@@ -103,6 +105,17 @@ extern "C" bem_status bem_planar_operators(bem_ctx* ctx, const double* verts, in
     const int64_t nn = (int64_t)n * n;
     Seg* d_seg = nullptr;
     c128 *locS = nullptr, *locD = nullptr;
+    {
+        // the two per-pair scratch arrays (64 n^2 bytes each) are the binding limit: refuse up front
+        size_t fr = 0, tot = 0;
+        const size_t need = 2 * sizeof(c128) * 4 * (size_t)nn + sizeof(Seg) * (size_t)n;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && need > fr) {
+            char buf[200];
+            snprintf(buf, sizeof buf, "bem_planar_operators: n = %d needs %zu bytes of scratch, %zu bytes free", n,
+                     need, fr);
+            return fail(BEM_ENOMEM, buf);
+        }
+    }
     cudaError_t e = cudaMalloc(&d_seg, sizeof(Seg) * n);
     if (e == cudaSuccess) e = cudaMalloc(&locS, sizeof(c128) * 4 * nn);
     if (e == cudaSuccess) e = cudaMalloc(&locD, sizeof(c128) * 4 * nn);

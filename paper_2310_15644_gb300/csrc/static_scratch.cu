@@ -66,6 +66,13 @@ extern "C" bem_status bem_absorbed_power_static(bem_ctx* c, const void* x, int n
         bem_ctx_set_error(c, "bem_absorbed_power_static: bad arguments");
         return BEM_EINVAL;
     }
+    if (nrhs > BEM_MAX_NRHS) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "bem_absorbed_power_static: %d right-hand sides in one call; at most %d", nrhs,
+                 BEM_MAX_NRHS);
+        bem_ctx_set_error(c, buf);
+        return BEM_EINVAL;
+    }
     GeomDev g = bem_geom_view_for_static(c);
     const int nblk = (g.nt + 255) / 256;  // partial sums per right-hand side (blocks of power_abs)
     if ((int64_t)nblk * nrhs > BEM_STATIC_PARTIALS) {

@@ -1,0 +1,177 @@
+// Fifth-generation tensor-core primitives of sm_100-family GPUs (sm_103a), in
+// inline PTX: tensor-memory (TMEM) allocation, loads and stores, the tcgen05.mma
+// contraction with its instruction and shared-memory matrix descriptors, the
+// completion signal through an mbarrier, and the fences between the thread and
+// tensor-core views of shared and tensor memory.  Used by the many-right-hand-
+// side product (matvec_tc.cu); compiled into a small test harness as well, so the
+// descriptor conventions are checked on a single tile against a host GEMM.
+//
+// Conventions (cta_group::1, M = 128):
+//   * the accumulator D (128 x N, FP32) occupies TMEM lanes 0..127 (row m <-> lane m)
+//     and N consecutive 32-bit columns;
+//   * the A operand may sit in TMEM (row m <-> lane m, K consecutive 32-bit columns,
+//     one TF32 element per column) or in shared memory; the B operand (N x K) sits
+//     in shared memory;
+//   * shared-memory operands are K-major without swizzle: a "core matrix" is 8 rows
+//     of 16 contiguous bytes (four 32-bit elements along K); the descriptor's leading
+//     byte offset (LBO) is the distance between core matrices adjacent in K and its
+//     stride byte offset (SBO) the distance between groups of 8 rows;
+//   * a warp reaches only its quadrant of TMEM: lanes 32 (w mod 4) ... + 31.
+#pragma once
+
+#include <stdint.h>
+
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---------------------------------------------------------------------------
+// mbarriers (completion of tensor-core work)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make initialised barriers visible to the tensor core's (async proxy's) arrivals
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase of the given parity to complete, at most max_iter polls;
+// false if the limit ran out (the caller records an error and stops).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_iter) {
+    for (uint32_t i = 0; i < max_iter; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// tensor memory
+// ---------------------------------------------------------------------------
+// whole warp: allocate ncols (power of two, 32..512) columns of all 128 lanes; the
+// TMEM address (lane 0, first column) is written to *dst (shared memory)
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// order tensor-core operations before / after a thread synchronisation
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// make this thread's shared-memory stores visible to the tensor core
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// TMEM address of (lane, column) relative to an allocation base
+__device__ __forceinline__ uint32_t taddr(uint32_t base, uint32_t lane, uint32_t col) {
+    return base + (lane << 16) + col;
+}
+
+// whole warp: thread t writes 8 consecutive 32-bit columns of lane (lane(ta) + t)
+__device__ __forceinline__ void tmem_st8(uint32_t ta, const uint32_t (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(ta),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+// whole warp: wait until this thread's TMEM stores have completed
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// whole warp: thread t reads 16 consecutive 32-bit columns of lane (lane(ta) + t);
+// the load and its completion wait are one statement, so no use of the values can
+// be scheduled before the data have arrived
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, float (&f)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------------------
+// descriptors and the contraction
+// ---------------------------------------------------------------------------
+// Shared-memory matrix descriptor, K-major, no swizzle: start address, leading
+// byte offset (between core matrices adjacent in K), stride byte offset (between
+// 8-row groups), descriptor version 1 (bits 46-47), base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::tf32: FP32 accumulator (bits 4-5 = 1), A and B
+// TF32 (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), no negation,
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D (TMEM) (+)= A (TMEM) * B (shared memory)^T, one K step of 8 TF32 elements.
+// Issued by a single thread.  acc = 0 overwrites D.
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_t, uint32_t a_t, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_t),
+        "r"(a_t), "l"(b_desc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// the same with A in shared memory
+__device__ __forceinline__ void mma_tf32_ss(uint32_t d_t, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_t),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// one arrival on *bar once every tensor-core operation this thread issued so far has completed
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// three-term TF32 splitting (FP32-level products on the TF32 tensor path)
+// ---------------------------------------------------------------------------
+// v = hi + lo with hi = v rounded to TF32 (10 explicit mantissa bits, nearest,
+// ties away) and lo = v - hi exact in FP32; the product a b is taken as
+// hi_a hi_b + hi_a lo_b + lo_a hi_b, whose dropped term lo_a lo_b and the TF32
+// reading of lo (truncated to 10 bits) leave a relative error of about 2^-21.
+__device__ __forceinline__ uint32_t tf32_hi(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ void tf32_split(float v, uint32_t& hi, uint32_t& lo) {
+    hi = tf32_hi(v);
+    lo = __float_as_uint(v - __uint_as_float(hi));
+}
+
+}  // namespace tc
