@@ -82,6 +82,8 @@ typedef enum {
 #define BEM_C64 0
 #define BEM_C128 1
 #define BEM_C64_BF16F 2  /* complex64 vectors; bem_matvec uses the complex64 near entries and the BF16 factors */
+#define BEM_C64_TC 3     /* complex64 vectors; bem_matvec applies the complex64 operator on the tensor cores in
+                            passes of 64 vectors (three-term TF32 split, FP32-level accuracy) */
 
 typedef struct {
     int precision;       /* bit mask of BEM_PREC_*: which operators bem_assemble builds (default C64) */
@@ -262,11 +264,19 @@ bem_status bem_eval_entries(bem_ctx* ctx, const int32_t* rows, const int32_t* co
                             void* out, int dtype, void* stream);
 
 /* y = Z x for nrhs vectors.  x, y: device, 2ne x nrhs complex of type `dtype`
- * (BEM_C64, BEM_C128 or BEM_C64_BF16F, needing the operator of that precision:
- * BEM_PREC_C64, BEM_PREC_C128 or BEM_PREC_BF16F; BEM_C64_BF16F vectors are
- * complex64); x and y must not
+ * (BEM_C64, BEM_C128, BEM_C64_BF16F or BEM_C64_TC, needing the operator of that
+ * precision: BEM_PREC_C64, BEM_PREC_C128, BEM_PREC_BF16F, BEM_PREC_C64;
+ * BEM_C64_BF16F and BEM_C64_TC vectors are complex64); x and y must not
  * overlap.  Asynchronous on `stream`; no allocation after the first call with a
- * given nrhs.  The product reads each dense entry and each factor once per call. */
+ * given nrhs.  The CUDA-core forms stream the operator once per chunk of up to 8
+ * vectors; BEM_C64_TC streams it once per pass of up to 64 vectors, each stored
+ * block entering a dense contraction on the tensor cores (Eq. 8's matrix times
+ * many excitations at once; complex products embedded in real ones, each factor
+ * split into TF32 high and low parts so that the result keeps FP32 accuracy).
+ * The first BEM_C64_TC call builds that form's schedule and its workspaces
+ * (64 vectors, 64 x the t values of the far blocks), synchronises `stream` and
+ * needs a GB300 (sm_103); BEM_ETIMEOUT reports a tensor-core kernel of an earlier
+ * call whose bounded wait ran out. */
 bem_status bem_matvec(bem_ctx* ctx, const void* x, void* y, int nrhs, int dtype, void* stream);
 
 /* y = Z^H x, the conjugate transpose of the assembled operator (adjoint solves

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libbem.so")
 
 BEM_OK, BEM_EINVAL, BEM_ENOMEM, BEM_ECUDA, BEM_ENOCONV, BEM_ETIMEOUT, BEM_ESTATE = range(7)
 BEM_PREC_C64, BEM_PREC_C128, BEM_PREC_BF16F = 1, 2, 4
-BEM_C64, BEM_C128, BEM_C64_BF16F = 0, 1, 2
+BEM_C64, BEM_C128, BEM_C64_BF16F, BEM_C64_TC = 0, 1, 2, 3
 BEM_SOLVER_GMRES, BEM_SOLVER_CGS, BEM_SOLVER_BICGSTAB, BEM_SOLVER_CGNR = 0, 1, 2, 3
 STATUS_NAMES = {0: "BEM_OK", 1: "BEM_EINVAL", 2: "BEM_ENOMEM", 3: "BEM_ECUDA", 4: "BEM_ENOCONV",
                 5: "BEM_ETIMEOUT", 6: "BEM_ESTATE"}

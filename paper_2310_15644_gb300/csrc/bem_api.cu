@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <numeric>
 
 #include "common.cuh"
@@ -78,6 +79,11 @@ struct Operator {
     int64_t factor_entries[3] = {0, 0, 0};
     int max_rank = 0;
     std::vector<FarRec> recs;
+    // tensor-core product (complex64 operator, passes of 64 vectors); built on first use
+    bool tc_built = false;
+    RowsPlan tcp;                      // rows schedule with BEM_TC_ROW_TARGET slots
+    DevBuf tc_tasks, tc_pairs, tc_xp, tc_t, tc_ypart, tc_counters;
+    int tc_ntask = 0;
 };
 
 struct GmresWork {
@@ -142,6 +148,9 @@ struct bem_ctx {
         DevBuf d_edges, d_sign;
     };
     std::vector<Region> regions;
+    int num_sms = 0;              // persistent CTAs of the tensor-core kernels
+    int* tc_err_host = nullptr;   // set by a tensor-core kernel whose bounded wait ran out (mapped host memory)
+    int* tc_err_dev = nullptr;
     DevBuf d_rx, d_ry;   // one region's operand and product
     DevBuf d_xext;       // the currents of the exterior boundary (powers)
 };
@@ -190,7 +199,7 @@ static cudaError_t ensure(DevBuf& b, size_t bytes) {
 #define DT_C64_IN_FP64 100
 static int esize_of(int dtype) { return (dtype == BEM_C128 || dtype == DT_C64_IN_FP64) ? 16 : 8; }
 // element type of the vectors of a product dtype
-static int vec_dtype(int dtype) { return dtype == BEM_C64_BF16F ? BEM_C64 : dtype; }
+static int vec_dtype(int dtype) { return (dtype == BEM_C64_BF16F || dtype == BEM_C64_TC) ? BEM_C64 : dtype; }
 
 static GeomDev geom_view(const bem_ctx* c) {
     GeomDev g;
@@ -250,6 +259,11 @@ static c128 csqrt_principal(c128 z) {
 static void release_operator(Operator& o) {
     release_rows_plan(o.fwd);
     release_rows_plan(o.adj);
+    release_rows_plan(o.tcp);
+    DevBuf* tcb[] = {&o.tc_tasks, &o.tc_pairs, &o.tc_xp, &o.tc_t, &o.tc_ypart, &o.tc_counters};
+    for (DevBuf* b : tcb) dfree(*b);
+    o.tc_built = false;
+    o.tc_ntask = 0;
     o.row_target = BEM_ROW_TARGET_CTAS;
     o.adj_built = false;
     dfree(o.nearT);
@@ -344,6 +358,7 @@ extern "C" void bem_destroy(bem_ctx* c) {
                       &c->cgw.v[1], &c->cgw.v[2], &c->cgw.v[3], &c->cgw.v[4], &c->cgw.v[5], &c->cgw.v[6],
                       &c->cgw.v[7]};
     for (DevBuf* b : bufs) dfree(*b);
+    if (c->tc_err_host) cudaFreeHost(c->tc_err_host);
     delete c;
 }
 
@@ -936,8 +951,9 @@ static bem_status build_leaves(bem_ctx* c, cudaStream_t st) {
 // far block gives a piece to every leaf of its rows; adjoint: items are the
 // transposed items and a far block gives a piece to every leaf of its columns.
 static bem_status build_rows_plan(bem_ctx* c, const Operator& o, const std::vector<BlockDesc>& dense, bool adjoint,
-                                  RowsPlan& rp, size_t es, cudaStream_t st) {
-    const int target = o.row_target;
+                                  RowsPlan& rp, size_t es, cudaStream_t st, int target_slots = 0,
+                                  int ypart_nr = BEM_MAX_NR) {
+    const int target = target_slots > 0 ? target_slots : o.row_target;
     const int nleaf = (int)c->leaf_lo.size();
     std::vector<int> leaf_of(c->ne + 1, -1);
     for (int l = 0; l < nleaf; ++l) leaf_of[c->leaf_lo[l]] = l;
@@ -1042,7 +1058,7 @@ static bem_status build_rows_plan(bem_ctx* c, const Operator& o, const std::vect
         d.t_off = R.off_t;
     }
     CK(upload(rp.d_pieces, pieces, st));
-    CK(dalloc(rp.d_ypart, es * 2 * c->ne * (rp.pmax > 1 ? rp.pmax : 1) * BEM_MAX_NR));
+    CK(dalloc(rp.d_ypart, es * 2 * c->ne * (rp.pmax > 1 ? rp.pmax : 1) * ypart_nr));
     CK(dalloc(rp.d_arrive, sizeof(unsigned int) * std::max(1, nleaf)));
     CK(cudaMemsetAsync(rp.d_arrive.p, 0, sizeof(unsigned int) * std::max(1, nleaf), st));
     CK(cudaStreamSynchronize(st));
@@ -1513,7 +1529,7 @@ static bool bf16_built(const bem_ctx* c) {
 }
 
 static bool dtype_ok(const bem_ctx* c, int dtype) {
-    if (dtype == BEM_C64) return op_built(c, 0);
+    if (dtype == BEM_C64 || dtype == BEM_C64_TC) return op_built(c, 0);
     if (dtype == BEM_C128) return op_built(c, 1);
     if (dtype == BEM_C64_BF16F) return bf16_built(c);
     return false;
@@ -1535,8 +1551,8 @@ extern "C" bem_status bem_eval_entries(bem_ctx* c, const int32_t* rows, const in
     return BEM_OK;
 }
 
-static MatvecPlan make_plan(const bem_ctx* c, const Operator& o, bool adjoint = false) {
-    const RowsPlan& rp = adjoint ? o.adj : o.fwd;
+static MatvecPlan make_plan(const bem_ctx* c, const Operator& o, bool adjoint = false, bool tc = false) {
+    const RowsPlan& rp = tc ? o.tcp : (adjoint ? o.adj : o.fwd);
     MatvecPlan p;
     p.ne = (int)c->ne;
     p.nleaf = (int)c->leaf_lo.size();
@@ -1618,6 +1634,80 @@ static bem_status ensure_adjoint_for(bem_ctx* c, int dtype, cudaStream_t st) {
     return fail(c, BEM_EINVAL, "the adjoint product exists for BEM_C64 and BEM_C128");
 }
 
+// Schedule and workspaces of the tensor-core product of the complex64 operator
+// (first use): V^H x tasks (the far blocks' W column pairs grouped by column
+// cluster and vector half, at most 32 pairs per task, largest first), a rows
+// schedule with BEM_TC_ROW_TARGET slots, and the 64-vector workspaces.
+static bem_status ensure_tc(bem_ctx* c, Operator& o, cudaStream_t st) {
+    if (o.tc_built) return BEM_OK;
+    {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+        int cc_major = 0, cc_minor = 0;
+        CK(cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, dev));
+        CK(cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, dev));
+        if (cc_major != 10 || cc_minor != 3)
+            return fail(c, BEM_EINVAL, "the tensor-core product is built for sm_103 (GB300) only");
+    }
+    if (!c->tc_err_host) {
+        CK(cudaHostAlloc((void**)&c->tc_err_host, sizeof(int), cudaHostAllocMapped));
+        *c->tc_err_host = 0;
+        CK(cudaHostGetDevicePointer((void**)&c->tc_err_dev, c->tc_err_host, 0));
+    }
+    // group (column cluster, half) -> list of pairs
+    std::map<std::tuple<int, int, int>, std::vector<TcPair>> groups;
+    for (const FarRec& r : o.recs) {
+        const int kp[3] = {(r.rk[0] + 1) / 2, (r.rk[1] + 1) / 2, (r.rk[2] + 1) / 2};
+        // t segments [tA | tB(J) | tB(M) | tC]
+        const int64_t seg[4] = {0, 2 * (int64_t)kp[0], 2 * (int64_t)(kp[0] + kp[1]),
+                                2 * (int64_t)(kp[0] + 2 * kp[1])};
+        // half J: A -> tA, B -> tB(J); half M: B -> tB(M), C -> tC
+        const int part_of[2][2] = {{0, 1}, {1, 2}};
+        const int seg_of[2][2] = {{0, 1}, {2, 3}};
+        for (int g = 0; g < 2; ++g) {
+            auto& v = groups[std::make_tuple(r.c0, r.n, g)];
+            for (int u = 0; u < 2; ++u) {
+                const int q = part_of[g][u];
+                for (int k = 0; k < kp[q]; ++k)
+                    v.push_back({r.off_v[q] + 2 * (int64_t)k * r.n, r.off_t + seg[seg_of[g][u]] + 2 * (int64_t)k});
+            }
+        }
+    }
+    std::vector<TcVhxTask> tasks;
+    std::vector<TcPair> pairs;
+    for (auto& kv : groups) {
+        const auto& v = kv.second;
+        for (size_t p0 = 0; p0 < v.size(); p0 += 32) {
+            TcVhxTask T{};
+            T.c0 = std::get<0>(kv.first);
+            T.n = std::get<1>(kv.first);
+            T.g = std::get<2>(kv.first);
+            T.npairs = (int)std::min<size_t>(32, v.size() - p0);
+            T.pair0 = (int)pairs.size();
+            for (int k = 0; k < T.npairs; ++k) pairs.push_back(v[p0 + k]);
+            tasks.push_back(T);
+        }
+    }
+    std::stable_sort(tasks.begin(), tasks.end(), [](const TcVhxTask& a, const TcVhxTask& b) {
+        return (int64_t)a.n * a.npairs > (int64_t)b.n * b.npairs;
+    });
+    o.tc_ntask = (int)tasks.size();
+    CK(upload(o.tc_tasks, tasks, st));
+    CK(upload(o.tc_pairs, pairs, st));
+    bem_status s;
+    if ((s = build_rows_plan(c, o, o.items, false, o.tcp, sizeof(c64), st, BEM_TC_ROW_TARGET, 1)) != BEM_OK)
+        return s;
+    const size_t nn = 2 * (size_t)c->ne;
+    CK(dalloc(o.tc_xp, sizeof(c64) * nn * BEM_TC_NR));
+    CK(dalloc(o.tc_t, sizeof(c64) * std::max<int64_t>(1, o.t_len) * BEM_TC_NR));
+    CK(dalloc(o.tc_ypart, sizeof(c64) * nn * BEM_TC_NR * (o.tcp.pmax > 1 ? o.tcp.pmax : 1)));
+    CK(dalloc(o.tc_counters, 2 * sizeof(int)));
+    CK(cudaStreamSynchronize(st));
+    o.tc_built = true;
+    return BEM_OK;
+}
+
 static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int nrhs, cudaStream_t st,
                               bool record = false, bool adjoint = false);
 
@@ -1655,6 +1745,8 @@ static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int
         size_t passes = 0;
         if (dtype == DT_C64_IN_FP64) {
             passes = (size_t)nrhs;
+        } else if (dtype == BEM_C64_TC) {
+            passes = (size_t)((nrhs + BEM_TC_NR - 1) / BEM_TC_NR);
         } else {
             for (int left = nrhs; left > 0;) {
                 left -= left >= 8 ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1));
@@ -1670,6 +1762,23 @@ static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int
         }
         ev = c->ev_pool.data() + c->ev_used;
         c->ev_used = need;
+    }
+    if (dtype == BEM_C64_TC) {
+        if (adjoint) return cudaErrorInvalidValue;
+        Operator& o = c->op[0];
+        if (!o.tc_built) return cudaErrorNotReady;  // ensure_tc first
+        const MatvecPlan p = make_plan(c, o, false, true);
+        TcPlan tp;
+        tp.tasks = (const TcVhxTask*)o.tc_tasks.p;
+        tp.pairs = (const TcPair*)o.tc_pairs.p;
+        tp.ntask = o.tc_ntask;
+        tp.nsm = c->num_sms;
+        tp.xp = (c64*)o.tc_xp.p;
+        tp.t = (c64*)o.tc_t.p;
+        tp.ypart = (c64*)o.tc_ypart.p;
+        tp.counters = (int*)o.tc_counters.p;
+        tp.err = c->tc_err_dev;
+        return matvec_tc_run(p, tp, o.near.p, o.arena.p, (const c64*)x, (c64*)y, nrhs, st, ev);
     }
     if (dtype == BEM_C64 || dtype == BEM_C64_BF16F) {
         Operator& o = c->op[0];
@@ -1882,6 +1991,23 @@ extern "C" bem_status bem_profile_end(bem_ctx* c, double* ms_sum, int64_t* launc
     return BEM_OK;
 }
 
+// The tensor-core product's schedule on this context (every region of a layered
+// body), and the report of a tensor-core kernel whose bounded wait ran out
+static bem_status prepare_tc(bem_ctx* c, cudaStream_t st) {
+    if (layered(c)) {
+        for (auto& R : c->regions) {
+            bem_status s = prepare_tc(R.sub, st);
+            if (s != BEM_OK) return fail(c, s, R.sub->err);
+        }
+        return BEM_OK;
+    }
+    bem_status s = ensure_tc(c, c->op[0], st);
+    if (s != BEM_OK) return s;
+    if (c->tc_err_host && *(volatile int*)c->tc_err_host)
+        return fail(c, BEM_ETIMEOUT, "a tensor-core kernel gave up waiting for the tensor core (earlier call)");
+    return BEM_OK;
+}
+
 extern "C" bem_status bem_matvec(bem_ctx* c, const void* x, void* y, int nrhs, int dtype, void* stream) {
     if (!c) return BEM_EINVAL;
     if (!c->assembled) return fail(c, BEM_ESTATE, "bem_matvec needs bem_assemble");
@@ -1891,6 +2017,10 @@ extern "C" bem_status bem_matvec(bem_ctx* c, const void* x, void* y, int nrhs, i
     const char* xa = (const char*)x;
     const char* ya = (const char*)y;
     if (xa < ya + bytes && ya < xa + bytes) return fail(c, BEM_EINVAL, "x and y overlap");
+    if (dtype == BEM_C64_TC) {
+        bem_status s = prepare_tc(c, (cudaStream_t)stream);
+        if (s != BEM_OK) return s;
+    }
     CK(matvec_any(c, dtype, x, y, nrhs, (cudaStream_t)stream, true));
     return BEM_OK;
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -24,6 +25,8 @@
 #define BEM_MAX_NRHS 65535  // right-hand sides per call of an entry point that launches one grid row per vector
 #define BEM_ROW_GROUPS 1     // 64-thread groups per CTA of the rows kernel (one work slot each)
 #define BEM_ROW_TARGET_CTAS (48 * 152)  // rows-kernel CTAs aimed at per product (about 3 waves)
+#define BEM_TC_NR 64                   // right-hand sides per pass of the tensor-core product
+#define BEM_TC_ROW_TARGET (12 * 152)    // work slots of the tensor-core rows kernel (persistent CTAs take them in turn)
 
 // ---------------------------------------------------------------------------
 // complex arithmetic on interleaved (re, im) pairs
@@ -272,6 +275,36 @@ struct MatvecPlan {
     void* ypart;                 // pmax x 2ne partial rows (pmax > 1)
     unsigned int* arrive;        // nleaf arrival counters, zero between products
 };
+// Tensor-core product (matvec_tc.cu).  V^H x work: a task is up to 32 column pairs
+// of W (two ranks each) of the far blocks sharing one column cluster, all applied
+// to the same half (J or M) of the vectors.
+struct TcPair {
+    int64_t w;     // complex offset in the arena of the pair's W column pair (pair (kp, j) at w + 2 j)
+    int64_t trow;  // t row of the pair's first rank (the second follows)
+};
+struct TcVhxTask {
+    int c0, n;     // column cluster (tree positions)
+    int g;         // 0: x_J, 1: x_M
+    int npairs;    // 1..32
+    int pair0;     // first entry in the pair list
+    int pad[3];
+};
+struct TcPlan {
+    const TcVhxTask* tasks;
+    const TcPair* pairs;
+    int ntask;
+    int nsm;           // persistent CTAs (one per SM)
+    c64* xp;           // 2ne x 64 vectors, tree order
+    c64* t;            // t_len x 64
+    c64* ypart;        // pmax x 64 x 2ne partial rows (tree order)
+    int* counters;     // 2 work counters, zeroed before each pass
+    int* err;          // device-visible flag, 1 after a bounded wait ran out
+};
+// y = Z x for nrhs complex64 vectors in passes of 64 (rows schedule p, complex64
+// entries and factors); ev: NULL, or 6 events per pass as for matvec_run
+cudaError_t matvec_tc_run(const MatvecPlan& p, const TcPlan& tp, const void* near, const void* arena, const c64* x,
+                          c64* y, int nrhs, cudaStream_t st, const cudaEvent_t* ev);
+
 // ev: NULL, or 6 events per right-hand side recorded around the three kernels
 template <typename R>
 cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x,

@@ -160,10 +160,11 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 // ---------------------------------------------------------------------------
 // three-term TF32 splitting (FP32-level products on the TF32 tensor path)
 // ---------------------------------------------------------------------------
-// v = hi + lo with hi = v rounded to TF32 (10 explicit mantissa bits, nearest,
-// ties away) and lo = v - hi exact in FP32; the product a b is taken as
-// hi_a hi_b + hi_a lo_b + lo_a hi_b, whose dropped term lo_a lo_b and the TF32
-// reading of lo (truncated to 10 bits) leave a relative error of about 2^-21.
+// v ~ hi + lo with hi = v rounded to TF32 (10 explicit mantissa bits, nearest,
+// ties away) and lo = (v - hi) rounded to TF32 the same way (v - hi is exact in
+// FP32 and at most 2^-11 |v|); the product a b is taken as
+// hi_a hi_b + hi_a lo_b + lo_a hi_b, whose dropped term lo_a lo_b and the rounding
+// of lo leave a relative error of about 2^-22 per product.
 __device__ __forceinline__ uint32_t tf32_hi(float v) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
@@ -171,7 +172,7 @@ __device__ __forceinline__ uint32_t tf32_hi(float v) {
 }
 __device__ __forceinline__ void tf32_split(float v, uint32_t& hi, uint32_t& lo) {
     hi = tf32_hi(v);
-    lo = __float_as_uint(v - __uint_as_float(hi));
+    lo = tf32_hi(v - __uint_as_float(hi));
 }
 
 }  // namespace tc

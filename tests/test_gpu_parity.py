@@ -63,7 +63,7 @@ def make(B, v, t, k0=K0, eps=EPS, prec=3, leaf=32, eta=2.0, aca_tol=1e-6, **kw):
 
 
 def matvec(B, h, x, dtype):
-    ct = torch.complex64 if dtype == B.BEM_C64 else torch.complex128
+    ct = torch.complex128 if dtype == B.BEM_C128 else torch.complex64   # every other form takes complex64
     xd = torch.from_numpy(np.ascontiguousarray(x)).to(DEV, ct)
     nrhs = 1 if x.ndim == 1 else x.shape[1]
     if x.ndim == 2:
