@@ -319,31 +319,50 @@ def run_native(args, rank, world, dist):
     e2e = {"value": round(world * args.steps / (e2e_ms / 1e3), 2), "unit": UNIT,
            "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
            "d2h_bytes_per_step": int(yh.numel() * yh.element_size())}
-    # batched right-hand sides: every entry streamed once per chunk of 8 vectors
+    # batched right-hand sides: the CUDA-core forms stream the operator once per chunk
+    # of 8 vectors, the tensor-core form (BEM_C64_TC) once per pass of 64
     batched = {}
-    for nrhs in (8, 64):
+    entry_bytes = stats["matvec_bytes_c64"] - 8 * 2 * n  # entries only (vectors excluded)
+    for label, dtype, nrhs, chunk in (("cuda_cores_8", B.BEM_C64, 8, 8), ("cuda_cores_64", B.BEM_C64, 64, 8),
+                                      ("tensor_cores_64", B.BEM_C64_TC, 64, 64),
+                                      ("tensor_cores_128", B.BEM_C64_TC, 128, 64)):
         X = W.complex_normal(n, seed=3, nrhs=nrhs).astype(np.complex64)
         Xd = torch.from_numpy(np.ascontiguousarray(X.T)).to(dev)
         Yd = torch.empty_like(Xd)
-        kb_ = max(3, args.steps // (4 * nrhs))
+        kb_ = max(3, args.steps // (2 * nrhs))
         for _ in range(3):
-            B.bem_matvec(h64, Xd.data_ptr(), Yd.data_ptr(), nrhs, B.BEM_C64, sp)
+            B.bem_matvec(h64, Xd.data_ptr(), Yd.data_ptr(), nrhs, dtype, sp)
         torch.cuda.synchronize(dev)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        B.bem_profile_begin(h64)
         e0.record(stream)
         for _ in range(kb_):
-            B.bem_matvec(h64, Xd.data_ptr(), Yd.data_ptr(), nrhs, B.BEM_C64, sp)
+            B.bem_matvec(h64, Xd.data_ptr(), Yd.data_ptr(), nrhs, dtype, sp)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         bms = e0.elapsed_time(e1) / kb_
-        passes = (nrhs + 7) // 8
-        entry_bytes = stats["matvec_bytes_c64"] - 8 * 2 * n  # entries only (vectors excluded)
-        byt = passes * entry_bytes + 8 * 2 * n * nrhs
-        batched[str(nrhs)] = {"matvecs_per_s": round(world * nrhs / (bms / 1e3), 1), "ms_per_call": round(bms, 4),
-                              "calls": kb_, "operator_passes": passes,
-                              "hbm_gbps_algorithmic": round(byt / (bms * 1e-3) / 1e9, 1)}
+        pk_ms, pk_cnt = B.bem_profile_end(h64)
+        passes = (nrhs + chunk - 1) // chunk
+        byt = passes * entry_bytes + 8 * 2 * n * nrhs * 2   # operator once per pass, x read and y written once
+        rec = {"matvecs_per_s": round(world * nrhs / (bms / 1e3), 1), "ms_per_call": round(bms, 4),
+               "calls": kb_, "operator_passes": passes,
+               "hbm_gbps_algorithmic": round(byt / (bms * 1e-3) / 1e9, 1),
+               "hbm_frac_of_peak": round(byt / (bms * 1e-3) / 1e9 / peak, 4),
+               "kernel_ms_per_pass": {B.KERNEL_NAMES[i]: round(pk_ms[i] / max(1, pk_cnt[i]), 4) for i in range(3)}}
+        if dtype == B.BEM_C64_TC:
+            kbt = stats["kernel_bytes_tc"]
+            rec["kernel_gbps_algorithmic"] = {
+                B.KERNEL_NAMES[i]: round(kbt[i] / (pk_ms[i] / max(1, pk_cnt[i]) * 1e-3) / 1e9, 1)
+                for i in range(3) if pk_ms[i] > 0}
+            rec["t_bytes_per_pass"] = int(8 * stats["t_rows"] * 64)
+            ref8 = torch.empty_like(Xd[:8])
+            B.bem_matvec(h64, Xd[:8].data_ptr(), ref8.data_ptr(), 8, B.BEM_C64, sp)
+            torch.cuda.synchronize(dev)
+            d = (Yd[:8] - ref8).abs().max().item() / ref8.abs().max().item()
+            rec["max_abs_diff_vs_cuda_cores_rel"] = d
+        batched[label] = rec
     B.bem_destroy(h64)
 
     out = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -141,6 +141,12 @@ typedef struct {
     int64_t kernel_bytes_c128[3]; /* same for complex128 */
     int64_t matvec_bytes_bf16f;   /* same as matvec_bytes_c64 with the factors read as BF16 (BEM_C64_BF16F) */
     int64_t kernel_bytes_bf16f[3]; /* same as kernel_bytes_c64 for BEM_C64_BF16F */
+    int64_t matvec_bytes_tc;      /* one BEM_C64_TC pass of 64 vectors: every stored entry once, 64 vectors read
+                                     and 64 written (complex64) */
+    int64_t kernel_bytes_tc[3];   /* its kernels: gather (x read, tree-order copy written), V^H x (V factors,
+                                     the tree-order vectors once, t written: 64 values per t row), rows (dense
+                                     entries, U factors, t read, the tree-order vectors once, y written) */
+    int64_t t_rows;             /* t values per vector: sum over factored blocks of 2 (kA + 2 kB + kC) pairs */
     double assemble_ms;         /* wall time of the last bem_assemble */
     double assemble_phase_ms[BEM_PHASES]; /* its parts: see BEM_PHASE_* (ACA, near and plan summed over precisions) */
 } bem_stats;

@@ -57,7 +57,9 @@ class bem_stats(ctypes.Structure):
         ("singular_pairs", ctypes.c_int64), ("matvec_bytes_c64", ctypes.c_int64),
         ("matvec_bytes_c128", ctypes.c_int64), ("kernel_bytes_c64", ctypes.c_int64 * 3),
         ("kernel_bytes_c128", ctypes.c_int64 * 3),
-        ("matvec_bytes_bf16f", ctypes.c_int64), ("kernel_bytes_bf16f", ctypes.c_int64 * 3), ("assemble_ms", ctypes.c_double),
+        ("matvec_bytes_bf16f", ctypes.c_int64), ("kernel_bytes_bf16f", ctypes.c_int64 * 3),
+        ("matvec_bytes_tc", ctypes.c_int64), ("kernel_bytes_tc", ctypes.c_int64 * 3), ("t_rows", ctypes.c_int64),
+        ("assemble_ms", ctypes.c_double),
         ("assemble_phase_ms", ctypes.c_double * 5),
     ]
 
@@ -235,7 +237,7 @@ def bem_stats_get(ctx) -> dict:
     s = bem_stats()
     _check(ctx, lib.bem_stats_get(ctx, ctypes.byref(s)))
     d = {name: getattr(s, name) for name, _ in bem_stats._fields_}
-    for k in ("factor_entries", "kernel_bytes_c64", "kernel_bytes_c128", "kernel_bytes_bf16f"):
+    for k in ("factor_entries", "kernel_bytes_c64", "kernel_bytes_c128", "kernel_bytes_bf16f", "kernel_bytes_tc"):
         d[k] = list(getattr(s, k))
     d["assemble_phase_ms"] = dict(zip(PHASE_NAMES, s.assemble_phase_ms))
     return d

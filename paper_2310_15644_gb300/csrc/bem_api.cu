@@ -1442,6 +1442,9 @@ extern "C" bem_status bem_stats_get(const bem_ctx* cc, bem_stats* out) {
             out->matvec_bytes_c64 += q.matvec_bytes_c64;
             out->matvec_bytes_c128 += q.matvec_bytes_c128;
             out->matvec_bytes_bf16f += q.matvec_bytes_bf16f;
+            out->matvec_bytes_tc += q.matvec_bytes_tc;
+            out->t_rows += q.t_rows;
+            for (int k = 0; k < 3; ++k) out->kernel_bytes_tc[k] += q.kernel_bytes_tc[k];
         }
         out->ne = c->ne;
         out->nt = c->nt;
@@ -1488,10 +1491,18 @@ extern "C" bem_status bem_stats_get(const bem_ctx* cc, bem_stats* out) {
             out->kernel_bytes_bf16f[BEM_KERNEL_ROWS] = es * (3 * dense + 2 * nv) + 4 * fu;
             out->matvec_bytes_bf16f = es * (3 * dense + 2 * nv) + 4 * (fu + fv);
         }
-        if (p == 0)
+        if (p == 0) {
             out->matvec_bytes_c64 = bytes;
-        else
+            // tensor-core pass of BEM_TC_NR vectors
+            const int64_t V = es * nv * BEM_TC_NR, T = es * q.t_len * BEM_TC_NR;
+            out->matvec_bytes_tc = es * (3 * dense + fu + fv) + 2 * V;
+            out->kernel_bytes_tc[BEM_KERNEL_GATHER] = 2 * V;
+            out->kernel_bytes_tc[BEM_KERNEL_VHX] = es * fv + V + T;
+            out->kernel_bytes_tc[BEM_KERNEL_ROWS] = es * (3 * dense + fu) + T + 2 * V;
+            out->t_rows = q.t_len;
+        } else {
             out->matvec_bytes_c128 = bytes;
+        }
     }
     out->assemble_ms = c->assemble_ms;
     for (int i = 0; i < BEM_PHASES; ++i) out->assemble_phase_ms[i] = c->phase_ms[i];
