@@ -781,6 +781,42 @@ def run_multi_mesh(args, dev, stream, B, W, count=16):
     return out
 
 
+def run_tc_only(args):
+    """Tensor-core product of 64 vectors alone, W warm-up and K timed calls (one
+    process, one GPU): the command profiling captures of its kernels run."""
+    import torch
+
+    import paper_2310_15644_gb300.bem as B
+    import workloads as W
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    v, t = W.icosphere(LEVEL)
+    opt = B.bem_default_options()
+    opt.precision, opt.leaf_size, opt.eta, opt.aca_tol = B.BEM_PREC_C64, LEAF, ETA, ACA_TOL
+    h = B.bem_create(opt)
+    B.bem_set_mesh(h, v, t)
+    B.bem_set_media(h, K0, EPS)
+    B.bem_assemble(h, sp)
+    n = B.bem_num_unknowns(h)
+    X = torch.from_numpy(np.ascontiguousarray(W.complex_normal(n, seed=3, nrhs=64).astype(np.complex64).T)).to(dev)
+    Y = torch.empty_like(X)
+    for _ in range(args.warmup):
+        B.bem_matvec(h, X.data_ptr(), Y.data_ptr(), 64, B.BEM_C64_TC, sp)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        B.bem_matvec(h, X.data_ptr(), Y.data_ptr(), 64, B.BEM_C64_TC, sp)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    B.bem_destroy(h)
+    return {"workload": workload_name(LEVEL), "vectors": 64, "ms_per_call": round(ms, 4),
+            "matvecs_per_s": round(64 / (ms * 1e-3), 1)}
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the oracle alone on host cores
 # ---------------------------------------------------------------------------
@@ -826,6 +862,8 @@ def main():
     ap.add_argument("--no-multi", action="store_true", help="skip the 16-mesh graph batch")
     ap.add_argument("--no-layered", action="store_true", help="skip the coated (two-region) sphere")
     ap.add_argument("--no-planar", action="store_true", help="skip the 2-D operator assembly")
+    ap.add_argument("--tc-only", action="store_true",
+                    help="only the tensor-core product of 64 vectors (profiling captures of its kernels)")
     ap.add_argument("--level", type=int, default=5,
                     help="icosphere level (5 = the 61440-unknown workload; smaller levels for profiling captures)")
     args = ap.parse_args()
@@ -849,7 +887,7 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         tdist.init_process_group("nccl")
         dist = tdist
-    out = run_native(args, rank, world, dist)
+    out = run_tc_only(args) if args.tc_only else run_native(args, rank, world, dist)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

@@ -43,9 +43,20 @@ struct RowsPlan {
     int nslot = 0, pmax = 1;           // rows-kernel CTAs; most slots of one leaf
     DevBuf d_work_ptr, d_work_item, d_near_c0, d_near_n, d_near_off, d_pieces, d_ypart, d_arrive;
     DevBuf d_leaf_parts, d_slot_order, d_slot_leaf, d_slot_part;
+    // host copies (schedules built from this one, e.g. the tensor-core product's)
+    std::vector<int> h_wptr, h_witem, h_nc0, h_nn;
+    std::vector<int64_t> h_noff, h_scost;
+    std::vector<PieceDesc> h_pieces;
 };
 
 static void release_rows_plan(RowsPlan& r) {
+    r.h_wptr.clear();
+    r.h_witem.clear();
+    r.h_nc0.clear();
+    r.h_nn.clear();
+    r.h_noff.clear();
+    r.h_scost.clear();
+    r.h_pieces.clear();
     DevBuf* plan[] = {&r.d_work_ptr,   &r.d_work_item, &r.d_near_c0,  &r.d_near_n,     &r.d_near_off,
                       &r.d_pieces,     &r.d_ypart,     &r.d_arrive,   &r.d_leaf_parts,
                       &r.d_slot_order, &r.d_slot_leaf, &r.d_slot_part};
@@ -82,7 +93,8 @@ struct Operator {
     // tensor-core product (complex64 operator, passes of 64 vectors); built on first use
     bool tc_built = false;
     RowsPlan tcp;                      // rows schedule with BEM_TC_ROW_TARGET slots
-    DevBuf tc_tasks, tc_pairs, tc_xp, tc_t, tc_ypart, tc_counters;
+    DevBuf tc_tasks, tc_pairs, tc_xp, tc_t, tc_ypart, tc_vcta, tc_wcopy, tc_cta_slot_ptr, tc_cta_slots, tc_rec_ptr,
+        tc_recs;
     int tc_ntask = 0;
 };
 
@@ -260,7 +272,8 @@ static void release_operator(Operator& o) {
     release_rows_plan(o.fwd);
     release_rows_plan(o.adj);
     release_rows_plan(o.tcp);
-    DevBuf* tcb[] = {&o.tc_tasks, &o.tc_pairs, &o.tc_xp, &o.tc_t, &o.tc_ypart, &o.tc_counters};
+    DevBuf* tcb[] = {&o.tc_tasks, &o.tc_pairs, &o.tc_xp, &o.tc_t, &o.tc_ypart, &o.tc_vcta, &o.tc_wcopy,
+                     &o.tc_cta_slot_ptr, &o.tc_cta_slots, &o.tc_rec_ptr, &o.tc_recs};
     for (DevBuf* b : tcb) dfree(*b);
     o.tc_built = false;
     o.tc_ntask = 0;
@@ -1058,6 +1071,13 @@ static bem_status build_rows_plan(bem_ctx* c, const Operator& o, const std::vect
         d.t_off = R.off_t;
     }
     CK(upload(rp.d_pieces, pieces, st));
+    rp.h_wptr = wptr;
+    rp.h_witem = witem;
+    rp.h_nc0 = nc0;
+    rp.h_nn = nn;
+    rp.h_noff = noff;
+    rp.h_scost = scost;
+    rp.h_pieces = pieces;
     CK(dalloc(rp.d_ypart, es * 2 * c->ne * (rp.pmax > 1 ? rp.pmax : 1) * ypart_nr));
     CK(dalloc(rp.d_arrive, sizeof(unsigned int) * std::max(1, nleaf)));
     CK(cudaMemsetAsync(rp.d_arrive.p, 0, sizeof(unsigned int) * std::max(1, nleaf), st));
@@ -1685,7 +1705,7 @@ static bem_status ensure_tc(bem_ctx* c, Operator& o, cudaStream_t st) {
             }
         }
     }
-    std::vector<TcVhxTask> tasks;
+    std::vector<TcVhxTask> all;
     std::vector<TcPair> pairs;
     for (auto& kv : groups) {
         const auto& v = kv.second;
@@ -1697,23 +1717,110 @@ static bem_status ensure_tc(bem_ctx* c, Operator& o, cudaStream_t st) {
             T.npairs = (int)std::min<size_t>(32, v.size() - p0);
             T.pair0 = (int)pairs.size();
             for (int k = 0; k < T.npairs; ++k) pairs.push_back(v[p0 + k]);
-            tasks.push_back(T);
+            all.push_back(T);
         }
     }
-    std::stable_sort(tasks.begin(), tasks.end(), [](const TcVhxTask& a, const TcVhxTask& b) {
-        return (int64_t)a.n * a.npairs > (int64_t)b.n * b.npairs;
-    });
-    o.tc_ntask = (int)tasks.size();
-    CK(upload(o.tc_tasks, tasks, st));
-    CK(upload(o.tc_pairs, pairs, st));
+    // Longest-processing-time assignment of work to the persistent CTAs: heaviest
+    // first, each to the least loaded CTA (ties: lowest index); each CTA's share is
+    // contiguous, in the order assigned.
+    const int nsm = c->num_sms;
+    auto lpt = [nsm](const std::vector<int64_t>& cost, std::vector<std::vector<int>>& per) {
+        std::vector<int> order(cost.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        per.assign(nsm, {});
+        std::vector<int64_t> load(nsm, 0);
+        for (int i : order) {
+            int best = 0;
+            for (int q = 1; q < nsm; ++q)
+                if (load[q] < load[best]) best = q;
+            load[best] += cost[i];
+            per[best].push_back(i);
+        }
+    };
+    {
+        std::vector<int64_t> cost(all.size());
+        for (size_t i = 0; i < all.size(); ++i)  // K steps (one per 4 columns) plus a per-task epilogue
+            cost[i] = (int64_t)((all[i].n + 3) / 4) + 16;
+        std::vector<std::vector<int>> per;
+        lpt(cost, per);
+        std::vector<TcVhxTask> tasks;
+        std::vector<int> vptr(1, 0);
+        int64_t woff = 0;
+        for (int b = 0; b < nsm; ++b) {
+            for (int i : per[b]) {
+                TcVhxTask T = all[i];
+                T.wcopy = woff;
+                woff += (int64_t)((T.n + 31) / 32) * 32 * 32;
+                tasks.push_back(T);
+            }
+            vptr.push_back((int)tasks.size());
+        }
+        o.tc_ntask = (int)tasks.size();
+        CK(upload(o.tc_tasks, tasks, st));
+        CK(upload(o.tc_pairs, pairs, st));
+        CK(upload(o.tc_vcta, vptr, st));
+        CK(dalloc(o.tc_wcopy, sizeof(float4) * std::max<int64_t>(1, woff)));
+        CK(tc_build_wcopy((const TcVhxTask*)o.tc_tasks.p, o.tc_ntask, (const TcPair*)o.tc_pairs.p, (const c64*)o.arena.p,
+                          (float4*)o.tc_wcopy.p, st));
+    }
     bem_status s;
     if ((s = build_rows_plan(c, o, o.items, false, o.tcp, sizeof(c64), st, BEM_TC_ROW_TARGET, 1)) != BEM_OK)
         return s;
+    {
+        // rows: slots by LPT; per CTA its slots' item records, an end record after each slot
+        const RowsPlan& rp = o.tcp;
+        std::vector<std::vector<int>> per;
+        std::vector<int64_t> cost(rp.nslot);
+        for (int k = 0; k < rp.nslot; ++k)
+            cost[k] = rp.h_scost[k] + 2048 * (int64_t)(rp.h_wptr[k + 1] - rp.h_wptr[k]);  // + per-item overhead
+        lpt(cost, per);
+        std::vector<int> sptr(1, 0), slots, rptr(1, 0);
+        std::vector<TcRec> recs;
+        for (int b = 0; b < nsm; ++b) {
+            for (int k : per[b]) {
+                slots.push_back(k);
+                for (int w = rp.h_wptr[k]; w < rp.h_wptr[k + 1]; ++w) {
+                    const int item = rp.h_witem[w];
+                    TcRec r{};
+                    if (item >= 0) {
+                        const int n = rp.h_nn[item];
+                        for (int q = 0; q < 3; ++q) {
+                            r.base[q] = rp.h_noff[item] + q * rp.near_stride;
+                            r.npair[q] = (n + 1) / 2;
+                        }
+                        r.vec = rp.h_nc0[item];
+                        r.n = n;
+                        r.kind = 0;
+                        r.ld = -1;  // the leaf's rows (set by the kernel from the slot)
+                    } else {
+                        const PieceDesc& d = rp.h_pieces[-1 - item];
+                        for (int q = 0; q < 3; ++q) {
+                            r.base[q] = d.base[q];
+                            r.npair[q] = d.kp[q];
+                        }
+                        r.vec = d.t_off;
+                        r.ld = d.ld;
+                        r.kind = 1;
+                    }
+                    recs.push_back(r);
+                }
+                TcRec e{};
+                e.kind = 2;
+                recs.push_back(e);
+            }
+            sptr.push_back((int)slots.size());
+            rptr.push_back((int)recs.size());
+        }
+        CK(upload(o.tc_cta_slot_ptr, sptr, st));
+        CK(upload(o.tc_cta_slots, slots, st));
+        CK(upload(o.tc_rec_ptr, rptr, st));
+        CK(upload(o.tc_recs, recs, st));
+    }
     const size_t nn = 2 * (size_t)c->ne;
     CK(dalloc(o.tc_xp, sizeof(c64) * nn * BEM_TC_NR));
     CK(dalloc(o.tc_t, sizeof(c64) * std::max<int64_t>(1, o.t_len) * BEM_TC_NR));
     CK(dalloc(o.tc_ypart, sizeof(c64) * nn * BEM_TC_NR * (o.tcp.pmax > 1 ? o.tcp.pmax : 1)));
-    CK(dalloc(o.tc_counters, 2 * sizeof(int)));
     CK(cudaStreamSynchronize(st));
     o.tc_built = true;
     return BEM_OK;
@@ -1784,10 +1891,15 @@ static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int
         tp.pairs = (const TcPair*)o.tc_pairs.p;
         tp.ntask = o.tc_ntask;
         tp.nsm = c->num_sms;
+        tp.vcta_ptr = (const int*)o.tc_vcta.p;
+        tp.wcopy = (const float4*)o.tc_wcopy.p;
+        tp.cta_slot_ptr = (const int*)o.tc_cta_slot_ptr.p;
+        tp.cta_slots = (const int*)o.tc_cta_slots.p;
+        tp.cta_rec_ptr = (const int*)o.tc_rec_ptr.p;
+        tp.recs = (const TcRec*)o.tc_recs.p;
         tp.xp = (c64*)o.tc_xp.p;
         tp.t = (c64*)o.tc_t.p;
         tp.ypart = (c64*)o.tc_ypart.p;
-        tp.counters = (int*)o.tc_counters.p;
         tp.err = c->tc_err_dev;
         return matvec_tc_run(p, tp, o.near.p, o.arena.p, (const c64*)x, (c64*)y, nrhs, st, ev);
     }

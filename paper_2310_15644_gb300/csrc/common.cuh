@@ -283,23 +283,43 @@ struct TcPair {
     int64_t trow;  // t row of the pair's first rank (the second follows)
 };
 struct TcVhxTask {
-    int c0, n;     // column cluster (tree positions)
-    int g;         // 0: x_J, 1: x_M
-    int npairs;    // 1..32
-    int pair0;     // first entry in the pair list
-    int pad[3];
+    int c0, n;       // column cluster (tree positions)
+    int g;           // 0: x_J, 1: x_M
+    int npairs;      // 1..32
+    int pair0;       // first entry in the pair list
+    int pad;
+    int64_t wcopy;   // float4 offset of the task's W copy: chunk c, column j, pair p at wcopy + (32 c + j) 32 + p
+};
+// One work item of the tensor-core rows kernel, in the order a CTA processes them
+// (the items of each of its slots, then an end record)
+struct __align__(16) TcRec {
+    int64_t base[3];   // complex offsets of the operator parts A, B, C (dense entries, or the arena for far pieces)
+    int64_t vec;       // dense item: first column (tree position); far piece: t row of its t_A
+    int npair[3];      // column (rank) pairs per part
+    int ld;            // pair stride (rows of the leaf)
+    int n;             // dense item: columns
+    int kind;          // 0 dense item, 1 far piece, 2 end of slot
+    int pad[2];
 };
 struct TcPlan {
-    const TcVhxTask* tasks;
+    const TcVhxTask* tasks;   // grouped by CTA: CTA b takes [vcta_ptr[b], vcta_ptr[b + 1])
     const TcPair* pairs;
     int ntask;
-    int nsm;           // persistent CTAs (one per SM)
-    c64* xp;           // 2ne x 64 vectors, tree order
-    c64* t;            // t_len x 64
-    c64* ypart;        // pmax x 64 x 2ne partial rows (tree order)
-    int* counters;     // 2 work counters, zeroed before each pass
-    int* err;          // device-visible flag, 1 after a bounded wait ran out
+    int nsm;                  // persistent CTAs (one per SM)
+    const int* vcta_ptr;      // nsm + 1
+    const float4* wcopy;      // task-major copy of the W factors (see TcVhxTask::wcopy)
+    const int* cta_slot_ptr;  // nsm + 1: rows slots of CTA b at cta_slots[cta_slot_ptr[b] ..]
+    const int* cta_slots;
+    const int* cta_rec_ptr;   // nsm + 1: item records of CTA b
+    const TcRec* recs;
+    c64* xp;                  // 2ne x 64 vectors, tree order
+    c64* t;                   // t_len x 64
+    c64* ypart;               // pmax x 64 x 2ne partial rows (tree order)
+    int* err;                 // device-visible flag, 1 after a bounded wait ran out
 };
+// task-major copy of the W factors of the V^H x tasks
+cudaError_t tc_build_wcopy(const TcVhxTask* tasks, int ntask, const TcPair* pairs, const c64* arena, float4* wcopy,
+                           cudaStream_t st);
 // y = Z x for nrhs complex64 vectors in passes of 64 (rows schedule p, complex64
 // entries and factors); ev: NULL, or 6 events per pass as for matvec_run
 cudaError_t matvec_tc_run(const MatvecPlan& p, const TcPlan& tp, const void* near, const void* arena, const c64* x,

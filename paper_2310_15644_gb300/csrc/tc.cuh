@@ -56,6 +56,63 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
     return false;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// one arrival that also announces `bytes` of bulk copies completing on this barrier
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// bulk copies global -> shared (the tensor memory accelerator), completion
+// counted in bytes on an mbarrier; addresses 16-byte aligned, size a multiple of 16
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// L2 policy for data read once (evicted first)
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+// named barrier over `count` threads (a multiple of 32), id 1..15
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// signal arrival at a named barrier without waiting (the barrier completes when
+// `count` threads have arrived or synced on it)
+__device__ __forceinline__ void named_arrive(uint32_t id, uint32_t count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// the same barrier, returning the OR of `pred` over the participating threads (every
+// thread gets the same answer, so a decision taken from it keeps them in step)
+__device__ __forceinline__ bool named_sync_or(uint32_t id, uint32_t count, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
 // ---------------------------------------------------------------------------
 // tensor memory
 // ---------------------------------------------------------------------------
@@ -165,11 +222,11 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 // FP32 and at most 2^-11 |v|); the product a b is taken as
 // hi_a hi_b + hi_a lo_b + lo_a hi_b, whose dropped term lo_a lo_b and the rounding
 // of lo leave a relative error of about 2^-22 per product.
-__device__ __forceinline__ uint32_t tf32_hi(float v) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return r;
-}
+// Round to the nearest TF32 value, ties away from zero, on the bit pattern: add half
+// a unit of the 10th mantissa bit to the magnitude and clear the 13 bits below it
+// (a carry into the exponent is the correct rounding up; finite inputs only).  Two
+// integer operations instead of a conversion instruction.
+__device__ __forceinline__ uint32_t tf32_hi(float v) { return (__float_as_uint(v) + 0x1000u) & 0xFFFFE000u; }
 __device__ __forceinline__ void tf32_split(float v, uint32_t& hi, uint32_t& lo) {
     hi = tf32_hi(v);
     lo = tf32_hi(v - __uint_as_float(hi));
