@@ -26,7 +26,7 @@
 #define BEM_ROW_GROUPS 1     // 64-thread groups per CTA of the rows kernel (one work slot each)
 #define BEM_ROW_TARGET_CTAS (48 * 152)  // rows-kernel CTAs aimed at per product (about 3 waves)
 #define BEM_TC_NR 64                   // right-hand sides per pass of the tensor-core product
-#define BEM_TC_ROW_TARGET (12 * 152)    // work slots of the tensor-core rows kernel (persistent CTAs take them in turn)
+#define BEM_TC_ROW_TARGET (4 * 152)     // work slots of the tensor-core rows kernel (persistent CTAs take them in turn)
 
 // ---------------------------------------------------------------------------
 // complex arithmetic on interleaved (re, im) pairs

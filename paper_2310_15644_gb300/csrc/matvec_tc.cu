@@ -67,7 +67,7 @@ constexpr int TILE_ROWS_BYTES = 64 * 16;   // 64 vector rows x 16 bytes (one row
 
 // ---- rows kernel ---------------------------------------------------------------
 constexpr int RKS = 2;                     // K steps (4 complex columns each) per chunk
-constexpr int FLUSH_STEPS = 8;             // K steps between moves of the accumulators into registers
+constexpr int FLUSH_STEPS = 4;             // K steps between moves of the accumulators into registers
 constexpr int R_GROUPS = 8;                // vector row groups per tile (see above)
 constexpr int R_TILE_BYTES = 2 * R_GROUPS * TILE_ROWS_BYTES;       // one K step: 2 K chunks x 512 rows (16 KiB)
 constexpr int R_TILES_BYTES = 2 * RKS * R_TILE_BYTES;              // 2 buffers (64 KiB)
@@ -90,7 +90,8 @@ constexpr int V_TILES_BYTES = 2 * VKS * V_TILE_BYTES;              // 2 buffers 
 constexpr int V_W_BYTES = VCOLS * 32 * 16;                          // staged W: [column][32 pairs] x 16 bytes
 constexpr int V_STAGE_BYTES = V_W_BYTES + VCOLS * NR * 8;          // + vector rows (32.5 KiB)
 constexpr int VSTAGES = 3;
-constexpr int V_OUT_FLOATS = 4 * 16 * NR * 2;                      // 32 KiB epilogue staging
+constexpr int V_OUT_ROW = NR * 2 + 2;                              // staged t row (floats; padded: no bank conflicts)
+constexpr int V_OUT_FLOATS = 4 * 16 * V_OUT_ROW;                   // epilogue staging: 4 quadrants x 16 rank rows
 constexpr int V_SMEM_BYTES = V_TILES_BYTES + VSTAGES * V_STAGE_BYTES + V_OUT_FLOATS * 4 + 128;
 constexpr uint32_t VCOL_DH = 0, VCOL_DL = 64, VCOL_A = 128;
 constexpr int VFLUSH_STEPS = 16;
@@ -474,16 +475,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_rows(TcRowsArgs a) {
             int since = 0;
             for (;; ++chunk) {
                 const int buf = chunk & 1, sidx = chunk % RSTAGES;
-                if (since >= FLUSH_STEPS) {
-                    // drain, then move the accumulators into registers
-                    if (chunk > 0 && !failed) {
-                        const uint32_t last = chunk - 1;
-                        if (!tc::mbar_wait(&mma_bar[last & 1], (last >> 1) & 1, WAIT_LIMIT)) failed = true;
-                    }
-                    tc::fence_after_sync();
-                    if (!failed) flush_rows(tb, warp, rj, rm);
-                    since = 0;
-                }
+                // move the accumulators into registers before this chunk's MMAs (after its
+                // operands are built, so that the build overlaps the previous chunk's MMAs)
+                const bool do_flush = since >= FLUSH_STEPS;
+                if (do_flush) since = 0;
                 // after a failure the builders keep the arrival protocol but do no work
                 if (!failed && chunk >= 2 && !tc::mbar_wait(&mma_bar[buf], ((chunk >> 1) - 1) & 1, WAIT_LIMIT))
                     failed = true;
@@ -538,6 +533,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_rows(TcRowsArgs a) {
                         }
                         tc::fence_async_smem();
                     }
+                }
+                if (do_flush && h.kind == 0) {
+                    if (!failed) {
+                        const uint32_t last = chunk - 1;  // since > 0: an earlier chunk of this slot
+                        if (!tc::mbar_wait(&mma_bar[last & 1], (last >> 1) & 1, WAIT_LIMIT)) failed = true;
+                    }
+                    tc::fence_after_sync();
+                    if (!failed) flush_rows(tb, warp, rj, rm);
                 }
                 if (tid == 0) hdrb[buf] = h;  // for the issuer (kind 1 also after a failure: end of slot)
                 tc::fence_before_sync();
@@ -788,16 +791,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_vhx(TcVhxArgs va) {
             int since = 0;
             for (int c = 0; c < nch; ++c, ++chunk) {
                 const int ks = min(VKS, nsteps - VKS * c);
-                if (since >= VFLUSH_STEPS) {
-                    const uint32_t last = chunk - 1;
-                    if (!failed && !tc::mbar_wait(&mma_bar[last & 1], (last >> 1) & 1, WAIT_LIMIT)) failed = true;
-                    tc::fence_after_sync();
-                    if (!failed) {
-                        take_d();
-                        clear_d();
-                    }
-                    since = 0;
-                }
+                const bool do_flush = since >= VFLUSH_STEPS;  // as in the rows kernel: after the build
+                if (do_flush) since = 0;
                 since += ks;
                 const int buf = chunk & 1, sidx = chunk % VSTAGES;
                 if (!failed && chunk >= 2 && !tc::mbar_wait(&mma_bar[buf], ((chunk >> 1) - 1) & 1, WAIT_LIMIT))
@@ -805,36 +800,46 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_vhx(TcVhxArgs va) {
                 if (!failed && !tc::mbar_wait(&full[sidx], (chunk / VSTAGES) & 1, WAIT_LIMIT)) failed = true;
                 const unsigned char* st = stages + sidx * V_STAGE_BYTES;
                 if (!failed) {
-                    if (warp < 4) {
-                        const float4* wp = reinterpret_cast<const float4*>(st) + pr;  // column jl at wp[32 jl]
-                        const bool pv = pr < T.npairs;
+                    // warps w and w + 4 share TMEM quadrant w: w embeds the W rows of the even
+                    // K steps and builds the vector tiles of the odd ones, w + 4 the reverse
+                    const int par = warp < 4 ? 0 : 1;
+                    const float4* wp = reinterpret_cast<const float4*>(st) + pr;  // column jl at wp[32 jl]
+                    const bool pv = pr < T.npairs;
 #pragma unroll
-                        for (int s = 0; s < VKS; ++s) {
-                            if (s >= ks) break;
-                            // W[j, 2 pair + hh] for the 4 columns j of this K step
-                            float2 w4[4];
+                    for (int s = 0; s < VKS; ++s) {
+                        if (s >= ks) break;
+                        if ((s & 1) != par) continue;
+                        // W[j, 2 pair + hh] for the 4 columns j of this K step
+                        float2 w4[4];
 #pragma unroll
-                            for (int jj = 0; jj < 4; ++jj) {
-                                const int jl = 4 * s + jj;
-                                w4[jj] = make_float2(0.f, 0.f);
-                                if (pv && VCOLS * c + jl < T.n) {
-                                    const float4 v = wp[32 * jl];
-                                    w4[jj] = hh ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
-                                }
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int jl = 4 * s + jj;
+                            w4[jj] = make_float2(0.f, 0.f);
+                            if (pv && VCOLS * c + jl < T.n) {
+                                const float4 v = wp[32 * jl];
+                                w4[jj] = hh ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
                             }
-                            uint32_t hi[8], lo[8];
-                            embed_split(make_float4(w4[0].x, w4[0].y, w4[1].x, w4[1].y),
-                                        make_float4(w4[2].x, w4[2].y, w4[3].x, w4[3].y), dpart, hi, lo);
-                            tc::tmem_st8(tc::taddr(tb, 32 * warp, va_col(buf, s, 0)), hi);
-                            tc::tmem_st8(tc::taddr(tb, 32 * warp, va_col(buf, s, 1)), lo);
                         }
-                        tc::tmem_st_wait();
-                    } else {
-                        const float2* xs = reinterpret_cast<const float2*>(st + V_W_BYTES);
-                        for (int s = 0; s < ks; ++s)
-                            build_b_rows(tiles + (buf * VKS + s) * V_TILE_BYTES, 2, xs, 4 * s, VCOLS * c + 4 * s, T.n,
-                                         tid - 128, 0, -1);
-                        tc::fence_async_smem();
+                        uint32_t hi[8], lo[8];
+                        embed_split(make_float4(w4[0].x, w4[0].y, w4[1].x, w4[1].y),
+                                    make_float4(w4[2].x, w4[2].y, w4[3].x, w4[3].y), dpart, hi, lo);
+                        tc::tmem_st8(tc::taddr(tb, 32 * (warp & 3), va_col(buf, s, 0)), hi);
+                        tc::tmem_st8(tc::taddr(tb, 32 * (warp & 3), va_col(buf, s, 1)), lo);
+                    }
+                    const float2* xs = reinterpret_cast<const float2*>(st + V_W_BYTES);
+                    for (int s = 1 - par; s < ks; s += 2)
+                        build_b_rows(tiles + (buf * VKS + s) * V_TILE_BYTES, 2, xs, 4 * s, VCOLS * c + 4 * s, T.n,
+                                     tid & 127, 0, -1);
+                    tc::tmem_st_wait();
+                    tc::fence_async_smem();
+                }
+                if (do_flush) {
+                    const uint32_t last = chunk - 1;
+                    if (!failed && !tc::mbar_wait(&mma_bar[last & 1], (last >> 1) & 1, WAIT_LIMIT)) failed = true;
+                    tc::fence_after_sync();
+                    if (!failed) {
+                        take_d();
+                        clear_d();
                     }
                 }
                 tc::fence_before_sync();
@@ -856,21 +861,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_vhx(TcVhxArgs va) {
             take_d();
             {
                 // lane (rank slot, part) -> [16 slots of the quadrant][NR][re, im]
-                float* so = out + (warp & 3) * 16 * NR * 2;
+                float* so = out + (warp & 3) * 16 * V_OUT_ROW;
                 const int kl = lane >> 1;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) so[(kl * NR + cb + j) * 2 + dpart] = acc[j];
+                for (int j = 0; j < 32; ++j) so[kl * V_OUT_ROW + (cb + j) * 2 + dpart] = acc[j];
             }
             tc::named_sync(BAR_BUILD, NBUILD);
             if (warp < 4) {
-                const float* so = out + warp * 16 * NR * 2;
+                const float* so = out + warp * 16 * V_OUT_ROW;
                 // 16 rank rows of 512 bytes each, one row per step of the warp
                 for (int kl2 = 0; kl2 < 16; ++kl2) {
                     const int pp = 8 * warp + (kl2 >> 1);
                     if (pp >= T.npairs) break;
                     const int64_t trow = a.pairs[T.pair0 + pp].trow + (kl2 & 1);
-                    const float4 v = reinterpret_cast<const float4*>(so + kl2 * NR * 2)[lane];
-                    reinterpret_cast<float4*>(a.t + trow * NR)[lane] = v;
+                    const float2* src = reinterpret_cast<const float2*>(so + kl2 * V_OUT_ROW) + 2 * lane;
+                    const float2 u0 = src[0], u1 = src[1];
+                    reinterpret_cast<float4*>(a.t + trow * NR)[lane] = make_float4(u0.x, u0.y, u1.x, u1.y);
                 }
             }
             tc::fence_before_sync();
