@@ -395,6 +395,7 @@ def run_native(args, rank, world, dist):
             dt = time.perf_counter() - t0
             pa, pe, ps = B.bem_power(h, xs.data_ptr(), bd.data_ptr(), 1, sp)
             return {"form": label, "seconds": round(dt, 3), "solves_per_s": round(1.0 / dt, 3), "iterations": it,
+                    "ms_per_iteration": round(dt * 1e3 / max(1, it), 4),
                     "relative_residual": float(rel[0]), "converged": status == 0,
                     "Q_abs": pa[0] / np.pi, "Q_ext": pe[0] / np.pi, "Q_sca": ps[0] / np.pi}
 
@@ -404,6 +405,11 @@ def run_native(args, rank, world, dist):
             opt_s = dict(maxit=3000, gmres_restart=80)
             hs, _ = context(B.BEM_PREC_C64, **opt_s)
             solves.append(solve(hs, "complex64 GMRES, tol 1e-6"))
+            # GMRES overhead: time per iteration over the time of one product (restart products included)
+            solves[-1]["per_iteration_over_product"] = round(solves[-1]["ms_per_iteration"] / ms_per_step, 3)
+            if not args.no_batched_solve:
+                out["batched_solve"] = run_batched_solve(dev, stream, B, W, hs,
+                                                         batched["tensor_cores_64"]["ms_per_call"])
             B.bem_destroy(hs)
             h128, asm128_ms = context(B.BEM_PREC_C128)
             s128 = B.bem_stats_get(h128)
@@ -432,11 +438,29 @@ def run_native(args, rank, world, dist):
             out["rel_err_vs_oracle"] = float(np.abs(y64[rows] - ref).max() / scale)
             if "fp64_baseline" in out:
                 out["fp64_baseline"]["rel_err_vs_oracle"] = float(np.abs(y128[rows] - ref).max() / scale)
+            if "batched_solve" in out:
+                bs = out["batched_solve"]
+                Xh, bh = bs.pop("_x"), bs.pop("_b")
+                rows_b = sample_rows(g.ne, 2 * threads, seed=12)
+                zx, _ = oracle_rows(g, Xh, rows_b, threads)
+                res = np.abs(bh[rows_b] - zx).max(axis=0) / np.sqrt(np.mean(np.abs(bh) ** 2, axis=0))
+                from oracle import mie
+
+                q = mie.efficiencies_eps(K0, EPS)
+                bs["oracle_check"] = {
+                    "residual_rows": f"{len(rows_b)} sampled rows of b - Z x, Z the dense float64 PMCHWT rows",
+                    "max_row_residual_over_rms_b": [float(v_) for v_ in res],
+                    "mie": {"Q_abs": q["abs"], "Q_ext": q["ext"]},
+                    "Q_abs_rel_err_vs_mie": [abs(v_ - q["abs"]) / q["abs"] for v_ in bs["Q_abs"]],
+                    "Q_ext_rel_err_vs_mie": [abs(v_ - q["ext"]) / q["ext"] for v_ in bs["Q_ext"]]}
             out["cpu_baseline"] = {"value": round(len(rows) / dt / (2 * g.ne), 6), "unit": UNIT, "cores": threads,
                                    "kind": "oracle",
                                    "sample": f"{len(rows)} of {2 * g.ne} rows of the dense float64 PMCHWT product, "
                                              f"evaluated on the fly (numpy, {threads} threads), {dt:.1f} s",
                                    "error_metric": "max |y_gpu - y_oracle| over sampled rows / rms(y_gpu)"}
+        if "batched_solve" in out:
+            out["batched_solve"].pop("_x", None)
+            out["batched_solve"].pop("_b", None)
         if not args.no_large:
             out["large"] = run_large(args, dev, stream, B, W, peak, not args.no_cpu_baseline)
         if not args.no_multi:
@@ -446,6 +470,64 @@ def run_native(args, rank, world, dist):
         if not args.no_planar:
             out["planar"] = run_planar(args, dev, stream, B, W)
     return out
+
+
+# ---------------------------------------------------------------------------
+# batched solves: 64 plane waves on the sphere
+# ---------------------------------------------------------------------------
+def run_batched_solve(dev, stream, B, W, h, tc_ms):
+    """64 plane waves (Fibonacci-sphere directions, seeded random polarisations) on
+    the sphere, solved together by the batched GMRES (complex64, tol 1e-6, restart
+    80; products on the tensor cores), and 4 of them one at a time for comparison.
+    Returns timings, per-wave residuals and efficiencies; the solutions and
+    right-hand sides ride along under private keys for the oracle check."""
+    import torch
+
+    sp = stream.cuda_stream
+    n = 2 * B.bem_num_edges(h)
+    nw = 64
+    khat, e0 = W.plane_wave_batch(nw, seed=0)
+    bd = torch.empty((nw, n), dtype=torch.complex128, device=dev)
+    B.bem_rhs_planewave(h, khat, e0, bd.data_ptr(), B.BEM_C128, sp)
+    # warm-up: the tensor-core plan and one pass
+    xw = torch.zeros((nw, n), dtype=torch.complex64, device=dev)
+    yw = torch.empty_like(xw)
+    B.bem_matvec(h, xw.data_ptr(), yw.data_ptr(), nw, B.BEM_C64_TC, sp)
+    del xw, yw
+    xs = torch.zeros_like(bd)
+    torch.cuda.synchronize(dev)
+    p0 = B.bem_stats_get(h)["tc_passes"]
+    t0 = time.perf_counter()
+    it, rel, status = B.bem_solve(h, bd.data_ptr(), xs.data_ptr(), nw, sp, raise_on_noconv=False)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    passes = B.bem_stats_get(h)["tc_passes"] - p0
+    pa, pe, ps = B.bem_power(h, xs.data_ptr(), bd.data_ptr(), nw, sp)
+    # the same waves one at a time (first 4)
+    x1 = torch.zeros_like(bd[:4])
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    it1 = 0
+    for r in range(4):
+        i1, _, _ = B.bem_solve(h, bd[r].data_ptr(), x1[r].data_ptr(), 1, sp, raise_on_noconv=False)
+        it1 += i1
+    torch.cuda.synchronize(dev)
+    dt1 = time.perf_counter() - t1
+    d1 = float(((x1 - xs[:4]).abs().pow(2).sum(1).sqrt() / xs[:4].abs().pow(2).sum(1).sqrt()).max().item())
+    return {"workload": workload_name(LEVEL), "waves": nw,
+            "form": "batched complex64 GMRES(80), tol 1e-6, products on the tensor cores (BEM_C64_TC)",
+            "seconds": round(dt, 3), "solves_per_s": round(nw / dt, 2), "converged": status == 0,
+            "iterations_total": it, "iterations_mean": round(it / nw, 1),
+            "batched_iterations": int(passes),
+            "ms_per_batched_iteration": round(dt * 1e3 / max(1, passes), 3),
+            "tc_product_ms_64": tc_ms,
+            "per_iteration_over_product": round(dt * 1e3 / max(1, passes) / tc_ms, 3),
+            "relres_max": float(np.max(rel)), "relres": [float(v) for v in rel],
+            "Q_abs": [float(v) / np.pi for v in pa], "Q_ext": [float(v) / np.pi for v in pe],
+            "one_at_a_time": {"waves": 4, "seconds": round(dt1, 3), "solves_per_s": round(4 / dt1, 3),
+                              "iterations_total": it1, "max_rel_diff_vs_batched": d1},
+            "batched_speedup": round((nw / dt) / (4 / dt1), 2),
+            "_x": xs.cpu().numpy().T.copy(), "_b": bd.cpu().numpy().T.copy()}
 
 
 # ---------------------------------------------------------------------------
@@ -862,6 +944,7 @@ def main():
     ap.add_argument("--no-multi", action="store_true", help="skip the 16-mesh graph batch")
     ap.add_argument("--no-layered", action="store_true", help="skip the coated (two-region) sphere")
     ap.add_argument("--no-planar", action="store_true", help="skip the 2-D operator assembly")
+    ap.add_argument("--no-batched-solve", action="store_true", help="skip the 64-plane-wave batched solve")
     ap.add_argument("--tc-only", action="store_true",
                     help="only the tensor-core product of 64 vectors (profiling captures of its kernels)")
     ap.add_argument("--level", type=int, default=5,

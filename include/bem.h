@@ -94,7 +94,8 @@ typedef struct {
                             than the break-even m n / (m + n), is split into its children's block pairs
                             (stored densely once both clusters are leaves) */
     int gmres_restart;   /* GMRES restart length (default 50) */
-    int maxit;           /* maximum inner GMRES iterations in total (default 1000) */
+    int maxit;           /* maximum inner iterations: per right-hand side for GMRES, in total for the
+                            CG-type solvers (default 1000) */
     double tol;          /* inner GMRES relative residual tolerance (default 1e-6) */
     double refine_tol;   /* outer FP64 iterative-refinement target; 0 disables refinement (default 0) */
     int refine_maxit;    /* maximum outer refinement steps (default 10) */
@@ -103,7 +104,9 @@ typedef struct {
 
 /* Inner Krylov solvers (bem_options.solver).  maxit counts iterations: one product
  * per GMRES iteration, two per CGS, BiCGStab and CGNR iteration. */
-#define BEM_SOLVER_GMRES 0     /* restarted GMRES, classical Gram-Schmidt with reorthogonalisation */
+#define BEM_SOLVER_GMRES 0     /* restarted GMRES on all right-hand sides at once: one batched product per
+                                  iteration, classical Gram-Schmidt (second pass where the first cancels),
+                                  rotations and restarts on the device */
 #define BEM_SOLVER_CGS 1       /* conjugate gradient squared */
 #define BEM_SOLVER_BICGSTAB 2  /* stabilised bi-conjugate gradient */
 #define BEM_SOLVER_CGNR 3      /* conjugate gradient on Z^H Z x = Z^H b (uses the adjoint product; not with
@@ -149,6 +152,8 @@ typedef struct {
     int64_t t_rows;             /* t values per vector: sum over factored blocks of 2 (kA + 2 kB + kC) pairs */
     double assemble_ms;         /* wall time of the last bem_assemble */
     double assemble_phase_ms[BEM_PHASES]; /* its parts: see BEM_PHASE_* (ACA, near and plan summed over precisions) */
+    int64_t tc_passes;          /* tensor-core operator passes (64 vectors each) run since bem_assemble, by
+                                   bem_matvec with BEM_C64_TC and by batched solves */
 } bem_stats;
 
 /* Kernels of one product, in launch order (index into the profiling arrays). */
@@ -338,16 +343,23 @@ bem_status bem_rhs_planewave(bem_ctx* ctx, const double* khat, const bem_c128* e
                              void* b, int dtype, void* stream);
 
 /* Solve Z x = b for nrhs right-hand sides, b and x device complex128 2ne x nrhs.
- * Inner solver: restarted GMRES with FP64 inner products on the least precise
- * operator assembled (BF16 factors, else complex64, else complex128); if
- * refine_tol > 0 an outer loop recomputes r = b - Z x with FP64 vectors and sums
- * through the most precise operator assembled (complex128 entries, else the
- * complex64 entries and FP32 factors) and corrects x until |r|/|b| <= refine_tol.
+ * Inner solver: restarted GMRES on the least precise operator assembled (BF16
+ * factors, else complex64, else complex128), all right-hand sides together: each
+ * iteration applies the operator once to every active basis vector (the
+ * tensor-core product, BEM_C64_TC, for 16 or more right-hand sides of a complex64
+ * solve on an sm_103 device), and each right-hand side keeps its own basis,
+ * Hessenberg matrix and tolerance; inner products FP32 within a warp's rows and
+ * FP64 beyond (complex64 inner solves) or FP64 throughout (complex128).  The
+ * CG-type solvers (bem_options.solver) take the right-hand sides one at a time.
+ * If refine_tol > 0 an outer loop recomputes r = b - Z x with complex128 vectors
+ * through the most precise operator assembled (complex128 entries in FP64, else
+ * the complex64 entries and FP32 factors with double-float products and sums,
+ * about 2^-44 relative) and corrects x until |r|/|b| <= refine_tol.
  * x is used as the initial guess.
- * iters (host, may be NULL): total inner iterations; relres (host, may be NULL):
- * final relative residual per right-hand side (nrhs doubles), measured with the
- * most accurate operator available.  Synchronises `stream`.  BEM_ENOCONV if any
- * right-hand side misses its tolerance. */
+ * iters (host, may be NULL): total inner iterations over all right-hand sides;
+ * relres (host, may be NULL): final relative residual per right-hand side (nrhs
+ * doubles), measured with the most accurate operator available.  Synchronises
+ * `stream`.  BEM_ENOCONV if any right-hand side misses its tolerance. */
 bem_status bem_solve(bem_ctx* ctx, const void* b, void* x, int nrhs, void* stream, int* iters, double* relres);
 
 /* Solve Z^H lambda = g (the adjoint system of gradient computations) for nrhs

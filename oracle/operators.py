@@ -350,7 +350,8 @@ def operator_rows(rwg: RWG, k: complex, rows):
 
 
 def pmchwt_rows_apply(rwg: RWG, k0: float, eps_r: complex, x, rows, mu_r: complex = 1.0):
-    """Entries ``rows`` (indices into the 2ne unknowns) of Z @ x, Z never stored."""
+    """Entries ``rows`` (indices into the 2ne unknowns) of Z @ x, Z never stored
+    (x a vector, or a matrix of several right-hand sides as columns)."""
     ne = rwg.ne
     rows = np.asarray(rows, dtype=np.int64)
     k1, eta_r = media(k0, eps_r, mu_r)
@@ -358,7 +359,7 @@ def pmchwt_rows_apply(rwg: RWG, k0: float, eps_r: complex, x, rows, mu_r: comple
     T0, K0 = operator_rows(rwg, k0, edge_rows)
     T1, K1 = operator_rows(rwg, k1, edge_rows)
     xJ, xM = x[:ne], x[ne:]
-    out = np.empty(len(rows), dtype=np.complex128)
+    out = np.empty((len(rows),) + np.shape(x)[1:], dtype=np.complex128)
     for i, r in enumerate(rows):
         B = K0[i] + K1[i]
         if r < ne:

@@ -61,6 +61,7 @@ class bem_stats(ctypes.Structure):
         ("matvec_bytes_tc", ctypes.c_int64), ("kernel_bytes_tc", ctypes.c_int64 * 3), ("t_rows", ctypes.c_int64),
         ("assemble_ms", ctypes.c_double),
         ("assemble_phase_ms", ctypes.c_double * 5),
+        ("tc_passes", ctypes.c_int64),
     ]
 
 

@@ -98,11 +98,22 @@ struct Operator {
     int tc_ntask = 0;
 };
 
-struct GmresWork {
+struct GmresWork {  // the CG-type solvers' inner right-hand side and iterate
     int dtype = -1;
     int64_t n = 0;
-    int restart = 0;
-    DevBuf V, w, z, r, xin, rin, hpart, hdev, npart;
+    DevBuf xin, rin;
+};
+
+// workspace of the batched GMRES (gmres.cu): basis, iterate, right-hand sides and
+// the per-right-hand-side Hessenberg state for nrhs columns of n
+struct BgsWork {
+    int dtype = -1, nrhs = 0, m = 0, chunk = 0, nblk = 0;
+    int npart_cap = 0;  // partial norms per right-hand side that npart holds
+    int64_t n = 0;
+    DevBuf V, x, b, cplx, dbl, ints, part, npart;
+    DevBuf zr, rr, cn;         // refinement: Z x and b - Z x (complex128), column norms
+    int* host_active = nullptr;  // mapped host memory
+    int* dev_active = nullptr;
 };
 
 }  // namespace
@@ -139,6 +150,7 @@ struct bem_ctx {
     // reductions and small transfers
     DevBuf d_part, d_red, d_tmp_in, d_one, d_gl;
     GmresWork gw;
+    BgsWork bw;
     struct {
         int dtype = -1;
         int64_t n = 0;
@@ -161,6 +173,7 @@ struct bem_ctx {
     };
     std::vector<Region> regions;
     int num_sms = 0;              // persistent CTAs of the tensor-core kernels
+    int64_t tc_passes = 0;        // tensor-core operator passes since the last assembly
     int* tc_err_host = nullptr;   // set by a tensor-core kernel whose bounded wait ran out (mapped host memory)
     int* tc_err_dev = nullptr;
     DevBuf d_rx, d_ry;   // one region's operand and product
@@ -301,6 +314,7 @@ static void release_operator(Operator& o) {
 
 static void invalidate(bem_ctx* c) {
     c->assembled = false;
+    c->tc_passes = 0;
     for (int i = 0; i < 2; ++i) release_operator(c->op[i]);
 }
 
@@ -366,12 +380,14 @@ extern "C" void bem_destroy(bem_ctx* c) {
                       &c->d_tri_coef, &c->d_edge_tri, &c->d_edge_loc, &c->d_mid, &c->d_sing_ptr, &c->d_sing_b,
                       &c->d_sing_val, &c->d_perm, &c->d_leaf_r0, &c->d_leaf_m, &c->d_pos_leaf_lo,
                       &c->d_pos_leaf_m, &c->d_part, &c->d_trif,
-                      &c->d_red, &c->d_tmp_in, &c->d_one, &c->d_gl, &c->gw.V, &c->gw.w, &c->gw.z, &c->gw.r,
-                      &c->gw.xin, &c->gw.rin, &c->gw.hpart, &c->gw.hdev, &c->gw.npart, &c->cgw.v[0],
+                      &c->d_red, &c->d_tmp_in, &c->d_one, &c->d_gl,
+                      &c->gw.xin, &c->gw.rin, &c->cgw.v[0],
                       &c->cgw.v[1], &c->cgw.v[2], &c->cgw.v[3], &c->cgw.v[4], &c->cgw.v[5], &c->cgw.v[6],
-                      &c->cgw.v[7]};
+                      &c->cgw.v[7], &c->bw.V, &c->bw.x, &c->bw.b, &c->bw.cplx, &c->bw.dbl, &c->bw.ints,
+                      &c->bw.part, &c->bw.npart, &c->bw.zr, &c->bw.rr, &c->bw.cn};
     for (DevBuf* b : bufs) dfree(*b);
     if (c->tc_err_host) cudaFreeHost(c->tc_err_host);
+    if (c->bw.host_active) cudaFreeHost(c->bw.host_active);
     delete c;
 }
 
@@ -1464,6 +1480,7 @@ extern "C" bem_status bem_stats_get(const bem_ctx* cc, bem_stats* out) {
             out->matvec_bytes_bf16f += q.matvec_bytes_bf16f;
             out->matvec_bytes_tc += q.matvec_bytes_tc;
             out->t_rows += q.t_rows;
+            out->tc_passes += q.tc_passes;
             for (int k = 0; k < 3; ++k) out->kernel_bytes_tc[k] += q.kernel_bytes_tc[k];
         }
         out->ne = c->ne;
@@ -1525,6 +1542,7 @@ extern "C" bem_status bem_stats_get(const bem_ctx* cc, bem_stats* out) {
         }
     }
     out->assemble_ms = c->assemble_ms;
+    out->tc_passes = c->tc_passes;
     for (int i = 0; i < BEM_PHASES; ++i) out->assemble_phase_ms[i] = c->phase_ms[i];
     return BEM_OK;
 }
@@ -1858,16 +1876,15 @@ static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int
     if (layered(c)) return matvec_layered(c, dtype, x, y, nrhs, st, record, adjoint);
     const cudaEvent_t* ev = nullptr;
     if (record && c->prof) {
-        // 6 events per operator pass: chunks of 8, 4, 2, 1 right-hand sides (one pass
-        // per right-hand side for the FP64-sum form)
+        // 6 events per operator pass: chunks of 8, 4, 2, 1 right-hand sides (at most 4
+        // for the FP64-sum form)
         size_t passes = 0;
-        if (dtype == DT_C64_IN_FP64) {
-            passes = (size_t)nrhs;
-        } else if (dtype == BEM_C64_TC) {
+        if (dtype == BEM_C64_TC) {
             passes = (size_t)((nrhs + BEM_TC_NR - 1) / BEM_TC_NR);
         } else {
+            const int maxc = dtype == DT_C64_IN_FP64 ? 4 : 8;
             for (int left = nrhs; left > 0;) {
-                left -= left >= 8 ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1));
+                left -= (left >= 8 && maxc >= 8) ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1));
                 ++passes;
             }
         }
@@ -1885,6 +1902,7 @@ static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int
         if (adjoint) return cudaErrorInvalidValue;
         Operator& o = c->op[0];
         if (!o.tc_built) return cudaErrorNotReady;  // ensure_tc first
+        c->tc_passes += (nrhs + BEM_TC_NR - 1) / BEM_TC_NR;
         const MatvecPlan p = make_plan(c, o, false, true);
         TcPlan tp;
         tp.tasks = (const TcVhxTask*)o.tc_tasks.p;
@@ -1912,8 +1930,8 @@ static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int
                                  nrhs, o.t_len, st, ev, bf ? BEM_FORM_BF16F : BEM_FORM_NATIVE, adjoint);
     }
     if (dtype == DT_C64_IN_FP64) {
-        // complex128 vectors through the complex64 operator (its workspaces hold one
-        // complex128 right-hand side)
+        // complex128 vectors through the complex64 operator (double-float arithmetic,
+        // chunks of up to 4 right-hand sides)
         Operator& o = c->op[0];
         return matvec_run<double>(make_plan(c, o, adjoint), adjoint ? o.nearT.p : o.near.p, o.arena.p,
                                   (const c128*)x, (c128*)y, (c128*)o.xp.p, (c128*)o.t.p, nrhs, o.t_len, st, ev,
@@ -2218,105 +2236,273 @@ static bem_status norm_dev(bem_ctx* c, int dtype, const void* v, int64_t n, doub
     return BEM_OK;
 }
 
-static bem_status gmres_work(bem_ctx* c, int dtype, int restart) {
+// inner right-hand side and iterate of the CG-type solvers
+static bem_status krylov_work(bem_ctx* c, int dtype) {
     GmresWork& w = c->gw;
     int64_t n = 2 * c->ne;
-    if (w.dtype == dtype && w.n == n && w.restart == restart && w.V.p) return BEM_OK;
+    if (w.dtype == dtype && w.n == n && w.xin.p) return BEM_OK;
     size_t es = esize_of(dtype);
-    CK(dalloc(w.V, es * n * (restart + 1)));
-    CK(dalloc(w.w, es * n));
-    CK(dalloc(w.z, es * n));
-    CK(dalloc(w.r, es * n));
     CK(dalloc(w.xin, es * n));
     CK(dalloc(w.rin, es * n));
-    CK(dalloc(w.hpart, sizeof(c128) * NPART * (restart + 1)));
-    CK(dalloc(w.hdev, sizeof(c128) * (restart + 1)));
     w.dtype = dtype;
     w.n = n;
-    w.restart = restart;
+    return BEM_OK;
+}
+// ---------------------------------------------------------------------------
+// batched GMRES: all right-hand sides of a solve advance together, one product
+// call per iteration over every basis vector; Gram-Schmidt, rotations, residual
+// estimates and the restart's triangular solve run on the device (gmres.cu), and
+// the host reads one mapped counter per iteration, one iteration behind.
+// ---------------------------------------------------------------------------
+static bem_status bgs_ensure(bem_ctx* c, int dtype, int nrhs, int m, cudaStream_t st) {
+    BgsWork& w = c->bw;
+    const int64_t n = 2 * c->ne;
+    if (!w.host_active) {
+        CK(cudaHostAlloc((void**)&w.host_active, sizeof(int), cudaHostAllocMapped));
+        *w.host_active = 0;
+        CK(cudaHostGetDevicePointer((void**)&w.dev_active, w.host_active, 0));
+    }
+    if (w.dtype == dtype && w.n == n && w.nrhs == nrhs && w.m == m && w.V.p) return BEM_OK;
+    const size_t es = esize_of(dtype);
+    int chunk, nblk, chunk16, nblk16;
+    bgs_layout(n, nrhs, (int)es, &chunk, &nblk);
+    bgs_layout(n, nrhs, 16, &chunk16, &nblk16);  // complex128 column norms (col_norms2)
+    const int nblk_cap = std::max(nblk, nblk16);
+    const size_t nc = (size_t)nrhs * ((size_t)(m + 1) * m + 3 * (size_t)(m + 1) + 3 * (size_t)m);
+    CK(dalloc(w.V, es * n * nrhs * (m + 1)));
+    CK(dalloc(w.x, es * n * nrhs));
+    CK(dalloc(w.b, es * n * nrhs));
+    CK(dalloc(w.cplx, sizeof(c128) * nc));
+    CK(dalloc(w.dbl, sizeof(double) * 8 * nrhs));
+    CK(dalloc(w.ints, sizeof(int) * 4 * nrhs));
+    CK(dalloc(w.part, sizeof(c128) * nrhs * (m + 2) * (size_t)nblk));
+    CK(dalloc(w.npart, sizeof(double) * nrhs * (size_t)nblk_cap));
+    CK(dalloc(w.zr, sizeof(c128) * n * nrhs));
+    CK(dalloc(w.rr, sizeof(c128) * n * nrhs));
+    CK(dalloc(w.cn, sizeof(double) * nrhs));
+    CK(cudaMemsetAsync(w.ints.p, 0, sizeof(int) * 4 * nrhs, st));  // arrival counters start at zero
+    w.dtype = dtype;
+    w.n = n;
+    w.nrhs = nrhs;
+    w.m = m;
+    w.chunk = chunk;
+    w.nblk = nblk;
+    w.npart_cap = nblk_cap;
     return BEM_OK;
 }
 
-// solve Z x = rhs (dtype vectors in gw.rin / gw.xin), x starts at zero; absolute tolerance
-static bem_status gmres(bem_ctx* c, int pdt, double tol_abs, int maxit, int* iters, double* final_res,
-                        cudaStream_t st, bool adjoint = false) {
-    const int dtype = vec_dtype(pdt);  // vectors; pdt selects the product
-    GmresWork& w = c->gw;
+static BgsArgs bgs_args(bem_ctx* c, int maxit) {
+    BgsWork& w = c->bw;
+    BgsArgs a{};
+    const int nr = w.nrhs, m = w.m;
+    a.V = w.V.p;
+    a.x = w.x.p;
+    a.b = w.b.p;
+    a.n = w.n;
+    a.nrhs = nr;
+    a.m = m;
+    a.chunk = w.chunk;
+    a.nblk = w.nblk;
+    a.maxit = maxit;
+    // Hessenberg state in the vectors' precision: complex values of es bytes
+    const size_t es = esize_of(w.dtype);
+    char* cp = (char*)w.cplx.p;
+    a.H = cp;
+    cp += es * nr * (m + 1) * m;
+    a.g = cp;
+    cp += es * nr * (m + 1);
+    a.h1 = cp;
+    cp += es * nr * (m + 1);
+    a.h2 = cp;
+    cp += es * nr * (m + 1);
+    a.cs = cp;
+    cp += es * nr * m;
+    a.sn = cp;
+    cp += es * nr * m;
+    a.y = cp;
+    double* dp = (double*)w.dbl.p;
+    a.wn0 = dp;
+    a.wn1 = dp + nr;
+    a.wn2 = dp + 2 * nr;
+    a.beta = dp + 3 * nr;
+    a.tol = dp + 4 * nr;
+    a.scale = dp + 5 * nr;
+    a.res = dp + 6 * nr;
+    int* ip = (int*)w.ints.p;
+    a.cnt = (unsigned*)ip;
+    a.state = ip + nr;
+    a.kk = ip + 2 * nr;
+    a.it = ip + 3 * nr;
+    a.part = (c128*)w.part.p;
+    a.npart = (double*)w.npart.p;
+    a.host_active = w.dev_active;
+    return a;
+}
+
+// Z x = b for the nrhs columns of bw.b (dtype vectors), x (bw.x) from zero.
+// tol_abs: host, per right-hand side (infinity: leave it at zero); it_io: host,
+// iterations so far per right-hand side (updated; each stops at maxit);
+// beta_out: host, the true residual norm of the last restart per right-hand side.
+static bem_status gmres_batched(bem_ctx* c, int pdt, const double* tol_abs, int maxit, int* it_io, double* beta_out,
+                                cudaStream_t st, bool adjoint) {
+    BgsWork& w = c->bw;
+    const int nr = w.nrhs, m = w.m;
     const int64_t n = w.n;
-    const int m = w.restart;
-    const size_t es = esize_of(dtype);
+    const size_t es = esize_of(w.dtype);
+    const bool fp64 = w.dtype != BEM_C64;
+    BgsArgs a = bgs_args(c, maxit);
+    CK(cudaMemcpyAsync(a.tol, tol_abs, sizeof(double) * nr, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(a.it, it_io, sizeof(int) * nr, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(w.x.p, 0, es * n * nr, st));
     char* V = (char*)w.V.p;
-    CK(cudaMemsetAsync(w.xin.p, 0, es * n, st));
-    CK(cudaMemcpyAsync(w.r.p, w.rin.p, es * n, cudaMemcpyDeviceToDevice, st));
-    std::vector<c128> H((m + 1) * m), g(m + 1), cs(m), sn(m), hv(m + 1);
-    double beta;
-    bem_status s;
-    int it = 0;
-    while (true) {
-        if ((s = norm_dev(c, dtype, w.r.p, n, &beta, st)) != BEM_OK) return s;
-        if (!std::isfinite(beta))
-            return fail(c, BEM_ENOCONV, "non-finite GMRES residual (NaN or Inf in the operator or the right-hand side)");
-        if (beta <= tol_abs || it >= maxit) break;
-        CK(kv_scale_copy(w.r.p, dtype, 1.0 / beta, n, V, st));
-        std::fill(H.begin(), H.end(), mk<double>(0, 0));
-        std::fill(g.begin(), g.end(), mk<double>(0, 0));
-        g[0] = mk<double>(beta, 0);
-        int jl = -1;
+    const size_t slot = es * n * nr;
+    cudaEvent_t ev[2];
+    CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    struct GE {
+        cudaEvent_t* e;
+        ~GE() {
+            cudaEventDestroy(e[0]);
+            cudaEventDestroy(e[1]);
+        }
+    } gev{ev};
+    bool x_zero = true;
+    for (;;) {
+        // restart: slot 0 = b - Z x, normalised; which right-hand sides go on
+        if (!x_zero) CK(matvec_any(c, pdt, w.x.p, V, nr, st, false, adjoint));
+        CK(fp64 ? bgs_cycle_start<double>(a, x_zero, st) : bgs_cycle_start<float>(a, x_zero, st));
+        x_zero = false;
+        CK(cudaStreamSynchronize(st));
+        if (*(volatile int*)w.host_active == 0) break;
         for (int j = 0; j < m; ++j) {
-            CK(matvec_any(c, pdt, V + es * n * j, w.w.p, 1, st, false, adjoint));
-            for (int pass = 0; pass < 2; ++pass) {
-                CK(kv_multidot(V, dtype, n, j + 1, w.w.p, n, (c128*)w.hpart.p, NPART, st));
-                CK(kv_reduce_partials((const c128*)w.hpart.p, NPART, j + 1, (c128*)w.hdev.p, st));
-                CK(kv_update(w.w.p, V, dtype, n, j + 1, (const c128*)w.hdev.p, -1.0, n, st));
-                CK(cudaMemcpyAsync(hv.data(), w.hdev.p, sizeof(c128) * (j + 1), cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-                for (int i = 0; i <= j; ++i) H[i * m + j] = H[i * m + j] + hv[i];
+            CK(matvec_any(c, pdt, V + slot * j, V + slot * (j + 1), nr, st, false, adjoint));
+            CK(fp64 ? bgs_iteration<double>(a, j, st) : bgs_iteration<float>(a, j, st));
+            CK(cudaEventRecord(ev[j & 1], st));
+            if (j >= 1) {
+                // iteration j is queued: wait for j - 1 and stop once nothing is active
+                CK(cudaEventSynchronize(ev[(j - 1) & 1]));
+                if (*(volatile int*)w.host_active == 0) break;
             }
-            double hn;
-            if ((s = norm_dev(c, dtype, w.w.p, n, &hn, st)) != BEM_OK) return s;
-            H[(j + 1) * m + j] = mk<double>(hn, 0);
-            if (hn > 0) CK(kv_scale_copy(w.w.p, dtype, 1.0 / hn, n, V + es * n * (j + 1), st));
-            // previous rotations
-            for (int i = 0; i < j; ++i) {
-                c128 a = H[i * m + j], b = H[(i + 1) * m + j];
-                H[i * m + j] = cs[i] * a + sn[i] * b;
-                H[(i + 1) * m + j] = cconj(sn[i]) * mk<double>(-a.re, -a.im) + cs[i] * b;
-            }
-            c128 a = H[j * m + j], b = H[(j + 1) * m + j];
-            double na = std::sqrt(cabs2(a)), nb = std::sqrt(cabs2(b));
-            double t = std::sqrt(na * na + nb * nb);
-            if (na == 0) {
-                cs[j] = mk<double>(0, 0);
-                sn[j] = mk<double>(1, 0);
-            } else {
-                cs[j] = mk<double>(na / t, 0);
-                sn[j] = (1.0 / t) * (cdiv(a, mk<double>(na, 0)) * cconj(b));
-            }
-            H[j * m + j] = cs[j] * a + sn[j] * b;
-            H[(j + 1) * m + j] = mk<double>(0, 0);
-            g[j + 1] = cconj(sn[j]) * mk<double>(-g[j].re, -g[j].im);
-            g[j] = cs[j] * g[j];
-            ++it;
-            jl = j;
-            double res = std::sqrt(cabs2(g[j + 1]));
-            if (res <= tol_abs || it >= maxit || hn == 0) break;
         }
-        // y = H^-1 g, x += V y
-        int k = jl + 1;
-        std::vector<c128> y(k);
-        for (int i = k - 1; i >= 0; --i) {
-            c128 acc = g[i];
-            for (int l = i + 1; l < k; ++l) acc = acc - H[i * m + l] * y[l];
-            y[i] = cdiv(acc, H[i * m + i]);
-        }
-        CK(cudaMemcpyAsync(w.hdev.p, y.data(), sizeof(c128) * k, cudaMemcpyHostToDevice, st));
-        CK(kv_update(w.xin.p, V, dtype, n, k, (const c128*)w.hdev.p, 1.0, n, st));
-        // true residual
-        CK(matvec_any(c, pdt, w.xin.p, w.z.p, 1, st, false, adjoint));
-        CK(kv_sub(w.rin.p, w.z.p, w.r.p, dtype, n, st));
+        CK(fp64 ? bgs_cycle_end<double>(a, st) : bgs_cycle_end<float>(a, st));
     }
-    *iters += it;
-    *final_res = beta;
+    CK(cudaMemcpyAsync(it_io, a.it, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(beta_out, a.beta, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int r = 0; r < nr; ++r)
+        if (!std::isfinite(beta_out[r]))
+            return fail(c, BEM_ENOCONV,
+                        "non-finite GMRES residual (NaN or Inf in the operator or the right-hand side)");
+    return BEM_OK;
+}
+
+// Batched GMRES with optional FP64 refinement for nrhs right-hand sides (b, x device
+// complex128, column-major), in groups whose basis fits the workspace budget.
+static bem_status solve_gmres_batched(bem_ctx* c, const void* b, void* x, int nrhs, cudaStream_t st, int* iters,
+                                      double* relres, bool adjoint, int din, int dres) {
+    const int64_t n = 2 * c->ne;
+    const int vin = vec_dtype(din);
+    const int m = c->opt.gmres_restart;
+    const size_t per_rhs = (size_t)esize_of(vin) * n * (m + 1);
+    const size_t budget = (size_t)8 << 30;  // bytes of Krylov basis per group
+    int nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)nrhs, budget / per_rhs));
+    if (nb >= BEM_TC_NR) nb -= nb % BEM_TC_NR;
+    // many right-hand sides of a complex64 solve: the tensor-core product
+    int pin = din;
+    if (!adjoint && vin == BEM_C64 && nb >= BEM_TC_MIN_RHS && op_built(c, 0)) {
+        int dev = 0, mj = 0, mn = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&mj, cudaDevAttrComputeCapabilityMajor, dev));
+        CK(cudaDeviceGetAttribute(&mn, cudaDevAttrComputeCapabilityMinor, dev));
+        if (mj == 10 && mn == 3) {
+            bem_status s0 = prepare_tc(c, st);
+            if (s0 != BEM_OK) return s0;
+            pin = BEM_C64_TC;
+        }
+    }
+    int total_it = 0;
+    bool all_ok = true;
+    for (int r0 = 0; r0 < nrhs; r0 += nb) {
+        const int k = std::min(nb, nrhs - r0);
+        bem_status s;
+        if ((s = bgs_ensure(c, vin, k, m, st)) != BEM_OK) return s;
+        BgsWork& w = c->bw;
+        const c128* br = (const c128*)b + (size_t)r0 * n;
+        c128* xr = (c128*)x + (size_t)r0 * n;
+        unsigned* cnt = (unsigned*)w.ints.p;
+        double* cn = (double*)w.cn.p;
+        std::vector<double> bn(k), rn(k), rel(k, 0.0), tol_abs(k), fres(k);
+        std::vector<int> used(k, 0), before(k);
+        std::vector<char> stopped(k, 0), fin(k, 0), inner_ok(k, 1);
+        std::vector<double> xn(k);
+        CK(col_norms2(br, true, n, k, (double*)w.npart.p, w.npart_cap, cnt, cn, st));
+        CK(cudaMemcpyAsync(bn.data(), cn, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        CK(col_norms2(xr, true, n, k, (double*)w.npart.p, w.npart_cap, cnt, cn, st));
+        CK(cudaMemcpyAsync(xn.data(), cn, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        bool x_zero = true;  // the usual start: the first residual is b itself
+        for (int r = 0; r < k; ++r) x_zero = x_zero && xn[r] == 0.0;
+        for (int r = 0; r < k; ++r) {
+            if (!std::isfinite(bn[r])) return fail(c, BEM_EINVAL, "the right-hand side has non-finite entries");
+            bn[r] = std::sqrt(bn[r]);
+            if (bn[r] == 0) CK(cudaMemsetAsync(xr + (size_t)r * n, 0, sizeof(c128) * n, st));
+        }
+        const bool refine = c->opt.refine_tol > 0;
+        const int steps = refine ? c->opt.refine_maxit : 1;
+        for (int step = 0;; ++step) {
+            // r = b - Z x with the most accurate operator, for every column of the group
+            if (step == 0 && x_zero) {
+                CK(cudaMemcpyAsync(w.rr.p, br, sizeof(c128) * n * k, cudaMemcpyDeviceToDevice, st));
+            } else {
+                CK(matvec_any(c, dres, xr, w.zr.p, k, st, false, adjoint));
+                CK(kv_sub(br, w.zr.p, w.rr.p, BEM_C128, n * k, st));
+            }
+            CK(col_norms2(w.rr.p, true, n, k, (double*)w.npart.p, w.npart_cap, cnt, cn, st));
+            CK(cudaMemcpyAsync(rn.data(), cn, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            bool more = false;
+            for (int r = 0; r < k; ++r) {
+                rn[r] = std::sqrt(rn[r]);
+                if (bn[r] == 0) {
+                    rel[r] = 0;
+                    fin[r] = 1;
+                    continue;
+                }
+                rel[r] = rn[r] / bn[r];
+                fin[r] = refine ? rel[r] <= c->opt.refine_tol : step >= 1;
+                if (!fin[r] && !stopped[r] && step < steps) more = true;
+            }
+            if (!more) break;
+            for (int r = 0; r < k; ++r) {
+                const bool go = !fin[r] && !stopped[r] && bn[r] != 0;
+                tol_abs[r] = go ? c->opt.tol * rn[r] : HUGE_VAL;
+                before[r] = used[r];
+            }
+            // inner system Z d = r in the inner precision
+            if (vin == BEM_C64)
+                CK(kv_cast<float>(w.rr.p, BEM_C128, (c64*)w.b.p, n * k, st));
+            else
+                CK(cudaMemcpyAsync(w.b.p, w.rr.p, sizeof(c128) * n * k, cudaMemcpyDeviceToDevice, st));
+            if ((s = gmres_batched(c, pin, tol_abs.data(), c->opt.maxit, used.data(), fres.data(), st, adjoint)) !=
+                BEM_OK)
+                return s;
+            for (int r = 0; r < k; ++r) {
+                if (tol_abs[r] == HUGE_VAL) continue;
+                inner_ok[r] = fres[r] <= tol_abs[r] * 1.0000001;
+                if (used[r] >= c->opt.maxit || used[r] == before[r]) stopped[r] = 1;  // measured next, then left
+            }
+            CK(kv_axpy_c128(xr, w.x.p, vin, (const c128*)c->d_one.p, 1.0, n * k, 1, n * k, st));
+        }
+        for (int r = 0; r < k; ++r) {
+            total_it += used[r];
+            if (relres) relres[r0 + r] = rel[r];
+            const bool ok = bn[r] == 0 || (refine ? rel[r] <= c->opt.refine_tol : (bool)inner_ok[r]);
+            all_ok = all_ok && ok;
+        }
+    }
+    CK(cudaStreamSynchronize(st));
+    if (iters) *iters = total_it;
+    if (!all_ok) return fail(c, BEM_ENOCONV, "solver did not reach its tolerance");
     return BEM_OK;
 }
 
@@ -2476,7 +2662,13 @@ static bem_status solve_impl(bem_ctx* c, const void* b, void* x, int nrhs, void*
         if ((s0 = ensure_adjoint_for(c, dres, st)) != BEM_OK) return s0;
     }
     bem_status s;
-    if ((s = gmres_work(c, vin, c->opt.gmres_restart)) != BEM_OK) return s;
+    if (c->opt.solver == BEM_SOLVER_GMRES) {
+        CK(ensure(c->d_one, sizeof(c128)));
+        const c128 one1 = mk<double>(1, 0);
+        CK(cudaMemcpyAsync(c->d_one.p, &one1, sizeof(c128), cudaMemcpyHostToDevice, st));
+        return solve_gmres_batched(c, b, x, nrhs, st, iters, relres, adjoint, din, dres);
+    }
+    if ((s = krylov_work(c, vin)) != BEM_OK) return s;
     const int64_t n = 2 * c->ne;
     DevBuf zr, rr;
     struct G {
@@ -2523,11 +2715,8 @@ static bem_status solve_impl(bem_ctx* c, const void* b, void* x, int nrhs, void*
                 CK(cudaMemcpyAsync(c->gw.rin.p, rr.p, sizeof(c128) * n, cudaMemcpyDeviceToDevice, st));
             double fres;
             int before = total_it;
-            if (c->opt.solver == BEM_SOLVER_GMRES)
-                s = gmres(c, din, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st, adjoint);
-            else
-                s = cg_family(c, din, c->opt.solver, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st,
-                              adjoint);
+            s = cg_family(c, din, c->opt.solver, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st,
+                          adjoint);
             if (s != BEM_OK)
                 return s;
             inner_ok = fres <= c->opt.tol * rn * 1.0000001;

@@ -26,6 +26,7 @@
 #define BEM_ROW_GROUPS 1     // 64-thread groups per CTA of the rows kernel (one work slot each)
 #define BEM_ROW_TARGET_CTAS (48 * 152)  // rows-kernel CTAs aimed at per product (about 3 waves)
 #define BEM_TC_NR 64                   // right-hand sides per pass of the tensor-core product
+#define BEM_TC_MIN_RHS 16              // batched solves of at least this many right-hand sides use it
 #define BEM_TC_ROW_TARGET (4 * 152)     // work slots of the tensor-core rows kernel (persistent CTAs take them in turn)
 
 // ---------------------------------------------------------------------------
@@ -359,13 +360,47 @@ cudaError_t kv_reduce_real(const double* partial, int npart, int count, double* 
 cudaError_t kv_update(void* w, const void* V, int dtype, int64_t ld, int k, const c128* h, double sign, int64_t n,
                       cudaStream_t st);
 cudaError_t kv_norm2(const void* w, int dtype, int64_t n, double* out_partial, int npart, cudaStream_t st);
-cudaError_t kv_scale_copy(const void* w, int dtype, double s, int64_t n, void* v, cudaStream_t st);
 cudaError_t kv_axpy_c128(c128* y, const void* x, int dtype, const c128* coef, double sign, int64_t n, int k,
                          int64_t ld, cudaStream_t st);
 cudaError_t kv_sub(const void* b, const void* zx, void* r, int dtype, int64_t n, cudaStream_t st);
 // z = a x + b y + c w (null operands skipped; z may alias them)
 cudaError_t kv_lincomb(void* z, int dtype, c128 a, const void* x, c128 b, const void* y, c128 c, const void* w,
                        int64_t n, cudaStream_t st);
+
+// Batched GMRES on the device (gmres.cu).  Per right-hand side r (nrhs of them,
+// vectors n long, column r at offset r n of each block): basis V = (m + 1) blocks of
+// nrhs vectors, slot j + 1 receiving Z v_j.  The Hessenberg state is in the
+// vectors' precision R (cx<R> unless noted): H (m + 1) x m row-major, g (m + 1),
+// rotation cosines cs (m, real R) and sines sn (m), pass results h1, h2 (m + 1),
+// y (m); state bits below.
+#define BGS_ACTIVE 1
+#define BGS_REORTH 2
+struct BgsArgs {
+    void* V;            // (m + 1) x nrhs x n vectors (complex64 or complex128)
+    void* x;            // nrhs x n: the cycle corrections accumulate here
+    const void* b;      // nrhs x n: right-hand sides of the inner system
+    int64_t n;
+    int nrhs, m, chunk, nblk, maxit;
+    void *H, *g, *cs, *sn, *h1, *h2, *y;
+    c128* part;         // nrhs x (m + 2) x nblk partial inner products (FP64)
+    double *wn0, *wn1, *wn2, *beta, *tol, *scale, *res, *npart;  // npart: nrhs x nblk partial norms
+    int *state, *kk, *it;
+    unsigned* cnt;      // nrhs arrival counters (zero between launches)
+    int* host_active;   // host-mapped: right-hand sides still iterating
+};
+// CTA rows and CTAs per right-hand side for vectors of n complex values of esize bytes
+void bgs_layout(int64_t n, int nrhs, int esize, int* chunk, int* nblk);
+template <typename R>
+cudaError_t bgs_iteration(const BgsArgs& a, int j, cudaStream_t st);
+template <typename R>
+cudaError_t bgs_cycle_start(const BgsArgs& a, bool x_zero, cudaStream_t st);
+template <typename R>
+cudaError_t bgs_cycle_end(const BgsArgs& a, cudaStream_t st);
+// out[r] = |v_r|^2 (FP64 sums) for k columns of n complex64 (fp64: complex128)
+// values; npart holds k x npart_cap partials (at least the nblk of bgs_layout for
+// this element size, else cudaErrorInvalidValue), cnt k zeroed counters
+cudaError_t col_norms2(const void* v, bool fp64, int64_t n, int k, double* npart, int npart_cap, unsigned* cnt,
+                       double* out, cudaStream_t st);
 // layered bodies: xs = sign * x[edges] (both halves [J ; M] of every column) and
 // y[edges] += sign * ys; esize 8 (complex64) or 16 (complex128); edges distinct
 cudaError_t region_gather(const void* x, int esize, int64_t ne, const int* edges, const signed char* sign,

@@ -1,9 +1,10 @@
-// Vector kernels of the restarted GMRES driver: Gram-Schmidt inner products and
-// norms with FP64 accumulation (fixed reduction trees, so results do not depend
-// on scheduling), basis updates, casts between complex64 and complex128, and the
-// residual r = b - Z x of the iterative refinement.  The Krylov solve itself is
-// not in the paper (its Eq. 18 inverts the compressed operator directly); it is
-// the iterative counterpart applied to the same compressed product.
+// Vector kernels of the CG-type solvers, the iterative refinement and the
+// gradient's weighted sums: inner products and norms with FP64 accumulation
+// (fixed reduction trees, so results do not depend on scheduling), linear
+// combinations, casts between complex64 and complex128, and the residual
+// r = b - Z x.  The Krylov solves are not in the paper (its Eq. 18 inverts the
+// compressed operator directly); they are the iterative counterpart applied to
+// the same compressed product.  The batched GMRES has its own kernels (gmres.cu).
 #include "common.cuh"
 
 namespace bem {
@@ -174,23 +175,6 @@ cudaError_t kv_norm2(const void* w, int dtype, int64_t n, double* out_partial, i
         k_norm2<float><<<npart, 256, 0, st>>>((const c64*)w, n, out_partial);
     else
         k_norm2<double><<<npart, 256, 0, st>>>((const c128*)w, n, out_partial);
-    return cudaGetLastError();
-}
-
-// v = s * w
-template <typename R>
-__global__ void k_scale(const cx<R>* __restrict__ w, double s, int64_t n, cx<R>* __restrict__ v) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        v[i] = mk<R>((R)(w[i].re * s), (R)(w[i].im * s));
-}
-
-cudaError_t kv_scale_copy(const void* w, int dtype, double s, int64_t n, void* v, cudaStream_t st) {
-    int blocks = (int)((n + 255) / 256);
-    if (blocks > 4096) blocks = 4096;
-    if (dtype == BEM_C64)
-        k_scale<float><<<blocks, 256, 0, st>>>((const c64*)w, s, n, (c64*)v);
-    else
-        k_scale<double><<<blocks, 256, 0, st>>>((const c128*)w, s, n, (c128*)v);
     return cudaGetLastError();
 }
 

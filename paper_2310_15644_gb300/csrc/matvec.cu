@@ -22,6 +22,111 @@
 
 namespace bem {
 
+// Double-float numbers: value hi + lo with two FP32 numbers (|lo| <= ulp(hi) / 2
+// after each operation), about 44 significant bits.  They carry the FP64-sum form
+// of the complex64 operator (BEM_FORM_C64_IN_FP64, the residuals of iterative
+// refinement): FP32 entries times vectors kept to ~2^-44, summed with error-free
+// transformations (Knuth's TwoSum, Dekker's FastTwoSum, the product error of one
+// fused multiply-add) on the FP32 pipe instead of the GPU's much narrower FP64
+// pipe.  A product a b keeps a.hi b.hi exactly and the cross terms to FP32; the
+// lo * lo term (2^-48 relative) is dropped.
+struct df {
+    float hi, lo;
+    df() = default;
+    __host__ __device__ df(float h) : hi(h), lo(0.f) {}
+    __host__ __device__ df(float h, float l) : hi(h), lo(l) {}
+};
+__device__ __forceinline__ df operator+(df a, df b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);  // TwoSum: s + e = a.hi + b.hi exactly
+    e += a.lo + b.lo;
+    const float h = s + e;                     // FastTwoSum (|s| >= |e|)
+    return df(h, e - (h - s));
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);            // exact rounding error of p
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float h = p + e;
+    return df(h, e - (h - p));
+}
+__device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
+__device__ __forceinline__ df& operator-=(df& a, df b) { return a = a - b; }
+
+// Products with a stored entry.  In every product below the entry is the left
+// operand of `*` and the middle operand of cfma, and an entry is an FP32 value
+// widened with lo = 0: these overloads skip its lo terms and keep each entry x
+// vector product exact up to the vector's lo part (e = fma(b, hi, -p) is the exact
+// error of p = b hi), accumulating with one TwoSum per term and one renormalisation
+// per component.
+__device__ __forceinline__ void df_acc(df& a, float b, df c, bool neg) {
+    float p = b * c.hi;
+    float e = fmaf(b, c.hi, -p);
+    e = fmaf(b, c.lo, e);
+    if (neg) {
+        p = -p;
+        e = -e;
+    }
+    const float s = a.hi + p;
+    const float bb = s - a.hi;
+    const float t = (a.hi - (s - bb)) + (p - bb);  // TwoSum
+    a.hi = s;
+    a.lo += t + e;
+}
+__device__ __forceinline__ void df_norm(df& a) {
+    const float h = a.hi + a.lo;  // FastTwoSum
+    a.lo = a.lo - (h - a.hi);
+    a.hi = h;
+}
+__device__ __forceinline__ void cfma(cx<df>& a, cx<df> b, cx<df> c) {
+    df_acc(a.re, b.re.hi, c.re, false);
+    df_acc(a.re, b.im.hi, c.im, true);
+    df_acc(a.im, b.re.hi, c.im, false);
+    df_acc(a.im, b.im.hi, c.re, false);
+    df_norm(a.re);
+    df_norm(a.im);
+}
+__device__ __forceinline__ cx<df> operator*(cx<df> b, cx<df> c) {
+    cx<df> a = mk<df>(df(0.f), df(0.f));
+    cfma(a, b, c);
+    return a;
+}
+
+// warp shuffles of the arithmetic types (a double-float moves as two floats)
+template <typename T>
+__device__ __forceinline__ T xshfl(unsigned mask, T v, int o) {
+    return __shfl_xor_sync(mask, v, o);
+}
+template <>
+__device__ __forceinline__ df xshfl<df>(unsigned mask, df v, int o) {
+    return df(__shfl_xor_sync(mask, v.hi, o), __shfl_xor_sync(mask, v.lo, o));
+}
+
+// Element type of the caller's vectors for a product arithmetic R (double-float
+// products read and write complex128) and the conversions at the boundary.
+template <typename R>
+struct Caller {
+    using T = cx<R>;
+    static __device__ __forceinline__ cx<R> in(T v) { return v; }
+    static __device__ __forceinline__ T out(cx<R> v) { return v; }
+};
+template <>
+struct Caller<df> {
+    using T = c128;
+    static __device__ __forceinline__ df split(double v) {
+        const float h = (float)v;
+        return df(h, (float)(v - (double)h));
+    }
+    static __device__ __forceinline__ cx<df> in(c128 v) { return mk<df>(split(v.re), split(v.im)); }
+    static __device__ __forceinline__ c128 out(cx<df> v) {
+        return mk<double>((double)v.re.hi + (double)v.re.lo, (double)v.im.hi + (double)v.im.lo);
+    }
+};
+
 // Loads of two consecutive complex values of the stored operator, converted to
 // the arithmetic R of the product.  Storage F: complex64 (one 16-byte load),
 // complex128 (two), or BF16 pairs (one 8-byte load; far factors of the complex64
@@ -69,6 +174,10 @@ __device__ __forceinline__ c128 ld_cg(const c128* q) {
     double2 v = __ldcg(reinterpret_cast<const double2*>(q));
     return mk<double>(v.x, v.y);
 }
+__device__ __forceinline__ cx<df> ld_cg(const cx<df>* q) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(q));
+    return mk<df>(df(v.x, v.y), df(v.z, v.w));
+}
 
 // NR consecutive complex values (one vector entry for NR right-hand sides)
 template <typename R, int NR>
@@ -89,15 +198,15 @@ __device__ __forceinline__ void ldv(const cx<R>* __restrict__ q, cx<R> (&v)[NR])
 // xp[(pos) * NR + r] = x[r * 2ne + edge(pos)] for both halves (J: pos < ne, M: ne + pos),
 // conjugated for the adjoint product
 template <typename R, int NR, bool CONJ>
-__global__ void k_gather(const cx<R>* __restrict__ x, const int64_t* __restrict__ perm, cx<R>* __restrict__ xp,
-                         int ne) {
+__global__ void k_gather(const typename Caller<R>::T* __restrict__ x, const int64_t* __restrict__ perm,
+                         cx<R>* __restrict__ xp, int ne) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
     const int64_t e = perm[i];
     const int64_t nn = 2 * (int64_t)ne;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        cx<R> a = x[r * nn + e], b = x[r * nn + ne + e];
+        cx<R> a = Caller<R>::in(x[r * nn + e]), b = Caller<R>::in(x[r * nn + ne + e]);
         if (CONJ) {
             a.im = -a.im;
             b.im = -b.im;
@@ -189,15 +298,15 @@ __device__ __forceinline__ void vhx_unit(const FarRec* __restrict__ far, int2 un
 #pragma unroll
     for (int r = 0; r < NR; ++r)
         for (int o = 4; o > 0; o >>= 1) {
-            a0[r].re += __shfl_xor_sync(mask, a0[r].re, o);
-            a0[r].im += __shfl_xor_sync(mask, a0[r].im, o);
-            a1[r].re += __shfl_xor_sync(mask, a1[r].re, o);
-            a1[r].im += __shfl_xor_sync(mask, a1[r].im, o);
+            a0[r].re += xshfl(mask, a0[r].re, o);
+            a0[r].im += xshfl(mask, a0[r].im, o);
+            a1[r].re += xshfl(mask, a1[r].re, o);
+            a1[r].im += xshfl(mask, a1[r].im, o);
             if (op == 1) {
-                b0[r].re += __shfl_xor_sync(mask, b0[r].re, o);
-                b0[r].im += __shfl_xor_sync(mask, b0[r].im, o);
-                b1[r].re += __shfl_xor_sync(mask, b1[r].re, o);
-                b1[r].im += __shfl_xor_sync(mask, b1[r].im, o);
+                b0[r].re += xshfl(mask, b0[r].re, o);
+                b0[r].im += xshfl(mask, b0[r].im, o);
+                b1[r].re += xshfl(mask, b1[r].re, o);
+                b1[r].im += xshfl(mask, b1[r].im, o);
             }
         }
     if (jj == 0) {
@@ -301,15 +410,15 @@ __device__ __forceinline__ void vhx_unit_rhs(const FarRec* __restrict__ far, int
         const unsigned mask = 0xffu << (threadIdx.x & 24);
 #pragma unroll
         for (int o = NR; o < 8; o <<= 1) {
-            a0.re += __shfl_xor_sync(mask, a0.re, o);
-            a0.im += __shfl_xor_sync(mask, a0.im, o);
-            a1.re += __shfl_xor_sync(mask, a1.re, o);
-            a1.im += __shfl_xor_sync(mask, a1.im, o);
+            a0.re += xshfl(mask, a0.re, o);
+            a0.im += xshfl(mask, a0.im, o);
+            a1.re += xshfl(mask, a1.re, o);
+            a1.im += xshfl(mask, a1.im, o);
             if (op == 1) {
-                b0.re += __shfl_xor_sync(mask, b0.re, o);
-                b0.im += __shfl_xor_sync(mask, b0.im, o);
-                b1.re += __shfl_xor_sync(mask, b1.re, o);
-                b1.im += __shfl_xor_sync(mask, b1.im, o);
+                b0.re += xshfl(mask, b0.re, o);
+                b0.im += xshfl(mask, b0.im, o);
+                b1.re += xshfl(mask, b1.re, o);
+                b1.im += xshfl(mask, b1.im, o);
             }
         }
     }
@@ -411,15 +520,15 @@ __device__ __forceinline__ void uhx_unit(const FarRec* __restrict__ far, int2 un
 #pragma unroll
     for (int r = 0; r < NR; ++r)
         for (int o = 4; o > 0; o >>= 1) {
-            a0[r].re += __shfl_xor_sync(mask, a0[r].re, o);
-            a0[r].im += __shfl_xor_sync(mask, a0[r].im, o);
-            a1[r].re += __shfl_xor_sync(mask, a1[r].re, o);
-            a1[r].im += __shfl_xor_sync(mask, a1[r].im, o);
+            a0[r].re += xshfl(mask, a0[r].re, o);
+            a0[r].im += xshfl(mask, a0[r].im, o);
+            a1[r].re += xshfl(mask, a1[r].re, o);
+            a1[r].im += xshfl(mask, a1[r].im, o);
             if (op == 1) {
-                b0[r].re += __shfl_xor_sync(mask, b0[r].re, o);
-                b0[r].im += __shfl_xor_sync(mask, b0[r].im, o);
-                b1[r].re += __shfl_xor_sync(mask, b1[r].re, o);
-                b1[r].im += __shfl_xor_sync(mask, b1[r].im, o);
+                b0[r].re += xshfl(mask, b0[r].re, o);
+                b0[r].im += xshfl(mask, b0[r].im, o);
+                b1[r].re += xshfl(mask, b1[r].re, o);
+                b1[r].im += xshfl(mask, b1[r].im, o);
             }
         }
     if (jj == 0) {
@@ -638,8 +747,8 @@ template <typename R, typename NS, typename FS, int NR, bool ADJ>
 __global__ void __launch_bounds__(ROW_THREADS, (NR == 1 && sizeof(R) == 4) ? 16 : 1) k_rows(MatvecPlan p, const NS* __restrict__ near,
                                                       const FS* __restrict__ arena,
                                                       const cx<R>* __restrict__ xp, const cx<R>* __restrict__ t,
-                                                      cx<R>* __restrict__ y, cx<R>* __restrict__ ypart,
-                                                      unsigned int* __restrict__ arrive) {
+                                                      typename Caller<R>::T* __restrict__ y,
+                                                      cx<R>* __restrict__ ypart, unsigned int* __restrict__ arrive) {
     __shared__ bool s_last;
     const int slot = p.slot_order[blockIdx.x];
     const int leaf = p.slot_leaf[slot], part = p.slot_part[slot];
@@ -675,8 +784,8 @@ __global__ void __launch_bounds__(ROW_THREADS, (NR == 1 && sizeof(R) == 4) ? 16 
                     aJ[r].im = -aJ[r].im;
                     aM[r].im = -aM[r].im;
                 }
-                y[r * nn + e] = aJ[r];
-                y[r * nn + ne + e] = aM[r];
+                y[r * nn + e] = Caller<R>::out(aJ[r]);
+                y[r * nn + ne + e] = Caller<R>::out(aM[r]);
             }
         }
         return;
@@ -707,16 +816,17 @@ __global__ void __launch_bounds__(ROW_THREADS, (NR == 1 && sizeof(R) == 4) ? 16 
                 sj.im = -sj.im;
                 sm.im = -sm.im;
             }
-            y[r * nn + e] = sj;
-            y[r * nn + ne + e] = sm;
+            y[r * nn + e] = Caller<R>::out(sj);
+            y[r * nn + ne + e] = Caller<R>::out(sm);
         }
     }
     if (threadIdx.x == 0) arrive[leaf] = 0u;  // ready for the next product
 }
 
 template <typename R, typename NS, typename FS, int NR, bool ADJ>
-static cudaError_t product_chunk(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x,
-                                 cx<R>* y, cx<R>* xp, cx<R>* t, cudaStream_t st, const cudaEvent_t* e) {
+static cudaError_t product_chunk(const MatvecPlan& p, const void* near_entries, const void* arena,
+                                 const typename Caller<R>::T* x, typename Caller<R>::T* y, cx<R>* xp, cx<R>* t,
+                                 cudaStream_t st, const cudaEvent_t* e) {
     if (e) BEM_CUDA_TRY(cudaEventRecord(e[0], st));
     k_gather<R, NR, ADJ><<<(p.ne + 255) / 256, 256, 0, st>>>(x, p.perm, xp, p.ne);
     BEM_CUDA_TRY(cudaGetLastError());
@@ -739,22 +849,29 @@ static cudaError_t product_chunk(const MatvecPlan& p, const void* near_entries, 
     return cudaSuccess;
 }
 
-// Right-hand sides are processed in chunks of 8, 4, 2, 1: every chunk streams the
-// operator once and applies each loaded entry to all of its right-hand sides.
-template <typename R, typename NS, typename FS, bool ADJ>
-static cudaError_t matvec_chunks(const MatvecPlan& p, const void* near_entries, const void* arena, const cx<R>* x,
-                                 cx<R>* y, cx<R>* xp, cx<R>* t, int nrhs, cudaStream_t st, const cudaEvent_t* ev) {
+// Right-hand sides are processed in chunks of 8 (at most MAXC), 4, 2, 1: every
+// chunk streams the operator once and applies each loaded entry to all of its
+// right-hand sides.
+template <typename R, typename NS, typename FS, bool ADJ, int MAXC = 8>
+static cudaError_t matvec_chunks(const MatvecPlan& p, const void* near_entries, const void* arena,
+                                 const typename Caller<R>::T* x, typename Caller<R>::T* y, cx<R>* xp, cx<R>* t,
+                                 int nrhs, cudaStream_t st, const cudaEvent_t* ev) {
     const int64_t nn = 2 * (int64_t)p.ne;
     int r = 0, chunk = 0;
     while (r < nrhs) {
         const int left = nrhs - r;
-        const int nr = left >= 8 ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1));
+        const int nr = (left >= 8 && MAXC >= 8) ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1));
         const cudaEvent_t* e = ev ? ev + 6 * chunk : nullptr;
-        const cx<R>* xr = x + r * nn;
-        cx<R>* yr = y + r * nn;
+        const typename Caller<R>::T* xr = x + r * nn;
+        typename Caller<R>::T* yr = y + r * nn;
         cudaError_t err;
         switch (nr) {
-            case 8: err = product_chunk<R, NS, FS, 8, ADJ>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
+            case 8:
+                if constexpr (MAXC >= 8) {
+                    err = product_chunk<R, NS, FS, 8, ADJ>(p, near_entries, arena, xr, yr, xp, t, st, e);
+                    break;
+                }
+                [[fallthrough]];
             case 4: err = product_chunk<R, NS, FS, 4, ADJ>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
             case 2: err = product_chunk<R, NS, FS, 2, ADJ>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
             default: err = product_chunk<R, NS, FS, 1, ADJ>(p, near_entries, arena, xr, yr, xp, t, st, e); break;
@@ -779,19 +896,13 @@ cudaError_t matvec_run(const MatvecPlan& p, const void* near_entries, const void
         if (form != BEM_FORM_NATIVE) return cudaErrorInvalidValue;
     } else {
         if (form == BEM_FORM_C64_IN_FP64) {
-            // complex64 operator applied in FP64 (residuals of iterative refinement);
-            // one right-hand side per pass
-            const int64_t nn = 2 * (int64_t)p.ne;
-            for (int r = 0; r < nrhs; ++r) {
-                const cudaEvent_t* e = ev ? ev + 6 * r : nullptr;
-                cudaError_t err =
-                    adjoint ? product_chunk<double, c64, c64, 1, true>(p, near_entries, arena, x + r * nn, y + r * nn,
-                                                                       xp, t, st, e)
-                            : product_chunk<double, c64, c64, 1, false>(p, near_entries, arena, x + r * nn,
-                                                                        y + r * nn, xp, t, st, e);
-                if (err != cudaSuccess) return err;
-            }
-            return cudaSuccess;
+            // complex64 operator applied to complex128 vectors with double-float
+            // products and sums (residuals of iterative refinement); the complex64
+            // workspaces (8 values of 8 bytes per unknown) hold 4 right-hand sides
+            cx<df>* xd = reinterpret_cast<cx<df>*>(xp);
+            cx<df>* td = reinterpret_cast<cx<df>*>(t);
+            if (adjoint) return matvec_chunks<df, c64, c64, true, 4>(p, near_entries, arena, x, y, xd, td, nrhs, st, ev);
+            return matvec_chunks<df, c64, c64, false, 4>(p, near_entries, arena, x, y, xd, td, nrhs, st, ev);
         }
         if (form != BEM_FORM_NATIVE) return cudaErrorInvalidValue;
     }
