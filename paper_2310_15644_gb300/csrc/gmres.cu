@@ -12,8 +12,11 @@
 // solve (Woodbury inverse, Section III) in iterative form.
 //
 // Orthogonalisation: classical Gram-Schmidt, h = V^H w, w -= V h, repeated for a
-// right-hand side only when the first pass cancelled most of w
-// (|w_after| < 0.7 |w_before|, the "twice is enough" test).  Precision follows the
+// right-hand side only when the first pass cancelled nearly all of w
+// (|w_after| < 0.22 |w_before|; a second pass then restores orthogonality to
+// working precision, "twice is enough").  Without it, the orthogonality lost in
+// one step is about eps |w_before|^2 / |w_after|^2 <= 20 eps, below the accuracy
+// the FP32 basis stores anyway.  Precision follows the
 // vectors (R = float for complex64, double for complex128): products and sums
 // over a thread's rows and a warp's lanes (a pairwise tree) in R, sums across
 // warps and CTAs in FP64 in a fixed order (results do not depend on scheduling);
@@ -36,8 +39,9 @@ namespace {
 constexpr int BG_THREADS = 256;
 constexpr int BG_WARPS = BG_THREADS / 32;
 constexpr int BG_LD = 4;               // 16-byte loads per vector per thread (at most)
-constexpr int QG = 4;                  // basis vectors per step of the Gram-Schmidt loops
-constexpr double REORTH_KEEP2 = 0.49;  // second pass if |w_after|^2 < 0.49 |w_before|^2
+constexpr int QG = 4;                  // basis vectors per step of the inner-product loop
+constexpr int QGU = 8;                 // basis vectors per step of the update loop
+constexpr double REORTH_KEEP2 = 0.05;  // second pass if |w_after|^2 < 0.05 |w_before|^2
 
 // 16-byte packs of complex values
 template <typename R>
@@ -111,25 +115,31 @@ __device__ __forceinline__ double warp_sum_blocks(const double* p, int nblk, int
 
 // h[q] = sum_i conj(V_q[i]) w[i] for q <= j (and |w|^2 in pass 1), w = basis slot
 // j + 1 of right-hand side r (the product's output).  Pass 1 runs for the active
-// right-hand sides, pass 2 for those flagged for a second pass.
+// right-hand sides, pass 2 for those flagged for a second pass.  CTA (blk, s) of a
+// right-hand side takes rows chunk blk and basis vectors [s qs, (s + 1) qs): with
+// few right-hand sides the basis is split too, so that enough loads are in flight.
 template <typename R>
-__global__ void __launch_bounds__(BG_THREADS) k_bgs_dot(BgsArgs a, int j, int pass) {
+__global__ void __launch_bounds__(BG_THREADS) k_bgs_dot(BgsArgs a, int j, int pass, int qs) {
     constexpr int PC = Pk<R>::PC;
-    extern __shared__ double sh[];  // [(j + 2)][BG_WARPS][2]
+    extern __shared__ double sh[];  // [qs + 1][BG_WARPS][2]
     __shared__ int s_flag;
     const int r = blockIdx.y;
     const int flag = a.state[r];
     if (!(flag & (pass == 1 ? BGS_ACTIVE : BGS_REORTH))) return;
+    const int blk = blockIdx.x % a.nblk, sl = blockIdx.x / a.nblk;
+    const int nslab = gridDim.x / a.nblk;
     const int64_t n = a.n;
     const cx<R>* V = reinterpret_cast<const cx<R>*>(a.V) + (int64_t)r * n;
     const int64_t slot = (int64_t)a.nrhs * n;
     const cx<R>* w = V + (int64_t)(j + 1) * slot;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t row0 = (int64_t)blk * a.chunk;
+    auto urow = [&](int k) { return row0 + ((int64_t)threadIdx.x + (int64_t)k * BG_THREADS) * PC; };
     cx<R> wv[BG_LD][PC];
     R nrm = 0;
 #pragma unroll
     for (int k = 0; k < BG_LD; ++k) {
-        const int64_t i = unit_row<R>(a, k);
+        const int64_t i = urow(k);
         if (unit_ok<R>(a, k, i)) {
             Pk<R>::ld(w + i, wv[k]);
         } else {
@@ -140,17 +150,18 @@ __global__ void __launch_bounds__(BG_THREADS) k_bgs_dot(BgsArgs a, int j, int pa
         for (int p = 0; p < PC; ++p) nrm += wv[k][p].re * wv[k][p].re + wv[k][p].im * wv[k][p].im;
     }
     const int nq = j + 1;
-    for (int q = 0; q < nq; q += QG) {
+    const int q0 = sl * qs, q1 = min(nq, q0 + qs);
+    for (int q = q0; q < q1; q += QG) {
         cx<R> acc[QG];
 #pragma unroll
         for (int u = 0; u < QG; ++u) acc[u] = mk<R>(0, 0);
 #pragma unroll
         for (int k = 0; k < BG_LD; ++k) {
-            const int64_t i = unit_row<R>(a, k);
-            if (!unit_ok<R>(a, k, i)) continue;
+            const int64_t i = urow(k);
+            if (!(k * BG_THREADS * PC < a.chunk && i < n)) continue;
 #pragma unroll
             for (int u = 0; u < QG; ++u) {
-                if (q + u >= nq) continue;
+                if (q + u >= q1) continue;
                 cx<R> v[PC];
                 Pk<R>::ld(V + (int64_t)(q + u) * slot + i, v);
 #pragma unroll
@@ -165,31 +176,35 @@ __global__ void __launch_bounds__(BG_THREADS) k_bgs_dot(BgsArgs a, int j, int pa
         if (lane == 0) {
 #pragma unroll
             for (int u = 0; u < QG; ++u)
-                if (q + u < nq) {
-                    sh[((q + u) * BG_WARPS + warp) * 2] = (double)acc[u].re;
-                    sh[((q + u) * BG_WARPS + warp) * 2 + 1] = (double)acc[u].im;
+                if (q + u < q1) {
+                    sh[((q + u - q0) * BG_WARPS + warp) * 2] = (double)acc[u].re;
+                    sh[((q + u - q0) * BG_WARPS + warp) * 2 + 1] = (double)acc[u].im;
                 }
         }
     }
     nrm = warp_sum(nrm);
     if (lane == 0) {
-        sh[(nq * BG_WARPS + warp) * 2] = (double)nrm;
-        sh[(nq * BG_WARPS + warp) * 2 + 1] = 0.0;
+        sh[(qs * BG_WARPS + warp) * 2] = (double)nrm;
+        sh[(qs * BG_WARPS + warp) * 2 + 1] = 0.0;
     }
     __syncthreads();
     const int stride = a.m + 2;
     double* part = reinterpret_cast<double*>(a.part);  // [r][q][blk][re, im]
-    for (int q = threadIdx.x; q <= nq; q += BG_THREADS) {
+    // this CTA's basis vectors, and |w|^2 (slab 0 only) at q = nq
+    for (int t = threadIdx.x; t <= q1 - q0; t += BG_THREADS) {
+        const int q = t < q1 - q0 ? q0 + t : nq;
+        const int ts = t < q1 - q0 ? t : qs;
+        if (q == nq && sl != 0) continue;
         double re = 0, im = 0;
         for (int u = 0; u < BG_WARPS; ++u) {
-            re += sh[(q * BG_WARPS + u) * 2];
-            im += sh[(q * BG_WARPS + u) * 2 + 1];
+            re += sh[(ts * BG_WARPS + u) * 2];
+            im += sh[(ts * BG_WARPS + u) * 2 + 1];
         }
-        double* d = part + 2 * (((int64_t)r * stride + q) * a.nblk + blockIdx.x);
+        double* d = part + 2 * (((int64_t)r * stride + q) * a.nblk + blk);
         d[0] = re;
         d[1] = im;
     }
-    if (!last_arrival(a.cnt + r, a.nblk, &s_flag)) return;
+    if (!last_arrival(a.cnt + r, a.nblk * nslab, &s_flag)) return;
     cx<R>* h = reinterpret_cast<cx<R>*>(pass == 1 ? a.h1 : a.h2) + (int64_t)r * (a.m + 1);
     for (int q = warp; q <= nq; q += BG_WARPS) {
         const double* d = part + 2 * ((int64_t)r * stride + q) * a.nblk;
@@ -237,16 +252,16 @@ __global__ void __launch_bounds__(BG_THREADS) k_bgs_update(BgsArgs a, int j, int
             for (int p = 0; p < PC; ++p) wv[k][p] = mk<R>(0, 0);
         }
     }
-    for (int q = 0; q < nq; q += QG) {
-        cx<R> c[QG];
+    for (int q = 0; q < nq; q += QGU) {
+        cx<R> c[QGU];
 #pragma unroll
-        for (int u = 0; u < QG; ++u) c[u] = q + u < nq ? hc[q + u] : mk<R>(0, 0);
+        for (int u = 0; u < QGU; ++u) c[u] = q + u < nq ? hc[q + u] : mk<R>(0, 0);
 #pragma unroll
         for (int k = 0; k < BG_LD; ++k) {
             const int64_t i = unit_row<R>(a, k);
             if (!unit_ok<R>(a, k, i)) continue;
 #pragma unroll
-            for (int u = 0; u < QG; ++u) {
+            for (int u = 0; u < QGU; ++u) {
                 if (q + u >= nq) continue;
                 cx<R> v[PC];
                 Pk<R>::ld(V + (int64_t)(q + u) * slot + i, v);
@@ -294,12 +309,32 @@ __global__ void __launch_bounds__(BG_THREADS) k_bgs_update(BgsArgs a, int j, int
 // Krylov space is exhausted (|w| = 0), at the restart length or at the iteration
 // cap; `scale` then becomes 0 so its next basis vector is zero.  The rotations
 // have real cosines.  Thread 0 publishes how many right-hand sides remain active.
+// With few right-hand sides (`staged`) the CTA first copies every column and the
+// earlier rotations into shared memory, so that the sequential rotations read
+// nothing from global memory.
 template <typename R>
-__global__ void k_bgs_givens(BgsArgs a, int j) {
+__global__ void k_bgs_givens(BgsArgs a, int j, int staged) {
+    extern __shared__ double gsm[];  // staged: columns [nrhs][j + 1], sines [nrhs][j], cosines [nrhs][j]
     __shared__ int s_count;
     if (threadIdx.x == 0) s_count = 0;
-    __syncthreads();
     const int m = a.m;
+    cx<R>* scol = reinterpret_cast<cx<R>*>(gsm);
+    cx<R>* ssn = scol + (size_t)a.nrhs * (j + 1);
+    R* scs = reinterpret_cast<R*>(ssn + (size_t)a.nrhs * j);
+    if (staged) {
+        for (int e = threadIdx.x; e < a.nrhs * (j + 1); e += blockDim.x) {
+            const int r = e / (j + 1), i = e - r * (j + 1);
+            const int flag = a.state[r];
+            const cx<R> v = reinterpret_cast<const cx<R>*>(a.h1)[(int64_t)r * (m + 1) + i];
+            scol[e] = (flag & BGS_REORTH) ? v + reinterpret_cast<const cx<R>*>(a.h2)[(int64_t)r * (m + 1) + i] : v;
+        }
+        for (int e = threadIdx.x; e < a.nrhs * j; e += blockDim.x) {
+            const int r = e / j, i = e - r * j;
+            ssn[e] = reinterpret_cast<const cx<R>*>(a.sn)[(int64_t)r * m + i];
+            scs[e] = reinterpret_cast<const R*>(a.cs)[(int64_t)r * m + i];
+        }
+    }
+    __syncthreads();
     int mine = 0;
     for (int r = threadIdx.x; r < a.nrhs; r += blockDim.x) {
         const int flag = a.state[r];
@@ -311,13 +346,16 @@ __global__ void k_bgs_givens(BgsArgs a, int j) {
         cx<R>* __restrict__ sn = reinterpret_cast<cx<R>*>(a.sn) + (int64_t)r * m;
         const cx<R>* __restrict__ h1 = reinterpret_cast<const cx<R>*>(a.h1) + (int64_t)r * (m + 1);
         const cx<R>* __restrict__ h2 = reinterpret_cast<const cx<R>*>(a.h2) + (int64_t)r * (m + 1);
+        const cx<R>* sc = scol + (size_t)r * (j + 1);
+        const cx<R>* ss = ssn + (size_t)r * j;
+        const R* sk = scs + (size_t)r * j;
         const R hn = (R)sqrt(fmax(two ? a.wn2[r] : a.wn1[r], 0.0));
-        cx<R> prev = two ? h1[0] + h2[0] : h1[0];
+        cx<R> prev = staged ? sc[0] : (two ? h1[0] + h2[0] : h1[0]);
 #pragma unroll 4
         for (int i = 0; i < j; ++i) {
-            const cx<R> b = two ? h1[i + 1] + h2[i + 1] : h1[i + 1];
-            const R c = cs[i];
-            const cx<R> s = sn[i];
+            const cx<R> b = staged ? sc[i + 1] : (two ? h1[i + 1] + h2[i + 1] : h1[i + 1]);
+            const R c = staged ? sk[i] : cs[i];
+            const cx<R> s = staged ? ss[i] : sn[i];
             cx<R> top = c * prev;
             cfma(top, s, b);
             H[(int64_t)i * m + j] = top;
@@ -539,8 +577,6 @@ __global__ void __launch_bounds__(BG_THREADS) k_colnorm2(BgsArgs a, double* out)
     }
 }
 
-size_t bgs_dot_smem(int j) { return sizeof(double) * 2 * BG_WARPS * (size_t)(j + 2); }
-
 }  // namespace
 
 void bgs_layout(int64_t n, int nrhs, int esize, int* chunk, int* nblk) {
@@ -558,13 +594,23 @@ void bgs_layout(int64_t n, int nrhs, int esize, int* chunk, int* nblk) {
 template <typename R>
 cudaError_t bgs_iteration(const BgsArgs& a, int j, cudaStream_t st) {
     const dim3 grid(a.nblk, a.nrhs);
-    const size_t sd = bgs_dot_smem(j);
+    // inner products: split the basis into slabs of qs vectors when the row chunks
+    // of all right-hand sides give fewer than 8 CTAs per SM
+    const int nq = j + 1;
+    const int want = (8 * 152 + a.nblk * a.nrhs - 1) / (a.nblk * a.nrhs);
+    const int nslab = std::max(1, std::min(want, (nq + QG - 1) / QG));
+    const int qs = ((nq + nslab - 1) / nslab + QG - 1) / QG * QG;
+    const int nsl = (nq + qs - 1) / qs;
+    const dim3 gdot(a.nblk * nsl, a.nrhs);
+    const size_t sd = sizeof(double) * 2 * BG_WARPS * (size_t)(qs + 1);
     const size_t su = sizeof(double) * BG_WARPS + sizeof(cx<R>) * (size_t)(j + 1);
     for (int pass = 1; pass <= 2; ++pass) {
-        k_bgs_dot<R><<<grid, BG_THREADS, sd, st>>>(a, j, pass);
+        k_bgs_dot<R><<<gdot, BG_THREADS, sd, st>>>(a, j, pass, qs);
         k_bgs_update<R><<<grid, BG_THREADS, su, st>>>(a, j, pass);
     }
-    k_bgs_givens<R><<<1, std::min(1024, ((a.nrhs + 31) / 32) * 32), 0, st>>>(a, j);
+    const size_t sg = (sizeof(cx<R>) * (size_t)(2 * j + 1) + sizeof(R) * (size_t)j) * a.nrhs;
+    const bool staged = sg <= 32768;
+    k_bgs_givens<R><<<1, std::min(1024, ((a.nrhs + 31) / 32) * 32), staged ? sg : 0, st>>>(a, j, staged ? 1 : 0);
     k_bgs_scale<R><<<grid, BG_THREADS, 0, st>>>(a, j + 1);
     return cudaGetLastError();
 }
