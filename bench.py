@@ -175,18 +175,25 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_traffic(name):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+def kernel_traffic(name, alg_now):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current
+    kernel source: (bytes, note).  A capture of a smaller workload of the same kernel
+    (its algorithmic bytes recorded beside it) is scaled by the algorithmic bytes of
+    this launch, since traffic grows in proportion to them."""
     src = os.path.join(ROOT, "paper_2310_15644_gb300", "csrc", "matvec.cu")
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(p):
-        return None
+        return None, None
     for line in open(p):
         parts = line.split()
-        if len(parts) >= 4 and parts[0] == name and parts[2] == digest and parts[3] == workload_name(LEVEL):
-            return float(parts[1])
-    return None
+        if len(parts) < 4 or parts[0] != name or parts[2] != digest:
+            continue
+        if parts[3] == workload_name(LEVEL):
+            return float(parts[1]), "captured on this workload"
+        if len(parts) >= 5:
+            return float(parts[1]) * alg_now / float(parts[4]), f"scaled from {parts[3]} by algorithmic bytes"
+    return None, None
 
 
 # ---------------------------------------------------------------------------
@@ -275,14 +282,19 @@ def run_native(args, rank, world, dist):
 
     # roofline of the dominant kernel
     peak, peak_kind = measured_peak()
+    # FMA peaks of this GPU (our own microbenchmark; no clock or power change)
+    fma_peaks = {"fp32_tflops": round(B.bem_measure_fma_peak(False, sp), 2),
+                 "fp64_tflops": round(B.bem_measure_fma_peak(True, sp), 3),
+                 "source": "bem_measure_fma_peak: 8 independent FMA chains per thread, 8 CTAs of 256 per SM"}
     kb = stats["kernel_bytes_c64"]
     names = B.KERNEL_NAMES
     mean_ms = [kms[i] / max(1, kcnt[i]) for i in range(3)]
     dom = int(np.argmax(mean_ms))
     achieved = kb[dom] / (mean_ms[dom] * 1e-3) / 1e9
-    traffic = kernel_traffic(names[dom])
+    traffic, traffic_note = kernel_traffic(names[dom], kb[dom])
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": round(traffic) if traffic else None, "traffic_source": traffic_note,
                 "peak_source": f"{peak_kind} HBM copy bandwidth",
                 "algorithmic_bytes_per_launch": int(kb[dom]), "mean_launch_ms": round(mean_ms[dom], 5),
                 "kernels": {names[i]: {"mean_ms": round(mean_ms[i], 5), "launches": int(kcnt[i]),
@@ -370,7 +382,7 @@ def run_native(args, rank, world, dist):
            "scaling": "weak", "vs_baseline": None, "dtype": "complex64 (fp32)", "data": "synthetic",
            "config": config_dict(), "hbm_gbps_algorithmic": round(step_gbs, 1),
            "hbm_frac_of_peak": round(step_gbs / peak, 4), "roofline": roofline, "e2e": e2e,
-           "gpu_launches": int(sum(kcnt)), "clocks": clk, "batched_rhs": batched,
+           "gpu_launches": int(sum(kcnt)), "clocks": clk, "batched_rhs": batched, "measured_fma_peaks": fma_peaks,
            "assembly": {"ms": round(asm64_ms, 1), "near_entries_per_op": stats["near_entries"],
                         "factor_entries": stats["factor_entries"], "max_rank": stats["max_rank"],
                         "far_blocks": stats["n_far"], "far_blocks_dense": stats["n_far_dense"],
@@ -418,7 +430,12 @@ def run_native(args, rank, world, dist):
             k128 = max(3, args.steps // 8)
             ms2, _, _ = time_steps(h128, xd2, yd2, B.BEM_C128, k128, max(3, args.warmup // 4), False)
             y128 = yd2.cpu().numpy()
+            # FP64 arithmetic of the complex128 product: one complex multiply-add (8 FLOP)
+            # per stored complex entry (16 bytes)
+            fp64_tf = 8.0 * (s128["matvec_bytes_c128"] / 16.0) / (ms2 / k128 * 1e-3) / 1e12
             out["fp64_baseline"] = {"value": round(k128 / (ms2 / 1e3), 2), "unit": UNIT,
+                                    "fp64_tflops": round(fp64_tf, 3),
+                                    "fp64_frac_of_measured_fma_peak": round(fp64_tf / fma_peaks["fp64_tflops"], 4),
                                     "ms_per_step": round(ms2 / k128, 4), "steps": k128, "dtype": "complex128 (fp64)",
                                     "assembly_ms": round(asm128_ms, 1),
                                     "hbm_gbps_algorithmic": round(s128["matvec_bytes_c128"] / (ms2 / k128 * 1e-3) / 1e9, 1),

@@ -464,6 +464,21 @@ bem_status bem_absorbed_power_static(bem_ctx* ctx, const void* x, int nrhs, doub
 bem_status bem_planar_operators(bem_ctx* ctx, const double* verts, int n, bem_c128 k, void* S, void* D, void* N,
                                 void* stream);
 
+/* FMA throughput of the current device in TFLOP/s (2 FLOP per fused multiply-add),
+ * FP64 if fp64 != 0 else FP32: the denominators of the arithmetic rooflines
+ * (quadrature and ACA assembly, the complex128 product).  Runs a few short
+ * launches of independent FMA chains on `stream` (about 5 ms in all) and returns
+ * the best; changes no clock or power setting.  Allocates a few KB of device
+ * memory for the duration of the call. */
+bem_status bem_measure_fma_peak(int fp64, void* stream, double* tflops);
+
+/* Test hook (host-side fault injection): after `after` further successful device
+ * allocations by the library (any context), each allocation fails as if the
+ * device were out of memory (cudaErrorMemoryAllocation, no CUDA call made), so
+ * that the entry point that needed it returns BEM_ENOMEM.  after < 0 turns the
+ * injection off (the default).  Not thread-safe against concurrent calls. */
+void bem_debug_fail_alloc_after(long long after);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,8 @@ EXPORTS = [
     "bem_power_density", "bem_profile_begin", "bem_profile_end", "bem_absorbed_power_static",
     "bem_matvec_adjoint", "bem_solve_adjoint", "bem_absorbed_power_gradient", "bem_grad_weights", "bem_grad_eps",
     "bem_autotune", "bem_batch_create", "bem_batch_launch", "bem_batch_destroy", "bem_set_regions",
-    "bem_region_boundary", "bem_num_regions", "bem_planar_operators",
+    "bem_region_boundary", "bem_num_regions", "bem_planar_operators", "bem_measure_fma_peak",
+    "bem_debug_fail_alloc_after",
 ]
 KERNEL_NAMES = ["k_gather", "k_vhx", "k_rows"]   # BEM_KERNEL_GATHER, _VHX, _ROWS
 
@@ -120,6 +121,8 @@ def _load():
         "bem_profile_begin": (ctypes.c_int, [ctx]),
         "bem_profile_end": (ctypes.c_int, [ctx, dp, i64p]),
         "bem_absorbed_power_static": (ctypes.c_int, [ctx, vp, ctypes.c_int, vp, vp]),
+        "bem_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, vp, dp]),
+        "bem_debug_fail_alloc_after": (None, [ctypes.c_longlong]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -296,6 +299,20 @@ def bem_solve_adjoint(ctx, g_ptr: int, lam_ptr: int, nrhs: int, stream: int = 0,
     if st != BEM_OK and not (st == BEM_ENOCONV and not raise_on_noconv):
         _check(ctx, st)
     return it.value, rel, st
+
+
+def bem_measure_fma_peak(fp64: bool, stream: int = 0) -> float:
+    """FMA throughput of the current device in TFLOP/s (FP64 if fp64 else FP32)."""
+    t = ctypes.c_double(0.0)
+    st = lib.bem_measure_fma_peak(1 if fp64 else 0, ctypes.c_void_p(stream), ctypes.byref(t))
+    if st != BEM_OK:
+        raise BemError(st, "bem_measure_fma_peak failed")
+    return t.value
+
+
+def bem_debug_fail_alloc_after(after: int) -> None:
+    """Test hook: the library's device allocations fail after `after` more (negative: off)."""
+    lib.bem_debug_fail_alloc_after(int(after))
 
 
 def bem_absorbed_power_gradient(ctx, x_ptr: int, g_ptr: int, nrhs: int, stream: int = 0) -> None:

@@ -13,9 +13,14 @@
 
 namespace bem {
 
+// allocations left before the injected failures of bem_debug_fail_alloc_after (< 0: off)
+static long long g_alloc_left = -1;
+
 cudaError_t dalloc(DevBuf& b, size_t bytes) {
     dfree(b);
     if (bytes == 0) return cudaSuccess;
+    if (g_alloc_left == 0) return cudaErrorMemoryAllocation;
+    if (g_alloc_left > 0) --g_alloc_left;
     cudaError_t e = cudaMalloc(&b.p, bytes);
     if (e != cudaSuccess) {
         b.p = nullptr;
@@ -24,6 +29,12 @@ cudaError_t dalloc(DevBuf& b, size_t bytes) {
     b.bytes = bytes;
     return cudaSuccess;
 }
+
+}  // namespace bem
+
+extern "C" void bem_debug_fail_alloc_after(long long after) { bem::g_alloc_left = after < 0 ? -1 : after; }
+
+namespace bem {
 
 void dfree(DevBuf& b) {
     if (b.p) cudaFree(b.p);
