@@ -15,6 +15,11 @@ rows and columns:
     stop when |u| |w| <= tol |S|_F
     i  = argmax over unused rows of |u_i|
   B ~= sum_l u_l w_l^T = U V^H with V = conj(W).
+
+Recompression (the factors ACA returns, truncated to the rank their singular
+values need): U = Q_U R_U, V = Q_V R_V (QR), R_U R_V^H = X S Y^H (SVD), keep the r
+largest singular values with r the smallest rank whose discarded tail satisfies
+sqrt(sum_{i > r} s_i^2) <= tol sqrt(sum_i s_i^2); U' = Q_U X_r S_r, V' = Q_V Y_r.
 """
 from __future__ import annotations
 
@@ -67,3 +72,23 @@ def aca(row, col, m: int, n: int, tol: float, rmax: int | None = None):
 def aca_dense(B: np.ndarray, tol: float, rmax: int | None = None):
     """ACA of an explicitly stored block (for tests)."""
     return aca(lambda i: B[i, :], lambda j: B[:, j], B.shape[0], B.shape[1], tol, rmax)
+
+
+def recompress(U: np.ndarray, V: np.ndarray, tol: float):
+    """Return (U', V') with U' V'^H the best approximation of U V^H whose discarded
+    singular values hold at most a fraction tol of its Frobenius norm."""
+    k = U.shape[1]
+    if k == 0:
+        return U, V
+    Qu, Ru = np.linalg.qr(U)
+    Qv, Rv = np.linalg.qr(V)
+    X, s, Yh = np.linalg.svd(Ru @ Rv.conj().T)
+    total = float(np.sum(s ** 2))
+    if total == 0.0:
+        return U[:, :0], V[:, :0]
+    r = k
+    tail = 0.0
+    while r > 1 and tail + s[r - 1] ** 2 <= tol * tol * total:
+        r -= 1
+        tail += s[r] ** 2
+    return Qu @ (X[:, :r] * s[:r]), Qv @ Yh[:r].conj().T

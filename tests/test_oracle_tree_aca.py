@@ -91,3 +91,61 @@ def test_aca_error_and_rank_vs_svd(far_blocks, tol):
             eps_rank = int(np.sum(tail > tol))
             assert err <= 10 * tol, (bi, err)
             assert U.shape[1] <= 2 * eps_rank + 2, (U.shape[1], eps_rank)
+
+
+def _eps_rank(s, tol):
+    tail = np.sqrt(np.cumsum((s ** 2)[::-1])[::-1]) / np.linalg.norm(s)
+    return int(np.sum(tail > tol))
+
+
+def test_recompress_keeps_an_exact_low_rank_product():
+    rng = np.random.default_rng(4)
+    B = (rng.standard_normal((60, 3)) + 1j * rng.standard_normal((60, 3))) @ \
+        (rng.standard_normal((3, 45)) + 1j * rng.standard_normal((3, 45)))
+    # an over-long factorisation of the rank-3 block: 7 columns
+    U = B[:, :7]
+    V = np.linalg.lstsq(U, B, rcond=None)[0].conj().T
+    assert np.linalg.norm(U @ V.conj().T - B) <= 1e-10 * np.linalg.norm(B)
+    U2, V2 = A.recompress(U, V, 1e-12)
+    assert U2.shape[1] == 3
+    assert np.linalg.norm(U2 @ V2.conj().T - B) <= 1e-10 * np.linalg.norm(B)
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-6])
+def test_recompress_is_the_truncated_svd(far_blocks, tol):
+    """The singular values of U' V'^H are the leading ones of U V^H, and what it drops
+    is within tol of |U V^H|_F (the definition of the truncated SVD)."""
+    perm, far, ops = far_blocks
+    order = np.argsort(-(far[:, 1] * far[:, 3]))
+    for bi in order[:4]:
+        r0, m, c0, n = far[bi]
+        Bk = ops[1][np.ix_(perm[r0:r0 + m], perm[c0:c0 + n])]
+        U, V = A.aca_dense(Bk, tol)
+        P = U @ V.conj().T
+        U2, V2 = A.recompress(U, V, tol)
+        r = U2.shape[1]
+        s = np.linalg.svd(P, compute_uv=False)
+        s2 = np.linalg.svd(U2 @ V2.conj().T, compute_uv=False)[:r]
+        assert np.allclose(s2, s[:r], rtol=1e-9, atol=1e-12 * s[0])
+        assert np.linalg.norm(P - U2 @ V2.conj().T) <= tol * np.linalg.norm(P) * (1 + 1e-9)
+        assert r == _eps_rank(s[:U.shape[1]], tol)
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-6])
+def test_recompressed_rank_within_two_of_the_svd_rank(far_blocks, tol):
+    """Against the exact block: after recompression every far block's rank is at
+    most its SVD eps-rank + 2, and the block error stays within the ACA bound (10 tol)
+    plus the truncation (2 tol)."""
+    perm, far, ops = far_blocks
+    order = np.argsort(-(far[:, 1] * far[:, 3]))
+    for bi in order[:8]:
+        r0, m, c0, n = far[bi]
+        for Op in ops:
+            Bk = Op[np.ix_(perm[r0:r0 + m], perm[c0:c0 + n])]
+            U, V = A.aca_dense(Bk, tol)
+            U2, V2 = A.recompress(U, V, tol)
+            s = np.linalg.svd(Bk, compute_uv=False)
+            assert U2.shape[1] <= _eps_rank(s, tol) + 2, (bi, U2.shape[1], _eps_rank(s, tol))
+            assert U2.shape[1] <= U.shape[1]
+            err = np.linalg.norm(Bk - U2 @ V2.conj().T) / np.linalg.norm(Bk)
+            assert err <= 10 * tol + 2 * tol, err
