@@ -100,6 +100,9 @@ typedef struct {
     double refine_tol;   /* outer FP64 iterative-refinement target; 0 disables refinement (default 0) */
     int refine_maxit;    /* maximum outer refinement steps (default 10) */
     int solver;          /* inner Krylov solver, BEM_SOLVER_* (default GMRES) */
+    int aca_recompress;  /* 1 (default): after ACA, truncate each block's factors to the rank its singular
+                            values need at aca_tol (Gram/Cholesky factors of U and V, SVD of the small core);
+                            0: keep the ACA ranks */
 } bem_options;
 
 /* Inner Krylov solvers (bem_options.solver).  maxit counts iterations: one product

@@ -41,7 +41,7 @@ class bem_options(ctypes.Structure):
         ("precision", ctypes.c_int), ("leaf_size", ctypes.c_int), ("eta", ctypes.c_double),
         ("aca_tol", ctypes.c_double), ("aca_max_rank", ctypes.c_int), ("gmres_restart", ctypes.c_int),
         ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("refine_tol", ctypes.c_double),
-        ("refine_maxit", ctypes.c_int), ("solver", ctypes.c_int),
+        ("refine_maxit", ctypes.c_int), ("solver", ctypes.c_int), ("aca_recompress", ctypes.c_int),
     ]
 
 

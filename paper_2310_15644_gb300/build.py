@@ -14,7 +14,7 @@ OBJ = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libbem.so")
 STAMP = os.path.join(OBJ, "libbem.stamp")
 SOURCES = ["bem_api.cu", "tree.cu", "singular.cu", "assemble.cu", "matvec.cu", "krylov.cu", "rhs_power.cu",
-           "gradient.cu", "planar.cu", "matvec_tc.cu", "gmres.cu", "peak.cu",
+           "gradient.cu", "planar.cu", "matvec_tc.cu", "gmres.cu", "peak.cu", "recompress.cu",
            "static_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",

@@ -362,6 +362,7 @@ extern "C" void bem_default_options(bem_options* o) {
     o->refine_tol = 0.0;
     o->refine_maxit = 10;
     o->solver = BEM_SOLVER_GMRES;
+    o->aca_recompress = 1;
 }
 
 extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
@@ -373,7 +374,7 @@ extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
     if (o.leaf_size < 2 || o.leaf_size > BEM_MAX_LEAF || (o.precision & 7) == 0 || (o.precision & ~7) != 0 ||
         o.aca_tol <= 0 || o.aca_max_rank < 1 || o.aca_max_rank > 128 || o.gmres_restart < 1 || o.gmres_restart > 200 || o.maxit < 1 ||
         o.tol <= 0 || o.refine_tol < 0 || o.refine_maxit < 1 || o.solver < BEM_SOLVER_GMRES ||
-        o.solver > BEM_SOLVER_CGNR)
+        o.solver > BEM_SOLVER_CGNR || o.aca_recompress < 0 || o.aca_recompress > 1)
         return BEM_EINVAL;
     bem_ctx* c = new (std::nothrow) bem_ctx();
     if (!c) return BEM_ENOMEM;
@@ -1240,6 +1241,34 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
             CK(cudaMemcpyAsync(rk.data(), d_ranks.p, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
             CK(cudaMemcpyAsync(fl.data(), d_flags.p, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
+            if (c->opt.aca_recompress) {
+                // truncate each converged task to the rank its singular values need;
+                // workspace: the two k x k transforms of each task
+                const int km = recompress_kmax<R>();
+                std::vector<int64_t> woff(nt, 0);
+                int64_t wl = 0;
+                for (int i = 0; i < nt; ++i)
+                    if (!fl[i] && rk[i] >= 2 && rk[i] <= km) {
+                        woff[i] = wl;
+                        wl += 2 * (int64_t)rk[i] * rk[i];
+                    }
+                if (wl > 0) {
+                    DevBuf d_ws, d_woff;
+                    struct G2 {
+                        DevBuf* b[2];
+                        ~G2() {
+                            for (DevBuf* x : b) dfree(*x);
+                        }
+                    } g2{{&d_ws, &d_woff}};
+                    CK(dalloc(d_ws, es * wl));
+                    CK(upload(d_woff, woff, st));
+                    CK(aca_recompress<R>((const AcaTask*)d_tasks.p, nt, (cx<R>*)d_scr.p, (int*)d_ranks.p,
+                                         (const int*)d_flags.p, c->opt.aca_tol, (cx<R>*)d_ws.p,
+                                         (const int64_t*)d_woff.p, st));
+                    CK(cudaMemcpyAsync(rk.data(), d_ranks.p, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
+                    CK(cudaStreamSynchronize(st));
+                }
+            }
             // factors of a converged task are kept (a failed task stores nothing)
             std::vector<int64_t> ou(nt), ov(nt);
             int64_t len = 0;

@@ -231,6 +231,14 @@ struct AcaTask {
 template <typename R>
 cudaError_t aca_run(GeomDev g, const int64_t* perm, const AcaTask* tasks, const int counts[6], cx<R>* scratch,
                     double tol, int* ranks, int* flags, cudaStream_t st, int max_m);
+// SVD recompression of converged ACA tasks in their scratch (recompress.cu): ranks
+// updated in place; ws holds 2 k^2 values per task at ws_off (k its ACA rank);
+// tasks with k above recompress_kmax<R>() keep their factors
+template <typename R>
+int recompress_kmax();
+template <typename R>
+cudaError_t aca_recompress(const AcaTask* tasks, int ntasks, cx<R>* scratch, int* ranks, const int* flags,
+                           double tol, cx<R>* ws, const int64_t* ws_off, cudaStream_t st);
 // U is written slice-major (leaf slices of the block rows), W column-pair-major
 template <typename R>
 cudaError_t aca_compact(const AcaTask* tasks, int ntasks, const cx<R>* scratch, const int* ranks,
