@@ -467,6 +467,45 @@ bem_status bem_absorbed_power_static(bem_ctx* ctx, const void* x, int nrhs, doub
 bem_status bem_planar_operators(bem_ctx* ctx, const double* verts, int n, bem_c128 k, void* S, void* D, void* N,
                                 void* stream);
 
+/* The paper's two-dimensional fast direct solver (Sec. III), FP64 on the GPU.
+ * Polygons as in bem_planar_operators (n vertices, counter-clockwise, closed);
+ * dense matrices device complex128 n x n row-major; U n x r column-major (column c
+ * at U + c n); Vt r x n row-major; omega, b, x column-major with n rows.  Each call
+ * synchronises `stream`; ctx (may be NULL) only receives the error message. */
+
+/* Calderon-preconditioned CFIE of Eq. 16: Cp = N~ G^-1 S + (G/2 - D*~) G^-1 (G/2 + D*)
+ * with S, D, N at k0 and D*~, N~ at k~ = k0 - 0.4 j k0^(1/3) a^(-2/3) (a <= 0: the
+ * perimeter over 2 pi), G the Gram matrix of the hat functions (solved as a cyclic
+ * tridiagonal system).  Le = N~ G^-1 and Lh = (G/2 - D*~) G^-1 (may be NULL) map the
+ * right-hand side: rhs_p = Le (e / (j k0)) + Lh (eta0 h).  Allocates about 10 n^2 x
+ * 16 bytes of scratch. */
+bem_status bem_planar_calderon(bem_ctx* ctx, const double* verts, int n, double k0, double a, void* Cp, void* Le,
+                               void* Lh, void* stream);
+
+/* In-place FFT of `batch` vectors of length n (1..2048), vector b at x + b * batch_stride,
+ * element stride `stride` (complex128 elements): forward sum_j x_j exp(-2 pi i jk/n),
+ * inverse (inverse != 0) with exp(+2 pi i jk/n) / n.  Bluestein's chirp convolution
+ * on radix-2 transforms, one CTA per vector. */
+bem_status bem_fft(bem_ctx* ctx, void* x, int n, long long stride, int batch, long long batch_stride, int inverse,
+                   void* stream);
+
+/* Skeleton of Eq. 17 by the adaptive randomized range finder: orthonormal U with
+ * |(I - U U^H) A w| <= tol * (largest |A w| of the first block) for the test vectors w,
+ * taken `block` at a time from the p columns of omega (the random numbers are an
+ * input), each block orthogonalised twice against U and among itself; Vt = U^H A.
+ * A: the matrix to compress (C_p - C_p,c); U: capacity n x p; Vt: capacity p x n
+ * (may be NULL); rank: host, the columns of U used.  BEM_ENOCONV if the test vectors
+ * run out first. */
+bem_status bem_planar_skeleton(bem_ctx* ctx, const void* A, int n, const void* omega, int p, double tol, int block,
+                               void* U, void* Vt, int* rank, void* stream);
+
+/* Woodbury solve of Eq. 18: x = (C_c + U Vt)^-1 b for nrhs right-hand sides, C_c the
+ * circulant matrix whose first column is cc0 (device, n values; its eigenvalues by
+ * FFT), U and Vt of rank r (r = 0: x = C_c^-1 b).  The r x r core is solved by LU
+ * with partial pivoting (BEM_EINVAL if singular). */
+bem_status bem_planar_woodbury_solve(bem_ctx* ctx, const void* cc0, int n, const void* U, const void* Vt, int r,
+                                     const void* b, void* x, int nrhs, void* stream);
+
 /* FMA throughput of the current device in TFLOP/s (2 FLOP per fused multiply-add),
  * FP64 if fp64 != 0 else FP32: the denominators of the arithmetic rooflines
  * (quadrature and ACA assembly, the complex128 product).  Runs a few short

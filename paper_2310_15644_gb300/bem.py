@@ -31,7 +31,8 @@ EXPORTS = [
     "bem_matvec_adjoint", "bem_solve_adjoint", "bem_absorbed_power_gradient", "bem_grad_weights", "bem_grad_eps",
     "bem_autotune", "bem_batch_create", "bem_batch_launch", "bem_batch_destroy", "bem_set_regions",
     "bem_region_boundary", "bem_num_regions", "bem_planar_operators", "bem_measure_fma_peak",
-    "bem_debug_fail_alloc_after",
+    "bem_debug_fail_alloc_after", "bem_planar_calderon", "bem_fft", "bem_planar_skeleton",
+    "bem_planar_woodbury_solve",
 ]
 KERNEL_NAMES = ["k_gather", "k_vhx", "k_rows"]   # BEM_KERNEL_GATHER, _VHX, _ROWS
 
@@ -122,6 +123,14 @@ def _load():
         "bem_profile_end": (ctypes.c_int, [ctx, dp, i64p]),
         "bem_absorbed_power_static": (ctypes.c_int, [ctx, vp, ctypes.c_int, vp, vp]),
         "bem_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, vp, dp]),
+        "bem_planar_calderon": (ctypes.c_int, [ctx, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp, vp, vp,
+                                               vp]),
+        "bem_fft": (ctypes.c_int, [ctx, vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_longlong,
+                                   ctypes.c_int, vp]),
+        "bem_planar_skeleton": (ctypes.c_int, [ctx, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                               vp, vp, ctypes.POINTER(ctypes.c_int), vp]),
+        "bem_planar_woodbury_solve": (ctypes.c_int, [ctx, vp, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp,
+                                                     ctypes.c_int, vp]),
         "bem_debug_fail_alloc_after": (None, [ctypes.c_longlong]),
     }
     for name, (res, args) in sig.items():
@@ -299,6 +308,37 @@ def bem_solve_adjoint(ctx, g_ptr: int, lam_ptr: int, nrhs: int, stream: int = 0,
     if st != BEM_OK and not (st == BEM_ENOCONV and not raise_on_noconv):
         _check(ctx, st)
     return it.value, rel, st
+
+
+def bem_planar_calderon(ctx, verts, k0: float, cp_ptr: int, le_ptr: int = 0, lh_ptr: int = 0, a: float = 0.0,
+                        stream: int = 0) -> None:
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    _check(ctx, lib.bem_planar_calderon(ctx, _np_ptr(v, ctypes.c_double), int(v.shape[0]), float(k0), float(a),
+                                        ctypes.c_void_p(cp_ptr), ctypes.c_void_p(le_ptr or None),
+                                        ctypes.c_void_p(lh_ptr or None), ctypes.c_void_p(stream)))
+
+
+def bem_fft(ctx, x_ptr: int, n: int, stride: int = 1, batch: int = 1, batch_stride: int | None = None,
+            inverse: bool = False, stream: int = 0) -> None:
+    bs = n * stride if batch_stride is None else batch_stride
+    _check(ctx, lib.bem_fft(ctx, ctypes.c_void_p(x_ptr), int(n), int(stride), int(batch), int(bs), 1 if inverse else 0,
+                            ctypes.c_void_p(stream)))
+
+
+def bem_planar_skeleton(ctx, a_ptr: int, n: int, omega_ptr: int, p: int, tol: float, block: int, u_ptr: int,
+                        vt_ptr: int = 0, stream: int = 0) -> int:
+    r = ctypes.c_int(0)
+    _check(ctx, lib.bem_planar_skeleton(ctx, ctypes.c_void_p(a_ptr), int(n), ctypes.c_void_p(omega_ptr), int(p),
+                                        float(tol), int(block), ctypes.c_void_p(u_ptr), ctypes.c_void_p(vt_ptr or None),
+                                        ctypes.byref(r), ctypes.c_void_p(stream)))
+    return r.value
+
+
+def bem_planar_woodbury_solve(ctx, cc0_ptr: int, n: int, u_ptr: int, vt_ptr: int, r: int, b_ptr: int, x_ptr: int,
+                              nrhs: int = 1, stream: int = 0) -> None:
+    _check(ctx, lib.bem_planar_woodbury_solve(ctx, ctypes.c_void_p(cc0_ptr), int(n), ctypes.c_void_p(u_ptr or None),
+                                              ctypes.c_void_p(vt_ptr or None), int(r), ctypes.c_void_p(b_ptr),
+                                              ctypes.c_void_p(x_ptr), int(nrhs), ctypes.c_void_p(stream)))
 
 
 def bem_measure_fma_peak(fp64: bool, stream: int = 0) -> float:
