@@ -103,7 +103,25 @@ typedef struct {
     int aca_recompress;  /* 1 (default): after ACA, truncate each block's factors to the rank its singular
                             values need at aca_tol (Gram/Cholesky factors of U and V, SVD of the small core);
                             0: keep the ACA ranks */
+    int preconditioner;  /* BEM_PRECOND_*: preconditioner of the GMRES solves (default BEM_PRECOND_NONE) */
+    double precond_aca_tol; /* ACA tolerance of the refined-mesh operator inside the Calderon preconditioner
+                               (default 1e-3): the preconditioner only has to be spectrally close */
 } bem_options;
+
+/* Preconditioners (bem_options.preconditioner).  Only the GMRES solver applies one;
+ * the CG-type solvers return BEM_EINVAL when it is set, and adjoint solves run
+ * without it. */
+#define BEM_PRECOND_NONE 0
+#define BEM_PRECOND_CALDERON 1  /* Calderon multiplicative preconditioner of PMCHWT, the 3-D counterpart of the
+                                   Calderon-preconditioned CFIE of Sec. III: P = -Gb^-T Cb^T Z_fine Cb Gb^-1,
+                                   applied on the right (Z P y = b, x = P y).  Z_fine is the PMCHWT operator of
+                                   the barycentric refinement (six triangles per triangle, assembled and
+                                   compressed like Z at precond_aca_tol), C holds the Buffa-Christiansen
+                                   functions of the edges in its RWG basis, G[m, e] = int (n x f_m) . g_e dS
+                                   is the mixed Gram matrix (Gb = diag(G, G), Cb = diag(C, C)) and G^-1 is a
+                                   fixed Chebyshev polynomial in D^-1 G (D = diag G) reaching 1e-6.
+                                   bem_assemble builds it (about 6x the unknowns of Z); single-body contexts
+                                   only.  GMRES iteration counts then stay bounded under mesh refinement. */
 
 /* Inner Krylov solvers (bem_options.solver).  maxit counts iterations: one product
  * per GMRES iteration, two per CGS, BiCGStab and CGNR iteration. */
@@ -157,6 +175,15 @@ typedef struct {
     double assemble_phase_ms[BEM_PHASES]; /* its parts: see BEM_PHASE_* (ACA, near and plan summed over precisions) */
     int64_t tc_passes;          /* tensor-core operator passes (64 vectors each) run since bem_assemble, by
                                    bem_matvec with BEM_C64_TC and by batched solves */
+    int64_t precond_fine_ne;    /* Calderon preconditioner (else 0): RWG edges of the barycentric refinement */
+    int64_t precond_gram_nnz;   /* nonzeros of the mixed Gram matrix G */
+    int64_t precond_gram_steps; /* Chebyshev steps per solve with G or G^T */
+    int64_t precond_bytes_c64;  /* algorithmic bytes of one complex64 application of P to one vector: the
+                                   refined operator's product bytes, C and C^T once, G and G^T once per
+                                   Chebyshev step, and the vectors each step reads and writes */
+    double precond_gram_interval[2]; /* eigenvalue interval of D^-1 G that the Chebyshev steps assume */
+    double precond_assemble_ms; /* wall time of the preconditioner's share of bem_assemble (refinement, refined
+                                   operator, BC and Gram matrices, Chebyshev plan) */
 } bem_stats;
 
 /* Kernels of one product, in launch order (index into the profiling arrays). */
@@ -337,6 +364,27 @@ void bem_batch_destroy(bem_batch* batch);
  * host, 3 int64), then stops recording.  Either output may be NULL. */
 bem_status bem_profile_begin(bem_ctx* ctx);
 bem_status bem_profile_end(bem_ctx* ctx, double* ms_sum, int64_t* launches);
+
+/* Apply the Calderon preconditioner (BEM_PRECOND_CALDERON at bem_assemble): y = P x
+ * for nrhs vectors; x, y device 2ne x nrhs (column-major) of type dtype (BEM_C64,
+ * BEM_C64_BF16F, BEM_C64_TC or BEM_C128, as for bem_matvec; the refined operator
+ * uses the same form).  x and y must not overlap.  Asynchronous on `stream`.
+ * BEM_ESTATE without the preconditioner. */
+bem_status bem_precond_apply(bem_ctx* ctx, const void* x, void* y, int nrhs, int dtype, void* stream);
+
+/* A sparse matrix of the Calderon preconditioner, FP64 compressed rows (host):
+ * which = 0: C, the Buffa-Christiansen function of every edge written in the RWG
+ *            basis of the barycentric refinement (rows: refined edges, in the
+ *            lexicographic order of the refined vertices, numbered vertices, then
+ *            edge midpoints in edge order, then centroids in triangle order;
+ *            columns: edges);
+ * which = 1: the mixed Gram matrix G[m, e] = int (n x f_m) . g_e dS.
+ * rows, cols, nnz (host, may be NULL) receive the sizes; ptr (rows + 1), col and
+ * val (nnz each) receive the matrix when not NULL.  Host computation, available
+ * once the mesh is set (no device work).  BEM_EINVAL if the context was not
+ * created with BEM_PRECOND_CALDERON, BEM_ESTATE without a single-body mesh. */
+bem_status bem_precond_matrix(const bem_ctx* ctx, int which, int64_t* rows, int64_t* cols, int64_t* nnz,
+                              int32_t* ptr, int32_t* col, double* val);
 
 /* Normalised plane-wave right-hand sides (tested fields after Eq. 8):
  * E_inc = e0 exp(-j k0 khat.r), H_inc = khat x E_inc / eta0, b = [e ; eta0 h].

@@ -19,6 +19,7 @@ BEM_OK, BEM_EINVAL, BEM_ENOMEM, BEM_ECUDA, BEM_ENOCONV, BEM_ETIMEOUT, BEM_ESTATE
 BEM_PREC_C64, BEM_PREC_C128, BEM_PREC_BF16F = 1, 2, 4
 BEM_C64, BEM_C128, BEM_C64_BF16F, BEM_C64_TC = 0, 1, 2, 3
 BEM_SOLVER_GMRES, BEM_SOLVER_CGS, BEM_SOLVER_BICGSTAB, BEM_SOLVER_CGNR = 0, 1, 2, 3
+BEM_PRECOND_NONE, BEM_PRECOND_CALDERON = 0, 1
 STATUS_NAMES = {0: "BEM_OK", 1: "BEM_EINVAL", 2: "BEM_ENOMEM", 3: "BEM_ECUDA", 4: "BEM_ENOCONV",
                 5: "BEM_ETIMEOUT", 6: "BEM_ESTATE"}
 
@@ -32,7 +33,7 @@ EXPORTS = [
     "bem_autotune", "bem_batch_create", "bem_batch_launch", "bem_batch_destroy", "bem_set_regions",
     "bem_region_boundary", "bem_num_regions", "bem_planar_operators", "bem_measure_fma_peak",
     "bem_debug_fail_alloc_after", "bem_planar_calderon", "bem_fft", "bem_planar_skeleton",
-    "bem_planar_woodbury_solve",
+    "bem_planar_woodbury_solve", "bem_precond_apply", "bem_precond_matrix",
 ]
 KERNEL_NAMES = ["k_gather", "k_vhx", "k_rows"]   # BEM_KERNEL_GATHER, _VHX, _ROWS
 
@@ -43,6 +44,7 @@ class bem_options(ctypes.Structure):
         ("aca_tol", ctypes.c_double), ("aca_max_rank", ctypes.c_int), ("gmres_restart", ctypes.c_int),
         ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("refine_tol", ctypes.c_double),
         ("refine_maxit", ctypes.c_int), ("solver", ctypes.c_int), ("aca_recompress", ctypes.c_int),
+        ("preconditioner", ctypes.c_int), ("precond_aca_tol", ctypes.c_double),
     ]
 
 
@@ -64,6 +66,9 @@ class bem_stats(ctypes.Structure):
         ("assemble_ms", ctypes.c_double),
         ("assemble_phase_ms", ctypes.c_double * 5),
         ("tc_passes", ctypes.c_int64),
+        ("precond_fine_ne", ctypes.c_int64), ("precond_gram_nnz", ctypes.c_int64),
+        ("precond_gram_steps", ctypes.c_int64), ("precond_bytes_c64", ctypes.c_int64),
+        ("precond_gram_interval", ctypes.c_double * 2), ("precond_assemble_ms", ctypes.c_double),
     ]
 
 
@@ -132,6 +137,8 @@ def _load():
         "bem_planar_woodbury_solve": (ctypes.c_int, [ctx, vp, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp,
                                                      ctypes.c_int, vp]),
         "bem_debug_fail_alloc_after": (None, [ctypes.c_longlong]),
+        "bem_precond_apply": (ctypes.c_int, [ctx, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
+        "bem_precond_matrix": (ctypes.c_int, [ctx, ctypes.c_int, i64p, i64p, i64p, i32p, i32p, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -250,7 +257,8 @@ def bem_stats_get(ctx) -> dict:
     s = bem_stats()
     _check(ctx, lib.bem_stats_get(ctx, ctypes.byref(s)))
     d = {name: getattr(s, name) for name, _ in bem_stats._fields_}
-    for k in ("factor_entries", "kernel_bytes_c64", "kernel_bytes_c128", "kernel_bytes_bf16f", "kernel_bytes_tc"):
+    for k in ("factor_entries", "kernel_bytes_c64", "kernel_bytes_c128", "kernel_bytes_bf16f", "kernel_bytes_tc",
+              "precond_gram_interval"):
         d[k] = list(getattr(s, k))
     d["assemble_phase_ms"] = dict(zip(PHASE_NAMES, s.assemble_phase_ms))
     return d
@@ -269,6 +277,27 @@ def bem_partition(ctx):
 def bem_eval_entries(ctx, rows_ptr: int, cols_ptr: int, count: int, out_ptr: int, dtype: int, stream: int = 0) -> None:
     _check(ctx, lib.bem_eval_entries(ctx, ctypes.c_void_p(rows_ptr), ctypes.c_void_p(cols_ptr), int(count),
                                      ctypes.c_void_p(out_ptr), int(dtype), ctypes.c_void_p(stream)))
+
+
+def bem_precond_apply(ctx, x_ptr: int, y_ptr: int, nrhs: int, dtype: int, stream: int = 0) -> None:
+    """y = P x with the Calderon preconditioner (device pointers, 2ne x nrhs)."""
+    _check(ctx, lib.bem_precond_apply(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), int(nrhs), int(dtype),
+                                      ctypes.c_void_p(stream)))
+
+
+def bem_precond_matrix(ctx, which: int):
+    """(rows, cols, ptr, col, val) of the preconditioner's matrix `which` (0: C, 1: G), host arrays."""
+    rows, cols, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, lib.bem_precond_matrix(ctx, int(which), ctypes.byref(rows), ctypes.byref(cols), ctypes.byref(nnz),
+                                       None, None, None))
+    ptr = np.empty(rows.value + 1, np.int32)
+    col = np.empty(nnz.value, np.int32)
+    val = np.empty(nnz.value, np.float64)
+    _check(ctx, lib.bem_precond_matrix(ctx, int(which), None, None, None,
+                                       ptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       val.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return rows.value, cols.value, ptr, col, val
 
 
 def bem_matvec(ctx, x_ptr: int, y_ptr: int, nrhs: int, dtype: int, stream: int = 0) -> None:

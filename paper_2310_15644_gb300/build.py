@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "libbem.so")
 STAMP = os.path.join(OBJ, "libbem.stamp")
 SOURCES = ["bem_api.cu", "tree.cu", "singular.cu", "assemble.cu", "matvec.cu", "krylov.cu", "rhs_power.cu",
            "gradient.cu", "planar.cu", "matvec_tc.cu", "gmres.cu", "peak.cu", "recompress.cu",
-           "planar_pipeline.cu",
+           "planar_pipeline.cu", "calderon.cu",
            "static_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",

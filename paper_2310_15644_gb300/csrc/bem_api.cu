@@ -189,6 +189,19 @@ struct bem_ctx {
     int* tc_err_dev = nullptr;
     DevBuf d_rx, d_ry;   // one region's operand and product
     DevBuf d_xext;       // the currents of the exterior boundary (powers)
+    // Calderon preconditioner (BEM_PRECOND_CALDERON): refined-mesh context, sparse
+    // matrices (host copies and FP32/FP64 device copies), Chebyshev plan, work
+    struct Calderon {
+        bem_ctx* fine = nullptr;
+        cald::Csr C, Ct, G, Gt;
+        cald::ChebPlan plan;
+        DevBuf ptr[4], col[4], val32[4], val64[4];  // C, C^T, G, G^T
+        DevBuf dinv32, dinv64;
+        DevBuf u, r, d0, d1, vf, wf, py;
+        double ms = 0;
+        bool host = false;   // refinement, C, G and the plan (host only)
+        bool built = false;  // plus the refined operator and the device copies
+    } cal;
 };
 
 // ---------------------------------------------------------------------------
@@ -323,13 +336,33 @@ static void release_operator(Operator& o) {
     for (int i = 0; i < 3; ++i) o.factor_entries[i] = 0;
 }
 
+extern "C" void bem_destroy(bem_ctx* c);
+
+static void release_calderon(bem_ctx* c) {
+    auto& K = c->cal;
+    if (K.fine) bem_destroy(K.fine);
+    K.fine = nullptr;
+    for (int i = 0; i < 4; ++i) {
+        dfree(K.ptr[i]);
+        dfree(K.col[i]);
+        dfree(K.val32[i]);
+        dfree(K.val64[i]);
+    }
+    DevBuf* w[] = {&K.dinv32, &K.dinv64, &K.u, &K.r, &K.d0, &K.d1, &K.vf, &K.wf, &K.py};
+    for (DevBuf* b : w) dfree(*b);
+    K.C = K.Ct = K.G = K.Gt = cald::Csr();
+    K.plan = cald::ChebPlan();
+    K.ms = 0;
+    K.host = false;
+    K.built = false;
+}
+
 static void invalidate(bem_ctx* c) {
     c->assembled = false;
     c->tc_passes = 0;
     for (int i = 0; i < 2; ++i) release_operator(c->op[i]);
+    release_calderon(c);
 }
-
-extern "C" void bem_destroy(bem_ctx* c);
 
 // back to one body: drop the regions' contexts
 static void clear_regions(bem_ctx* c) {
@@ -363,6 +396,8 @@ extern "C" void bem_default_options(bem_options* o) {
     o->refine_maxit = 10;
     o->solver = BEM_SOLVER_GMRES;
     o->aca_recompress = 1;
+    o->preconditioner = BEM_PRECOND_NONE;
+    o->precond_aca_tol = 1e-3;
 }
 
 extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
@@ -374,7 +409,9 @@ extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
     if (o.leaf_size < 2 || o.leaf_size > BEM_MAX_LEAF || (o.precision & 7) == 0 || (o.precision & ~7) != 0 ||
         o.aca_tol <= 0 || o.aca_max_rank < 1 || o.aca_max_rank > 128 || o.gmres_restart < 1 || o.gmres_restart > 200 || o.maxit < 1 ||
         o.tol <= 0 || o.refine_tol < 0 || o.refine_maxit < 1 || o.solver < BEM_SOLVER_GMRES ||
-        o.solver > BEM_SOLVER_CGNR || o.aca_recompress < 0 || o.aca_recompress > 1)
+        o.solver > BEM_SOLVER_CGNR || o.aca_recompress < 0 || o.aca_recompress > 1 ||
+        o.preconditioner < BEM_PRECOND_NONE || o.preconditioner > BEM_PRECOND_CALDERON ||
+        !(o.precond_aca_tol > 0) || !(o.precond_aca_tol < 1))
         return BEM_EINVAL;
     bem_ctx* c = new (std::nothrow) bem_ctx();
     if (!c) return BEM_ENOMEM;
@@ -1458,9 +1495,92 @@ static bem_status assemble_layered(bem_ctx* c, void* stream) {
     return BEM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Calderon preconditioner: the refined-mesh context and the sparse matrices
+// (calderon.cu holds the constructions and the kernels)
+// ---------------------------------------------------------------------------
+static MeshTables mesh_tables(const bem_ctx* c) {
+    MeshTables m;
+    m.nv = c->nv;
+    m.nt = c->nt;
+    m.ne = c->ne;
+    m.verts = c->verts.data();
+    m.tris = c->tris.data();
+    m.edge_v = c->edge_v.data();
+    m.edge_tri = c->edge_tri.data();
+    m.edge_loc = c->edge_loc.data();
+    m.tri_edge = c->tri_edge.data();
+    m.tri_coef = c->tri_coef.data();
+    m.area = c->area.data();
+    m.nrm = c->nrm.data();
+    return m;
+}
+
+// refinement, refined-mesh context with its mesh, BC and Gram matrices, Chebyshev plan
+static bem_status calderon_host(bem_ctx* c) {
+    auto& K = c->cal;
+    if (K.host) return BEM_OK;
+    const MeshTables mc = mesh_tables(c);
+    std::vector<double> fv;
+    std::vector<int> ft;
+    cald::refine(mc, fv, ft);
+    bem_options fo = c->opt;
+    fo.preconditioner = BEM_PRECOND_NONE;
+    fo.aca_tol = c->opt.precond_aca_tol;
+    bem_status s = bem_create(&fo, &K.fine);
+    if (s != BEM_OK) return fail(c, s, "Calderon preconditioner: cannot create the refined-mesh context");
+    auto sub_fail = [&](bem_status s2, const char* what) {
+        return fail(c, s2, std::string("Calderon preconditioner, ") + what + ": " + K.fine->err);
+    };
+    if ((s = bem_set_mesh(K.fine, fv.data(), (int64_t)fv.size() / 3, ft.data(), (int64_t)ft.size() / 3)) != BEM_OK)
+        return sub_fail(s, "refined mesh");
+    const MeshTables mf = mesh_tables(K.fine);
+    std::string err;
+    if (!cald::bc_matrix(mc, mf, K.C, err)) return fail(c, BEM_EINVAL, "Calderon preconditioner: " + err);
+    K.Ct = cald::transpose(K.C);
+    cald::mixed_gram(mc, mf, K.C, K.G);
+    K.Gt = cald::transpose(K.G);
+    if (!cald::chebyshev_plan(K.G, 1e-6, 60, K.plan, err)) return fail(c, BEM_EINVAL, "Calderon preconditioner: " + err);
+    K.host = true;
+    return BEM_OK;
+}
+
+static bem_status build_calderon(bem_ctx* c, cudaStream_t st) {
+    auto t0 = std::chrono::steady_clock::now();
+    auto& K = c->cal;
+    bem_status s;
+    if ((s = calderon_host(c)) != BEM_OK) return s;
+    const bem_c128 e{c->eps.re, c->eps.im}, m{c->mu.re, c->mu.im};
+    if ((s = bem_set_media(K.fine, c->k0, e, m)) != BEM_OK)
+        return fail(c, s, std::string("Calderon preconditioner, media: ") + K.fine->err);
+    if ((s = bem_assemble(K.fine, st)) != BEM_OK)
+        return fail(c, s, std::string("Calderon preconditioner, refined operator: ") + K.fine->err);
+    const cald::Csr* mats[4] = {&K.C, &K.Ct, &K.G, &K.Gt};
+    for (int i = 0; i < 4; ++i) {
+        CK(upload(K.ptr[i], mats[i]->ptr, st));
+        CK(upload(K.col[i], mats[i]->col, st));
+        CK(upload(K.val64[i], mats[i]->val, st));
+        const std::vector<float> v32(mats[i]->val.begin(), mats[i]->val.end());
+        CK(upload(K.val32[i], v32, st));
+    }
+    std::vector<double> dinv(c->ne, 0.0);
+    for (int64_t r = 0; r < c->ne; ++r)
+        for (int p = K.G.ptr[r]; p < K.G.ptr[r + 1]; ++p)
+            if (K.G.col[p] == r) dinv[r] = 1.0 / K.G.val[p];
+    CK(upload(K.dinv64, dinv, st));
+    const std::vector<float> d32(dinv.begin(), dinv.end());
+    CK(upload(K.dinv32, d32, st));
+    CK(cudaStreamSynchronize(st));
+    K.built = true;
+    K.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return BEM_OK;
+}
+
 extern "C" bem_status bem_assemble(bem_ctx* c, void* stream) {
     if (!c) return BEM_EINVAL;
     if (!c->has_mesh || !c->has_media) return fail(c, BEM_ESTATE, "bem_assemble needs bem_set_mesh and bem_set_media");
+    if (layered(c) && c->opt.preconditioner != BEM_PRECOND_NONE)
+        return fail(c, BEM_EINVAL, "the Calderon preconditioner is available for single-body contexts only");
     if (layered(c)) return assemble_layered(c, stream);
     cudaStream_t st = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
@@ -1482,6 +1602,8 @@ extern "C" bem_status bem_assemble(bem_ctx* c, void* stream) {
     if (c->opt.precision & BEM_PREC_C128)
         if ((s = build_operator<double>(c, c->op[1], st)) != BEM_OK) return s;
     CK(cudaStreamSynchronize(st));
+    if (c->opt.preconditioner == BEM_PRECOND_CALDERON)
+        if ((s = build_calderon(c, st)) != BEM_OK) return s;
     c->assemble_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     c->assembled = true;
     c->err.clear();
@@ -1584,6 +1706,25 @@ extern "C" bem_status bem_stats_get(const bem_ctx* cc, bem_stats* out) {
     out->assemble_ms = c->assemble_ms;
     out->tc_passes = c->tc_passes;
     for (int i = 0; i < BEM_PHASES; ++i) out->assemble_phase_ms[i] = c->phase_ms[i];
+    if (c->cal.built) {
+        const auto& K = c->cal;
+        bem_stats fs;
+        bem_status s = bem_stats_get(K.fine, &fs);
+        if (s != BEM_OK) return fail(c, s, K.fine->err);
+        const int64_t ne = c->ne, nf = K.fine->ne, es = 8;
+        const int64_t nnzC = (int64_t)K.C.val.size(), nnzG = (int64_t)K.G.val.size();
+        // per vector (two blocks of ne): Chebyshev init reads b and writes r, d, x; every
+        // further step reads G and d, reads and writes r and x, writes d'
+        const int64_t gram = es * 2 * ne * 4 + (K.plan.steps - 1) * (8 * nnzG + es * 2 * ne * 6);
+        const int64_t csr = 8 * nnzC + es * 2 * (ne + nf);
+        out->precond_fine_ne = nf;
+        out->precond_gram_nnz = nnzG;
+        out->precond_gram_steps = K.plan.steps;
+        out->precond_bytes_c64 = fs.matvec_bytes_c64 + 2 * gram + 2 * csr;
+        out->precond_gram_interval[0] = K.plan.lmin;
+        out->precond_gram_interval[1] = K.plan.lmax;
+        out->precond_assemble_ms = K.ms;
+    }
     return BEM_OK;
 }
 
@@ -1982,6 +2123,59 @@ static cudaError_t matvec_any(bem_ctx* c, int dtype, const void* x, void* y, int
                               (c128*)y, (c128*)o.xp.p, (c128*)o.t.p, nrhs, o.t_len, st, ev, BEM_FORM_NATIVE, adjoint);
 }
 
+// y = P x with the Calderon preconditioner for k vectors (2 k blocks of ne):
+// u = G^-1 x, v = C u, w = Z_fine v, u = -C^T w, y = G^-T u
+template <typename R>
+static cudaError_t calderon_steps(bem_ctx* c, int dtype, const void* x, void* y, int k, cudaStream_t st) {
+    auto& K = c->cal;
+    typedef cx<R> V;
+    const bool dp = sizeof(R) == 8;
+    const int64_t ne = c->ne, nf = K.fine->ne;
+    const int nb = 2 * k;
+    auto ptr = [&](int i) { return (const int*)K.ptr[i].p; };
+    auto col = [&](int i) { return (const int*)K.col[i].p; };
+    auto val = [&](int i) { return (const R*)(dp ? K.val64[i].p : K.val32[i].p); };
+    const R* dinv = (const R*)(dp ? K.dinv64.p : K.dinv32.p);
+    V *u = (V*)K.u.p, *r = (V*)K.r.p, *d0 = (V*)K.d0.p, *d1 = (V*)K.d1.p, *vf = (V*)K.vf.p, *wf = (V*)K.wf.p;
+    BEM_CUDA_TRY(cald::chebyshev_solve<R>(ptr(2), col(2), val(2), dinv, ne, K.plan, (const V*)x, u, r, d0, d1, nb, st));
+    BEM_CUDA_TRY(cald::csr_apply<R>(ptr(0), col(0), val(0), nf, u, ne, vf, nf, nb, (R)1, st));
+    BEM_CUDA_TRY(matvec_any(K.fine, dtype, vf, wf, k, st));
+    BEM_CUDA_TRY(cald::csr_apply<R>(ptr(1), col(1), val(1), ne, wf, nf, u, ne, nb, (R)-1, st));
+    return cald::chebyshev_solve<R>(ptr(3), col(3), val(3), dinv, ne, K.plan, u, (V*)y, r, d0, d1, nb, st);
+}
+
+static cudaError_t calderon_apply(bem_ctx* c, int dtype, const void* x, void* y, int nrhs, cudaStream_t st) {
+    auto& K = c->cal;
+    const bool dp = vec_dtype(dtype) == BEM_C128;
+    const size_t es = dp ? sizeof(c128) : sizeof(c64);
+    const int64_t ne = c->ne, nf = K.fine->ne;
+    const int chunk = 32767;  // two blocks per vector on grid.y
+    const int kmax = std::min(nrhs, chunk);
+    BEM_CUDA_TRY(ensure(K.u, es * ne * 2 * kmax));
+    BEM_CUDA_TRY(ensure(K.r, es * ne * 2 * kmax));
+    BEM_CUDA_TRY(ensure(K.d0, es * ne * 2 * kmax));
+    BEM_CUDA_TRY(ensure(K.d1, es * ne * 2 * kmax));
+    BEM_CUDA_TRY(ensure(K.vf, es * nf * 2 * kmax));
+    BEM_CUDA_TRY(ensure(K.wf, es * nf * 2 * kmax));
+    for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+        const int k = std::min(chunk, nrhs - r0);
+        const char* xk = (const char*)x + es * 2 * ne * r0;
+        char* yk = (char*)y + es * 2 * ne * r0;
+        BEM_CUDA_TRY(dp ? calderon_steps<double>(c, dtype, xk, yk, k, st)
+                        : calderon_steps<float>(c, dtype, xk, yk, k, st));
+    }
+    return cudaSuccess;
+}
+
+// the operator the inner solver iterates on: Z, or Z P with the Calderon preconditioner
+static cudaError_t apply_op(bem_ctx* c, int dtype, const void* x, void* y, int nrhs, cudaStream_t st, bool adjoint) {
+    if (adjoint || !c->cal.built) return matvec_any(c, dtype, x, y, nrhs, st, false, adjoint);
+    const size_t es = vec_dtype(dtype) == BEM_C128 ? sizeof(c128) : sizeof(c64);
+    BEM_CUDA_TRY(ensure(c->cal.py, es * 2 * c->ne * nrhs));
+    BEM_CUDA_TRY(calderon_apply(c, dtype, x, c->cal.py.p, nrhs, st));
+    return matvec_any(c, dtype, c->cal.py.p, y, nrhs, st, false, false);
+}
+
 // ---------------------------------------------------------------------------
 // autotuner of the rows-kernel schedule
 // ---------------------------------------------------------------------------
@@ -2223,6 +2417,45 @@ extern "C" bem_status bem_matvec_adjoint(bem_ctx* c, const void* x, void* y, int
     return BEM_OK;
 }
 
+extern "C" bem_status bem_precond_apply(bem_ctx* c, const void* x, void* y, int nrhs, int dtype, void* stream) {
+    if (!c) return BEM_EINVAL;
+    if (!c->assembled || !c->cal.built)
+        return fail(c, BEM_ESTATE, "bem_precond_apply needs bem_assemble with BEM_PRECOND_CALDERON");
+    if (!dtype_ok(c, dtype)) return fail(c, BEM_EINVAL, "no operator of that precision was assembled");
+    if (nrhs < 1 || !x || !y) return fail(c, BEM_EINVAL, "bad arguments");
+    const int64_t bytes = (int64_t)esize_of(dtype) * 2 * c->ne * nrhs;
+    const char* xa = (const char*)x;
+    const char* ya = (const char*)y;
+    if (xa < ya + bytes && ya < xa + bytes) return fail(c, BEM_EINVAL, "x and y overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == BEM_C64_TC) {
+        bem_status s = prepare_tc(c->cal.fine, st);
+        if (s != BEM_OK) return fail(c, s, c->cal.fine->err);
+    }
+    CK(calderon_apply(c, dtype, x, y, nrhs, st));
+    return BEM_OK;
+}
+
+extern "C" bem_status bem_precond_matrix(const bem_ctx* cc, int which, int64_t* rows, int64_t* cols, int64_t* nnz,
+                                         int32_t* ptr, int32_t* col, double* val) {
+    bem_ctx* c = const_cast<bem_ctx*>(cc);
+    if (!c) return BEM_EINVAL;
+    if (c->opt.preconditioner != BEM_PRECOND_CALDERON)
+        return fail(c, BEM_EINVAL, "bem_precond_matrix needs a context created with BEM_PRECOND_CALDERON");
+    if (!c->has_mesh || layered(c)) return fail(c, BEM_ESTATE, "bem_precond_matrix needs a single-body mesh");
+    if (which != 0 && which != 1) return fail(c, BEM_EINVAL, "which: 0 (BC functions) or 1 (mixed Gram matrix)");
+    bem_status s = calderon_host(c);
+    if (s != BEM_OK) return s;
+    const cald::Csr& a = which == 0 ? c->cal.C : c->cal.G;
+    if (rows) *rows = a.rows;
+    if (cols) *cols = a.cols;
+    if (nnz) *nnz = (int64_t)a.val.size();
+    if (ptr) std::copy(a.ptr.begin(), a.ptr.end(), ptr);
+    if (col) std::copy(a.col.begin(), a.col.end(), col);
+    if (val) std::copy(a.val.begin(), a.val.end(), val);
+    return BEM_OK;
+}
+
 extern "C" bem_status bem_rhs_planewave(bem_ctx* c, const double* khat, const bem_c128* e0, int nrhs, void* b,
                                         int dtype, void* stream) {
     if (!c) return BEM_EINVAL;
@@ -2409,13 +2642,13 @@ static bem_status gmres_batched(bem_ctx* c, int pdt, const double* tol_abs, int 
     bool x_zero = true;
     for (;;) {
         // restart: slot 0 = b - Z x, normalised; which right-hand sides go on
-        if (!x_zero) CK(matvec_any(c, pdt, w.x.p, V, nr, st, false, adjoint));
+        if (!x_zero) CK(apply_op(c, pdt, w.x.p, V, nr, st, adjoint));
         CK(fp64 ? bgs_cycle_start<double>(a, x_zero, st) : bgs_cycle_start<float>(a, x_zero, st));
         x_zero = false;
         CK(cudaStreamSynchronize(st));
         if (*(volatile int*)w.host_active == 0) break;
         for (int j = 0; j < m; ++j) {
-            CK(matvec_any(c, pdt, V + slot * j, V + slot * (j + 1), nr, st, false, adjoint));
+            CK(apply_op(c, pdt, V + slot * j, V + slot * (j + 1), nr, st, adjoint));
             CK(fp64 ? bgs_iteration<double>(a, j, st) : bgs_iteration<float>(a, j, st));
             CK(cudaEventRecord(ev[j & 1], st));
             if (j >= 1) {
@@ -2457,6 +2690,7 @@ static bem_status solve_gmres_batched(bem_ctx* c, const void* b, void* x, int nr
         if (mj == 10 && mn == 3) {
             bem_status s0 = prepare_tc(c, st);
             if (s0 != BEM_OK) return s0;
+            if (c->cal.built && (s0 = prepare_tc(c->cal.fine, st)) != BEM_OK) return fail(c, s0, c->cal.fine->err);
             pin = BEM_C64_TC;
         }
     }
@@ -2515,7 +2749,10 @@ static bem_status solve_gmres_batched(bem_ctx* c, const void* b, void* x, int nr
             if (!more) break;
             for (int r = 0; r < k; ++r) {
                 const bool go = !fin[r] && !stopped[r] && bn[r] != 0;
-                tol_abs[r] = go ? c->opt.tol * rn[r] : HUGE_VAL;
+                // refinement steps after the first need only reach the outer target
+                tol_abs[r] = go ? (refine ? std::max(c->opt.tol * rn[r], 0.5 * c->opt.refine_tol * bn[r])
+                                          : c->opt.tol * rn[r])
+                                : HUGE_VAL;
                 before[r] = used[r];
             }
             // inner system Z d = r in the inner precision
@@ -2531,7 +2768,13 @@ static bem_status solve_gmres_batched(bem_ctx* c, const void* b, void* x, int nr
                 inner_ok[r] = fres[r] <= tol_abs[r] * 1.0000001;
                 if (used[r] >= c->opt.maxit || used[r] == before[r]) stopped[r] = 1;  // measured next, then left
             }
-            CK(kv_axpy_c128(xr, w.x.p, vin, (const c128*)c->d_one.p, 1.0, n * k, 1, n * k, st));
+            const void* dx = w.x.p;
+            if (c->cal.built && !adjoint) {  // right preconditioning: the correction is P y
+                CK(ensure(c->cal.py, (size_t)esize_of(vin) * n * k));
+                CK(calderon_apply(c, pin, w.x.p, c->cal.py.p, k, st));
+                dx = c->cal.py.p;
+            }
+            CK(kv_axpy_c128(xr, dx, vin, (const c128*)c->d_one.p, 1.0, n * k, 1, n * k, st));
         }
         for (int r = 0; r < k; ++r) {
             total_it += used[r];
@@ -2708,6 +2951,8 @@ static bem_status solve_impl(bem_ctx* c, const void* b, void* x, int nrhs, void*
         CK(cudaMemcpyAsync(c->d_one.p, &one1, sizeof(c128), cudaMemcpyHostToDevice, st));
         return solve_gmres_batched(c, b, x, nrhs, st, iters, relres, adjoint, din, dres);
     }
+    if (c->cal.built && !adjoint)
+        return fail(c, BEM_EINVAL, "the Calderon preconditioner is applied by the GMRES solver only");
     if ((s = krylov_work(c, vin)) != BEM_OK) return s;
     const int64_t n = 2 * c->ne;
     DevBuf zr, rr;
@@ -2755,11 +3000,12 @@ static bem_status solve_impl(bem_ctx* c, const void* b, void* x, int nrhs, void*
                 CK(cudaMemcpyAsync(c->gw.rin.p, rr.p, sizeof(c128) * n, cudaMemcpyDeviceToDevice, st));
             double fres;
             int before = total_it;
-            s = cg_family(c, din, c->opt.solver, c->opt.tol * rn, c->opt.maxit - total_it, &total_it, &fres, st,
+            const double tin = refine ? std::max(c->opt.tol * rn, 0.5 * c->opt.refine_tol * bn) : c->opt.tol * rn;
+            s = cg_family(c, din, c->opt.solver, tin, c->opt.maxit - total_it, &total_it, &fres, st,
                           adjoint);
             if (s != BEM_OK)
                 return s;
-            inner_ok = fres <= c->opt.tol * rn * 1.0000001;
+            inner_ok = fres <= tin * 1.0000001;
             CK(kv_axpy_c128(xr, c->gw.xin.p, vin, (const c128*)c->d_one.p, 1.0, n, 1, n, st));
             if (total_it >= c->opt.maxit || total_it == before) {
                 // out of iterations (or no progress possible): measure and stop

@@ -416,6 +416,51 @@ cudaError_t region_gather(const void* x, int esize, int64_t ne, const int* edges
 cudaError_t region_scatter_add(const void* ys, int esize, int64_t ne, const int* edges, const signed char* sign,
                                int64_t ns, int nrhs, void* y, cudaStream_t st);
 
+
+// ---------------------------------------------------------------------------
+// Calderon preconditioner (calderon.cu): Buffa-Christiansen functions on the
+// barycentric refinement, their mixed Gram matrix and its Chebyshev inverse
+// ---------------------------------------------------------------------------
+struct MeshTables {  // host views of a mesh and its RWG table (bem_set_mesh conventions)
+    int64_t nv = 0, nt = 0, ne = 0;
+    const double* verts = nullptr;    // nv x 3
+    const int* tris = nullptr;        // nt x 3, outward (counter-clockwise) order
+    const int* edge_v = nullptr;      // ne x 2, lexicographic (lo, hi)
+    const int* edge_tri = nullptr;    // ne x 2: T+, T-
+    const int* edge_loc = nullptr;    // ne x 2: corner of the free vertex in T+, T-
+    const int* tri_edge = nullptr;    // nt x 3: edge opposite corner i
+    const double* tri_coef = nullptr; // nt x 3: +l on T+, -l on T-
+    const double* area = nullptr;     // nt
+    const double* nrm = nullptr;      // nt x 3 unit outward normals
+};
+namespace cald {
+struct Csr {  // compressed sparse rows, FP64 values
+    int64_t rows = 0, cols = 0;
+    std::vector<int> ptr, col;
+    std::vector<double> val;
+};
+struct ChebPlan {  // fixed Chebyshev iteration for D^-1 A x = D^-1 b, eigenvalues in [lmin, lmax]
+    double lmin = 0, lmax = 0, theta = 0;
+    int steps = 0;                 // updates of x
+    std::vector<double> c1, c2;    // d_{k+1} = c1[k] d_k + c2[k] r_{k+1}
+    double reduction = 0;          // residual reduction measured on the host at plan time
+};
+void refine(const MeshTables& c, std::vector<double>& fverts, std::vector<int>& ftris);
+bool bc_matrix(const MeshTables& c, const MeshTables& f, Csr& C, std::string& err);
+Csr transpose(const Csr& a);
+void mixed_gram(const MeshTables& c, const MeshTables& f, const Csr& C, Csr& G);
+bool chebyshev_plan(const Csr& G, double target, int max_steps, ChebPlan& plan, std::string& err);
+// y_b = scale * A x_b for nblk blocks (x_b = x + b * xs, y_b = y + b * ys, complex R)
+template <typename R>
+cudaError_t csr_apply(const int* ptr, const int* col, const R* val, int64_t rows, const cx<R>* x, int64_t xs,
+                      cx<R>* y, int64_t ys, int nblk, R scale, cudaStream_t st);
+// x_b ~ A^-1 b_b for nblk blocks of n (stride n) by the plan's fixed Chebyshev steps;
+// dinv = 1 / diag(A); r, d0, d1: work of nblk * n values each
+template <typename R>
+cudaError_t chebyshev_solve(const int* ptr, const int* col, const R* val, const R* dinv, int64_t n,
+                            const ChebPlan& p, const cx<R>* b, cx<R>* x, cx<R>* r, cx<R>* d0, cx<R>* d1, int nblk,
+                            cudaStream_t st);
+}  // namespace cald
 }  // namespace bem
 
 #define BEM_CUDA_TRY(expr)                      \

@@ -479,7 +479,9 @@ __global__ void __launch_bounds__(BG_THREADS) k_bgs_xupdate(BgsArgs a) {
 // `x_zero`), beta = |b - Z x| per right-hand side, g_0 = beta, and the right-hand
 // side active while beta is above its tolerance and iterations remain; `scale` =
 // 1 / beta for the normalisation that follows (the rest of g is written by the
-// rotations before it is read).
+// rotations before it is read).  A right-hand side also stops when the previous
+// cycle reached the tolerance by its estimate but the recomputed residual did not
+// follow (rounding floor of the product, which outer refinement then removes).
 template <typename R>
 __global__ void __launch_bounds__(BG_THREADS) k_bgs_resid(BgsArgs a, int x_zero) {
     constexpr int PC = Pk<R>::PC;
@@ -518,8 +520,11 @@ __global__ void __launch_bounds__(BG_THREADS) k_bgs_resid(BgsArgs a, int x_zero)
         const double s = warp_sum_blocks(a.npart + (int64_t)r * a.nblk, a.nblk, 1);
         if (threadIdx.x == 0) {
             const double beta = sqrt(s);
+            // stalled at the product's rounding floor: the last cycle met the tolerance by
+            // its residual estimate, yet the true residual is above it and less than halved
+            const bool stalled = !x_zero && a.res[r] <= a.tol[r] && beta > 0.5 * a.beta[r];
             a.beta[r] = beta;
-            const bool act = beta > a.tol[r] && a.it[r] < a.maxit && beta == beta;
+            const bool act = beta > a.tol[r] && a.it[r] < a.maxit && beta == beta && !stalled;
             a.state[r] = act ? BGS_ACTIVE : 0;
             a.scale[r] = act ? 1.0 / beta : 0.0;
             a.kk[r] = 0;

@@ -258,3 +258,57 @@ def test_planar_operators_reject_bad_input_before_any_launch(B):
         with pytest.raises(B.BemError) as ei:
             B.bem_planar_operators(None, verts, k, 0, 0, 0)
         assert ei.value.status == B.BEM_EINVAL
+
+
+def _precond_ctx(B, v, t):
+    opt = B.bem_default_options()
+    opt.preconditioner = B.BEM_PRECOND_CALDERON
+    h = B.bem_create(opt)
+    B.bem_set_mesh(h, v, t)
+    return h
+
+
+def _dense(rows, cols, ptr, col, val):
+    A = np.zeros((rows, cols))
+    for r in range(rows):
+        A[r, col[ptr[r]:ptr[r + 1]]] += val[ptr[r]:ptr[r + 1]]
+    return A
+
+
+@pytest.mark.parametrize("mesh", ["ico2", "box"])
+def test_calderon_matrices_match_oracle(B, mesh):
+    """The library's Buffa-Christiansen coefficients C and mixed Gram matrix G (host,
+    FP64, built from the closed-form fluxes and a three-point rule) against the
+    oracle's (least-norm solves, seven-point rule) on a sphere and on a box whose
+    vertices have 4 to 8 neighbours."""
+    from oracle import calderon as CA
+
+    v, t = W.icosphere(2) if mesh == "ico2" else W.box_mesh(1.0, 0.7, 0.3, 4, 3, 2)
+    ref = CA.refine(rwg.build(v, t))
+    h = _precond_ctx(B, v, t)
+    try:
+        C = _dense(*B.bem_precond_matrix(h, 0))
+        G = _dense(*B.bem_precond_matrix(h, 1))
+    finally:
+        B.bem_destroy(h)
+    assert C.shape == ref.C.shape
+    assert np.abs(C - ref.C).max() <= 1e-12 * np.abs(ref.C).max()
+    Go = CA.mixed_gram(ref)
+    assert np.abs(G - Go).max() <= 1e-12 * np.abs(Go).max()
+
+
+def test_calderon_matrix_argument_checks(B):
+    v, t = W.icosphere(1)
+    h = B.bem_create()
+    try:
+        B.bem_set_mesh(h, v, t)
+        with pytest.raises(B.BemError):
+            B.bem_precond_matrix(h, 0)  # created without the preconditioner
+    finally:
+        B.bem_destroy(h)
+    h = _precond_ctx(B, v, t)
+    try:
+        with pytest.raises(B.BemError):
+            B.bem_precond_matrix(h, 2)
+    finally:
+        B.bem_destroy(h)
