@@ -44,7 +44,7 @@ class bem_options(ctypes.Structure):
         ("aca_tol", ctypes.c_double), ("aca_max_rank", ctypes.c_int), ("gmres_restart", ctypes.c_int),
         ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("refine_tol", ctypes.c_double),
         ("refine_maxit", ctypes.c_int), ("solver", ctypes.c_int), ("aca_recompress", ctypes.c_int),
-        ("preconditioner", ctypes.c_int), ("precond_aca_tol", ctypes.c_double),
+        ("preconditioner", ctypes.c_int), ("precond_aca_tol", ctypes.c_double), ("precond_near_only", ctypes.c_int),
     ]
 
 

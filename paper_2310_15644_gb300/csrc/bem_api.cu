@@ -183,6 +183,7 @@ struct bem_ctx {
         DevBuf d_edges, d_sign;
     };
     std::vector<Region> regions;
+    bool near_only = false;       // drop the far blocks (near-field refined operator of a preconditioner)
     int num_sms = 0;              // persistent CTAs of the tensor-core kernels
     int64_t tc_passes = 0;        // tensor-core operator passes since the last assembly
     int* tc_err_host = nullptr;   // set by a tensor-core kernel whose bounded wait ran out (mapped host memory)
@@ -397,7 +398,8 @@ extern "C" void bem_default_options(bem_options* o) {
     o->solver = BEM_SOLVER_GMRES;
     o->aca_recompress = 1;
     o->preconditioner = BEM_PRECOND_NONE;
-    o->precond_aca_tol = 1e-3;
+    o->precond_aca_tol = 3e-2;
+    o->precond_near_only = 0;
 }
 
 extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
@@ -411,7 +413,7 @@ extern "C" bem_status bem_create(const bem_options* opt, bem_ctx** out) {
         o.tol <= 0 || o.refine_tol < 0 || o.refine_maxit < 1 || o.solver < BEM_SOLVER_GMRES ||
         o.solver > BEM_SOLVER_CGNR || o.aca_recompress < 0 || o.aca_recompress > 1 ||
         o.preconditioner < BEM_PRECOND_NONE || o.preconditioner > BEM_PRECOND_CALDERON ||
-        !(o.precond_aca_tol > 0) || !(o.precond_aca_tol < 1))
+        !(o.precond_aca_tol > 0) || !(o.precond_aca_tol < 1) || o.precond_near_only < 0 || o.precond_near_only > 1)
         return BEM_EINVAL;
     bem_ctx* c = new (std::nothrow) bem_ctx();
     if (!c) return BEM_ENOMEM;
@@ -1207,7 +1209,8 @@ static bem_status build_operator(bem_ctx* c, Operator& o, cudaStream_t st) {
     }
     const int64_t budget = std::max<int64_t>(1, budget_bytes / (int64_t)es);  // complex elements
     const int rcap = c->opt.aca_max_rank;
-    std::vector<BlockDesc> work = c->far_blocks;
+    // the refined operator of a near-field Calderon preconditioner keeps no far blocks
+    std::vector<BlockDesc> work = c->near_only ? std::vector<BlockDesc>() : c->far_blocks;
     o.n_far_split = 0;
     while (!work.empty()) {
         const int nw = (int)work.size();
@@ -1540,7 +1543,11 @@ static bem_status calderon_host(bem_ctx* c) {
     K.Ct = cald::transpose(K.C);
     cald::mixed_gram(mc, mf, K.C, K.G);
     K.Gt = cald::transpose(K.G);
-    if (!cald::chebyshev_plan(K.G, 1e-6, 60, K.plan, err)) return fail(c, BEM_EINVAL, "Calderon preconditioner: " + err);
+    // G^-1 as accurate as the refined operator needs: a hundredth of its ACA tolerance,
+    // between 1e-10 and 1e-4
+    const double gram_target = std::min(1e-4, std::max(1e-10, 0.01 * c->opt.precond_aca_tol));
+    if (!cald::chebyshev_plan(K.G, gram_target, 60, K.plan, err))
+        return fail(c, BEM_EINVAL, "Calderon preconditioner: " + err);
     K.host = true;
     return BEM_OK;
 }
@@ -1553,6 +1560,7 @@ static bem_status build_calderon(bem_ctx* c, cudaStream_t st) {
     const bem_c128 e{c->eps.re, c->eps.im}, m{c->mu.re, c->mu.im};
     if ((s = bem_set_media(K.fine, c->k0, e, m)) != BEM_OK)
         return fail(c, s, std::string("Calderon preconditioner, media: ") + K.fine->err);
+    K.fine->near_only = c->opt.precond_near_only != 0;
     if ((s = bem_assemble(K.fine, st)) != BEM_OK)
         return fail(c, s, std::string("Calderon preconditioner, refined operator: ") + K.fine->err);
     const cald::Csr* mats[4] = {&K.C, &K.Ct, &K.G, &K.Gt};

@@ -35,7 +35,7 @@
 //   * G^-1 by a fixed number of Chebyshev steps on D^-1 G (D = diag G), whose
 //     eigenvalues are real to a few 1e-3 and lie in a fixed interval under
 //     refinement: the interval comes from power iterations, the step count from a
-//     host run on a pseudo-random vector.  A fixed polynomial keeps the
+//     host run on a pseudo-random vector (to the caller's target).  A fixed polynomial keeps the
 //     preconditioner linear, so GMRES sees one fixed operator.
 #include "common.cuh"
 

@@ -4,7 +4,7 @@ oracle (oracle/calderon.py):
   * bem_precond_apply equals the oracle's dense P = -Gb^-T Z_BC Gb^-1 applied to
     seeded vectors, element by element (max |y - y_ref| / max |y_ref|), with the
     refined operator compressed at 1e-8 so that only the Chebyshev inverse of G
-    (1e-6) and the vector precision separate them: 2e-5 for complex128, 1e-4 for
+    (1e-10, a hundredth of that tolerance) and the vector precision separate them: 2e-5 for complex128, 1e-4 for
     complex64;
   * the preconditioned GMRES solve reaches the oracle's dense LU solution to the
     tolerance the compression allows, and its iteration count stays flat from
