@@ -537,7 +537,7 @@ def run_batched_solve(dev, stream, B, W, h, tc_ms):
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
     passes = B.bem_stats_get(h)["tc_passes"] - p0
-    pa, pe, ps = B.bem_power(h, xs.data_ptr(), bd.data_ptr(), nw, sp)
+    pa, pe, _ = B.bem_power(h, xs.data_ptr(), bd.data_ptr(), nw, sp, scattered=False)
     # the same waves one at a time (first 4)
     x1 = torch.zeros_like(bd[:4])
     torch.cuda.synchronize(dev)
@@ -815,7 +815,7 @@ def calderon_batched(dev, sp, B, W, h, n, nw=64):
     it, rel, st = B.bem_solve(h, bw.data_ptr(), xw.data_ptr(), nw, sp, raise_on_noconv=False)
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
-    pa, _, _ = B.bem_power(h, xw.data_ptr(), bw.data_ptr(), nw, sp)
+    pa, _, _ = B.bem_power(h, xw.data_ptr(), bw.data_ptr(), nw, sp, scattered=False)
     return {"waves": nw, "seconds": round(dt, 3), "solves_per_s": round(nw / dt, 2), "converged": st == 0,
             "iterations_mean": round(it / nw, 1), "relres_max": float(np.max(rel)),
             "Q_abs_first4": [float(q) / np.pi for q in pa[:4]]}
@@ -1158,6 +1158,8 @@ def main():
     ap.add_argument("--no-calderon", action="store_true", help="skip the Calderon-preconditioned solves")
     ap.add_argument("--tc-only", action="store_true",
                     help="only the tensor-core product of 64 vectors (profiling captures of its kernels)")
+    ap.add_argument("--calderon-only", action="store_true",
+                    help="only the plain and Calderon-preconditioned solves at --level (profiling captures)")
     ap.add_argument("--level", type=int, default=5,
                     help="icosphere level (5 = the 61440-unknown workload; smaller levels for profiling captures)")
     args = ap.parse_args()
@@ -1181,7 +1183,18 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         tdist.init_process_group("nccl")
         dist = tdist
-    out = run_tc_only(args) if args.tc_only else run_native(args, rank, world, dist)
+    if args.tc_only:
+        out = run_tc_only(args)
+    elif args.calderon_only:
+        import torch
+
+        import paper_2310_15644_gb300.bem as B
+        import workloads as W
+
+        dev = torch.device("cuda", 0)
+        out = run_calderon(args, dev, torch.cuda.current_stream(dev), B, W, levels=(LEVEL,))
+    else:
+        out = run_native(args, rank, world, dist)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

@@ -445,13 +445,15 @@ def bem_batch_destroy(batch) -> None:
     lib.bem_batch_destroy(batch)
 
 
-def bem_power(ctx, x_ptr: int, b_ptr: int, nrhs: int, stream: int = 0):
+def bem_power(ctx, x_ptr: int, b_ptr: int, nrhs: int, stream: int = 0, scattered: bool = True):
+    """(P_abs, P_ext, P_sca) per right-hand side; scattered=False skips the far-field
+    integral of P_sca (returned as NaN)."""
     pa = np.zeros(nrhs)
     pe = np.zeros(nrhs)
-    ps = np.zeros(nrhs)
+    ps = np.zeros(nrhs) if scattered else np.full(nrhs, np.nan)
     _check(ctx, lib.bem_power(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(b_ptr), int(nrhs),
                               _np_ptr(pa, ctypes.c_double), _np_ptr(pe, ctypes.c_double),
-                              _np_ptr(ps, ctypes.c_double), ctypes.c_void_p(stream)))
+                              _np_ptr(ps, ctypes.c_double) if scattered else None, ctypes.c_void_p(stream)))
     return pa, pe, ps
 
 

@@ -369,31 +369,43 @@ bool chebyshev_plan(const Csr& G, double target, int max_steps, ChebPlan& plan, 
 }
 
 // ---------------------------------------------------------------------------
-// device: sparse products and Chebyshev steps on nblk blocks (grid.y)
+// device: sparse products and Chebyshev steps on nblk blocks.  A thread takes one
+// row for BCH consecutive blocks (grid.y = blocks / BCH), so each matrix row is
+// read once per BCH blocks; the blocks' vectors are gathered from L2.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int CT = 256;
 
-template <typename R>
+template <typename R, int BCH>
 __global__ void __launch_bounds__(CT) k_csr_apply(const int* __restrict__ ptr, const int* __restrict__ col,
                                                  const R* __restrict__ val, int64_t rows,
                                                  const cx<R>* __restrict__ x, int64_t xs, cx<R>* __restrict__ y,
-                                                 int64_t ys, R scale) {
+                                                 int64_t ys, int nblk, R scale) {
     const int64_t r = (int64_t)blockIdx.x * CT + threadIdx.x;
     if (r >= rows) return;
-    const cx<R>* xb = x + (int64_t)blockIdx.y * xs;
-    cx<R> s = mk<R>(0, 0);
+    const int b0 = blockIdx.y * BCH;
+    const int nb = min(BCH, nblk - b0);
+    cx<R> s[BCH];
+#pragma unroll
+    for (int u = 0; u < BCH; ++u) s[u] = mk<R>(0, 0);
     for (int p = ptr[r]; p < ptr[r + 1]; ++p) {
         const R a = val[p];
-        const cx<R> v = xb[col[p]];
-        s.re += a * v.re;
-        s.im += a * v.im;
+        const cx<R>* xc = x + (int64_t)b0 * xs + col[p];
+#pragma unroll
+        for (int u = 0; u < BCH; ++u)
+            if (u < nb) {
+                const cx<R> v = xc[(int64_t)u * xs];
+                s[u].re += a * v.re;
+                s[u].im += a * v.im;
+            }
     }
-    y[(int64_t)blockIdx.y * ys + r] = scale * s;
+#pragma unroll
+    for (int u = 0; u < BCH; ++u)
+        if (u < nb) y[(int64_t)(b0 + u) * ys + r] = scale * s[u];
 }
 
-// r = D^-1 b, d0 = r / theta, x = d0 (the first update)
+// r = D^-1 b, d0 = r / theta, x = d0 (the first update); one thread per entry
 template <typename R>
 __global__ void __launch_bounds__(CT) k_cheb_init(const R* __restrict__ dinv, int64_t n, R inv_theta,
                                                  const cx<R>* __restrict__ b, cx<R>* __restrict__ x,
@@ -409,28 +421,45 @@ __global__ void __launch_bounds__(CT) k_cheb_init(const R* __restrict__ dinv, in
 }
 
 // r -= D^-1 A d; d' = c1 d + c2 r; x += d'
-template <typename R>
+template <typename R, int BCH>
 __global__ void __launch_bounds__(CT) k_cheb_step(const int* __restrict__ ptr, const int* __restrict__ col,
                                                  const R* __restrict__ val, const R* __restrict__ dinv, int64_t n,
                                                  const cx<R>* __restrict__ d, cx<R>* __restrict__ dn,
-                                                 cx<R>* __restrict__ r, cx<R>* __restrict__ x, R c1, R c2) {
+                                                 cx<R>* __restrict__ r, cx<R>* __restrict__ x, int nblk, R c1,
+                                                 R c2) {
     const int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x;
     if (i >= n) return;
-    const int64_t base = (int64_t)blockIdx.y * n;
-    const cx<R>* db = d + base;
-    cx<R> s = mk<R>(0, 0);
+    const int b0 = blockIdx.y * BCH;
+    const int nb = min(BCH, nblk - b0);
+    cx<R> s[BCH];
+#pragma unroll
+    for (int u = 0; u < BCH; ++u) s[u] = mk<R>(0, 0);
     for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
         const R a = val[p];
-        const cx<R> v = db[col[p]];
-        s.re += a * v.re;
-        s.im += a * v.im;
+        const cx<R>* dc = d + (int64_t)b0 * n + col[p];
+#pragma unroll
+        for (int u = 0; u < BCH; ++u)
+            if (u < nb) {
+                const cx<R> v = dc[(int64_t)u * n];
+                s[u].re += a * v.re;
+                s[u].im += a * v.im;
+            }
     }
-    const cx<R> ri = r[base + i] - dinv[i] * s;
-    r[base + i] = ri;
-    const cx<R> di = c1 * db[i] + c2 * ri;
-    dn[base + i] = di;
-    x[base + i] = x[base + i] + di;
+    const R di = dinv[i];
+#pragma unroll
+    for (int u = 0; u < BCH; ++u)
+        if (u < nb) {
+            const int64_t o = (int64_t)(b0 + u) * n + i;
+            const cx<R> ri = r[o] - di * s[u];
+            r[o] = ri;
+            const cx<R> dv = c1 * d[o] + c2 * ri;
+            dn[o] = dv;
+            x[o] = x[o] + dv;
+        }
 }
+
+constexpr int BCH_MANY = 8;  // blocks per thread for many right-hand sides
+constexpr int BCH_FEW = 2;   // one right-hand side: its J and M blocks
 
 }  // namespace
 
@@ -438,9 +467,14 @@ template <typename R>
 cudaError_t csr_apply(const int* ptr, const int* col, const R* val, int64_t rows, const cx<R>* x, int64_t xs,
                       cx<R>* y, int64_t ys, int nblk, R scale, cudaStream_t st) {
     if (rows <= 0 || nblk <= 0) return cudaSuccess;
-    if (nblk > 65535) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)((rows + CT - 1) / CT), (unsigned)nblk);
-    k_csr_apply<R><<<grid, CT, 0, st>>>(ptr, col, val, rows, x, xs, y, ys, scale);
+    const int bch = nblk >= BCH_MANY ? BCH_MANY : BCH_FEW;
+    const int gy = (nblk + bch - 1) / bch;
+    if (gy > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((rows + CT - 1) / CT), (unsigned)gy);
+    if (bch == BCH_MANY)
+        k_csr_apply<R, BCH_MANY><<<grid, CT, 0, st>>>(ptr, col, val, rows, x, xs, y, ys, nblk, scale);
+    else
+        k_csr_apply<R, BCH_FEW><<<grid, CT, 0, st>>>(ptr, col, val, rows, x, xs, y, ys, nblk, scale);
     return cudaGetLastError();
 }
 
@@ -453,10 +487,17 @@ cudaError_t chebyshev_solve(const int* ptr, const int* col, const R* val, const 
     dim3 grid((unsigned)((n + CT - 1) / CT), (unsigned)nblk);
     k_cheb_init<R><<<grid, CT, 0, st>>>(dinv, n, (R)(1.0 / p.theta), b, x, r, d0);
     cudaError_t e = cudaGetLastError();
+    const int bch = nblk >= BCH_MANY ? BCH_MANY : BCH_FEW;
+    dim3 sgrid(grid.x, (unsigned)((nblk + bch - 1) / bch));
     for (int k = 0; k + 1 < p.steps && e == cudaSuccess; ++k) {
         const cx<R>* d = (k & 1) ? d1 : d0;
         cx<R>* dn = (k & 1) ? d0 : d1;
-        k_cheb_step<R><<<grid, CT, 0, st>>>(ptr, col, val, dinv, n, d, dn, r, x, (R)p.c1[k], (R)p.c2[k]);
+        if (bch == BCH_MANY)
+            k_cheb_step<R, BCH_MANY><<<sgrid, CT, 0, st>>>(ptr, col, val, dinv, n, d, dn, r, x, nblk, (R)p.c1[k],
+                                                            (R)p.c2[k]);
+        else
+            k_cheb_step<R, BCH_FEW><<<sgrid, CT, 0, st>>>(ptr, col, val, dinv, n, d, dn, r, x, nblk, (R)p.c1[k],
+                                                           (R)p.c2[k]);
         e = cudaGetLastError();
     }
     return e;
