@@ -383,6 +383,7 @@ cudaError_t kv_lincomb(void* z, int dtype, c128 a, const void* x, c128 b, const 
 // y (m); state bits below.
 #define BGS_ACTIVE 1
 #define BGS_REORTH 2
+#define BGS_MISS_SHIFT 8  // bits 8..15 of the state: cycles in a row whose residual did not follow its estimate
 struct BgsArgs {
     void* V;            // (m + 1) x nrhs x n vectors (complex64 or complex128)
     void* x;            // nrhs x n: the cycle corrections accumulate here

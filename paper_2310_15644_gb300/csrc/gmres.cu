@@ -479,8 +479,8 @@ __global__ void __launch_bounds__(BG_THREADS) k_bgs_xupdate(BgsArgs a) {
 // `x_zero`), beta = |b - Z x| per right-hand side, g_0 = beta, and the right-hand
 // side active while beta is above its tolerance and iterations remain; `scale` =
 // 1 / beta for the normalisation that follows (the rest of g is written by the
-// rotations before it is read).  A right-hand side also stops when the previous
-// cycle reached the tolerance by its estimate but the recomputed residual did not
+// rotations before it is read).  A right-hand side also stops when three cycles in
+// a row reached the tolerance by their estimate but the recomputed residual did not
 // follow (rounding floor of the product, which outer refinement then removes).
 template <typename R>
 __global__ void __launch_bounds__(BG_THREADS) k_bgs_resid(BgsArgs a, int x_zero) {
@@ -520,12 +520,15 @@ __global__ void __launch_bounds__(BG_THREADS) k_bgs_resid(BgsArgs a, int x_zero)
         const double s = warp_sum_blocks(a.npart + (int64_t)r * a.nblk, a.nblk, 1);
         if (threadIdx.x == 0) {
             const double beta = sqrt(s);
-            // stalled at the product's rounding floor: the last cycle met the tolerance by
-            // its residual estimate, yet the true residual is above it and less than halved
-            const bool stalled = !x_zero && a.res[r] <= a.tol[r] && beta > 0.5 * a.beta[r];
+            // rounding floor of the product: a cycle met the tolerance by its residual
+            // estimate, yet the recomputed residual is above it and less than half the
+            // previous cycle's; the third such cycle in a row stops the right-hand side
+            int misses = x_zero ? 0 : (a.state[r] >> BGS_MISS_SHIFT) & 0xff;
+            if (!x_zero)
+                misses = (a.res[r] <= a.tol[r] && beta > a.tol[r] && beta > 0.5 * a.beta[r]) ? misses + 1 : 0;
             a.beta[r] = beta;
-            const bool act = beta > a.tol[r] && a.it[r] < a.maxit && beta == beta && !stalled;
-            a.state[r] = act ? BGS_ACTIVE : 0;
+            const bool act = beta > a.tol[r] && a.it[r] < a.maxit && beta == beta && misses < 3;
+            a.state[r] = (act ? BGS_ACTIVE : 0) | (misses << BGS_MISS_SHIFT);
             a.scale[r] = act ? 1.0 / beta : 0.0;
             a.kk[r] = 0;
             reinterpret_cast<cx<R>*>(a.g)[(int64_t)r * (a.m + 1)] = mk<R>((R)beta, 0);
