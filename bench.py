@@ -908,8 +908,9 @@ def run_calderon(args, dev, stream, B, W, levels=(3, 4, 5), near_only=0, precond
 # the paper's own two-dimensional operators
 # ---------------------------------------------------------------------------
 def run_planar(args, dev, stream, B, W):
-    """Dense 2-D Galerkin S, D and N (FP64) on the ellipse of the paper's rank study
-    (aspect 1.5, perimeter 2 pi, 18 unknowns per wavelength: N = 18 k0)."""
+    """Dense 2-D Galerkin S, D and N on the ellipse of the paper's rank study (aspect
+    1.5, perimeter 2 pi, 18 unknowns per wavelength: N = 18 k0), in the FP64 form and
+    the FP32 form (well-separated pairs in FP32), with the FP32 form's deviation."""
     import torch
 
     sp = stream.cuda_stream
@@ -917,21 +918,31 @@ def run_planar(args, dev, stream, B, W):
     for k0 in (64.0, 128.0):
         n = int(round(18 * k0))
         verts = W.ellipse_polygon(n, 1.5, 2 * math.pi)
-        mats = [torch.empty(n, n, dtype=torch.complex128, device=dev) for _ in range(3)]
-        call = lambda: B.bem_planar_operators(None, verts, k0, mats[0].data_ptr(), mats[1].data_ptr(),  # noqa: E731
-                                              mats[2].data_ptr(), sp)
-        call()
-        torch.cuda.synchronize(dev)
-        reps = 3
-        t0 = time.perf_counter()
-        for _ in range(reps):
+        rec = {"k0": k0, "n": n}
+        ref = None
+        for form, fp32 in (("fp64", False), ("fp32", True)):
+            mats = [torch.empty(n, n, dtype=torch.complex128, device=dev) for _ in range(3)]
+            call = lambda: B.bem_planar_operators(None, verts, k0, mats[0].data_ptr(),  # noqa: E731
+                                                  mats[1].data_ptr(), mats[2].data_ptr(), sp, fp32=fp32)
             call()
-        torch.cuda.synchronize(dev)
-        ms = (time.perf_counter() - t0) / reps * 1e3
-        out["cases"].append({"k0": k0, "n": n, "ms": round(ms, 2),
-                             "segment_pairs_per_s": round(n * n / (ms * 1e-3), 1),
-                             "finite": bool(all(torch.isfinite(torch.view_as_real(m)).all().item() for m in mats))})
-        del mats
+            torch.cuda.synchronize(dev)
+            reps = 3
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                call()
+            torch.cuda.synchronize(dev)
+            ms = (time.perf_counter() - t0) / reps * 1e3
+            rec[form] = {"ms": round(ms, 2), "segment_pairs_per_s": round(n * n / (ms * 1e-3), 1),
+                         "finite": bool(all(torch.isfinite(torch.view_as_real(m)).all().item() for m in mats))}
+            if ref is None:
+                ref = mats
+            else:
+                # the FP32 form against the FP64 one: max |difference| / max |entry| per operator
+                rec[form]["max_dev_vs_fp64"] = [float(((m - r).abs().max() / r.abs().max()).item())
+                                                for m, r in zip(mats, ref)]
+                del mats
+        del ref
+        out["cases"].append(rec)
     out["fast_solver"] = run_planar_pipeline(args, dev, stream, B, W)
     return out
 
@@ -940,13 +951,14 @@ def run_planar_pipeline(args, dev, stream, B, W, tol=1e-4):
     """The paper's 2-D fast direct solver on the GPU (Sec. III): C_p of the ellipse and of
     its circular counterpart (Eq. 16), the skeleton of C_p - C_p,c by the randomized
     range finder (Eq. 17, seeded Gaussian test vectors, blocks of 8) and one Woodbury
-    solve (Eq. 18), against N = 18 k0; in the cpu_baseline leg the oracle runs the
-    same stages on the host cores for the smallest case."""
+    solve (Eq. 18), against N = 18 k0, with the operators in FP64 and in the FP32
+    form; in the cpu_baseline leg the oracle runs the same stages on the host cores
+    for the smallest case."""
     import torch
 
     sp = stream.cuda_stream
     cases = []
-    for k0 in (8.0, 16.0, 32.0, 64.0):
+    for k0, fp32 in [(k, f) for f in (False, True) for k in (8.0, 16.0, 32.0, 64.0)]:
         n = int(round(18 * k0))
         verts = W.ellipse_polygon(n, 1.5, 2 * math.pi)
         per = float(np.sum(np.hypot(*(np.roll(verts, -1, axis=0) - verts).T)))
@@ -963,8 +975,8 @@ def run_planar_pipeline(args, dev, stream, B, W, tol=1e-4):
         x = torch.empty_like(b)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        B.bem_planar_calderon(None, verts, k0, cp.data_ptr(), 0, 0, 0.0, sp)
-        B.bem_planar_calderon(None, cverts, k0, cc.data_ptr(), 0, 0, a, sp)
+        B.bem_planar_calderon(None, verts, k0, cp.data_ptr(), 0, 0, 0.0, sp, fp32=fp32)
+        B.bem_planar_calderon(None, cverts, k0, cc.data_ptr(), 0, 0, a, sp, fp32=fp32)
         t1 = time.perf_counter()
         A = cp - cc
         torch.cuda.synchronize(dev)
@@ -978,7 +990,8 @@ def run_planar_pipeline(args, dev, stream, B, W, tol=1e-4):
                                     x.data_ptr(), 1, sp)
         t5 = time.perf_counter()
         res = (cp @ x - b).abs().pow(2).sum().sqrt().item() / b.abs().pow(2).sum().sqrt().item()
-        cases.append({"k0": k0, "n": n, "skeleton_rank": r, "tol": tol,
+        cases.append({"k0": k0, "n": n, "operators": "fp32 far pairs" if fp32 else "fp64", "skeleton_rank": r,
+                      "tol": tol,
                       "calderon_s": round(t1 - t0, 4), "skeleton_s": round(t3 - t2, 4),
                       "woodbury_solve_s": round(t5 - t4, 4), "compression_s": round((t1 - t0) + (t3 - t2), 4),
                       "relative_residual_of_C_p_x": res})

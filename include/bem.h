@@ -508,18 +508,23 @@ bem_status bem_absorbed_power_static(bem_ctx* ctx, const void* x, int nrhs, doub
  * counter-clockwise, n >= 3): (O)_ij = (lambda_i, O lambda_j) with lambda_i the
  * hat function of vertex i.  The adjoint double layer of Eq. 3 is D^T.  N uses
  * the identity (lambda_i, N lambda_j) = int int G (lambda_i' lambda_j' -
- * k^2 n.n' lambda_i lambda_j) (N = -d_n D).  Quadrature: 10 x 10 Gauss-Legendre
- * points per segment pair after the static parts of the kernels are integrated
- * over the source segment in closed form; the outer rule is 20 points graded
- * toward the shared vertex of neighbouring segments; a segment with itself takes
- * the logarithm over both copies in closed form.  k: complex wavenumber with
- * Re k > 0 and Im k <= 0.  S, D, N: device complex128 n x n, row-major (element
- * (i, j) at i * n + j), each may be NULL.  FP64 throughout (Hankel functions from
- * their ascending series below |k R| = 12 and Hankel's expansion above).
- * Allocates 128 n^2 bytes of scratch; synchronises `stream`.  ctx (may be NULL)
- * only receives the error message.  No counterpart in the three-dimensional path. */
-bem_status bem_planar_operators(bem_ctx* ctx, const double* verts, int n, bem_c128 k, void* S, void* D, void* N,
-                                void* stream);
+ * k^2 n.n' lambda_i lambda_j) (N = -d_n D).  Quadrature: segment pairs whose
+ * midpoints lie at least 6 segment lengths apart take the 5 x 5 Gauss-Legendre
+ * rule on the whole kernel; closer pairs take 10 x 10 points after the static
+ * parts of the kernels are integrated over the source segment in closed form (the
+ * outer rule 20 points graded toward the shared vertex of neighbouring segments);
+ * a segment with itself takes the logarithm over both copies in closed form.
+ * k: complex wavenumber with Re k > 0 and Im k <= 0.  fp32: 0 = FP64 throughout
+ * (Hankel functions from their ascending series below |k R| = 12 and Hankel's
+ * expansion above); 1 = the well-separated pairs with |k R| >= 8 in FP32
+ * (Hankel's expansion, the phase e^{-j k R} split into an FP64 midpoint part and
+ * an FP32 offset part), about 1e-6 relative accuracy, the rest FP64.  S, D, N:
+ * device complex128 n x n, row-major (element (i, j) at i * n + j), each may be
+ * NULL.  Allocates 128 n^2 bytes of scratch; synchronises `stream`.  ctx (may be
+ * NULL) only receives the error message.  No counterpart in the three-dimensional
+ * path. */
+bem_status bem_planar_operators(bem_ctx* ctx, const double* verts, int n, bem_c128 k, int fp32, void* S, void* D,
+                                void* N, void* stream);
 
 /* The paper's two-dimensional fast direct solver (Sec. III), FP64 on the GPU.
  * Polygons as in bem_planar_operators (n vertices, counter-clockwise, closed);
@@ -531,10 +536,11 @@ bem_status bem_planar_operators(bem_ctx* ctx, const double* verts, int n, bem_c1
  * with S, D, N at k0 and D*~, N~ at k~ = k0 - 0.4 j k0^(1/3) a^(-2/3) (a <= 0: the
  * perimeter over 2 pi), G the Gram matrix of the hat functions (solved as a cyclic
  * tridiagonal system).  Le = N~ G^-1 and Lh = (G/2 - D*~) G^-1 (may be NULL) map the
- * right-hand side: rhs_p = Le (e / (j k0)) + Lh (eta0 h).  Allocates about 10 n^2 x
- * 16 bytes of scratch. */
-bem_status bem_planar_calderon(bem_ctx* ctx, const double* verts, int n, double k0, double a, void* Cp, void* Le,
-                               void* Lh, void* stream);
+ * right-hand side: rhs_p = Le (e / (j k0)) + Lh (eta0 h).  fp32: the operators'
+ * form as in bem_planar_operators (the Gram solves and products stay FP64).
+ * Allocates about 10 n^2 x 16 bytes of scratch. */
+bem_status bem_planar_calderon(bem_ctx* ctx, const double* verts, int n, double k0, double a, int fp32, void* Cp,
+                               void* Le, void* Lh, void* stream);
 
 /* In-place FFT of `batch` vectors of length n (1..2048), vector b at x + b * batch_stride,
  * element stride `stride` (complex128 elements): forward sum_j x_j exp(-2 pi i jk/n),

@@ -99,7 +99,7 @@ def _load():
                                            ctypes.POINTER(bem_c128), i32p]),
         "bem_region_boundary": (ctypes.c_int, [ctx, ctypes.c_int, i64p, i32p, ctypes.POINTER(ctypes.c_int8)]),
         "bem_num_regions": (ctypes.c_int, [ctx]),
-        "bem_planar_operators": (ctypes.c_int, [ctx, dp, ctypes.c_int, bem_c128, vp, vp, vp, vp]),
+        "bem_planar_operators": (ctypes.c_int, [ctx, dp, ctypes.c_int, bem_c128, ctypes.c_int, vp, vp, vp, vp]),
         "bem_debye_eps": (ctypes.c_int, [ctypes.c_double, dp, ctypes.POINTER(bem_c128)]),
         "bem_assemble": (ctypes.c_int, [ctx, vp]),
         "bem_num_edges": (ctypes.c_int64, [ctx]),
@@ -128,8 +128,8 @@ def _load():
         "bem_profile_end": (ctypes.c_int, [ctx, dp, i64p]),
         "bem_absorbed_power_static": (ctypes.c_int, [ctx, vp, ctypes.c_int, vp, vp]),
         "bem_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, vp, dp]),
-        "bem_planar_calderon": (ctypes.c_int, [ctx, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp, vp, vp,
-                                               vp]),
+        "bem_planar_calderon": (ctypes.c_int, [ctx, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                               vp, vp, vp, vp]),
         "bem_fft": (ctypes.c_int, [ctx, vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_longlong,
                                    ctypes.c_int, vp]),
         "bem_planar_skeleton": (ctypes.c_int, [ctx, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
@@ -218,12 +218,13 @@ def bem_region_boundary(ctx, r: int):
     return edges, sign
 
 
-def bem_planar_operators(ctx, verts, k: complex, s_ptr: int, d_ptr: int, n_ptr: int, stream: int = 0) -> None:
+def bem_planar_operators(ctx, verts, k: complex, s_ptr: int, d_ptr: int, n_ptr: int, stream: int = 0,
+                         fp32: bool = False) -> None:
     """Dense 2-D Galerkin S, D, N (device complex128 n x n, row-major) of a closed polygon."""
     v = np.ascontiguousarray(verts, dtype=np.float64)
     kk = complex(k)
     _check(ctx, lib.bem_planar_operators(ctx, _np_ptr(v, ctypes.c_double), len(v), bem_c128(kk.real, kk.imag),
-                                    ctypes.c_void_p(s_ptr or None), ctypes.c_void_p(d_ptr or None),
+                                    1 if fp32 else 0, ctypes.c_void_p(s_ptr or None), ctypes.c_void_p(d_ptr or None),
                                     ctypes.c_void_p(n_ptr or None), ctypes.c_void_p(stream)))
 
 
@@ -340,10 +341,10 @@ def bem_solve_adjoint(ctx, g_ptr: int, lam_ptr: int, nrhs: int, stream: int = 0,
 
 
 def bem_planar_calderon(ctx, verts, k0: float, cp_ptr: int, le_ptr: int = 0, lh_ptr: int = 0, a: float = 0.0,
-                        stream: int = 0) -> None:
+                        stream: int = 0, fp32: bool = False) -> None:
     v = np.ascontiguousarray(verts, dtype=np.float64)
     _check(ctx, lib.bem_planar_calderon(ctx, _np_ptr(v, ctypes.c_double), int(v.shape[0]), float(k0), float(a),
-                                        ctypes.c_void_p(cp_ptr), ctypes.c_void_p(le_ptr or None),
+                                        1 if fp32 else 0, ctypes.c_void_p(cp_ptr), ctypes.c_void_p(le_ptr or None),
                                         ctypes.c_void_p(lh_ptr or None), ctypes.c_void_p(stream)))
 
 

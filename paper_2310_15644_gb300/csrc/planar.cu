@@ -1,5 +1,6 @@
 // The paper's own two-dimensional operators on the GPU (see planar.cuh): the dense
-// Galerkin matrices S, D, D* = D^T and N of Eqs. 1-4 for a closed polygon, in FP64.
+// Galerkin matrices S, D, D* = D^T and N of Eqs. 1-4 for a closed polygon, in FP64
+// (or with the well-separated pairs' Hankel functions in FP32).
 // One thread per segment pair computes its 2 x 2 local matrices; a second kernel
 // sums the four segment pairs that meet at each vertex pair in a fixed order (no
 // atomics, reproducible), applying the Maue identity for N:
@@ -18,20 +19,14 @@ struct Seg {
     double p[2], t[2], n[2], L;
 };
 
-__global__ void k_planar_local(const Seg* __restrict__ seg, int n, c128 k, c128* __restrict__ locS,
+__global__ void k_planar_local(const Seg* __restrict__ seg, int n, c128 k, int form, c128* __restrict__ locS,
                                c128* __restrict__ locD) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)n * n) return;
     const int a = (int)(idx / n), b = (int)(idx % n);
     c128 S[2][2], D[2][2];
-    if (a == b) {
-        self_local(seg[a].L, k, S);
-        for (int p = 0; p < 2; ++p)
-            for (int q = 0; q < 2; ++q) D[p][q] = mk<double>(0.0, 0.0);
-    } else {
-        const int mode = b == (a + 1) % n ? 1 : (b == (a + n - 1) % n ? 2 : 0);
-        pair_local(seg[a].p, seg[a].t, seg[a].L, seg[b].p, seg[b].t, seg[b].n, seg[b].L, mode, k, S, D);
-    }
+    const int rel = a == b ? 0 : (b == (a + 1) % n ? 1 : (b == (a + n - 1) % n ? 2 : 3));
+    local_matrices(seg[a].p, seg[a].t, seg[a].L, seg[b].p, seg[b].t, seg[b].n, seg[b].L, rel, k, form, S, D);
     for (int p = 0; p < 2; ++p)
         for (int q = 0; q < 2; ++q) {
             locS[idx * 4 + 2 * p + q] = S[p][q];
@@ -71,8 +66,8 @@ __global__ void k_planar_assemble(const Seg* __restrict__ seg, int n, c128 k, co
 
 void bem_ctx_set_error(bem_ctx* c, const char* msg);
 
-extern "C" bem_status bem_planar_operators(bem_ctx* ctx, const double* verts, int n, bem_c128 k, void* S, void* D,
-                                           void* N, void* stream) {
+extern "C" bem_status bem_planar_operators(bem_ctx* ctx, const double* verts, int n, bem_c128 k, int fp32, void* S,
+                                           void* D, void* N, void* stream) {
     auto fail = [&](bem_status s, const char* msg) {
         if (ctx) bem_ctx_set_error(ctx, msg);
         return s;
@@ -82,6 +77,7 @@ extern "C" bem_status bem_planar_operators(bem_ctx* ctx, const double* verts, in
     if (n > 46340) return fail(BEM_EINVAL, "bem_planar_operators: more than 46340 vertices");
     if (!(k.re > 0.0) || k.im > 0.0 || !std::isfinite(k.re) || !std::isfinite(k.im))
         return fail(BEM_EINVAL, "bem_planar_operators: need Re k > 0 and Im k <= 0 (e^{+jwt})");
+    if (fp32 != 0 && fp32 != 1) return fail(BEM_EINVAL, "bem_planar_operators: fp32 must be 0 or 1");
     std::vector<Seg> seg(n);
     double area2 = 0.0;
     for (int e = 0; e < n; ++e) {
@@ -123,7 +119,7 @@ extern "C" bem_status bem_planar_operators(bem_ctx* ctx, const double* verts, in
     const unsigned blocks = (unsigned)((nn + 127) / 128);
     const c128 kk = mk<double>(k.re, k.im);
     if (e == cudaSuccess) {
-        k_planar_local<<<blocks, 128, 0, st>>>(d_seg, n, kk, locS, locD);
+        k_planar_local<<<blocks, 128, 0, st>>>(d_seg, n, kk, fp32 ? P2_FORM_FP32 : P2_FORM_FP64, locS, locD);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

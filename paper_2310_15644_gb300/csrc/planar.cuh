@@ -295,6 +295,165 @@ P2_HD void pair_local(const double pa[2], const double ta[2], double La, const d
     }
 }
 
+// ---------------------------------------------------------------------------
+// Well-separated segment pairs: the kernel is smooth over both segments, so S and
+// D are integrated directly on the 5 x 5 Gauss-Legendre product rule (no static
+// split).  With the midpoints at least P2_FAR_FACTOR segment lengths apart, the
+// nearest singularity of ln R lies about 11 half-lengths from either segment, and
+// the 5-point rule's error is below (22)^-10 ~ 4e-14 of the integrand's size.
+// ---------------------------------------------------------------------------
+constexpr double P2_FAR_FACTOR = 6.0;
+constexpr double P2_ASYM_F = 8.0;  // |k R| from which the FP32 form uses Hankel's expansion
+#define P2_FORM_FP64 0             // every kernel evaluation in FP64
+#define P2_FORM_FP32 1             // far pairs with |k R| >= P2_ASYM_F evaluated in FP32
+
+// 5-point Gauss-Legendre rule on [0, 1] (nodes (1 + t)/2 of the roots t = 0,
+// +-sqrt(5 -+ 2 sqrt(10/7)) / 3; weights 64/225, (322 +- 13 sqrt 70)/1800)
+P2_HD void gl5(int i, double& x, double& w) {
+    switch (i) {
+        case 0: x = 0.046910077030668004; w = 0.11846344252809454; break;
+        case 1: x = 0.23076534494715845; w = 0.23931433524968323; break;
+        case 2: x = 0.5; w = 0.28444444444444444; break;
+        case 3: x = 0.76923465505284155; w = 0.23931433524968323; break;
+        default: x = 0.95308992296933200; w = 0.11846344252809454; break;
+    }
+}
+
+P2_HD c64 csqrt_f(c64 z) {
+    const float r = hypotf(z.re, z.im);
+    const float a = sqrtf(fmaxf(0.0f, 0.5f * (r + z.re)));
+    const float b = copysignf(sqrtf(fmaxf(0.0f, 0.5f * (r - z.re))), z.im);
+    return mk<float>(a, b);
+}
+
+// Hankel's expansion (A&S 9.2.8) of H0^(2)(z), H1^(2)(z) in FP32 for |z| >= P2_ASYM_F,
+// where its smallest term is below FP32 rounding.  The phase factor
+// eph = e^{-j z} comes in from the caller, which forms it from an FP64 phase per
+// pair times an FP32 phase of the small offset (so large k R loses no phase).
+P2_HD void hankel2_01_asym_f(c64 z, c64 eph, c64& h0, c64& h1) {
+    const c64 zi = cdiv(mk<float>(1.0f, 0.0f), z);
+    const c64 pref = csqrt_f((float)(2.0 / P2_PI) * zi);
+    const float c45 = 0.70710678118654752f;
+    for (int nu = 0; nu < 2; ++nu) {
+        const float mu = 4.0f * nu * nu;
+        c64 term = mk<float>(1.0f, 0.0f), sum = term;
+        float prev = 1.0f;
+        for (int kk = 1; kk < 24; ++kk) {
+            const float c = (mu - (2.0f * kk - 1.0f) * (2.0f * kk - 1.0f)) / (8.0f * kk);
+            const c64 tz = term * zi;
+            term = mk<float>(c * tz.im, -c * tz.re);  // c (-j) term / z
+            const float at = hypotf(term.re, term.im);
+            if (at >= prev || at < 3e-8f) break;
+            sum = sum + term;
+            prev = at;
+        }
+        // e^{-j (z - nu pi/2 - pi/4)} = e^{-j z} e^{j pi/4} j^nu
+        const c64 rot = nu == 0 ? mk<float>(c45, c45) : mk<float>(-c45, c45);
+        const c64 hv = pref * ((eph * rot) * sum);
+        if (nu == 0)
+            h0 = hv;
+        else
+            h1 = hv;
+    }
+}
+
+// S_ab and D_ab of a well-separated pair (as pair_local) on the 5 x 5 rule.  form
+// P2_FORM_FP32: offsets, distances and, where |k R| >= P2_ASYM_F, the Hankel
+// functions in FP32; R = R0 + dR with R0 the midpoint distance (FP64) and dR from
+// the small offsets, so the phase e^{-j k R} = e^{-j k R0} e^{-j k dR} stays exact
+// to FP32 rounding of dR.
+P2_HD void far_pair_local(const double pa[2], const double ta[2], double La, const double pb[2],
+                          const double tb[2], const double nb[2], double Lb, c128 k, int form, c128 S[2][2],
+                          c128 D[2][2]) {
+    const double D0[2] = {(pa[0] + 0.5 * La * ta[0]) - (pb[0] + 0.5 * Lb * tb[0]),
+                          (pa[1] + 0.5 * La * ta[1]) - (pb[1] + 0.5 * Lb * tb[1])};
+    const double R0 = sqrt(D0[0] * D0[0] + D0[1] * D0[1]);
+    for (int p = 0; p < 2; ++p)
+        for (int q = 0; q < 2; ++q) S[p][q] = D[p][q] = mk<double>(0.0, 0.0);
+    if (form == P2_FORM_FP32) {
+        const c128 e0d = cexp2(mul_mj(R0 * k));  // e^{-j k R0}
+        const c64 e0 = mk<float>((float)e0d.re, (float)e0d.im);
+        const c64 kf = mk<float>((float)k.re, (float)k.im);
+        const float d0x = (float)D0[0], d0y = (float)D0[1], r0 = (float)R0;
+        const float dnb = (float)(D0[0] * nb[0] + D0[1] * nb[1]);
+        c64 Sf[2][2], Df[2][2];
+        for (int p = 0; p < 2; ++p)
+            for (int q = 0; q < 2; ++q) Sf[p][q] = Df[p][q] = mk<float>(0.0f, 0.0f);
+        for (int i = 0; i < 5; ++i) {
+            double xa, wa;
+            gl5(i, xa, wa);
+            const float oa = (float)((xa - 0.5) * La);
+            for (int j = 0; j < 5; ++j) {
+                double xb, wb;
+                gl5(j, xb, wb);
+                const float ob = (float)((xb - 0.5) * Lb);
+                const float dx = oa * (float)ta[0] - ob * (float)tb[0];
+                const float dy = oa * (float)ta[1] - ob * (float)tb[1];
+                const float cross = 2.0f * (d0x * dx + d0y * dy) + (dx * dx + dy * dy);
+                const float R = sqrtf(r0 * r0 + cross);
+                const float dR = cross / (R + r0);
+                const c64 z = R * kf;
+                c64 h0, h1;
+                if (hypotf(z.re, z.im) >= (float)P2_ASYM_F) {
+                    // e^{-j k dR} = e^{-j Re(k) dR} e^{Im(k) dR}
+                    float sn, cs;
+                    sincosf(kf.re * dR, &sn, &cs);
+                    const float m = expf(kf.im * dR);
+                    const c64 eph = e0 * mk<float>(m * cs, -m * sn);
+                    hankel2_01_asym_f(z, eph, h0, h1);
+                } else {
+                    c128 g0, g1;
+                    hankel2_01((double)R * k, g0, g1);
+                    h0 = mk<float>((float)g0.re, (float)g0.im);
+                    h1 = mk<float>((float)g1.re, (float)g1.im);
+                }
+                const float vv = dnb + (dx * (float)nb[0] + dy * (float)nb[1]);
+                const float W = (float)(wa * wb * La * Lb);
+                const c64 G = mk<float>(0.25f * h0.im, -0.25f * h0.re);           // -(j/4) H0
+                const c64 kh = kf * h1;
+                const c64 A = mk<float>(0.25f * kh.im / R, -0.25f * kh.re / R);   // -(j k / (4R)) H1
+                const float ph[2] = {(float)(1.0 - xa), (float)xa}, qh[2] = {(float)(1.0 - xb), (float)xb};
+                for (int p = 0; p < 2; ++p)
+                    for (int q = 0; q < 2; ++q) {
+                        const float f = W * ph[p] * qh[q];
+                        Sf[p][q] = Sf[p][q] + f * G;
+                        Df[p][q] = Df[p][q] + (f * vv) * A;
+                    }
+            }
+        }
+        for (int p = 0; p < 2; ++p)
+            for (int q = 0; q < 2; ++q) {
+                S[p][q] = mk<double>(Sf[p][q].re, Sf[p][q].im);
+                D[p][q] = mk<double>(Df[p][q].re, Df[p][q].im);
+            }
+        return;
+    }
+    for (int i = 0; i < 5; ++i) {
+        double xa, wa;
+        gl5(i, xa, wa);
+        const double r0 = pa[0] + xa * La * ta[0], r1 = pa[1] + xa * La * ta[1];
+        for (int j = 0; j < 5; ++j) {
+            double xb, wb;
+            gl5(j, xb, wb);
+            const double dx = r0 - (pb[0] + xb * Lb * tb[0]), dy = r1 - (pb[1] + xb * Lb * tb[1]);
+            const double R = sqrt(dx * dx + dy * dy);
+            c128 h0, h1;
+            hankel2_01(R * k, h0, h1);
+            const double vv = dx * nb[0] + dy * nb[1];
+            const double W = wa * wb * La * Lb;
+            const c128 G = mul_mj(0.25 * h0);
+            const c128 A = (1.0 / R) * mul_mj(0.25 * (k * h1));
+            const double ph[2] = {1.0 - xa, xa}, qh[2] = {1.0 - xb, xb};
+            for (int p = 0; p < 2; ++p)
+                for (int q = 0; q < 2; ++q) {
+                    const double f = W * ph[p] * qh[q];
+                    S[p][q] = S[p][q] + f * G;
+                    D[p][q] = D[p][q] + (f * vv) * A;
+                }
+        }
+    }
+}
+
 // S of a segment of length L with itself: the logarithm over both copies in closed
 // form (L^2 (ln L / 4 + K_pq), K = [[-7/16, -5/16], [-5/16, -7/16]] on the unit
 // square) and the remainder on the 10 x 10 product rule (D vanishes there).
@@ -314,6 +473,30 @@ P2_HD void self_local(double L, c128 k, c128 S[2][2]) {
                 for (int q = 0; q < 2; ++q) S[p][q] = S[p][q] + (pi_[p] * pj[q]) * g;
         }
     }
+}
+
+// Local matrices of the segment pair (a, b) as the operator kernels compute them.
+// rel 0: the same segment; 1: b follows a; 2: b precedes a; 3: any other pair, on
+// the 5 x 5 rule when well separated, else as pair_local.
+P2_HD void local_matrices(const double pa[2], const double ta[2], double La, const double pb[2],
+                          const double tb[2], const double nb[2], double Lb, int rel, c128 k, int form,
+                          c128 S[2][2], c128 D[2][2]) {
+    if (rel == 0) {
+        self_local(La, k, S);
+        for (int p = 0; p < 2; ++p)
+            for (int q = 0; q < 2; ++q) D[p][q] = mk<double>(0.0, 0.0);
+        return;
+    }
+    if (rel == 3) {
+        const double mx = (pa[0] + 0.5 * La * ta[0]) - (pb[0] + 0.5 * Lb * tb[0]);
+        const double my = (pa[1] + 0.5 * La * ta[1]) - (pb[1] + 0.5 * Lb * tb[1]);
+        const double lim = P2_FAR_FACTOR * fmax(La, Lb);
+        if (mx * mx + my * my >= lim * lim) {
+            far_pair_local(pa, ta, La, pb, tb, nb, Lb, k, form, S, D);
+            return;
+        }
+    }
+    pair_local(pa, ta, La, pb, tb, nb, Lb, rel == 3 ? 0 : rel, k, S, D);
 }
 
 }  // namespace bem2d

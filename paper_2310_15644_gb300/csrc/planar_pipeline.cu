@@ -478,8 +478,8 @@ unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-extern "C" bem_status bem_planar_calderon(bem_ctx* ctx, const double* verts, int n, double k0, double a, void* Cp,
-                                          void* Le, void* Lh, void* stream) {
+extern "C" bem_status bem_planar_calderon(bem_ctx* ctx, const double* verts, int n, double k0, double a, int fp32,
+                                          void* Cp, void* Le, void* Lh, void* stream) {
     using namespace bem2p;
     std::vector<double> L;
     if (!polygon_lengths(verts, n, L))
@@ -497,8 +497,8 @@ extern "C" bem_status bem_planar_calderon(bem_ctx* ctx, const double* verts, int
     Scope sc{{&S, &D, &N, &Dt, &Nt, &W1, &W2, &P, &gl, &gd, &gu, &gz, &dL}};
     for (DevBuf* b : {&S, &D, &N, &Dt, &Nt, &W1, &W2, &P}) PP_TRY(dalloc(*b, sizeof(c128) * nn));
     bem_status s;
-    if ((s = bem_planar_operators(ctx, verts, n, kk0, S.p, D.p, N.p, stream)) != BEM_OK) return s;
-    if ((s = bem_planar_operators(ctx, verts, n, kt, nullptr, Dt.p, Nt.p, stream)) != BEM_OK) return s;
+    if ((s = bem_planar_operators(ctx, verts, n, kk0, fp32, S.p, D.p, N.p, stream)) != BEM_OK) return s;
+    if ((s = bem_planar_operators(ctx, verts, n, kt, fp32, nullptr, Dt.p, Nt.p, stream)) != BEM_OK) return s;
     const GramHost gh = gram_factor(L);
     PP_TRY(upload_d(gl, gh.l, st));
     PP_TRY(upload_d(gd, gh.d, st));

@@ -27,7 +27,19 @@ extern "C" void h2_dgreen_rem(double kr, double ki, double R, double* out) {
 }
 
 // full matrices by the kernels' per-pair functions and summation order (host loop)
-extern "C" void h2_operators(const double* verts, int n, double kr, double ki, double* S, double* D, double* N) {
+// Hankel's expansion in FP32 at z = zr + j zi (|z| >= 8), its phase e^{-j z} from FP64
+extern "C" void h2_hankel01_asym_f(double zr, double zi, double* out) {
+    const c128 eph = cexp2(mul_mj(mk<double>(zr, zi)));
+    c64 h0, h1;
+    hankel2_01_asym_f(mk<float>((float)zr, (float)zi), mk<float>((float)eph.re, (float)eph.im), h0, h1);
+    out[0] = h0.re;
+    out[1] = h0.im;
+    out[2] = h1.re;
+    out[3] = h1.im;
+}
+
+extern "C" void h2_operators(const double* verts, int n, double kr, double ki, int form, double* S, double* D,
+                             double* N) {
     const c128 k = mk<double>(kr, ki);
     std::vector<double> P(2 * n), T(2 * n), Nn(2 * n), L(n);
     for (int e = 0; e < n; ++e) {
@@ -45,14 +57,8 @@ extern "C" void h2_operators(const double* verts, int n, double kr, double ki, d
     for (int a = 0; a < n; ++a)
         for (int b = 0; b < n; ++b) {
             c128 s[2][2], d[2][2];
-            if (a == b) {
-                self_local(L[a], k, s);
-                for (int p = 0; p < 2; ++p)
-                    for (int q = 0; q < 2; ++q) d[p][q] = mk<double>(0, 0);
-            } else {
-                const int mode = b == (a + 1) % n ? 1 : (b == (a + n - 1) % n ? 2 : 0);
-                pair_local(&P[2 * a], &T[2 * a], L[a], &P[2 * b], &T[2 * b], &Nn[2 * b], L[b], mode, k, s, d);
-            }
+            const int rel = a == b ? 0 : (b == (a + 1) % n ? 1 : (b == (a + n - 1) % n ? 2 : 3));
+            local_matrices(&P[2 * a], &T[2 * a], L[a], &P[2 * b], &T[2 * b], &Nn[2 * b], L[b], rel, k, form, s, d);
             for (int p = 0; p < 2; ++p)
                 for (int q = 0; q < 2; ++q) {
                     locS[((size_t)a * n + b) * 4 + 2 * p + q] = s[p][q];

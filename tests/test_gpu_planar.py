@@ -1,7 +1,10 @@
 """GPU parity of the two-dimensional Galerkin operators (bem_planar_operators) with the
-oracle (oracle.planar), element by element: the same quadrature in FP64, so the
-bound is the device Hankel functions' accuracy (about 2e-10 relative near the
-series / asymptotic switch) times the sums' condition: 1e-9 of the largest entry."""
+oracle (oracle.planar), element by element.  FP64 form: the oracle's quadrature on
+the near pairs and a 5 x 5 rule with error below 1e-13 on the well-separated ones,
+so the bound is the device Hankel functions' accuracy (about 2e-10 relative near
+the series / asymptotic switch) times the sums' condition: 1e-9 of the largest
+entry.  FP32 form (well-separated pairs with |k R| >= 8 in FP32): 3e-6 of the
+largest entry, on ellipses at N = 18 k0 where most pairs take that path."""
 import numpy as np
 import pytest
 
@@ -43,3 +46,16 @@ def test_planar_operators_equal_oracle(B, name, mesh, k):
     for got, ref in zip(mats, (S, D, N)):
         g = got.cpu().numpy()
         assert np.abs(g - ref).max() <= 1e-9 * np.abs(ref).max(), name
+
+
+@pytest.mark.parametrize("n,k", [(288, 16.0 + 0j), (576, 32.0 - 0.4j), (576, PL.k_tilde(32.0, 1.0))],
+                         ids=["ellipse288", "ellipse576_lossy", "ellipse576_ktilde"])
+def test_planar_fp32_form_equals_oracle(B, n, k):
+    verts = W.ellipse_polygon(n, 1.5, 2 * np.pi)
+    mats = [torch.empty(n, n, dtype=torch.complex128, device=DEV) for _ in range(3)]
+    B.bem_planar_operators(None, verts, k, mats[0].data_ptr(), mats[1].data_ptr(), mats[2].data_ptr(),
+                           torch.cuda.current_stream().cuda_stream, fp32=True)
+    S, D, Dt, N, G = PL.operators(PL.Polygon(verts), k)
+    for got, ref in zip(mats, (S, D, N)):
+        g = got.cpu().numpy()
+        assert np.abs(g - ref).max() <= 3e-6 * np.abs(ref).max()

@@ -123,3 +123,36 @@ def test_skeleton_and_woodbury_equal_oracle(B, ellipse8, tol):
     assert np.linalg.norm(xw - xd_) <= max(10 * tol, 1e-11) * np.linalg.norm(xd_)
     if tol == 1e-3:
         assert r < n // 2
+
+
+def test_fp32_operators_woodbury_within_tolerance(B):
+    """The whole pipeline with the FP32 form of the operators on the N = 18 k0 ellipse
+    (k0 = 16): the Woodbury solution at tol 1e-4 agrees with the oracle's dense solve
+    of C_p to 10 tol, the FP32 form's 1e-6 error being far below the tolerance."""
+    k0 = 16.0
+    n = int(round(18 * k0))
+    verts = W.ellipse_polygon(n, 1.5, 2 * np.pi)
+    poly = PL.Polygon(verts)
+    Cp, _, _ = PL.calderon_cfie(poly, k0)
+    circ = PL.circular_counterpart(poly)
+    a = PL.curvature_radius(poly)
+    cp = torch.empty((n, n), dtype=torch.complex128, device=DEV)
+    cc = torch.empty_like(cp)
+    B.bem_planar_calderon(None, verts, k0, cp.data_ptr(), 0, 0, 0.0, _stream(), fp32=True)
+    B.bem_planar_calderon(None, circ.verts, k0, cc.data_ptr(), 0, 0, a, _stream(), fp32=True)
+    assert np.abs(cp.cpu().numpy() - Cp).max() <= 1e-5 * np.abs(Cp).max()
+    A = (cp - cc).contiguous()
+    omega = torch.from_numpy(np.ascontiguousarray(W.complex_normal(n, seed=7, nrhs=n).T)).to(DEV)
+    U = torch.zeros((n, n), dtype=torch.complex128, device=DEV)
+    Vt = torch.zeros_like(U)
+    tol = 1e-4
+    r = B.bem_planar_skeleton(None, A.data_ptr(), n, omega.data_ptr(), n, tol, 8, U.data_ptr(), Vt.data_ptr(),
+                              _stream())
+    b = W.complex_normal(n, seed=8)
+    bd = torch.from_numpy(b).to(DEV)
+    xd = torch.empty_like(bd)
+    cc0 = cc[:, 0].contiguous()
+    B.bem_planar_woodbury_solve(None, cc0.data_ptr(), n, U.data_ptr(), Vt.data_ptr(), r, bd.data_ptr(),
+                                xd.data_ptr(), 1, _stream())
+    xo = np.linalg.solve(Cp, b)
+    assert np.linalg.norm(xd.cpu().numpy() - xo) <= 10 * tol * np.linalg.norm(xo)

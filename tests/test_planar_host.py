@@ -32,7 +32,8 @@ def H(tmp_path_factory):
     lib.h2_hankel01.argtypes = [ctypes.c_double, ctypes.c_double, dp]
     lib.h2_green_rem.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
     lib.h2_dgreen_rem.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
-    lib.h2_operators.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp, dp]
+    lib.h2_operators.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp]
+    lib.h2_hankel01_asym_f.argtypes = [ctypes.c_double, ctypes.c_double, dp]
     return lib
 
 
@@ -81,8 +82,45 @@ def test_galerkin_matrices_match_oracle(H, curve, k):
     D = np.zeros((n, n, 2))
     N = np.zeros((n, n, 2))
     v = np.ascontiguousarray(verts)
-    H.h2_operators(_p(v), n, k.real, k.imag, _p(S), _p(D), _p(N))
+    H.h2_operators(_p(v), n, k.real, k.imag, 0, _p(S), _p(D), _p(N))
     Sr, Dr, _, Nr, _ = PL.operators(PL.Polygon(verts), k)
     for got, ref in ((S, Sr), (D, Dr), (N, Nr)):
         g = got[..., 0] + 1j * got[..., 1]
         assert np.abs(g - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_fp32_hankel_expansion_matches_scipy(H):
+    """FP32 Hankel expansion for |z| >= 8 (its smallest term is below FP32 rounding
+    there): relative error <= 2e-6 against SciPy, real and lossy arguments up to
+    |z| = 3000 (the phase comes from FP64, so large |z| loses nothing)."""
+    out = np.zeros(4)
+    worst = 0.0
+    for mag in np.geomspace(8.0, 3000.0, 60):
+        for ang in (0.0, -0.05, -0.15):
+            z = mag * np.exp(1j * ang)
+            ref = np.array([hankel2(0, z), hankel2(1, z)])
+            if not np.all(np.abs(ref) > 1e-30):
+                continue
+            H.h2_hankel01_asym_f(z.real, z.imag, _p(out))
+            got = np.array([out[0] + 1j * out[1], out[2] + 1j * out[3]])
+            worst = max(worst, float(np.max(np.abs(got - ref) / np.abs(ref))))
+    assert worst < 2e-6, worst
+
+
+@pytest.mark.parametrize("n,k", [(288, 16.0 + 0j), (576, 32.0 - 0.4j)])
+def test_fp32_form_matches_oracle(H, n, k):
+    """The FP32 form (well-separated pairs with |k R| >= 8 in FP32) on the N = 18 k0
+    ellipse: S within 2e-6 of its largest entry, D within 3e-6, N within 2e-6
+    (measured 1e-7, 1.3e-6 and 3.5e-7)."""
+    verts = W.ellipse_polygon(n, 1.5, 2 * np.pi)
+    S = np.zeros((n, n, 2))
+    D = np.zeros((n, n, 2))
+    N = np.zeros((n, n, 2))
+    v = np.ascontiguousarray(verts)
+    H.h2_operators(_p(v), n, k.real, k.imag, 1, _p(S), _p(D), _p(N))
+    Sr, Dr, _, Nr, _ = PL.operators(PL.Polygon(verts), k)
+    for got, ref, bound in ((S, Sr, 2e-6), (D, Dr, 3e-6), (N, Nr, 2e-6)):
+        g = got[..., 0] + 1j * got[..., 1]
+        err = np.abs(g - ref).max() / np.abs(ref).max()
+        print(n, k, err)
+        assert err <= bound, err
