@@ -190,6 +190,7 @@ struct bem_ctx {
     int* tc_err_dev = nullptr;
     DevBuf d_rx, d_ry;   // one region's operand and product
     DevBuf d_xext;       // the currents of the exterior boundary (powers)
+    DevBuf d_far;        // quadrature points and weighted currents of the scattered power
     // Calderon preconditioner (BEM_PRECOND_CALDERON): refined-mesh context, sparse
     // matrices (host copies and FP32/FP64 device copies), Chebyshev plan, work
     struct Calderon {
@@ -435,7 +436,7 @@ extern "C" void bem_destroy(bem_ctx* c) {
                       &c->gw.xin, &c->gw.rin, &c->cgw.v[0],
                       &c->cgw.v[1], &c->cgw.v[2], &c->cgw.v[3], &c->cgw.v[4], &c->cgw.v[5], &c->cgw.v[6],
                       &c->cgw.v[7], &c->bw.V, &c->bw.x, &c->bw.b, &c->bw.cplx, &c->bw.dbl, &c->bw.ints,
-                      &c->bw.part, &c->bw.npart, &c->bw.zr, &c->bw.rr, &c->bw.cn};
+                      &c->bw.part, &c->bw.npart, &c->bw.zr, &c->bw.rr, &c->bw.cn, &c->d_far};
     for (DevBuf* b : bufs) dfree(*b);
     if (c->tc_err_host) cudaFreeHost(c->tc_err_host);
     if (c->bw.host_active) cudaFreeHost(c->bw.host_active);
@@ -3128,8 +3129,9 @@ extern "C" bem_status bem_power(bem_ctx* c, const void* x, const void* b, int nr
             gx.insert(gx.end(), gw.begin(), gw.end());
             CK(upload(c->d_gl, gx, st));
         }
+        CK(ensure(c->d_far, power_sca_scratch(g, nrhs)));
         CK(power_sca(g, xe, nrhs, (double*)c->d_part.p, nta, nph, (const double*)c->d_gl.p,
-                     (const double*)c->d_gl.p + nta, st));
+                     (const double*)c->d_gl.p + nta, c->d_far.p, st));
         CK(kv_reduce_real((const double*)c->d_part.p, nta * nph, nrhs, (double*)c->d_red.p, st));
         CK(cudaMemcpyAsync(host.data(), c->d_red.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));

@@ -353,8 +353,10 @@ cudaError_t power_abs(GeomDev g, const c128* x, int nrhs, double* per_tri, doubl
                       cudaStream_t st);
 // out = d P_abs / d conj(x) = (1/2) [X xM ; X^T xJ] (device complex128, 2ne x nrhs)
 cudaError_t power_abs_grad(GeomDev g, const c128* x, int nrhs, c128* out, cudaStream_t st);
+#define PSCA_CHUNK 16  // right-hand sides per pass of the scattered-power kernels (bounds their scratch)
+size_t power_sca_scratch(GeomDev g, int nrhs);
 cudaError_t power_sca(GeomDev g, const c128* x, int nrhs, double* partial, int ntheta, int nphi,
-                      const double* ct, const double* wt, cudaStream_t st);
+                      const double* ct, const double* wt, void* scratch, cudaStream_t st);
 cudaError_t dot_real_parts(const c128* a, const c128* b, int64_t n, int nrhs, double* partial, int npart,
                            cudaStream_t st);
 

@@ -171,69 +171,133 @@ cudaError_t power_abs(GeomDev g, const c128* x, int nrhs, double* per_tri, doubl
     return cudaGetLastError();
 }
 
-// scattered power: one CTA per direction (theta_i, phi_j); grid.y = right-hand side
-__global__ void k_psca(GeomDev g, const c128* __restrict__ x, double* __restrict__ partial, int nphi,
-                       const double* __restrict__ ct, const double* __restrict__ wt) {
-    __shared__ double sh[32];
-    int dir = blockIdx.x;
-    int r = blockIdx.y;
-    int it = dir / nphi, ip = dir % nphi;
-    double cth = ct[it], sth = sqrt(fmax(0.0, 1.0 - cth * cth));
-    double phi = 2.0 * BEM_PI * ip / nphi;
-    d3 rh = D3(sth * cos(phi), sth * sin(phi), cth);
-    const c128* xr = x + (int64_t)r * 2 * g.ne;
-    c128 N[3], L[3];
-    for (int d = 0; d < 3; ++d) N[d] = L[d] = mk<double>(0, 0);
-    for (int e = threadIdx.x; e < 7 * g.nt; e += blockDim.x) {
-        int t = e / 7, q = e % 7;
-        d3 v[3];
-        for (int i = 0; i < 3; ++i) v[i] = ld3(g.tv + 9 * t + 3 * i);
-        double A = g.area[t];
-        double l0, l1, l2, w;
-        rule7_d(q, l0, l1, l2, w);
-        d3 rq = l0 * v[0] + l1 * v[1] + l2 * v[2];
-        c128 J[3], M[3];
-        for (int d = 0; d < 3; ++d) J[d] = M[d] = mk<double>(0, 0);
-        for (int i = 0; i < 3; ++i) {
-            d3 f = (g.tri_coef[3 * t + i] / (2.0 * A)) * (rq - v[i]);
-            c128 xj = xr[g.tri_edge[3 * t + i]], xm = xr[g.ne + g.tri_edge[3 * t + i]];
-            J[0] = J[0] + f.x * xj; J[1] = J[1] + f.y * xj; J[2] = J[2] + f.z * xj;
-            M[0] = M[0] + f.x * xm; M[1] = M[1] + f.y * xm; M[2] = M[2] + f.z * xm;
-        }
-        double sn, cs;
-        sincos(g.k0 * dot(rh, rq), &sn, &cs);
-        c128 ph = (w * A) * mk<double>(cs, sn);
-        for (int d = 0; d < 3; ++d) {
-            N[d] = N[d] + ph * J[d];
-            L[d] = L[d] + ph * M[d];
-        }
+// Scattered power, in two kernels.  k_psca_points writes, once per call, every
+// quadrature point r_q (7 per triangle) and the weighted currents w_q A_t J(r_q),
+// w_q A_t M(r_q) of each right-hand side (6 complex values).  k_psca_dirs then takes
+// one direction (theta_i, phi_j) per CTA and PSCA_RB right-hand sides per grid.y,
+// forms each point's phase e^{j k0 rhat.r_q} once for all of them, and accumulates
+// N and L; the far-field magnitude follows in thread 0.  FP64 throughout.
+constexpr int PSCA_T = 256;
+constexpr int PSCA_RB = 4;
+
+__global__ void __launch_bounds__(PSCA_T) k_psca_points(GeomDev g, const c128* __restrict__ x, int r0, int nr,
+                                                        double* __restrict__ pts, c128* __restrict__ cur) {
+    const int64_t Q = 7 * (int64_t)g.nt;
+    const int64_t q = (int64_t)blockIdx.x * PSCA_T + threadIdx.x;
+    const int rr = blockIdx.y;
+    if (q >= Q || rr >= nr) return;
+    const int t = (int)(q / 7), iq = (int)(q % 7);
+    d3 v[3];
+    for (int i = 0; i < 3; ++i) v[i] = ld3(g.tv + 9 * t + 3 * i);
+    const double A = g.area[t];
+    double l0, l1, l2, w;
+    rule7_d(iq, l0, l1, l2, w);
+    const d3 rq = l0 * v[0] + l1 * v[1] + l2 * v[2];
+    if (rr == 0) {
+        pts[q] = rq.x;
+        pts[Q + q] = rq.y;
+        pts[2 * Q + q] = rq.z;
     }
-    double vals[12] = {N[0].re, N[0].im, N[1].re, N[1].im, N[2].re, N[2].im,
-                       L[0].re, L[0].im, L[1].re, L[1].im, L[2].re, L[2].im};
-    __shared__ double tot[12];
-    for (int k = 0; k < 12; ++k) {
-        double s = block_sum_d(vals[k], sh);
-        if (threadIdx.x == 0) tot[k] = s;
+    const c128* xr = x + (int64_t)(r0 + rr) * 2 * g.ne;
+    c128 J[3], M[3];
+    for (int d = 0; d < 3; ++d) J[d] = M[d] = mk<double>(0, 0);
+    for (int i = 0; i < 3; ++i) {
+        d3 f = (g.tri_coef[3 * t + i] / (2.0 * A)) * (rq - v[i]);
+        c128 xj = xr[g.tri_edge[3 * t + i]], xm = xr[g.ne + g.tri_edge[3 * t + i]];
+        J[0] = J[0] + f.x * xj; J[1] = J[1] + f.y * xj; J[2] = J[2] + f.z * xj;
+        M[0] = M[0] + f.x * xm; M[1] = M[1] + f.y * xm; M[2] = M[2] + f.z * xm;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        c128 Nt[3] = {mk<double>(tot[0], tot[1]), mk<double>(tot[2], tot[3]), mk<double>(tot[4], tot[5])};
-        c128 Lt[3] = {mk<double>(tot[6], tot[7]), mk<double>(tot[8], tot[9]), mk<double>(tot[10], tot[11])};
-        c128 rn = rh.x * Nt[0] + rh.y * Nt[1] + rh.z * Nt[2];
-        c128 Ntr[3] = {Nt[0] - rh.x * rn, Nt[1] - rh.y * rn, Nt[2] - rh.z * rn};
-        c128 rxL[3] = {rh.y * Lt[2] - rh.z * Lt[1], rh.z * Lt[0] - rh.x * Lt[2], rh.x * Lt[1] - rh.y * Lt[0]};
-        double e2 = 0.0;
-        for (int d = 0; d < 3; ++d) e2 += cabs2(rxL[d] - Ntr[d]);
-        e2 *= (g.k0 / (4.0 * BEM_PI)) * (g.k0 / (4.0 * BEM_PI));
-        partial[(int64_t)r * gridDim.x + dir] = wt[it] * (2.0 * BEM_PI / nphi) * e2;
+    const double wA = w * A;
+    c128* cr = cur + (int64_t)rr * 6 * Q;
+    for (int d = 0; d < 3; ++d) {
+        cr[d * Q + q] = wA * J[d];
+        cr[(3 + d) * Q + q] = wA * M[d];
     }
 }
 
+__global__ void __launch_bounds__(PSCA_T) k_psca_dirs(const double* __restrict__ pts, const c128* __restrict__ cur,
+                                                      int64_t Q, double k0, int nr, int r0, int nphi,
+                                                      const double* __restrict__ ct, const double* __restrict__ wt,
+                                                      double* __restrict__ partial) {
+    __shared__ double sh[PSCA_T / 32][12 * PSCA_RB];
+    const int dir = blockIdx.x;
+    const int rb = blockIdx.y * PSCA_RB;
+    const int nb = min(PSCA_RB, nr - rb);
+    const int it = dir / nphi, ip = dir % nphi;
+    const double cth = ct[it], sth = sqrt(fmax(0.0, 1.0 - cth * cth));
+    const double phi = 2.0 * BEM_PI * ip / nphi;
+    const d3 rh = D3(sth * cos(phi), sth * sin(phi), cth);
+    double acc[PSCA_RB][12];
+#pragma unroll
+    for (int u = 0; u < PSCA_RB; ++u)
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[u][c] = 0.0;
+    for (int64_t q = threadIdx.x; q < Q; q += PSCA_T) {
+        double sn, cs;
+        sincos(k0 * (rh.x * pts[q] + rh.y * pts[Q + q] + rh.z * pts[2 * Q + q]), &sn, &cs);
+#pragma unroll
+        for (int u = 0; u < PSCA_RB; ++u) {
+            if (u >= nb) break;
+            const c128* cr = cur + (int64_t)(rb + u) * 6 * Q + q;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const c128 v = cr[(int64_t)c * Q];
+                acc[u][2 * c] += cs * v.re - sn * v.im;
+                acc[u][2 * c + 1] += cs * v.im + sn * v.re;
+            }
+        }
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int u = 0; u < PSCA_RB; ++u)
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            double v = acc[u][c];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (l == 0) sh[w][12 * u + c] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x >= nb) return;
+    const int u = threadIdx.x;
+    double tot[12];
+    for (int c = 0; c < 12; ++c) {
+        double s = 0.0;
+        for (int k = 0; k < PSCA_T / 32; ++k) s += sh[k][12 * u + c];
+        tot[c] = s;
+    }
+    const c128 Nt[3] = {mk<double>(tot[0], tot[1]), mk<double>(tot[2], tot[3]), mk<double>(tot[4], tot[5])};
+    const c128 Lt[3] = {mk<double>(tot[6], tot[7]), mk<double>(tot[8], tot[9]), mk<double>(tot[10], tot[11])};
+    const c128 rn = rh.x * Nt[0] + rh.y * Nt[1] + rh.z * Nt[2];
+    const c128 Ntr[3] = {Nt[0] - rh.x * rn, Nt[1] - rh.y * rn, Nt[2] - rh.z * rn};
+    const c128 rxL[3] = {rh.y * Lt[2] - rh.z * Lt[1], rh.z * Lt[0] - rh.x * Lt[2], rh.x * Lt[1] - rh.y * Lt[0]};
+    double e2 = 0.0;
+    for (int d = 0; d < 3; ++d) e2 += cabs2(rxL[d] - Ntr[d]);
+    e2 *= (k0 / (4.0 * BEM_PI)) * (k0 / (4.0 * BEM_PI));
+    partial[(int64_t)(r0 + rb + u) * gridDim.x + dir] = wt[it] * (2.0 * BEM_PI / nphi) * e2;
+}
+
+size_t power_sca_scratch(GeomDev g, int nrhs) {
+    const int64_t Q = 7 * (int64_t)g.nt;
+    const int chunk = std::min(nrhs, PSCA_CHUNK);
+    return sizeof(double) * 3 * Q + sizeof(c128) * 6 * Q * chunk;
+}
+
 cudaError_t power_sca(GeomDev g, const c128* x, int nrhs, double* partial, int ntheta, int nphi, const double* ct,
-                      const double* wt, cudaStream_t st) {
-    dim3 grid(ntheta * nphi, nrhs);
-    k_psca<<<grid, 256, 0, st>>>(g, x, partial, nphi, ct, wt);
-    return cudaGetLastError();
+                      const double* wt, void* scratch, cudaStream_t st) {
+    const int64_t Q = 7 * (int64_t)g.nt;
+    double* pts = (double*)scratch;
+    c128* cur = (c128*)(pts + 3 * Q);
+    for (int r0 = 0; r0 < nrhs; r0 += PSCA_CHUNK) {
+        const int nr = std::min(PSCA_CHUNK, nrhs - r0);
+        k_psca_points<<<dim3((unsigned)((Q + PSCA_T - 1) / PSCA_T), nr), PSCA_T, 0, st>>>(g, x, r0, nr, pts, cur);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_psca_dirs<<<dim3(ntheta * nphi, (nr + PSCA_RB - 1) / PSCA_RB), PSCA_T, 0, st>>>(
+            pts, cur, Q, g.k0, nr, r0, nphi, ct, wt, partial);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Re(a_J^H b_J + b_M^H a_M) partial sums (grid.y = rhs)
