@@ -478,6 +478,92 @@ unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
+bem_status planar_operators_row0(bem_ctx* ctx, const double* verts, int n, bem_c128 k, int fp32, void* S, void* D,
+                                 void* N, void* stream);  // planar.cu
+
+namespace {
+
+bem_status fft_run(bem_ctx* ctx, c128* x, int n, int64_t s, int nb, int64_t bs, bool inverse, cudaStream_t st);
+
+// true when vertex i + 1 is vertex i turned by 2 pi / n about the centroid: the
+// polygon is regular and every operator on it (S, D, N, G and C_p) is circulant
+bool regular_polygon(const double* v, int n) {
+    double cx = 0, cy = 0;
+    for (int i = 0; i < n; ++i) {
+        cx += v[2 * i];
+        cy += v[2 * i + 1];
+    }
+    cx /= n;
+    cy /= n;
+    const double c = std::cos(2.0 * BEM_PI / n), s = std::sin(2.0 * BEM_PI / n);
+    const double r0 = std::hypot(v[0] - cx, v[1] - cy);
+    for (int i = 0; i < n; ++i) {
+        const int j = (i + 1) % n;
+        const double x = v[2 * i] - cx, y = v[2 * i + 1] - cy;
+        if (std::hypot(v[2 * j] - cx - (c * x - s * y), v[2 * j + 1] - cy - (s * x + c * y)) > 1e-11 * r0) return false;
+    }
+    return true;
+}
+
+// Circulant X[i][j] = r[(j - i) mod n] has eigenvalues lam_m = sum_k r_k e^{2 pi i k m / n}
+// = n ifft(r)_m (eigenvectors e^{2 pi i j m / n}); X^T has lam_{-m}.  lam holds ifft of the
+// rows of S, D, N, D~, N~, G; out receives the eigenvalues of C_p, L_e, L_h.
+__global__ void k_circ_combine(const c128* __restrict__ lam, int n, c128* __restrict__ out) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const int mm = (n - m) % n;
+    const double sc = (double)n;
+    const c128 lS = sc * lam[m], lDT = sc * lam[n + mm], lNt = sc * lam[4 * n + m], lDtT = sc * lam[3 * n + mm];
+    const c128 lG = sc * lam[5 * n + m];
+    const c128 g2 = 0.5 * lG;
+    const c128 le = cdiv(lNt, lG), lh = cdiv(g2 - lDtT, lG);
+    out[m] = le * lS + lh * (g2 + lDT);  // N~ G^-1 S + (G/2 - D~*) G^-1 (G/2 + D*)
+    out[n + m] = le;
+    out[2 * n + m] = lh;
+}
+
+// dense circulant from its row: out[i][j] = scale * row[(j - i) mod n]
+__global__ void k_circ_expand(const c128* __restrict__ row, int n, double scale, c128* __restrict__ out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * n) return;
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    out[idx] = scale * row[(j - i + n) % n];
+}
+
+// C_p (and L_e, L_h) of a regular polygon from the first rows of its operators
+bem_status calderon_circulant(bem_ctx* ctx, const double* verts, int n, bem_c128 k0, bem_c128 kt, int fp32,
+                              const std::vector<double>& L, void* Cp, void* Le, void* Lh, cudaStream_t st) {
+    DevBuf rows, outs;
+    Scope sc{{&rows, &outs}};
+    PP_TRY(dalloc(rows, sizeof(c128) * 6 * n));
+    PP_TRY(dalloc(outs, sizeof(c128) * 3 * n));
+    c128* r = (c128*)rows.p;
+    bem_status s;
+    if ((s = planar_operators_row0(ctx, verts, n, k0, fp32, r, r + n, r + 2 * n, st)) != BEM_OK) return s;
+    if ((s = planar_operators_row0(ctx, verts, n, kt, fp32, nullptr, r + 3 * n, r + 4 * n, st)) != BEM_OK) return s;
+    std::vector<c128> g(n, mk<double>(0.0, 0.0));  // row 0 of the hat-function Gram matrix
+    g[0] = mk<double>((L[n - 1] + L[0]) / 3.0, 0.0);
+    g[1] = g[1] + mk<double>(L[0] / 6.0, 0.0);
+    g[n - 1] = g[n - 1] + mk<double>(L[n - 1] / 6.0, 0.0);
+    PP_TRY(cudaMemcpyAsync(r + 5 * n, g.data(), sizeof(c128) * n, cudaMemcpyHostToDevice, st));
+    if ((s = fft_run(ctx, r, n, 1, 6, n, true, st)) != BEM_OK) return s;
+    c128* o = (c128*)outs.p;
+    k_circ_combine<<<blocks_for(n, 128), 128, 0, st>>>(r, n, o);
+    PP_TRY(cudaGetLastError());
+    if ((s = fft_run(ctx, o, n, 1, 3, n, false, st)) != BEM_OK) return s;  // rows (times n)
+    const unsigned bnn = blocks_for((int64_t)n * n, 256);
+    void* dst[3] = {Cp, Le, Lh};
+    for (int q = 0; q < 3; ++q)
+        if (dst[q]) {
+            k_circ_expand<<<bnn, 256, 0, st>>>(o + (int64_t)q * n, n, 1.0 / n, (c128*)dst[q]);
+            PP_TRY(cudaGetLastError());
+        }
+    PP_TRY(cudaStreamSynchronize(st));
+    return BEM_OK;
+}
+
+}  // namespace
+
 extern "C" bem_status bem_planar_calderon(bem_ctx* ctx, const double* verts, int n, double k0, double a, int fp32,
                                           void* Cp, void* Le, void* Lh, void* stream) {
     using namespace bem2p;
@@ -492,6 +578,10 @@ extern "C" bem_status bem_planar_calderon(bem_ctx* ctx, const double* verts, int
     if (!(a > 0)) a = per / (2.0 * BEM_PI);
     const bem_c128 kk0{k0, 0.0};
     const bem_c128 kt{k0, -0.4 * std::cbrt(k0) * std::pow(a, -2.0 / 3.0)};  // k~ = k0 - 0.4 j k0^(1/3) a^(-2/3)
+    // a regular polygon (the circular counterpart): everything is circulant, so the
+    // first rows and FFT eigenvalues replace the dense assembly and products
+    if (n <= FFT_MAXM / 2 && regular_polygon(verts, n))
+        return calderon_circulant(ctx, verts, n, kk0, kt, fp32, L, Cp, Le, Lh, st);
     const size_t nn = (size_t)n * n;
     DevBuf S, D, N, Dt, Nt, W1, W2, P, gl, gd, gu, gz, dL;
     Scope sc{{&S, &D, &N, &Dt, &Nt, &W1, &W2, &P, &gl, &gd, &gu, &gz, &dL}};
